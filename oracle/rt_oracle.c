@@ -1,0 +1,413 @@
+/*
+ * rt_oracle.c -- plain, slow FP64 CPU oracle for the hot path of the 3D
+ * radiative transfer framework of Hauschildt & Baron, "A 3D radiative
+ * transfer framework XIII: OpenCL implementation" (2011):
+ *
+ *   - the characteristics formal solution on a Cartesian voxel slab that is
+ *     periodic in x and y (Sect. 2.2, first paragraph), giving the
+ *     intensities I, the mean intensity J and the nearest-neighbour Lambda*
+ *     (Sect. 2.2; abstract);
+ *   - the operator-splitting step for the new J, solved by Jordan (=Jacobi)
+ *     iterations (Sect. 2.3);
+ *   - the outer iteration "formal solution -> operator splitting" (Sect. 2,
+ *     first paragraph) for coherent isotropic scattering,
+ *     S = eps B + (1 - eps) J (Sect. 3.1, list item 5).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the CPU
+ * baseline leg of the benchmark are the only users.  The GPU library never
+ * links, loads or calls this file, and this file shares no code, header or
+ * table with it.
+ *
+ * The paper states the problem but defers the discretisation to the
+ * earlier papers of its series, which are not at hand.  This file therefore
+ * DEFINES the discretisation, written straight from its mathematical
+ * statement, with no blocking, fusion or reordering:
+ *
+ *  Grid.  Voxel (i,j,k), i<nx, j<ny, k<nz, centres on the integer lattice
+ *   scaled by (dx,dy,dz).  k is the depth index: k=0 is the outer (top)
+ *   boundary, k=nz-1 the inner (bottom) one.  Arrays are [nz][ny][nx].
+ *   x and y are periodic (node i+nx == node i).
+ *
+ *  Directions.  d = (mu, phi, w); the propagation vector is
+ *   (sin t cos phi, sin t sin phi, mu) with sin t = sqrt(1-mu^2); mu > 0
+ *   propagates towards larger k.  J = sum_d w_d I_d.
+ *
+ *  Characteristic (long characteristic in gather form, one z-plane per
+ *   step).  For voxel (i0,j0,k0) the upstream points are
+ *     p_m = (i0 - m*ax, j0 - m*ay, k0 - m*s),   m = 0..M,
+ *   with s = sign(mu), ax = (dz/dx) sin t cos phi / |mu|,
+ *   ay = (dz/dy) sin t sin phi / |mu|, M = k0 for mu > 0 and nz-1-k0 for
+ *   mu < 0.  Each step has path length ds = dz/|mu|.
+ *
+ *  Interpolation.  chi, S and B at p_m are bilinear in the plane k - m*s
+ *   with periodic wrap of the four lattice nodes.
+ *
+ *  Optical depth.  dtau_m = ds (chi(p_m) + chi(p_{m+1})) / 2 (trapezoid).
+ *
+ *  Source integral.  S linear in tau on each segment.  With x = dtau and
+ *   e = exp(-x), the segment from p_{m+1} to p_m contributes
+ *     I(p_m) = I(p_{m+1}) e + w_cur S(p_m) + w_up S(p_{m+1}),
+ *     w_cur = 1 - (1-e)/x,   w_up = (1-e)/x - e,
+ *   i.e. the exact integral of S(t) e^{-t} over the segment for a linear
+ *   S(t).  I(p_M) = I_bc: 0 (zero mode) or B(p_M) (Planck mode).
+ *
+ *  Lambda*.  I is linear in S.  Lambda_{i,j} = sum_d w_d dI_{i,d}/dS_j with
+ *   the boundary intensity excluded; Lambda*_{i,o} = Lambda_{i,wrap(i+o)}
+ *   for the 27 offsets o in {-1,0,1}^3 (index o = (oz+1)*9+(oy+1)*3+(ox+1));
+ *   entries whose plane k0+oz lies outside the grid are 0.  Stored
+ *   [27][nz][ny][nx].
+ *
+ *  Operator splitting.  With D = diag(1 - eps), the new J solves
+ *     (1 - Lambda* D) J_new = J_fs - Lambda* D J_old ,
+ *   by Jacobi sweeps started from J_old, stopped when
+ *   max_i |J^{n+1}_i - J^n_i| / |J^{n+1}_i| < tol_inner or after max_sweeps.
+ *
+ *  Outer iteration.  J^0 = B unless given; S = eps B + (1-eps) J; formal
+ *   solution -> J_fs (Lambda* on the first pass); operator splitting ->
+ *   J_new; delta = max_i |J_new_i - J_i| / |J_new_i|; stop when delta < tol
+ *   or after max_iter.
+ */
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    int top_bc, bottom_bc;      /* 0: I_bc = 0, 1: I_bc = B at the entry point */
+} orc_grid;
+
+static long vidx(const orc_grid *g, long i, long j, long k)
+{
+    return (k * g->ny + j) * g->nx + i;
+}
+
+static long wrapi(long a, long n)       /* Euclidean modulo */
+{
+    long r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+/* Bilinear value of field f in plane k at the (real) lattice position (x,y),
+ * with periodic wrap of the nodes. */
+static double bilinear(const orc_grid *g, const double *f, long k, double x, double y)
+{
+    double fx0 = floor(x), fy0 = floor(y);
+    double tx = x - fx0, ty = y - fy0;
+    long i0 = wrapi((long)fx0, g->nx), i1 = wrapi((long)fx0 + 1, g->nx);
+    long j0 = wrapi((long)fy0, g->ny), j1 = wrapi((long)fy0 + 1, g->ny);
+    return (1.0 - tx) * (1.0 - ty) * f[vidx(g, i0, j0, k)]
+         + tx * (1.0 - ty) * f[vidx(g, i1, j0, k)]
+         + (1.0 - tx) * ty * f[vidx(g, i0, j1, k)]
+         + tx * ty * f[vidx(g, i1, j1, k)];
+}
+
+/* Linear-source segment weights (see header).  For small x the closed form
+ * cancels, so the Taylor series of e^{-x} is used:
+ *   w_cur = sum_{n>=1} (-1)^{n+1} x^n / (n+1)!
+ *   w_up  = sum_{n>=1} (-1)^{n+1} n x^n / (n+1)!
+ * below x = 0.1, through x^10 (truncation < 1e-17 relative); above it the
+ * closed form loses at most a factor ~20 to cancellation. */
+void orc_weights(double x, double *w_cur, double *w_up)
+{
+    if (x < 0.1) {
+        double wc = 0.0, wu = 0.0, xn = 1.0, fact = 1.0;
+        for (int n = 1; n <= 10; ++n) {
+            xn *= x;
+            fact *= (double)(n + 1);
+            double sgn = (n % 2) ? 1.0 : -1.0;
+            wc += sgn * xn / fact;
+            wu += sgn * (double)n * xn / fact;
+        }
+        *w_cur = wc;
+        *w_up = wu;
+    } else {
+        double one_minus_e = -expm1(-x);
+        double e = exp(-x);
+        *w_cur = 1.0 - one_minus_e / x;
+        *w_up = one_minus_e / x - e;
+    }
+}
+
+/* Geometry of one direction. */
+typedef struct {
+    int s;          /* +1: propagates to larger k (came from the top); -1 */
+    double ax, ay;  /* upstream shift per step, in grid units */
+    double ds;      /* path length per step */
+} orc_dir;
+
+static orc_dir dir_geometry(const orc_grid *g, double mu, double phi)
+{
+    orc_dir d;
+    double amu = fabs(mu);
+    double sint = sqrt(1.0 - mu * mu);
+    d.s = mu > 0.0 ? 1 : -1;
+    d.ax = (g->dz / g->dx) * sint * cos(phi) / amu;
+    d.ay = (g->dz / g->dy) * sint * sin(phi) / amu;
+    d.ds = g->dz / amu;
+    return d;
+}
+
+static int steps_to_boundary(const orc_grid *g, const orc_dir *d, long k0)
+{
+    return d->s > 0 ? (int)k0 : (int)(g->nz - 1 - k0);
+}
+
+/* Intensity at voxel (i0,j0,k0) in direction (mu,phi): textbook
+ * back-to-front recursion along the characteristic. */
+double orc_intensity(const orc_grid *g, const double *chi, const double *S,
+                     const double *B, double mu, double phi,
+                     long i0, long j0, long k0)
+{
+    orc_dir d = dir_geometry(g, mu, phi);
+    int M = steps_to_boundary(g, &d, k0);
+    int bc = d.s > 0 ? g->top_bc : g->bottom_bc;
+    double xM = (double)i0 - M * d.ax, yM = (double)j0 - M * d.ay;
+    long kM = k0 - (long)M * d.s;
+    double I = bc ? bilinear(g, B, kM, xM, yM) : 0.0;
+    for (int m = M - 1; m >= 0; --m) {
+        double xa = (double)i0 - m * d.ax, ya = (double)j0 - m * d.ay;
+        double xb = (double)i0 - (m + 1) * d.ax, yb = (double)j0 - (m + 1) * d.ay;
+        long ka = k0 - (long)m * d.s, kb = k0 - (long)(m + 1) * d.s;
+        double chi_a = bilinear(g, chi, ka, xa, ya), chi_b = bilinear(g, chi, kb, xb, yb);
+        double S_a = bilinear(g, S, ka, xa, ya), S_b = bilinear(g, S, kb, xb, yb);
+        double dtau = d.ds * (chi_a + chi_b) / 2.0;
+        double wc, wu;
+        orc_weights(dtau, &wc, &wu);
+        I = I * exp(-dtau) + wc * S_a + wu * S_b;
+    }
+    return I;
+}
+
+/* Offset index of node (a,b,kk) relative to voxel (i0,j0,k0), or -1 if the
+ * node is not one of the 27 periodic nearest neighbours. */
+static int neighbour_offset(const orc_grid *g, long a, long b, long kk,
+                            long i0, long j0, long k0)
+{
+    long rx = wrapi(a - i0, g->nx), ry = wrapi(b - j0, g->ny), dzv = kk - k0;
+    int ox, oy;
+    if (rx == 0) ox = 0; else if (rx == 1) ox = 1; else if (rx == g->nx - 1) ox = -1; else return -1;
+    if (ry == 0) oy = 0; else if (ry == 1) oy = 1; else if (ry == g->ny - 1) oy = -1; else return -1;
+    if (dzv < -1 || dzv > 1) return -1;
+    return ((int)dzv + 1) * 9 + (oy + 1) * 3 + (ox + 1);
+}
+
+/* Contribution of one (voxel, direction) to Lambda*: the coefficient of
+ * S(p_m) in I is c_m = T_m w_cur(m) [m < M] + T_{m-1} w_up(m-1) [m >= 1],
+ * T_m = prod_{l<m} exp(-dtau_l); c_m is shared among the four bilinear
+ * nodes of p_m and kept where the node is a nearest neighbour. */
+static void lstar_one(const orc_grid *g, const double *chi, double mu, double phi,
+                      double wd, long i0, long j0, long k0, double *lrow /*[27]*/)
+{
+    orc_dir d = dir_geometry(g, mu, phi);
+    int M = steps_to_boundary(g, &d, k0);
+    if (M == 0) return;
+    double *T = malloc(sizeof(double) * (M + 1));
+    double *wc = malloc(sizeof(double) * (M + 1));
+    double *wu = malloc(sizeof(double) * (M + 1));
+    T[0] = 1.0;
+    for (int m = 0; m < M; ++m) {
+        double xa = (double)i0 - m * d.ax, ya = (double)j0 - m * d.ay;
+        double xb = (double)i0 - (m + 1) * d.ax, yb = (double)j0 - (m + 1) * d.ay;
+        long ka = k0 - (long)m * d.s, kb = k0 - (long)(m + 1) * d.s;
+        double dtau = d.ds * (bilinear(g, chi, ka, xa, ya) + bilinear(g, chi, kb, xb, yb)) / 2.0;
+        orc_weights(dtau, &wc[m], &wu[m]);
+        T[m + 1] = T[m] * exp(-dtau);
+    }
+    for (int m = 0; m <= M; ++m) {
+        double c = 0.0;
+        if (m < M) c += T[m] * wc[m];
+        if (m >= 1) c += T[m - 1] * wu[m - 1];
+        double x = (double)i0 - m * d.ax, y = (double)j0 - m * d.ay;
+        long km = k0 - (long)m * d.s;
+        double fx0 = floor(x), fy0 = floor(y);
+        double tx = x - fx0, ty = y - fy0;
+        long nodes_x[2] = {(long)fx0, (long)fx0 + 1}, nodes_y[2] = {(long)fy0, (long)fy0 + 1};
+        double bx[2] = {1.0 - tx, tx}, by[2] = {1.0 - ty, ty};
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                int o = neighbour_offset(g, nodes_x[a], nodes_y[b], km, i0, j0, k0);
+                if (o >= 0) lrow[o] += wd * c * bx[a] * by[b];
+            }
+    }
+    free(T); free(wc); free(wu);
+}
+
+static int check_grid(const orc_grid *g)
+{
+    if (!g || g->nx < 3 || g->ny < 3 || g->nz < 2) return ORC_EINVAL;
+    if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+static int check_dirs(int ndir, const double *mu)
+{
+    if (ndir < 1) return ORC_EINVAL;
+    for (int d = 0; d < ndir; ++d)
+        if (!(fabs(mu[d]) > 0.0) || !(fabs(mu[d]) <= 1.0)) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+/* Formal solution for a given source function S: J_out[N] and, if
+ * lstar_out != NULL, Lambda* [27][N].  nthreads <= 0 uses the OpenMP
+ * default. */
+int orc_formal_solution(const orc_grid *g, const double *chi, const double *S,
+                        const double *B, int ndir, const double *mu,
+                        const double *phi, const double *w, double *J_out,
+                        double *lstar_out, int nthreads)
+{
+    if (check_grid(g) || check_dirs(ndir, mu)) return ORC_EINVAL;
+    long N = (long)g->nx * g->ny * g->nz;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long v = 0; v < N; ++v) {
+        long i0 = v % g->nx, j0 = (v / g->nx) % g->ny, k0 = v / ((long)g->nx * g->ny);
+        double J = 0.0;
+        for (int d = 0; d < ndir; ++d)
+            J += w[d] * orc_intensity(g, chi, S, B, mu[d], phi[d], i0, j0, k0);
+        J_out[v] = J;
+        if (lstar_out) {
+            double row[27] = {0};
+            for (int d = 0; d < ndir; ++d)
+                lstar_one(g, chi, mu[d], phi[d], w[d], i0, j0, k0, row);
+            for (int o = 0; o < 27; ++o) lstar_out[(long)o * N + v] = row[o];
+        }
+    }
+    return ORC_OK;
+}
+
+/* Mean intensity at a sample of voxels only (full-size spot checks). */
+int orc_mean_intensity_at(const orc_grid *g, const double *chi, const double *S,
+                          const double *B, int ndir, const double *mu,
+                          const double *phi, const double *w, long nsample,
+                          const long *voxels, double *J_out, int nthreads)
+{
+    if (check_grid(g) || check_dirs(ndir, mu)) return ORC_EINVAL;
+    long N = (long)g->nx * g->ny * g->nz;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long q = 0; q < nsample; ++q) {
+        long v = voxels[q];
+        if (v < 0 || v >= N) { J_out[q] = NAN; continue; }
+        long i0 = v % g->nx, j0 = (v / g->nx) % g->ny, k0 = v / ((long)g->nx * g->ny);
+        double J = 0.0;
+        for (int d = 0; d < ndir; ++d)
+            J += w[d] * orc_intensity(g, chi, S, B, mu[d], phi[d], i0, j0, k0);
+        J_out[q] = J;
+    }
+    return ORC_OK;
+}
+
+/* Index of the neighbour of voxel v at offset o, or -1 outside the grid. */
+static long neighbour_index(const orc_grid *g, long v, int o)
+{
+    long i0 = v % g->nx, j0 = (v / g->nx) % g->ny, k0 = v / ((long)g->nx * g->ny);
+    int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+    long kk = k0 + oz;
+    if (kk < 0 || kk >= g->nz) return -1;
+    return vidx(g, wrapi(i0 + ox, g->nx), wrapi(j0 + oy, g->ny), kk);
+}
+
+/* Operator-splitting step, Jacobi ("Jordan") iterations from J_old. */
+int orc_os_step(const orc_grid *g, const double *lstar, const double *eps,
+                const double *J_fs, const double *J_old, double *J_new,
+                double tol_inner, int max_sweeps, int *sweeps_out)
+{
+    if (check_grid(g) || max_sweeps < 1) return ORC_EINVAL;
+    long N = (long)g->nx * g->ny * g->nz;
+    double *rhs = malloc(sizeof(double) * N);
+    double *Jc = malloc(sizeof(double) * N);
+    double *Jn = malloc(sizeof(double) * N);
+    if (!rhs || !Jc || !Jn) { free(rhs); free(Jc); free(Jn); return ORC_ENOMEM; }
+    for (long v = 0; v < N; ++v) {
+        double r = J_fs[v];
+        for (int o = 0; o < 27; ++o) {
+            long j = neighbour_index(g, v, o);
+            if (j >= 0) r -= lstar[(long)o * N + v] * (1.0 - eps[j]) * J_old[j];
+        }
+        rhs[v] = r;
+        Jc[v] = J_old[v];
+    }
+    int sweeps = 0;
+    for (int n = 0; n < max_sweeps; ++n) {
+        double delta = 0.0;
+        for (long v = 0; v < N; ++v) {
+            double acc = rhs[v];
+            for (int o = 0; o < 27; ++o) {
+                if (o == 13) continue;
+                long j = neighbour_index(g, v, o);
+                if (j >= 0) acc += lstar[(long)o * N + v] * (1.0 - eps[j]) * Jc[j];
+            }
+            Jn[v] = acc / (1.0 - lstar[13L * N + v] * (1.0 - eps[v]));
+            double rel = fabs(Jn[v] - Jc[v]) / fabs(Jn[v]);
+            if (!(rel <= delta)) delta = rel;     /* NaN propagates */
+        }
+        memcpy(Jc, Jn, sizeof(double) * N);
+        sweeps = n + 1;
+        if (delta < tol_inner) break;
+    }
+    memcpy(J_new, Jc, sizeof(double) * N);
+    if (sweeps_out) *sweeps_out = sweeps;
+    free(rhs); free(Jc); free(Jn);
+    return ORC_OK;
+}
+
+/* Outer iteration.  J_inout holds J^0 on entry if use_initial != 0 (else
+ * J^0 = B) and the last iterate on exit.  deltas/sweeps (may be NULL) get
+ * one entry per outer iteration.  Returns 0 on convergence, 3 if max_iter
+ * was reached first (both leave J_inout valid). */
+int orc_solve(const orc_grid *g, const double *chi, const double *eps,
+              const double *B, int ndir, const double *mu, const double *phi,
+              const double *w, double tol, int max_iter, double tol_inner,
+              int max_sweeps, int use_initial, double *J_inout,
+              double *lstar_out, int *iters_out, double *deltas, int *sweeps,
+              int nthreads)
+{
+    if (check_grid(g) || check_dirs(ndir, mu) || max_iter < 1) return ORC_EINVAL;
+    long N = (long)g->nx * g->ny * g->nz;
+    double *J = malloc(sizeof(double) * N), *S = malloc(sizeof(double) * N);
+    double *Jfs = malloc(sizeof(double) * N), *Jn = malloc(sizeof(double) * N);
+    double *L = malloc(sizeof(double) * N * 27);
+    if (!J || !S || !Jfs || !Jn || !L) {
+        free(J); free(S); free(Jfs); free(Jn); free(L);
+        return ORC_ENOMEM;
+    }
+    for (long v = 0; v < N; ++v) J[v] = use_initial ? J_inout[v] : B[v];
+    int it, status = 3;
+    for (it = 1; it <= max_iter; ++it) {
+        for (long v = 0; v < N; ++v) S[v] = eps[v] * B[v] + (1.0 - eps[v]) * J[v];
+        orc_formal_solution(g, chi, S, B, ndir, mu, phi, w, Jfs, it == 1 ? L : NULL, nthreads);
+        int ns = 0;
+        orc_os_step(g, L, eps, Jfs, J, Jn, tol_inner, max_sweeps, &ns);
+        double delta = 0.0;
+        for (long v = 0; v < N; ++v) {
+            double rel = fabs(Jn[v] - J[v]) / fabs(Jn[v]);
+            if (!(rel <= delta)) delta = rel;
+        }
+        memcpy(J, Jn, sizeof(double) * N);
+        if (deltas) deltas[it - 1] = delta;
+        if (sweeps) sweeps[it - 1] = ns;
+        if (delta < tol) { status = 0; break; }
+    }
+    if (iters_out) *iters_out = it > max_iter ? max_iter : it;
+    memcpy(J_inout, J, sizeof(double) * N);
+    if (lstar_out) memcpy(lstar_out, L, sizeof(double) * N * 27);
+    free(J); free(S); free(Jfs); free(Jn); free(L);
+    return status;
+}
