@@ -1,0 +1,208 @@
+/*
+ * rt3d.h -- C ABI of the GB300 (sm_103a) hot path of the 3D radiative
+ * transfer framework of Hauschildt & Baron, "A 3D radiative transfer
+ * framework XIII: OpenCL implementation" (2011).
+ *
+ * The library solves, on one GPU, the problem the paper hands to its GPU
+ * kernels (Sect. 2, first paragraph; abstract): the formal solution on a
+ * Cartesian voxel slab with periodic boundary conditions in x and y, the
+ * construction of the nearest-neighbour Lambda*, and the operator-splitting
+ * step for the mean intensity J, iterated to convergence for coherent
+ * isotropic scattering S = eps B + (1 - eps) J (Sect. 3.1, list item 5).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Grid.  nx x ny x nz voxels, spacings dx, dy, dz.  Arrays are C-ordered
+ *   [nz][ny][nx] (x fastest), N = nx*ny*nz.  k is the depth index: k = 0 is
+ *   the outer (top) boundary, k = nz-1 the inner (bottom) one (Sect. 3.1:
+ *   z_max outside, z_min inside).  x and y are periodic (Sect. 2.2).
+ *  Directions.  d = (mu_d, phi_d, w_d); propagation vector
+ *   (sqrt(1-mu^2) cos phi, sqrt(1-mu^2) sin phi, mu); mu > 0 propagates
+ *   towards larger k.  J = sum_d w_d I_d.  1e-6 <= |mu| <= 1.
+ *  Characteristic.  Each (voxel, direction) is integrated back along its
+ *   characteristic one z-plane per step (path length dz/|mu| per step) to
+ *   the boundary plane it entered through; chi, S and B are bilinear in
+ *   each plane with periodic wrap; segment optical depths are trapezoidal;
+ *   the source is linear in tau on each segment.
+ *  Lambda*.  27 entries per voxel, Lambda*_{i,o} = dJ_i/dS_{wrap(i+o)},
+ *   offset index o = (oz+1)*9 + (oy+1)*3 + (ox+1), stored [27][nz][ny][nx];
+ *   entries whose plane lies outside the grid are 0.
+ *  Operator splitting (Sect. 2.3).  (1 - Lambda* D) J_new = J_fs -
+ *   Lambda* D J_old with D = diag(1 - eps), solved by Jacobi ("Jordan")
+ *   sweeps started from J_old until max|dJ|/|J| < tol_inner or max_sweeps.
+ *  Outer iteration (Sect. 2).  S = eps B + (1-eps) J -> formal solution ->
+ *   operator splitting; delta = max_i |J_new - J_old| / |J_new|; stop when
+ *   delta < tol or after max_iter.  J starts from B (set by rt_set_planck)
+ *   unless rt_set_J gave another start.
+ *
+ *  Precision.  RT_FP64: every step in FP64.  RT_FP32_SWEEP: the march
+ *   along the characteristics (interpolation, exp weights, transmission,
+ *   intensity) runs in FP32 on FP32 copies of chi and S; J, Lambda*, the
+ *   operator-splitting solve and the convergence test stay in FP64
+ *   (Sect. 3.1: smaller eps needs double precision for the operator
+ *   splitting equations).
+ *
+ *  Memory and ownership.  The caller owns every pointer it passes and
+ *   every buffer it receives.  Host-pointer calls copy in and out and
+ *   return when the result is in the caller's buffer.  *_dev calls take
+ *   device pointers of the context's device, run on the context's stream
+ *   (rt_set_stream; default: a stream the context creates) and return
+ *   without synchronising unless the call itself needs a value on the host
+ *   (solve and os_step read convergence flags).  The context allocates its
+ *   own working storage on the device (opacities, Lambda*, tables, scratch)
+ *   in the rt_set_* calls and frees it in rt_destroy; the paper keeps all
+ *   of it on the GPU and moves only inputs and J across the bus (Sect. 2).
+ *
+ *  Errors.  Every call returns an rt_status.  On error the context is left
+ *   usable, the outputs are unspecified and rt_last_error() describes the
+ *   cause.  Invalid arguments (null pointers, nx or ny < 3, nz < 2, chi <= 0
+ *   or not finite, eps outside (0,1], |mu| < 1e-6 or > 1, weights that do
+ *   not sum to 1 within 1e-12) give RT_EINVAL; calls before the data they
+ *   need was set give RT_ESTATE; CUDA failures give RT_ECUDA.
+ *
+ *  Threading.  A context may be used by one host thread at a time.
+ */
+#ifndef RT3D_H
+#define RT3D_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RT_OK = 0,
+    RT_EINVAL = 1,      /* invalid argument */
+    RT_ENOMEM = 2,      /* device allocation failed */
+    RT_ECUDA = 3,       /* a CUDA call failed */
+    RT_ENOTCONV = 4,    /* max_iter reached before delta < tol (outputs valid) */
+    RT_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    RT_ESTATE = 6       /* the call needs data that was not set yet */
+} rt_status;
+
+enum { RT_FP64 = 0, RT_FP32_SWEEP = 1 };
+enum { RT_BC_ZERO = 0, RT_BC_PLANCK = 1 };
+
+typedef struct rt_ctx rt_ctx;
+
+/* Library version string (static storage). */
+const char *rt_version(void);
+
+/* Create a context on CUDA device `device` for precision RT_FP64 or
+ * RT_FP32_SWEEP.  *ctx receives the handle (NULL on failure). */
+int rt_create(rt_ctx **ctx, int device, int precision);
+
+/* Free the context and every device buffer it owns.  NULL is accepted. */
+int rt_destroy(rt_ctx *ctx);
+
+/* Text of the last error on this context ("" if none; static storage of
+ * the context, valid until the next call on it). */
+const char *rt_last_error(const rt_ctx *ctx);
+
+/* Use `stream` (a cudaStream_t of the context's device, e.g. the current
+ * PyTorch stream) for all later work; NULL restores the context's own. */
+int rt_set_stream(rt_ctx *ctx, void *stream);
+
+/* Grid of nx x ny x nz voxels with spacings dx, dy, dz (> 0).  nx, ny >= 3
+ * (a smaller periodic grid would alias the 27-point neighbourhood), nz >= 2.
+ * Invalidates every field set before. */
+int rt_set_grid(rt_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz);
+
+/* Incoming intensity at the top (entered by mu > 0) and bottom (mu < 0):
+ * RT_BC_ZERO (I = 0, the outer boundary of Sect. 3.1) or RT_BC_PLANCK
+ * (I = B interpolated at the entry point).  Default: ZERO top, PLANCK bottom. */
+int rt_set_boundary(rt_ctx *ctx, int top_mode, int bottom_mode);
+
+/* Solid-angle quadrature: ndir directions, host arrays mu[ndir],
+ * phi[ndir] (radians), w[ndir] (sum 1).  Builds the per-(direction, plane)
+ * geometry tables on the device; needs the grid. */
+int rt_set_quadrature(rt_ctx *ctx, int ndir, const double *mu, const double *phi,
+                      const double *w);
+
+/* Opacity chi[N] (> 0, host).  Invalidates Lambda*. */
+int rt_set_opacity(rt_ctx *ctx, const double *chi);
+/* Thermalisation parameter eps[N] in (0, 1] (host). */
+int rt_set_epsilon(rt_ctx *ctx, const double *eps);
+/* Planck function B[N] (host).  Also resets the iterate J to B. */
+int rt_set_planck(rt_ctx *ctx, const double *B);
+
+/* Device-pointer forms of the three setters above (copied on the stream). */
+int rt_set_opacity_dev(rt_ctx *ctx, const double *chi);
+int rt_set_epsilon_dev(rt_ctx *ctx, const double *eps);
+int rt_set_planck_dev(rt_ctx *ctx, const double *B);
+
+/* Formal solution (Sect. 2.2).  S[N]: the source function on the voxel
+ * nodes, or NULL to use S = eps B + (1 - eps) J of the current iterate.
+ * J_fs[N] receives J = sum_d w_d I_d; lstar[27*N] (or NULL) receives
+ * Lambda*, which is built on the first call after the opacity changed.
+ * Host pointers. */
+int rt_formal_solution(rt_ctx *ctx, const double *S, double *J_fs, double *lstar);
+/* Same with device pointers (S may be NULL; lstar may be NULL). */
+int rt_formal_solution_dev(rt_ctx *ctx, const double *S, double *J_fs, double *lstar);
+
+/* One operator-splitting solve (Sect. 2.3) with the context's Lambda* and
+ * eps: J_new[N] from J_fs[N] and J_old[N].  *sweeps (or NULL) receives the
+ * number of Jacobi sweeps.  Needs Lambda* (a formal solution since the
+ * opacity was set).  Host pointers. */
+int rt_os_step(rt_ctx *ctx, const double *J_fs, const double *J_old, double *J_new,
+               double tol_inner, int max_sweeps, int *sweeps);
+/* Same with device pointers. */
+int rt_os_step_dev(rt_ctx *ctx, const double *J_fs, const double *J_old, double *J_new,
+                   double tol_inner, int max_sweeps, int *sweeps);
+
+/* Outer iteration from the context's current J until delta < tol or
+ * max_iter iterations; tol = 0 runs exactly max_iter iterations.  J_out[N]
+ * (host, or NULL) receives the final iterate, which also stays in the
+ * context.  iters, last_delta (or NULL) receive the count and the final
+ * delta; deltas[max_iter] and sweeps[max_iter] (host, or NULL) receive the
+ * per-iteration delta and Jacobi sweep count.  Returns RT_ENOTCONV if
+ * max_iter was reached with tol > 0 (outputs still valid). */
+int rt_solve(rt_ctx *ctx, double tol, int max_iter, double tol_inner, int max_sweeps,
+             double *J_out, int *iters, double *last_delta, double *deltas, int *sweeps);
+/* Same, J_out a device pointer (or NULL). */
+int rt_solve_dev(rt_ctx *ctx, double tol, int max_iter, double tol_inner, int max_sweeps,
+                 double *J_out, int *iters, double *last_delta, double *deltas, int *sweeps);
+
+/* Read or replace the current iterate J[N] (checkpoint / resume). */
+int rt_get_J(rt_ctx *ctx, double *J);
+int rt_set_J(rt_ctx *ctx, const double *J);
+
+/* Number of march steps executed by the last formal solution (steps cut by
+ * the transmission cutoff are not counted). */
+int rt_last_step_count(rt_ctx *ctx, unsigned long long *steps);
+
+/* Tuning: the directions are summed into J in 8 fixed slots (direction d in
+ * slot d mod 8, each slot in increasing d, then the slots in order), so J
+ * is bit-reproducible and independent of this knob.  `groups` (1..8) sets
+ * how many thread blocks share the slots of one voxel tile; 0 = auto. */
+int rt_set_direction_groups(rt_ctx *ctx, int groups);
+
+/* Tuning: relative transmission cutoff.  The march along a characteristic
+ * stops once T * max(|S|, |I_bc|) <= cut * |I| (the rest can change I by
+ * at most that much).  0 disables the cutoff.  Default 1e-17 (FP64) and
+ * 1e-9 (FP32 sweep). */
+int rt_set_cutoff(rt_ctx *ctx, double cut);
+
+/* Counters of this context since the last rt_reset_stats: kernel launches,
+ * formal-solution march launches and their device time, Jacobi sweeps and
+ * their device time, march steps executed.  Device times are measured with
+ * CUDA events recorded on the context's stream around those kernels, and
+ * only while profiling is on (rt_set_profiling); the other counters are
+ * always kept. */
+typedef struct {
+    unsigned long long launches;        /* all kernels of this library */
+    unsigned long long fs_launches;     /* formal-solution march kernels */
+    double fs_ms;                       /* their summed device time (profiling on) */
+    unsigned long long jacobi_launches; /* Jacobi sweep kernels */
+    double jacobi_ms;                   /* their summed device time (profiling on) */
+    unsigned long long steps;           /* march steps executed */
+    unsigned long long lstar_launches;  /* Lambda* builds */
+} rt_stats;
+
+int rt_set_profiling(rt_ctx *ctx, int on);
+int rt_get_stats(rt_ctx *ctx, rt_stats *out);
+int rt_reset_stats(rt_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT3D_H */

@@ -1,0 +1,412 @@
+// Formal solution kernels (Hauschildt & Baron 2011, Sect. 2.2): geometry
+// tables, the gather-form march along the characteristics, the J reduction
+// over directions and the nearest-neighbour Lambda*.
+//
+// Design (GB300).  The paper tracks every characteristic from the boundary
+// planes in a 2D kernel and collects per-voxel results in a second pass
+// with integer atomics, because OpenCL 1.x has no floating-point atomics
+// (Sect. 2.2).  Here each thread owns one voxel and integrates I back
+// along the characteristic of each of its directions, one z-plane per step.
+// Because voxel centres are lattice points, the upstream point of step m
+// has the same lattice offset and bilinear weights for every voxel of a
+// direction; they are tabulated once per (direction, step) and read as
+// warp-uniform broadcasts.  The 32 lanes of a warp are 32 consecutive
+// voxels of one plane, so at every step they read 32 consecutive nodes of
+// the same upstream plane (coalesced, mostly L1 hits) and run identical
+// loop bounds.  Each thread sums its directions in fixed order; direction
+// groups (grid z) are then summed in fixed order, so J is bit-reproducible
+// without atomics on floating-point data.
+#include "internal.h"
+
+#include <cmath>
+
+namespace rt3d {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ int wrap_mod(long long a, int n)
+{
+    long long r = a % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+__global__ void k_dir_tables(Geometry g, double dx, double dy, double dz,
+                             const double* __restrict__ mu, const double* __restrict__ phi,
+                             const double* __restrict__ w, DirInfo* __restrict__ info,
+                             StepGeo* __restrict__ off, Bw4d* __restrict__ bw,
+                             float4* __restrict__ bw32)
+{
+    const int d = blockIdx.x;
+    const double m_u = mu[d];
+    const double amu = fabs(m_u);
+    const double sint = sqrt(1.0 - m_u * m_u);
+    const double ax = (dz / dx) * sint * cos(phi[d]) / amu;
+    const double ay = (dz / dy) * sint * sin(phi[d]) / amu;
+    for (int m = threadIdx.x; m < g.nz; m += blockDim.x) {
+        const double X = -(double)m * ax, Y = -(double)m * ay;
+        const double fX = floor(X), fY = floor(Y);
+        const double tx = X - fX, ty = Y - fY;
+        StepGeo o;
+        o.ox = wrap_mod((long long)fX, g.nx);
+        o.oy = wrap_mod((long long)fY, g.ny);
+        const long long e = (long long)d * g.nz + m;
+        off[e] = o;
+        const Bw4d b = Bw4d{(1.0 - tx) * (1.0 - ty), tx * (1.0 - ty), (1.0 - tx) * ty, tx * ty};
+        bw[e] = b;
+        bw32[e] = make_float4((float)b.x, (float)b.y, (float)b.z, (float)b.w);
+    }
+    if (threadIdx.x == 0) {
+        DirInfo di;
+        di.hs = dz / (2.0 * amu);
+        di.hs32 = (float)di.hs;
+        di.pad = 0.f;
+        di.w = w[d];
+        di.sgn = m_u > 0.0 ? 1 : -1;
+        // Lambda* offsets of the four nodes of p_1 (plane k0 - sgn).
+        const long long ix = (long long)floor(-ax), iy = (long long)floor(-ay);
+        const int oz = -di.sgn;
+        for (int q = 0; q < 4; ++q) {
+            const int rx = wrap_mod(ix + (q & 1), g.nx), ry = wrap_mod(iy + (q >> 1), g.ny);
+            const int ox = rx == 0 ? 0 : rx == 1 ? 1 : rx == g.nx - 1 ? -1 : 9;
+            const int oy = ry == 0 ? 0 : ry == 1 ? 1 : ry == g.ny - 1 ? -1 : 9;
+            di.lo[q] = (ox == 9 || oy == 9 || g.nz < 2) ? -1 : (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1);
+        }
+        info[d] = di;
+    }
+}
+
+// Segment weights of the linear-in-tau source (exact integral of S(t)e^{-t}
+// over a segment of optical depth x):  w_cur = 1 - (1-e)/x on the
+// downstream node, w_up = (1-e)/x - e on the upstream node, e = exp(-x).
+// Below x = 1/4 the closed form cancels; there the Taylor series of e^{-x}
+// gives  w_cur = sum_{n>=1} (-1)^{n+1} x^n/(n+1)!  and
+//        w_up  = sum_{n>=1} (-1)^{n+1} n x^n/(n+1)!,  kept through x^12
+// (truncation < 3e-17 relative at x = 1/4).
+__device__ __forceinline__ void seg_weights64(double x, double& wc, double& wu, double& e)
+{
+    e = exp(-x);
+    if (x < 0.25) {
+        // a_n = (-1)^{n+1} / (n+1)!
+        constexpr double a1 = 1.0 / 2.0, a2 = -1.0 / 6.0, a3 = 1.0 / 24.0, a4 = -1.0 / 120.0,
+                         a5 = 1.0 / 720.0, a6 = -1.0 / 5040.0, a7 = 1.0 / 40320.0,
+                         a8 = -1.0 / 362880.0, a9 = 1.0 / 3628800.0, a10 = -1.0 / 39916800.0,
+                         a11 = 1.0 / 479001600.0, a12 = -1.0 / 6227020800.0;
+        double c = a12;
+        c = fma(c, x, a11); c = fma(c, x, a10); c = fma(c, x, a9); c = fma(c, x, a8);
+        c = fma(c, x, a7);  c = fma(c, x, a6);  c = fma(c, x, a5); c = fma(c, x, a4);
+        c = fma(c, x, a3);  c = fma(c, x, a2);  c = fma(c, x, a1);
+        wc = c * x;
+        double u = 12.0 * a12;
+        u = fma(u, x, 11.0 * a11); u = fma(u, x, 10.0 * a10); u = fma(u, x, 9.0 * a9);
+        u = fma(u, x, 8.0 * a8);   u = fma(u, x, 7.0 * a7);   u = fma(u, x, 6.0 * a6);
+        u = fma(u, x, 5.0 * a5);   u = fma(u, x, 4.0 * a4);   u = fma(u, x, 3.0 * a3);
+        u = fma(u, x, 2.0 * a2);   u = fma(u, x, a1);
+        wu = u * x;
+    } else {
+        const double om = 1.0 - e;
+        const double q = om / x;
+        wc = 1.0 - q;
+        wu = q - e;
+    }
+}
+
+struct Nodes {
+    int a00, a10, a01, a11;
+};
+
+__device__ __forceinline__ Nodes nodes_of(int i0, int j0, StepGeo o, int nx, int ny)
+{
+    int x0 = i0 + o.ox;
+    x0 -= (x0 >= nx) ? nx : 0;
+    int x1 = x0 + 1;
+    x1 = (x1 == nx) ? 0 : x1;
+    int y0 = j0 + o.oy;
+    y0 -= (y0 >= ny) ? ny : 0;
+    int y1 = y0 + 1;
+    y1 = (y1 == ny) ? 0 : y1;
+    return Nodes{y0 * nx + x0, y0 * nx + x1, y1 * nx + x0, y1 * nx + x1};
+}
+
+template <typename T, typename V4>
+__device__ __forceinline__ T bilin(const T* __restrict__ p, Nodes n, V4 b)
+{
+    return b.x * __ldg(p + n.a00) + b.y * __ldg(p + n.a10) + b.z * __ldg(p + n.a01) +
+           b.w * __ldg(p + n.a11);
+}
+
+__device__ __forceinline__ void add_steps(unsigned long long* steps, unsigned long long n)
+{
+    for (int s = 16; s > 0; s >>= 1) n += __shfl_down_sync(0xffffffffu, n, s);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(steps, n);
+}
+
+// One thread per voxel of plane blockIdx.y.  Direction d belongs to slot
+// d mod kSlots; each slot is summed in increasing d and written to
+// partial[slot]; block z walks slots zb, zb + gridDim.z, ...  The slot sums
+// are then added in slot order, so J does not depend on gridDim.z.
+__global__ void __launch_bounds__(kThreads)
+k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
+       const double* __restrict__ B, const DirInfo* __restrict__ info,
+       const StepGeo* __restrict__ off, const Bw4d* __restrict__ bw,
+       const double* __restrict__ smax_p, double cut, double* __restrict__ partial,
+       unsigned long long* __restrict__ steps)
+{
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const int t = blockIdx.x * kThreads + threadIdx.x;
+    const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
+    const bool active = t < nxy;
+    unsigned long long nsteps = 0;
+    if (active) {
+        const int j0 = t / nx, i0 = t - j0 * nx;
+        const long long v = (long long)k0 * nxy + t;
+        const double smax = *smax_p;
+        const double chi0 = chi[v], S0 = S[v];
+        for (int slot = zb; slot < kSlots; slot += ZB) {
+            double Jp = 0.0;
+            for (int d = slot; d < g.ndir; d += kSlots) {
+                const DirInfo di = info[d];
+                const int s = di.sgn;
+                const int M = s > 0 ? k0 : nz - 1 - k0;
+                const StepGeo* od = off + (long long)d * nz;
+                const Bw4d* bd = bw + (long long)d * nz;
+                double I = 0.0, T = 1.0, ca = chi0, sa = S0;
+                bool early = false;
+                int m = 0;
+                for (; m < M; ++m) {
+                    const long long pb = (long long)(k0 - (m + 1) * s) * nxy;
+                    const Nodes n = nodes_of(i0, j0, od[m + 1], nx, ny);
+                    const Bw4d b = bd[m + 1];
+                    const double cb = bilin(chi + pb, n, b);
+                    const double sb = bilin(S + pb, n, b);
+                    double wc, wu, e;
+                    seg_weights64(di.hs * (ca + cb), wc, wu, e);
+                    I = fma(T, fma(wc, sa, wu * sb), I);
+                    T *= e;
+                    ca = cb;
+                    sa = sb;
+                    if (T * smax <= cut * fabs(I)) {
+                        early = true;
+                        ++m;
+                        break;
+                    }
+                }
+                if (!early && (s > 0 ? g.top_bc : g.bottom_bc)) {
+                    const long long pb = (long long)(k0 - M * s) * nxy;
+                    const Nodes n = nodes_of(i0, j0, od[M], nx, ny);
+                    I = fma(T, bilin(B + pb, n, bd[M]), I);
+                }
+                nsteps += (unsigned long long)m;
+                Jp = fma(di.w, I, Jp);
+            }
+            partial[(long long)slot * g.N + v] = Jp;
+        }
+    }
+    if (steps) add_steps(steps, nsteps);
+}
+
+// FP32 segment weights: same definitions as seg_weights64.  Below x = 3/4
+// the Taylor series is kept through x^10 (truncation < 5e-9 relative);
+// above it the closed form loses less than a factor 3 to cancellation.
+__device__ __forceinline__ void seg_weights32(float x, float& wc, float& wu, float& e)
+{
+    e = expf(-x);
+    if (x < 0.75f) {
+        constexpr float a1 = 1.0f / 2.0f, a2 = -1.0f / 6.0f, a3 = 1.0f / 24.0f,
+                        a4 = -1.0f / 120.0f, a5 = 1.0f / 720.0f, a6 = -1.0f / 5040.0f,
+                        a7 = 1.0f / 40320.0f, a8 = -1.0f / 362880.0f, a9 = 1.0f / 3628800.0f,
+                        a10 = -1.0f / 39916800.0f;
+        float c = a10;
+        c = fmaf(c, x, a9); c = fmaf(c, x, a8); c = fmaf(c, x, a7); c = fmaf(c, x, a6);
+        c = fmaf(c, x, a5); c = fmaf(c, x, a4); c = fmaf(c, x, a3); c = fmaf(c, x, a2);
+        c = fmaf(c, x, a1);
+        wc = c * x;
+        float u = 10.0f * a10;
+        u = fmaf(u, x, 9.0f * a9); u = fmaf(u, x, 8.0f * a8); u = fmaf(u, x, 7.0f * a7);
+        u = fmaf(u, x, 6.0f * a6); u = fmaf(u, x, 5.0f * a5); u = fmaf(u, x, 4.0f * a4);
+        u = fmaf(u, x, 3.0f * a3); u = fmaf(u, x, 2.0f * a2); u = fmaf(u, x, a1);
+        wu = u * x;
+    } else {
+        const float om = 1.0f - e;
+        const float q = __fdividef(om, x);
+        wc = 1.0f - q;
+        wu = q - e;
+    }
+}
+
+// FP32 march, FP64 accumulation of J over directions.
+__global__ void __launch_bounds__(kThreads)
+k_fs32(Geometry g, const float* __restrict__ chi, const float* __restrict__ S,
+       const float* __restrict__ B, const DirInfo* __restrict__ info,
+       const StepGeo* __restrict__ off, const float4* __restrict__ bw,
+       const double* __restrict__ smax_p, float cut, double* __restrict__ partial,
+       unsigned long long* __restrict__ steps)
+{
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const int t = blockIdx.x * kThreads + threadIdx.x;
+    const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
+    const bool active = t < nxy;
+    unsigned long long nsteps = 0;
+    if (active) {
+        const int j0 = t / nx, i0 = t - j0 * nx;
+        const long long v = (long long)k0 * nxy + t;
+        const float smax = (float)*smax_p;
+        const float chi0 = chi[v], S0 = S[v];
+        for (int slot = zb; slot < kSlots; slot += ZB) {
+            double Jp = 0.0;
+            for (int d = slot; d < g.ndir; d += kSlots) {
+                const DirInfo di = info[d];
+                const int s = di.sgn;
+                const int M = s > 0 ? k0 : nz - 1 - k0;
+                const StepGeo* od = off + (long long)d * nz;
+                const float4* bd = bw + (long long)d * nz;
+                float I = 0.0f, T = 1.0f, ca = chi0, sa = S0;
+                bool early = false;
+                int m = 0;
+                for (; m < M; ++m) {
+                    const long long pb = (long long)(k0 - (m + 1) * s) * nxy;
+                    const Nodes n = nodes_of(i0, j0, od[m + 1], nx, ny);
+                    const float4 b = bd[m + 1];
+                    const float cb = bilin(chi + pb, n, b);
+                    const float sb = bilin(S + pb, n, b);
+                    float wc, wu, e;
+                    seg_weights32(di.hs32 * (ca + cb), wc, wu, e);
+                    I = fmaf(T, fmaf(wc, sa, wu * sb), I);
+                    T *= e;
+                    ca = cb;
+                    sa = sb;
+                    if (T * smax <= cut * fabsf(I)) {
+                        early = true;
+                        ++m;
+                        break;
+                    }
+                }
+                if (!early && (s > 0 ? g.top_bc : g.bottom_bc)) {
+                    const long long pb = (long long)(k0 - M * s) * nxy;
+                    const Nodes n = nodes_of(i0, j0, od[M], nx, ny);
+                    I = fmaf(T, bilin(B + pb, n, bd[M]), I);
+                }
+                nsteps += (unsigned long long)m;
+                Jp = fma(di.w, (double)I, Jp);
+            }
+            partial[(long long)slot * g.N + v] = Jp;
+        }
+    }
+    if (steps) add_steps(steps, nsteps);
+}
+
+__global__ void k_sum_groups(long long N, const double* __restrict__ partial,
+                             double* __restrict__ J)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < kSlots; ++q) s += partial[q * N + v];
+        J[v] = s;
+    }
+}
+
+// Lambda*: the coefficient of S at p_0 is w_cur(0); at p_1 it is
+// w_up(0) + e_0 w_cur(1) (just w_up(0) if p_1 is on the boundary).  p_m for
+// m >= 2 lies two or more planes away, outside the 27-point neighbourhood.
+// The p_1 coefficient is shared among its four bilinear nodes, whose
+// neighbour offsets are tabulated per direction.
+__global__ void __launch_bounds__(kThreads)
+k_lstar64(Geometry g, const double* __restrict__ chi, const DirInfo* __restrict__ info,
+          const StepGeo* __restrict__ off, const Bw4d* __restrict__ bw,
+          double* __restrict__ lstar)
+{
+    __shared__ double lam[27][kThreads];
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const int t = blockIdx.x * kThreads + threadIdx.x;
+    const int k0 = blockIdx.y;
+    for (int o = 0; o < 27; ++o) lam[o][threadIdx.x] = 0.0;
+    if (t >= nxy) return;
+    const int j0 = t / nx, i0 = t - j0 * nx;
+    const long long v = (long long)k0 * nxy + t;
+    const double chi0 = chi[v];
+    for (int d = 0; d < g.ndir; ++d) {
+        const DirInfo di = info[d];
+        const int s = di.sgn;
+        const int M = s > 0 ? k0 : nz - 1 - k0;
+        if (M == 0) continue;
+        const StepGeo* od = off + (long long)d * nz;
+        const Bw4d* bd = bw + (long long)d * nz;
+        const Bw4d b1 = bd[1];
+        const double chi1 = bilin(chi + (long long)(k0 - s) * nxy, nodes_of(i0, j0, od[1], nx, ny), b1);
+        double wc0, wu0, e0;
+        seg_weights64(di.hs * (chi0 + chi1), wc0, wu0, e0);
+        double c1 = wu0;
+        if (M >= 2) {
+            const double chi2 = bilin(chi + (long long)(k0 - 2 * s) * nxy,
+                                      nodes_of(i0, j0, od[2], nx, ny), bd[2]);
+            double wc1, wu1, e1;
+            seg_weights64(di.hs * (chi1 + chi2), wc1, wu1, e1);
+            c1 = fma(e0, wc1, wu0);
+        }
+        lam[13][threadIdx.x] += di.w * wc0;
+        const double cw = di.w * c1;
+        if (di.lo[0] >= 0) lam[di.lo[0]][threadIdx.x] += cw * b1.x;
+        if (di.lo[1] >= 0) lam[di.lo[1]][threadIdx.x] += cw * b1.y;
+        if (di.lo[2] >= 0) lam[di.lo[2]][threadIdx.x] += cw * b1.z;
+        if (di.lo[3] >= 0) lam[di.lo[3]][threadIdx.x] += cw * b1.w;
+    }
+    for (int o = 0; o < 27; ++o) lstar[(long long)o * g.N + v] = lam[o][threadIdx.x];
+}
+
+}  // namespace
+
+cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz,
+                              const double* mu, const double* phi, const double* w,
+                              DirInfo* info, StepGeo* off, Bw4d* bw, float4* bw32,
+                              cudaStream_t st)
+{
+    k_dir_tables<<<g.ndir, 128, 0, st>>>(g, dx, dy, dz, mu, phi, w, info, off, bw, bw32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, const double* B,
+                        const DirInfo* info, const StepGeo* off, const Bw4d* bw,
+                        const double* smax, double cut, int groups, double* partial,
+                        unsigned long long* steps, cudaStream_t st)
+{
+    const int nxy = g.nx * g.ny;
+    dim3 grid((nxy + kThreads - 1) / kThreads, g.nz, groups);
+    k_fs64<<<grid, kThreads, 0, st>>>(g, chi, S, B, info, off, bw, smax, cut, partial, steps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fs32(const Geometry& g, const float* chi, const float* S, const float* B,
+                        const DirInfo* info, const StepGeo* off, const float4* bw,
+                        const double* smax, double cut, int groups, double* partial,
+                        unsigned long long* steps, cudaStream_t st)
+{
+    const int nxy = g.nx * g.ny;
+    dim3 grid((nxy + kThreads - 1) / kThreads, g.nz, groups);
+    k_fs32<<<grid, kThreads, 0, st>>>(g, chi, S, B, info, off, bw, smax, (float)cut, partial,
+                                      steps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_groups(long long N, const double* partial, double* J,
+                              cudaStream_t st)
+{
+    const int threads = 256;
+    long long blocks = (N + threads - 1) / threads;
+    if (blocks > 65535LL * 16) blocks = 65535LL * 16;
+    k_sum_groups<<<(unsigned)blocks, threads, 0, st>>>(N, partial, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lstar64(const Geometry& g, const double* chi, const DirInfo* info,
+                           const StepGeo* off, const Bw4d* bw, double* lstar,
+                           cudaStream_t st)
+{
+    const int nxy = g.nx * g.ny;
+    dim3 grid((nxy + kThreads - 1) / kThreads, g.nz, 1);
+    k_lstar64<<<grid, kThreads, 0, st>>>(g, chi, info, off, bw, lstar);
+    return cudaGetLastError();
+}
+
+}  // namespace rt3d

@@ -1,0 +1,98 @@
+// Internal declarations shared by the translation units of librt3d.so.
+// Not part of the public ABI (include/rt3d.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace rt3d {
+
+// Directions are summed into J in kSlots fixed slots (d mod kSlots), each in
+// increasing d, then the slots in order: J is independent of the launch
+// shape.  The formal solution writes kSlots partial sums per voxel.
+constexpr int kSlots = 8;
+
+// Per-direction constants of the march (one entry per direction).
+struct DirInfo {
+    double hs;      // half path length per z-plane step, dz / (2 |mu|)
+    double w;       // quadrature weight
+    int sgn;        // +1: propagates to larger k (entered at the top), -1: from the bottom
+    int lo[4];      // Lambda* offset index of the four bilinear nodes of p_1, -1 if none
+    float hs32;     // hs in FP32 (sweep form)
+    float pad;
+};
+
+// Per-(direction, step m) lattice geometry.  The upstream point p_m of voxel
+// (i0, j0) lies at (i0 - m ax, j0 - m ay); because voxel centres are lattice
+// points its integer part and fraction do not depend on the voxel:
+//   node x0 = (i0 + ox) mod nx, x1 = x0 + 1 (mod nx), likewise y, and the
+//   bilinear weights of (x0,y0), (x1,y0), (x0,y1), (x1,y1).
+struct StepGeo {
+    int ox, oy;
+};
+
+// Bilinear weights of (x0,y0), (x1,y0), (x0,y1), (x1,y1) in FP64.
+struct alignas(32) Bw4d {
+    double x, y, z, w;
+};
+
+struct Geometry {
+    int nx, ny, nz, ndir;
+    long long N;            // nx * ny * nz
+    int top_bc, bottom_bc;  // 0 zero, 1 Planck
+};
+
+// ---- launchers (fs.cu) -----------------------------------------------------
+cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz,
+                              const double* mu, const double* phi, const double* w,
+                              DirInfo* info, StepGeo* off, Bw4d* bw, float4* bw32,
+                              cudaStream_t st);
+
+// FP64 formal solution: partial[kSlots][N]; `groups` (1..kSlots) is the
+// number of z-blocks walking the slots (a tuning knob, no effect on J).
+cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, const double* B,
+                        const DirInfo* info, const StepGeo* off, const Bw4d* bw,
+                        const double* smax, double cut, int groups, double* partial,
+                        unsigned long long* steps, cudaStream_t st);
+
+// FP32-sweep formal solution (FP64 accumulation of J): same output layout.
+cudaError_t launch_fs32(const Geometry& g, const float* chi, const float* S, const float* B,
+                        const DirInfo* info, const StepGeo* off, const float4* bw,
+                        const double* smax, double cut, int groups, double* partial,
+                        unsigned long long* steps, cudaStream_t st);
+
+// J[v] = sum_slot partial[slot][v] in slot order.
+cudaError_t launch_sum_groups(long long N, const double* partial, double* J,
+                              cudaStream_t st);
+
+// Lambda* [27][N] (FP64, exact elements, first two steps of each characteristic).
+cudaError_t launch_lstar64(const Geometry& g, const double* chi, const DirInfo* info,
+                           const StepGeo* off, const Bw4d* bw, double* lstar,
+                           cudaStream_t st);
+
+// ---- launchers (os.cu) -----------------------------------------------------
+// S = eps B + (1 - eps) J; smax = max(|S|, |B| if any Planck boundary).
+cudaError_t launch_source(long long N, const double* eps, const double* B, const double* J,
+                          double* S, float* S32, const double* Bbound, double* smax,
+                          cudaStream_t st);
+// smax = max(|S|, |B| if B != nullptr), also the FP32 copy of S if S32 != nullptr.
+cudaError_t launch_absmax(long long N, const double* S, const double* B, double* smax,
+                          float* S32, cudaStream_t st);
+cudaError_t launch_to_float(long long N, const double* x, float* y, cudaStream_t st);
+
+// Operator-splitting coefficients: c[o][v] = Lambda*_{v,o} (1 - eps_j) / diag_v,
+// rdiag[v] = 1 / diag_v, diag_v = 1 - Lambda*_{v,13} (1 - eps_v).
+cudaError_t launch_os_coef(const Geometry& g, const double* lstar, const double* eps,
+                           double* coef, double* rdiag, cudaStream_t st);
+// r[v] = J_fs[v] / diag_v - sum_o c[o][v] J_old[nb(v,o)]
+cudaError_t launch_os_rhs(const Geometry& g, const double* coef, const double* rdiag,
+                          const double* J_fs, const double* J_old, double* r, cudaStream_t st);
+// Jn[v] = r[v] + sum_{o != 13} c[o][v] J[nb(v,o)];  *delta = max |Jn - J| / |Jn|
+cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r,
+                          const double* J, double* Jn, double* delta, cudaStream_t st);
+// *delta = max |Jn - Jo| / |Jn|
+cudaError_t launch_rel_change(long long N, const double* Jn, const double* Jo, double* delta,
+                              cudaStream_t st);
+
+}  // namespace rt3d

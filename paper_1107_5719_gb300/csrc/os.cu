@@ -1,0 +1,260 @@
+// Operator splitting (Hauschildt & Baron 2011, Sect. 2.3), source update
+// and the max-reductions of the convergence tests.
+//
+// The new J solves (1 - Lambda* D) J_new = J_fs - Lambda* D J_old with
+// D = diag(1 - eps).  Jacobi ("Jordan") form, with the coefficients of the
+// 27-band operator precomputed once per (chi, eps):
+//   diag_v  = 1 - Lambda*_{v,13} (1 - eps_v)
+//   c_{v,o} = Lambda*_{v,o} (1 - eps_{nb(v,o)}) / diag_v
+//   r_v     = J_fs,v / diag_v - sum_o c_{v,o} J_old,nb(v,o)
+//   J^{n+1}_v = r_v + sum_{o != 13} c_{v,o} J^n_{nb(v,o)}
+// The coefficients are stored offset-major ([27][N]) so that a warp reads
+// 32 consecutive voxels of one offset (coalesced).  Max-reductions of
+// non-negative doubles use atomicMax on their bit patterns, which order
+// like the values; max is independent of the order, so results are
+// reproducible.
+#include "internal.h"
+
+namespace rt3d {
+
+namespace {
+
+__device__ __forceinline__ void block_max_to(double val, double* out)
+{
+    // val >= 0 or NaN; NaN must win so that a broken iterate never "converges".
+    __shared__ unsigned long long sm[32];
+    unsigned long long b = (unsigned long long)__double_as_longlong(val);
+    for (int s = 16; s > 0; s >>= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, b, s);
+        b = o > b ? o : b;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sm[wid] = b;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        b = lane < nw ? sm[lane] : 0ull;
+        for (int s = 16; s > 0; s >>= 1) {
+            const unsigned long long o = __shfl_down_sync(0xffffffffu, b, s);
+            b = o > b ? o : b;
+        }
+        if (lane == 0 && b) atomicMax((unsigned long long*)out, b);
+    }
+}
+
+__device__ __forceinline__ double nonneg(double x)
+{
+    return fabs(x);  // clears the sign bit of NaN too
+}
+
+__global__ void k_source(long long N, const double* __restrict__ eps, const double* __restrict__ B,
+                         const double* __restrict__ J, double* __restrict__ S,
+                         float* __restrict__ S32, const double* __restrict__ Bbound,
+                         double* __restrict__ smax)
+{
+    double m = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+        const double e = eps[v];
+        const double s = fma(e, B[v], (1.0 - e) * J[v]);
+        S[v] = s;
+        if (S32) S32[v] = (float)s;
+        double a = nonneg(s);
+        if (Bbound) a = fmax(a, nonneg(Bbound[v]));
+        if (!(a <= m)) m = a;
+    }
+    block_max_to(m, smax);
+}
+
+__global__ void k_absmax(long long N, const double* __restrict__ S, const double* __restrict__ B,
+                         double* __restrict__ smax, float* __restrict__ S32)
+{
+    double m = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+        const double s = S[v];
+        if (S32) S32[v] = (float)s;
+        double a = nonneg(s);
+        if (B) a = fmax(a, nonneg(B[v]));
+        if (!(a <= m)) m = a;
+    }
+    block_max_to(m, smax);
+}
+
+__global__ void k_to_float(long long N, const double* __restrict__ x, float* __restrict__ y)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x)
+        y[v] = (float)x[v];
+}
+
+// Neighbour (ox, oy, oz) of voxel (i, j, k) with periodic x, y.
+__device__ __forceinline__ int wrap1(int a, int n)
+{
+    return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+constexpr int kOsThreads = 128;
+
+__global__ void __launch_bounds__(kOsThreads)
+k_os_coef(Geometry g, const double* __restrict__ L, const double* __restrict__ eps,
+          double* __restrict__ c, double* __restrict__ rdiag)
+{
+    const int nx = g.nx, ny = g.ny, nxy = nx * ny;
+    const int t = blockIdx.x * kOsThreads + threadIdx.x;
+    const int k = blockIdx.y;
+    if (t >= nxy) return;
+    const int j = t / nx, i = t - j * nx;
+    const long long v = (long long)k * nxy + t;
+    const double rd = 1.0 / (1.0 - L[13 * g.N + v] * (1.0 - eps[v]));
+    rdiag[v] = rd;
+    for (int o = 0; o < 27; ++o) {
+        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+        const int kk = k + oz;
+        double cv = 0.0;
+        if (kk >= 0 && kk < g.nz) {
+            const long long nb = (long long)kk * nxy + wrap1(j + oy, ny) * nx + wrap1(i + ox, nx);
+            cv = L[o * g.N + v] * (1.0 - eps[nb]) * rd;
+        }
+        c[o * g.N + v] = cv;
+    }
+}
+
+// sum_o c[o][v] * J[nb(v,o)] over the offsets, skipping the centre if
+// SKIP_CENTRE and planes outside the grid.
+template <bool SKIP_CENTRE>
+__device__ __forceinline__ double stencil(const Geometry& g, const double* __restrict__ c,
+                                          const double* __restrict__ J, int i, int j, int k,
+                                          long long v)
+{
+    const int nx = g.nx, ny = g.ny, nxy = nx * ny;
+    const int xm = wrap1(i - 1, nx), xp = wrap1(i + 1, nx);
+    const int ym = wrap1(j - 1, ny), yp = wrap1(j + 1, ny);
+    const int xs[3] = {xm, i, xp};
+    const int ys[3] = {ym, j, yp};
+    double acc = 0.0;
+#pragma unroll
+    for (int oz = 0; oz < 3; ++oz) {
+        const int kk = k + oz - 1;
+        if (kk < 0 || kk >= g.nz) continue;
+        const double* Jp = J + (long long)kk * nxy;
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy) {
+            const double* Jr = Jp + ys[oy] * nx;
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+                const int o = oz * 9 + oy * 3 + ox;
+                if (SKIP_CENTRE && o == 13) continue;
+                acc = fma(__ldg(c + o * g.N + v), __ldg(Jr + xs[ox]), acc);
+            }
+        }
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kOsThreads)
+k_os_rhs(Geometry g, const double* __restrict__ c, const double* __restrict__ rdiag,
+         const double* __restrict__ Jfs, const double* __restrict__ Jold, double* __restrict__ r)
+{
+    const int nx = g.nx, nxy = nx * g.ny;
+    const int t = blockIdx.x * kOsThreads + threadIdx.x;
+    const int k = blockIdx.y;
+    if (t >= nxy) return;
+    const int j = t / nx, i = t - j * nx;
+    const long long v = (long long)k * nxy + t;
+    r[v] = Jfs[v] * rdiag[v] - stencil<false>(g, c, Jold, i, j, k, v);
+}
+
+__global__ void __launch_bounds__(kOsThreads)
+k_jacobi(Geometry g, const double* __restrict__ c, const double* __restrict__ r,
+         const double* __restrict__ J, double* __restrict__ Jn, double* __restrict__ delta)
+{
+    const int nx = g.nx, nxy = nx * g.ny;
+    const int t = blockIdx.x * kOsThreads + threadIdx.x;
+    const int k = blockIdx.y;
+    double rel = 0.0;
+    if (t < nxy) {
+        const int j = t / nx, i = t - j * nx;
+        const long long v = (long long)k * nxy + t;
+        const double jn = r[v] + stencil<true>(g, c, J, i, j, k, v);
+        Jn[v] = jn;
+        rel = nonneg((jn - J[v]) / jn);
+    }
+    block_max_to(rel, delta);
+}
+
+__global__ void k_rel_change(long long N, const double* __restrict__ Jn,
+                             const double* __restrict__ Jo, double* __restrict__ delta)
+{
+    double m = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+        const double a = nonneg((Jn[v] - Jo[v]) / Jn[v]);
+        if (!(a <= m)) m = a;
+    }
+    block_max_to(m, delta);
+}
+
+unsigned grid_1d(long long N, int threads)
+{
+    long long b = (N + threads - 1) / threads;
+    if (b > 152LL * 32) b = 152LL * 32;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_source(long long N, const double* eps, const double* B, const double* J,
+                          double* S, float* S32, const double* Bbound, double* smax,
+                          cudaStream_t st)
+{
+    k_source<<<grid_1d(N, 256), 256, 0, st>>>(N, eps, B, J, S, S32, Bbound, smax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(long long N, const double* S, const double* B, double* smax,
+                          float* S32, cudaStream_t st)
+{
+    k_absmax<<<grid_1d(N, 256), 256, 0, st>>>(N, S, B, smax, S32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_float(long long N, const double* x, float* y, cudaStream_t st)
+{
+    k_to_float<<<grid_1d(N, 256), 256, 0, st>>>(N, x, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_os_coef(const Geometry& g, const double* lstar, const double* eps,
+                           double* coef, double* rdiag, cudaStream_t st)
+{
+    dim3 grid((g.nx * g.ny + kOsThreads - 1) / kOsThreads, g.nz);
+    k_os_coef<<<grid, kOsThreads, 0, st>>>(g, lstar, eps, coef, rdiag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_os_rhs(const Geometry& g, const double* coef, const double* rdiag,
+                          const double* J_fs, const double* J_old, double* r, cudaStream_t st)
+{
+    dim3 grid((g.nx * g.ny + kOsThreads - 1) / kOsThreads, g.nz);
+    k_os_rhs<<<grid, kOsThreads, 0, st>>>(g, coef, rdiag, J_fs, J_old, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r,
+                          const double* J, double* Jn, double* delta, cudaStream_t st)
+{
+    dim3 grid((g.nx * g.ny + kOsThreads - 1) / kOsThreads, g.nz);
+    k_jacobi<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, Jn, delta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rel_change(long long N, const double* Jn, const double* Jo, double* delta,
+                              cudaStream_t st)
+{
+    k_rel_change<<<grid_1d(N, 256), 256, 0, st>>>(N, Jn, Jo, delta);
+    return cudaGetLastError();
+}
+
+}  // namespace rt3d

@@ -1,0 +1,339 @@
+"""Thin ctypes binding of librt3d.so (C ABI in include/rt3d.h).
+
+The functions carry the C names and only marshal arguments: numpy arrays
+for the host-pointer calls, CUDA torch tensors (or raw device addresses)
+for the ``*_dev`` calls.  Every step of the computation runs in the CUDA
+library; there is no fallback.  Loading fails loudly if ``librt3d.so`` is
+missing or cannot be loaded.
+
+``Solver`` bundles a context with one problem for convenience.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_ETIMEOUT, RT_ESTATE = range(7)
+RT_FP64, RT_FP32_SWEEP = 0, 1
+RT_BC_ZERO, RT_BC_PLANCK = 0, 1
+
+_NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV",
+          5: "RT_ETIMEOUT", 6: "RT_ESTATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librt3d.so")
+_lib = None
+_lock = threading.Lock()
+
+P = C.POINTER(C.c_double)
+VP = C.c_void_p
+
+
+class RtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rt_stats(C.Structure):
+    _fields_ = [("launches", C.c_ulonglong), ("fs_launches", C.c_ulonglong),
+                ("fs_ms", C.c_double), ("jacobi_launches", C.c_ulonglong),
+                ("jacobi_ms", C.c_double), ("steps", C.c_ulonglong),
+                ("lstar_launches", C.c_ulonglong)]
+
+
+# name -> (restype, argtypes); pointers to data are passed as void*
+_SIGS = {
+    "rt_version": (C.c_char_p, []),
+    "rt_create": (C.c_int, [C.POINTER(VP), C.c_int, C.c_int]),
+    "rt_destroy": (C.c_int, [VP]),
+    "rt_last_error": (C.c_char_p, [VP]),
+    "rt_set_stream": (C.c_int, [VP, VP]),
+    "rt_set_grid": (C.c_int, [VP, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]),
+    "rt_set_boundary": (C.c_int, [VP, C.c_int, C.c_int]),
+    "rt_set_quadrature": (C.c_int, [VP, C.c_int, VP, VP, VP]),
+    "rt_set_opacity": (C.c_int, [VP, VP]),
+    "rt_set_epsilon": (C.c_int, [VP, VP]),
+    "rt_set_planck": (C.c_int, [VP, VP]),
+    "rt_set_opacity_dev": (C.c_int, [VP, VP]),
+    "rt_set_epsilon_dev": (C.c_int, [VP, VP]),
+    "rt_set_planck_dev": (C.c_int, [VP, VP]),
+    "rt_formal_solution": (C.c_int, [VP, VP, VP, VP]),
+    "rt_formal_solution_dev": (C.c_int, [VP, VP, VP, VP]),
+    "rt_os_step": (C.c_int, [VP, VP, VP, VP, C.c_double, C.c_int, C.POINTER(C.c_int)]),
+    "rt_os_step_dev": (C.c_int, [VP, VP, VP, VP, C.c_double, C.c_int, C.POINTER(C.c_int)]),
+    "rt_solve": (C.c_int, [VP, C.c_double, C.c_int, C.c_double, C.c_int, VP,
+                           C.POINTER(C.c_int), P, VP, VP]),
+    "rt_solve_dev": (C.c_int, [VP, C.c_double, C.c_int, C.c_double, C.c_int, VP,
+                               C.POINTER(C.c_int), P, VP, VP]),
+    "rt_get_J": (C.c_int, [VP, VP]),
+    "rt_set_J": (C.c_int, [VP, VP]),
+    "rt_last_step_count": (C.c_int, [VP, C.POINTER(C.c_ulonglong)]),
+    "rt_set_direction_groups": (C.c_int, [VP, C.c_int]),
+    "rt_set_cutoff": (C.c_int, [VP, C.c_double]),
+    "rt_set_profiling": (C.c_int, [VP, C.c_int]),
+    "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
+    "rt_reset_stats": (C.c_int, [VP]),
+}
+
+
+def load(path: Optional[str] = None):
+    """Load librt3d.so (built by ``paper_1107_5719_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise ImportError(f"{p} is missing: build it with paper_1107_5719_gb300.build.build()")
+            lib = C.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def _check(ctx, rc, allow=()):
+    if rc != RT_OK and rc not in allow:
+        msg = load().rt_last_error(ctx).decode() if ctx else ""
+        raise RtError(rc, msg)
+    return rc
+
+
+def _host(a, dtype=np.float64):
+    """C-contiguous float64 host array and its address."""
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def _dev(t):
+    """Device address of a CUDA tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device calls need contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+# ---- C-named wrappers -----------------------------------------------------
+
+def rt_version() -> str:
+    return load().rt_version().decode()
+
+
+def rt_create(device: int = 0, precision: int = RT_FP64):
+    h = VP()
+    rc = load().rt_create(C.byref(h), device, precision)
+    if rc != RT_OK:
+        raise RtError(rc, f"rt_create(device={device}, precision={precision}) failed")
+    return h.value
+
+
+def rt_destroy(ctx):
+    return load().rt_destroy(ctx)
+
+
+def rt_last_error(ctx) -> str:
+    return load().rt_last_error(ctx).decode()
+
+
+def rt_set_stream(ctx, stream):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t address, or None."""
+    h = getattr(stream, "cuda_stream", stream)
+    return _check(ctx, load().rt_set_stream(ctx, h))
+
+
+def rt_set_grid(ctx, nx, ny, nz, dx=1.0, dy=1.0, dz=1.0):
+    return _check(ctx, load().rt_set_grid(ctx, nx, ny, nz, dx, dy, dz))
+
+
+def rt_set_boundary(ctx, top, bottom):
+    return _check(ctx, load().rt_set_boundary(ctx, top, bottom))
+
+
+def rt_set_quadrature(ctx, mu, phi, w):
+    mu, pm = _host(mu)
+    phi, pp = _host(phi)
+    w, pw = _host(w)
+    return _check(ctx, load().rt_set_quadrature(ctx, len(mu), pm, pp, pw))
+
+
+def _setter(name):
+    def f(ctx, arr):
+        a, p = _host(arr)
+        return _check(ctx, getattr(load(), name)(ctx, p))
+    f.__name__ = name
+    return f
+
+
+def _setter_dev(name):
+    def f(ctx, t):
+        return _check(ctx, getattr(load(), name)(ctx, _dev(t)))
+    f.__name__ = name
+    return f
+
+
+rt_set_opacity = _setter("rt_set_opacity")
+rt_set_epsilon = _setter("rt_set_epsilon")
+rt_set_planck = _setter("rt_set_planck")
+rt_set_opacity_dev = _setter_dev("rt_set_opacity_dev")
+rt_set_epsilon_dev = _setter_dev("rt_set_epsilon_dev")
+rt_set_planck_dev = _setter_dev("rt_set_planck_dev")
+
+
+def rt_formal_solution(ctx, S, shape, want_lstar=True):
+    """Host call: returns (J_fs, Lambda* [27, *shape] or None)."""
+    J = np.empty(shape)
+    L = np.empty((27, *shape)) if want_lstar else None
+    Sp = None
+    if S is not None:
+        S, Sp = _host(S)
+    _check(ctx, load().rt_formal_solution(ctx, Sp, J.ctypes.data, L.ctypes.data if want_lstar else None))
+    return J, L
+
+
+def rt_formal_solution_dev(ctx, S, J_fs, lstar=None):
+    return _check(ctx, load().rt_formal_solution_dev(ctx, _dev(S), _dev(J_fs), _dev(lstar)))
+
+
+def rt_os_step(ctx, J_fs, J_old, tol_inner=1e-12, max_sweeps=1000):
+    J_fs, pf = _host(J_fs)
+    J_old, po = _host(J_old)
+    Jn = np.empty_like(J_old)
+    ns = C.c_int()
+    _check(ctx, load().rt_os_step(ctx, pf, po, Jn.ctypes.data, tol_inner, max_sweeps, C.byref(ns)))
+    return Jn, ns.value
+
+
+def rt_os_step_dev(ctx, J_fs, J_old, J_new, tol_inner=1e-12, max_sweeps=1000):
+    ns = C.c_int()
+    _check(ctx, load().rt_os_step_dev(ctx, _dev(J_fs), _dev(J_old), _dev(J_new), tol_inner,
+                                      max_sweeps, C.byref(ns)))
+    return ns.value
+
+
+def rt_solve(ctx, shape, tol=1e-8, max_iter=500, tol_inner=1e-12, max_sweeps=1000):
+    """Host call: returns dict(J, iters, delta, deltas, sweeps, converged)."""
+    J = np.empty(shape)
+    it = C.c_int()
+    last = C.c_double()
+    deltas = np.zeros(max_iter)
+    sweeps = np.zeros(max_iter, dtype=np.int32)
+    rc = _check(ctx, load().rt_solve(ctx, tol, max_iter, tol_inner, max_sweeps, J.ctypes.data,
+                                     C.byref(it), C.byref(last), deltas.ctypes.data,
+                                     sweeps.ctypes.data), allow=(RT_ENOTCONV,))
+    n = it.value
+    return dict(J=J, iters=n, delta=last.value, deltas=deltas[:n], sweeps=sweeps[:n],
+                converged=(rc == RT_OK))
+
+
+def rt_solve_dev(ctx, J_out=None, tol=1e-8, max_iter=500, tol_inner=1e-12, max_sweeps=1000,
+                 deltas=None, sweeps=None):
+    """Device call (J_out a CUDA tensor or None): returns (iters, delta, converged)."""
+    it = C.c_int()
+    last = C.c_double()
+    pd = deltas.ctypes.data if deltas is not None else None
+    ps = sweeps.ctypes.data if sweeps is not None else None
+    rc = _check(ctx, load().rt_solve_dev(ctx, tol, max_iter, tol_inner, max_sweeps, _dev(J_out),
+                                         C.byref(it), C.byref(last), pd, ps), allow=(RT_ENOTCONV,))
+    return it.value, last.value, rc == RT_OK
+
+
+def rt_get_J(ctx, shape):
+    J = np.empty(shape)
+    _check(ctx, load().rt_get_J(ctx, J.ctypes.data))
+    return J
+
+
+def rt_set_J(ctx, J):
+    J, p = _host(J)
+    return _check(ctx, load().rt_set_J(ctx, p))
+
+
+def rt_last_step_count(ctx) -> int:
+    n = C.c_ulonglong()
+    _check(ctx, load().rt_last_step_count(ctx, C.byref(n)))
+    return n.value
+
+
+def rt_set_direction_groups(ctx, groups):
+    return _check(ctx, load().rt_set_direction_groups(ctx, groups))
+
+
+def rt_set_cutoff(ctx, cut):
+    return _check(ctx, load().rt_set_cutoff(ctx, cut))
+
+
+def rt_set_profiling(ctx, on=True):
+    return _check(ctx, load().rt_set_profiling(ctx, 1 if on else 0))
+
+
+def rt_get_stats(ctx) -> dict:
+    s = rt_stats()
+    _check(ctx, load().rt_get_stats(ctx, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in rt_stats._fields_}
+
+
+def rt_reset_stats(ctx):
+    return _check(ctx, load().rt_reset_stats(ctx))
+
+
+# ---- convenience ----------------------------------------------------------
+
+class Solver:
+    """One context holding one problem (a ``workloads.Problem``-like object)."""
+
+    def __init__(self, problem, device: int = 0, precision: int = RT_FP64, groups: int = 0,
+                 cutoff: Optional[float] = None):
+        self.p = problem
+        self.ctx = rt_create(device, precision)
+        self.shape = (problem.nz, problem.ny, problem.nx)
+        rt_set_grid(self.ctx, problem.nx, problem.ny, problem.nz, problem.dx, problem.dy, problem.dz)
+        rt_set_boundary(self.ctx, problem.top_bc, problem.bottom_bc)
+        rt_set_quadrature(self.ctx, problem.mu, problem.phi, problem.w)
+        rt_set_opacity(self.ctx, problem.chi)
+        rt_set_epsilon(self.ctx, problem.eps)
+        rt_set_planck(self.ctx, problem.B)
+        if groups:
+            rt_set_direction_groups(self.ctx, groups)
+        if cutoff is not None:
+            rt_set_cutoff(self.ctx, cutoff)
+
+    def formal_solution(self, S=None, want_lstar=True):
+        return rt_formal_solution(self.ctx, S, self.shape, want_lstar)
+
+    def os_step(self, J_fs, J_old, tol_inner=1e-12, max_sweeps=1000):
+        return rt_os_step(self.ctx, J_fs, J_old, tol_inner, max_sweeps)
+
+    def solve(self, tol=None, max_iter=500, tol_inner=1e-12, max_sweeps=1000):
+        tol = self.p.tol if tol is None else tol
+        return rt_solve(self.ctx, self.shape, tol, max_iter, tol_inner, max_sweeps)
+
+    def close(self):
+        if self.ctx:
+            rt_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
