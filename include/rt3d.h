@@ -76,7 +76,8 @@ typedef enum {
     RT_ECUDA = 3,       /* a CUDA call failed */
     RT_ENOTCONV = 4,    /* max_iter reached before delta < tol (outputs valid) */
     RT_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
-    RT_ESTATE = 6       /* the call needs data that was not set yet */
+    RT_ESTATE = 6,      /* the call needs data that was not set yet */
+    RT_ESCRATCH = 7     /* too large for rt_formal_solution_noalloc's fixed scratch */
 } rt_status;
 
 enum { RT_FP64 = 0, RT_FP32_SWEEP = 1 };
@@ -181,6 +182,46 @@ int rt_set_direction_groups(rt_ctx *ctx, int groups);
  * at most that much).  0 disables the cutoff.  Default 1e-17 (FP64) and
  * 1e-9 (FP32 sweep). */
 int rt_set_cutoff(rt_ctx *ctx, double cut);
+
+/* Allocation-free formal solution.
+ *
+ * Some callers must not allocate device memory once they are running: a
+ * plug-in inside a host application that owns every device allocation
+ * through its own pool, a service that budgets its memory up front and may
+ * not grow, or code that must not pay the implicit device-wide
+ * synchronisation a cudaMalloc can cause.  For them this entry point does
+ * the same work as rt_formal_solution_dev (the paper has no counterpart;
+ * it only changes where the working memory comes from) without creating a
+ * context and without any cudaMalloc, cudaFree or allocating library call:
+ * its working memory (geometry tables, the per-direction-slot partial sums
+ * of J, the source bound of the transmission cutoff) lives in one
+ * statically sized device array of RT_NOALLOC_SCRATCH_BYTES bytes that the
+ * library owns.  Every GPU that loads the library holds that array until
+ * the process exits.
+ *
+ * Arguments: grid (nx, ny >= 3, nz >= 2, spacings > 0), boundary modes,
+ * ndir and HOST arrays mu, phi, w of the quadrature (same rules as
+ * rt_set_quadrature); DEVICE pointers chi[N] (> 0), S[N], B[N] (only read
+ * where a boundary mode is RT_BC_PLANCK; may be NULL otherwise) and the
+ * output J_fs[N]; `stream` is a cudaStream_t of the current device (NULL:
+ * the legacy default stream).  The work runs in FP64 on the calling
+ * thread's current device and is enqueued on `stream`; the call returns
+ * without waiting for it (only the small quadrature copy from host memory
+ * is synchronous).  Returns RT_ESCRATCH, before touching the GPU, when
+ * 64*N + 56*ndir*nz + 72*ndir bytes (plus up to 2 KiB of alignment) exceed
+ * the scratch; RT_EINVAL for invalid arguments (device data is not
+ * inspected); RT_ECUDA if a CUDA call fails.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (once per device, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents, so calls whose GPU work may overlap (several
+ * streams, several host threads) race with each other: serialise them. */
+#define RT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int rt_formal_solution_noalloc(int nx, int ny, int nz, double dx, double dy, double dz,
+                               int top_mode, int bottom_mode, int ndir, const double *mu,
+                               const double *phi, const double *w, const double *chi,
+                               const double *S, const double *B, double *J_fs, void *stream);
 
 /* Counters of this context since the last rt_reset_stats: kernel launches,
  * formal-solution march launches and their device time, Jacobi sweeps and

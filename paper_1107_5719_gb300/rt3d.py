@@ -18,12 +18,13 @@ from typing import Optional
 
 import numpy as np
 
-RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_ETIMEOUT, RT_ESTATE = range(7)
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_ETIMEOUT, RT_ESTATE, RT_ESCRATCH = range(8)
+RT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 RT_FP64, RT_FP32_SWEEP = 0, 1
 RT_BC_ZERO, RT_BC_PLANCK = 0, 1
 
 _NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV",
-          5: "RT_ETIMEOUT", 6: "RT_ESTATE"}
+          5: "RT_ETIMEOUT", 6: "RT_ESTATE", 7: "RT_ESCRATCH"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librt3d.so")
@@ -79,6 +80,9 @@ _SIGS = {
     "rt_set_profiling": (C.c_int, [VP, C.c_int]),
     "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
     "rt_reset_stats": (C.c_int, [VP]),
+    "rt_formal_solution_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                             C.c_double, C.c_int, C.c_int, C.c_int, VP, VP, VP,
+                                             VP, VP, VP, VP, VP]),
 }
 
 
@@ -288,6 +292,20 @@ def rt_get_stats(ctx) -> dict:
 
 def rt_reset_stats(ctx):
     return _check(ctx, load().rt_reset_stats(ctx))
+
+
+def rt_formal_solution_noalloc(nx, ny, nz, dx, dy, dz, top, bottom, mu, phi, w, chi, S, B, J_fs,
+                               stream=None):
+    """Allocation-free formal solution for callers that may not allocate
+    device memory while running.  mu, phi, w: host arrays; chi, S, B, J_fs:
+    CUDA tensors (or device addresses).  Returns the status code; the work
+    is enqueued on `stream` (torch stream, raw handle, or None)."""
+    mu, pm = _host(mu)
+    phi, pp = _host(phi)
+    w, pw = _host(w)
+    h = getattr(stream, "cuda_stream", stream)
+    return load().rt_formal_solution_noalloc(nx, ny, nz, dx, dy, dz, top, bottom, len(mu), pm, pp,
+                                             pw, _dev(chi), _dev(S), _dev(B), _dev(J_fs), h)
 
 
 # ---- convenience ----------------------------------------------------------
