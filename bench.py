@@ -49,6 +49,7 @@ WORKLOADS = {
     "slab17": dict(desc="17^3 slab, chi = 10^(-4+8k/16)(1+0.2(U-1/2)), eps = 1e-2, B = 1, "
                         "16x16 directions, tol 1e-8",
                    make="slab_small"),
+    "batch": dict(desc="wavelength batch (see --lambdas)", make=None),
 }
 
 
@@ -133,7 +134,116 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
-def run_ours(args):
+def timed_solves(R, p, precision, dev, stream, flush, warmup, steps, max_iter, clk_id=None,
+                 groups=0):
+    """Converged solves of problem `p` through the device API: every step
+    re-sets the opacity (Lambda* rebuilt) and J = B, then iterates to
+    convergence.  Returns per-step ms, iteration counts, profiling counters,
+    the last J (host) and the clock summary."""
+    import torch
+    chi = torch.from_numpy(p.chi).to(dev)
+    eps = torch.from_numpy(p.eps).to(dev)
+    Bt = torch.from_numpy(p.B).to(dev)
+    Jout = torch.empty_like(Bt)
+    ctx = R.rt_create(dev.index, precision)
+    try:
+        R.rt_set_stream(ctx, stream)
+        R.rt_set_grid(ctx, p.nx, p.ny, p.nz, p.dx, p.dy, p.dz)
+        R.rt_set_boundary(ctx, p.top_bc, p.bottom_bc)
+        R.rt_set_quadrature(ctx, p.mu, p.phi, p.w)
+        R.rt_set_epsilon_dev(ctx, eps)
+        if groups:
+            R.rt_set_direction_groups(ctx, groups)
+
+        def step():
+            R.rt_set_opacity_dev(ctx, chi)      # new opacity: Lambda* is rebuilt
+            R.rt_set_planck_dev(ctx, Bt)        # J = B
+            it, delta, conv = R.rt_solve_dev(ctx, Jout, tol=p.tol, max_iter=max_iter)
+            if not conv:
+                raise RuntimeError(f"solve did not converge in {it} iterations ({delta:.3e})")
+            return it
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        R.rt_reset_stats(ctx)
+        R.rt_set_profiling(ctx, True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        times, iters = [], []
+        replicas_barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(clk_id) if clk_id is not None else None
+        if clk:
+            clk.__enter__()
+        try:
+            for _ in range(steps):
+                with torch.cuda.stream(stream):
+                    flush_l2(flush)
+                stream.synchronize()
+                ev0.record(stream)
+                iters.append(step())
+                ev1.record(stream)
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1))
+        finally:
+            if clk:
+                clk.__exit__(None, None, None)
+        torch.cuda.synchronize()
+        replicas_barrier()
+        st = R.rt_get_stats(ctx)
+        return dict(times=times, iters=iters, stats=st, J=Jout.cpu().numpy(),
+                    clocks=clk.summary() if clk else None)
+    finally:
+        R.rt_destroy(ctx)
+
+
+def replicas_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def e2e_solves(R, p, precision, dev, steps, max_iter):
+    """Solves/s through the host-pointer API from pinned host buffers, with
+    the host->device copies of chi, eps, B and the device->host copy of J in
+    the timed region."""
+    import ctypes as C
+    import torch
+    chi_h = torch.from_numpy(p.chi).pin_memory()
+    eps_h = torch.from_numpy(p.eps).pin_memory()
+    B_h = torch.from_numpy(p.B).pin_memory()
+    J_h = torch.empty_like(B_h).pin_memory()
+    ctx = R.rt_create(dev.index, precision)
+    lib = R.load()
+    try:
+        R.rt_set_grid(ctx, p.nx, p.ny, p.nz, p.dx, p.dy, p.dz)
+        R.rt_set_boundary(ctx, p.top_bc, p.bottom_bc)
+        R.rt_set_quadrature(ctx, p.mu, p.phi, p.w)
+
+        def one():
+            for f, t in ((lib.rt_set_opacity, chi_h), (lib.rt_set_epsilon, eps_h),
+                         (lib.rt_set_planck, B_h)):
+                if f(ctx, t.data_ptr()) != 0:
+                    raise RuntimeError(R.rt_last_error(ctx))
+            it = C.c_int()
+            last = C.c_double()
+            if lib.rt_solve(ctx, p.tol, max_iter, 1e-12, 1000, J_h.data_ptr(), C.byref(it),
+                            C.byref(last), None, None) != 0:
+                raise RuntimeError(R.rt_last_error(ctx))
+
+        one()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        torch.cuda.synchronize()
+        return steps / (time.perf_counter() - t0)
+    finally:
+        R.rt_destroy(ctx)
+
+
+def init_ranks():
     import torch
     ws, rank, local = dist_env()
     if ws > 1:
@@ -146,115 +256,62 @@ def run_ours(args):
     B.build()
     from paper_1107_5719_gb300 import rt3d as R
     R.load()
+    return ws, rank, local, dev, R
 
+
+def run_ours(args):
+    import torch
+    from paper_1107_5719_gb300 import replicas as RP
+    ws, rank, local, dev, R = init_ranks()
+    if args.workload.startswith("batch"):
+        return run_batch(args, ws, rank, dev, R)
     p = make_problem(args.workload)
-    chi = torch.from_numpy(p.chi).to(dev)
-    eps = torch.from_numpy(p.eps).to(dev)
-    Bt = torch.from_numpy(p.B).to(dev)
-    Jout = torch.empty_like(Bt)
     stream = torch.cuda.Stream(device=dev)
-    ctx = R.rt_create(local, R.RT_FP64)
-    R.rt_set_stream(ctx, stream)
-    R.rt_set_grid(ctx, p.nx, p.ny, p.nz, p.dx, p.dy, p.dz)
-    R.rt_set_boundary(ctx, p.top_bc, p.bottom_bc)
-    R.rt_set_quadrature(ctx, p.mu, p.phi, p.w)
-    R.rt_set_epsilon_dev(ctx, eps)
     flush = torch.zeros(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MiB > L2
 
-    def step():
-        R.rt_set_opacity_dev(ctx, chi)      # new opacity: Lambda* is rebuilt
-        R.rt_set_planck_dev(ctx, Bt)        # J = B
-        it, delta, conv = R.rt_solve_dev(ctx, Jout, tol=p.tol, max_iter=args.max_iter)
-        if not conv:
-            raise RuntimeError(f"solve did not converge in {it} iterations (delta {delta:.3e})")
-        return it
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    R.rt_reset_stats(ctx)
-    R.rt_set_profiling(ctx, True)
-    times = []
-    iters = []
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(smi_id(dev)) as clk:
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush_l2(flush)
-            stream.synchronize()
-            ev0.record(stream)
-            iters.append(step())
-            ev1.record(stream)
-            ev1.synchronize()
-            times.append(ev0.elapsed_time(ev1))
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    st = R.rt_get_stats(ctx)
-    R.rt_set_profiling(ctx, False)
-    total_ms = float(sum(times))
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    r64 = timed_solves(R, p, R.RT_FP64, dev, stream, flush, args.warmup, args.steps,
+                       args.max_iter, clk_id=smi_id(dev))
+    st = r64["stats"]
+    my_ms = float(sum(r64["times"]))
+    solves_per_s, total_ms = RP.weak_throughput(args.steps, my_ms)
     ms_per_step = total_ms / args.steps
-    solves_per_s = ws * args.steps / (total_ms / 1e3)
     fs_per_solve = st["fs_launches"] / args.steps
     pairs = p.nvox * p.ndir
-    vd_per_s = ws * st["fs_launches"] * pairs / (total_ms / 1e3)
-    steps_per_s = ws * st["steps"] / (total_ms / 1e3)
+    vd_per_s = RP.sum_over_ranks(st["fs_launches"] * pairs) / (total_ms / 1e3)
+    steps_per_s = RP.sum_over_ranks(st["steps"]) / (total_ms / 1e3)
 
     # dominant kernel: the FP64 formal-solution march
     fs_ms = st["fs_ms"] / max(st["fs_launches"], 1)
     steps_per_launch = st["steps"] / max(st["fs_launches"], 1)
-    flops_launch = FLOPS_PER_STEP_FP64 * steps_per_launch
-    achieved = flops_launch / (fs_ms / 1e3) / 1e12
+    achieved = FLOPS_PER_STEP_FP64 * steps_per_launch / (fs_ms / 1e3) / 1e12
     roofline = {"kernel": "k_fs64 (formal-solution march, FP64)", "bound": "alu",
                 "achieved": round(achieved, 4), "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(achieved / PEAK_FP64_TFLOPS, 4), "traffic": None,
                 "peak_source": "recipe FP64 figure (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                "flops_per_step": FLOPS_PER_STEP_FP64, "steps_per_launch": steps_per_launch,
+                "flops_per_step": FLOPS_PER_STEP_FP64,
+                "steps_per_launch": round(steps_per_launch),
                 "ms_per_launch": round(fs_ms, 4),
-                "share_of_step": round(st["fs_ms"] / total_ms, 4)}
+                "share_of_step": round(st["fs_ms"] / my_ms, 4)}
 
-    # end to end through the host-pointer API (pinned host buffers)
+    # the FP32-sweep form of the same workload on the same GPU
+    r32 = timed_solves(R, p, R.RT_FP32_SWEEP, dev, stream, flush, 1, args.fp32_steps,
+                       args.max_iter)
+    st32 = r32["stats"]
+    ms32 = float(sum(r32["times"]))
+    fs32_ms = st32["fs_ms"] / max(st32["fs_launches"], 1)
+    fp32 = {"value": round(RP.weak_throughput(args.fp32_steps, ms32)[0], 6), "unit": "solves/s",
+            "ms_per_step": round(ms32 / args.fp32_steps, 3),
+            "iters_per_solve": st32["fs_launches"] / args.fp32_steps,
+            "march_steps_per_s": round(st32["steps"] / (ms32 / 1e3), 1),
+            "ms_per_fs_launch": round(fs32_ms, 4),
+            "fs_steps_per_s": round(st32["steps"] / (st32["fs_ms"] / 1e3), 1),
+            "max_rel_dev_from_fp64_J": float(np.max(np.abs(r32["J"] - r64["J"]) / r64["J"])),
+            "speedup_vs_fp64": round(my_ms / args.steps / (ms32 / args.fp32_steps), 3)}
+
     e2e = None
     if args.e2e_steps > 0:
-        chi_h = torch.from_numpy(p.chi).pin_memory()
-        eps_h = torch.from_numpy(p.eps).pin_memory()
-        B_h = torch.from_numpy(p.B).pin_memory()
-        J_h = torch.empty_like(B_h).pin_memory()
-        ctx2 = R.rt_create(local, R.RT_FP64)
-        R.rt_set_grid(ctx2, p.nx, p.ny, p.nz, p.dx, p.dy, p.dz)
-        R.rt_set_boundary(ctx2, p.top_bc, p.bottom_bc)
-        R.rt_set_quadrature(ctx2, p.mu, p.phi, p.w)
-        lib = R.load()
-        import ctypes as C
-
-        def e2e_step():
-            lib.rt_set_opacity(ctx2, chi_h.data_ptr())
-            lib.rt_set_epsilon(ctx2, eps_h.data_ptr())
-            lib.rt_set_planck(ctx2, B_h.data_ptr())
-            it = C.c_int()
-            last = C.c_double()
-            rc = lib.rt_solve(ctx2, p.tol, args.max_iter, 1e-12, 1000, J_h.data_ptr(),
-                              C.byref(it), C.byref(last), None, None)
-            if rc != 0:
-                raise RuntimeError(R.rt_last_error(ctx2))
-
-        e2e_step()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        R.rt_destroy(ctx2)
-        e2e = {"value": round(ws * args.e2e_steps / dt, 6), "unit": "solves/s",
+        v = e2e_solves(R, p, R.RT_FP64, dev, args.e2e_steps, args.max_iter)
+        e2e = {"value": round(RP.sum_over_ranks(v), 6), "unit": "solves/s",
                "h2d_bytes_per_step": 3 * p.nvox * 8, "d2h_bytes_per_step": p.nvox * 8,
                "steps": args.e2e_steps, "api": "rt_set_opacity/epsilon/planck + rt_solve (host)"}
 
@@ -272,14 +329,82 @@ def run_ours(args):
         "march_steps_per_s": round(steps_per_s, 1),
         "iters_per_solve": round(fs_per_solve, 3),
         "roofline": roofline,
+        "fp32_sweep": fp32,
         "gpu_launches": int(st["launches"]),
-        "clocks": clk.summary(),
+        "clocks": r64["clocks"],
         "e2e": e2e,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(p, fs_per_solve, st["jacobi_launches"] / args.steps,
                                             args.cpu_seconds)
-    R.rt_destroy(ctx)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_batch(args, ws, rank, dev, R):
+    """Wavelength batch (FP32 sweep, fused launch): converged
+    wavelength-solves/s; each rank solves its share of the wavelengths."""
+    import torch
+    from paper_1107_5719_gb300 import replicas as RP
+    from paper_1107_5719_gb300 import workloads as W
+    nl = args.lambdas
+    mine = RP.shard([1] * nl, ws, rank)
+    probs_all = W.batch_65(n_lambda=nl)
+    probs = [probs_all[i] for i in mine]
+    b = R.rt_batch_create(probs, device=dev.index, precision=R.RT_FP32_SWEEP)
+    stream = torch.cuda.Stream(device=dev)
+    R.rt_batch_set_stream(b, stream)
+    flush = torch.zeros(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    try:
+        def step():
+            R.rt_batch_reset(b, rebuild_lstar=True)
+            r = R.rt_batch_solve(b, len(probs), tol=1e-8, max_iter=args.max_iter)
+            if not r["converged"]:
+                raise RuntimeError("batch did not converge")
+            return r
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        R.rt_batch_reset_stats(b)
+        R.rt_batch_set_profiling(b, True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        times = []
+        replicas_barrier()
+        with ClockSampler(smi_id(dev)) as clk:
+            for _ in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush_l2(flush)
+                stream.synchronize()
+                ev0.record(stream)
+                r = step()
+                ev1.record(stream)
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1))
+        replicas_barrier()
+        st = R.rt_batch_get_stats(b)
+    finally:
+        R.rt_batch_destroy(b)
+    my_ms = float(sum(times))
+    value, total_ms = RP.weak_throughput(args.steps * len(probs), my_ms)
+    fs_ms = st["fs_ms"] / max(st["fs_launches"], 1)
+    line = {"metric": "converged J solves/s (wavelength points)", "value": round(value, 6),
+            "unit": "solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 march / f64 J, Lambda*, OS",
+            "data": "synthetic",
+            "config": {"workload": f"batch: {nl} wavelengths x 65^3 slab, chi x 10^(-2+4U), "
+                                   "eps 10^(-5+5U), 32x32 directions, tol 1e-8",
+                       "precision": "FP32 sweep", "parallelism": f"wavelength shards x{ws}",
+                       "l2": "flushed between steps (512 MiB write)",
+                       "lstar": "rebuilt every step"},
+            "march_steps_per_s": round(RP.sum_over_ranks(st["steps"]) / (total_ms / 1e3), 1),
+            "fused_fs_ms_per_launch": round(fs_ms, 3),
+            "fused_fs_steps_per_s": round(st["steps"] / (st["fs_ms"] / 1e3), 1) if st["fs_ms"] else None,
+            "iters_max": int(np.max(r["iters"])), "iters_mean": float(np.mean(r["iters"])),
+            "gpu_launches": int(st["launches"]), "clocks": clk.summary(), "e2e": None}
     if ws > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -359,6 +484,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="slab65")
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--lambdas", type=int, default=512, help="wavelengths of the batch workload")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=float, default=60.0,

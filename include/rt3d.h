@@ -183,6 +183,15 @@ int rt_set_direction_groups(rt_ctx *ctx, int groups);
  * 1e-9 (FP32 sweep). */
 int rt_set_cutoff(rt_ctx *ctx, double cut);
 
+/* Diagnostic: evaluate, on the current device, the segment weights the
+ * march uses for n optical depths x[n] (device pointers): w_cur (weight of
+ * the downstream node), w_up (upstream node) and e = exp(-x) of the linear-
+ * in-tau source integral over one segment, in the arithmetic of `precision`
+ * (RT_FP64 or RT_FP32_SWEEP; FP32 results are widened to double).  Enqueued
+ * on `stream`. */
+int rt_segment_weights(int precision, long long n, const double *x, double *w_cur,
+                       double *w_up, double *e, void *stream);
+
 /* Allocation-free formal solution.
  *
  * Some callers must not allocate device memory once they are running: a
@@ -223,6 +232,53 @@ int rt_formal_solution_noalloc(int nx, int ny, int nz, double dx, double dy, dou
                                const double *phi, const double *w, const double *chi,
                                const double *S, const double *B, double *J_fs, void *stream);
 
+/* ---- Batched wavelengths ------------------------------------------------
+ *
+ * Many monochromatic problems (wavelength points), each its own 3DRT
+ * problem with its own grid, chi, eps and B, share one quadrature and
+ * boundary modes and are solved together: every outer iteration runs the
+ * formal solutions of all unconverged problems in ONE launch (RT_FP32_SWEEP;
+ * RT_FP64 launches per problem), then their Jacobi sweeps, then their
+ * convergence tests; a problem leaves the iteration when its own delta
+ * drops below tol.  The paper solves one wavelength at a time on the GPU
+ * (Sect. 2); this is the batched form of the same per-wavelength solve, and
+ * each problem's iterates are the ones rt_solve would produce for it. */
+typedef struct {
+    int nx, ny, nz;             /* grid of this problem (same rules as rt_set_grid) */
+    double dx, dy, dz;
+    const double *chi;          /* host [nz][ny][nx], > 0 */
+    const double *eps;          /* host, in (0, 1] */
+    const double *B;            /* host */
+} rt_problem;
+
+typedef struct rt_batch rt_batch;
+
+/* Create a batch of nprob problems on `device` (precision RT_FP32_SWEEP or
+ * RT_FP64), copying every problem's fields to the device and building its
+ * tables.  *batch receives a handle whenever the arguments are usable, also
+ * when creation then fails (read rt_batch_last_error, then destroy it). */
+int rt_batch_create(rt_batch **batch, int device, int precision, int nprob,
+                    const rt_problem *probs, int top_mode, int bottom_mode, int ndir,
+                    const double *mu, const double *phi, const double *w);
+int rt_batch_destroy(rt_batch *batch);
+const char *rt_batch_last_error(const rt_batch *batch);
+/* Run all work on `stream` (NULL: the batch's own stream). */
+int rt_batch_set_stream(rt_batch *batch, void *stream);
+/* Restart every problem from J = B; rebuild_lstar != 0 also rebuilds
+ * Lambda* (and the OS coefficients) at the next iteration. */
+int rt_batch_reset(rt_batch *batch, int rebuild_lstar);
+/* Iterate until every problem has delta < tol or max_iter iterations.
+ * iters[nprob], deltas[nprob] (host, may be NULL) receive each problem's
+ * iteration count and last delta; *n_converged the number converged.
+ * Returns RT_ENOTCONV if some problem did not converge (outputs valid). */
+int rt_batch_solve(rt_batch *batch, double tol, int max_iter, double tol_inner, int max_sweeps,
+                   int *iters, double *deltas, int *n_converged);
+/* J of problem p into host (get_J) or device (get_J_dev) memory. */
+int rt_batch_get_J(rt_batch *batch, int p, double *J);
+int rt_batch_get_J_dev(rt_batch *batch, int p, double *J);
+/* As rt_set_direction_groups, for the fused launch (0 = auto). */
+int rt_batch_set_direction_groups(rt_batch *batch, int groups);
+
 /* Counters of this context since the last rt_reset_stats: kernel launches,
  * formal-solution march launches and their device time, Jacobi sweeps and
  * their device time, march steps executed.  Device times are measured with
@@ -242,6 +298,10 @@ typedef struct {
 int rt_set_profiling(rt_ctx *ctx, int on);
 int rt_get_stats(rt_ctx *ctx, rt_stats *out);
 int rt_reset_stats(rt_ctx *ctx);
+/* The same counters for a batch (fs_ms: device time of the fused launches). */
+int rt_batch_set_profiling(rt_batch *batch, int on);
+int rt_batch_get_stats(rt_batch *batch, rt_stats *out);
+int rt_batch_reset_stats(rt_batch *batch);
 
 #ifdef __cplusplus
 }

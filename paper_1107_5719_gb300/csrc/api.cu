@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 using namespace rt3d;
@@ -24,7 +25,7 @@ struct rt_ctx {
     Geometry g{};
     double dx = 1, dy = 1, dz = 1;
     bool have_grid = false, have_quad = false, have_chi = false, have_eps = false, have_B = false;
-    bool lstar_valid = false, coef_valid = false, chi32_valid = false;
+    bool lstar_valid = false, coef_valid = false, b2_valid = false;
     int groups_req = 0;
     double cut = -1.0;
 
@@ -33,8 +34,12 @@ struct rt_ctx {
     double *Jfs = nullptr, *Jn = nullptr, *Ja = nullptr, *Jb = nullptr, *r = nullptr;
     double *lstar = nullptr, *coef = nullptr, *rdiag = nullptr, *partial = nullptr;
     int partial_groups = 0;
-    // FP32 copies for the sweep form
-    float *chi32 = nullptr, *S32 = nullptr, *B32 = nullptr;
+    // FP32-sweep form: padded {chi, S_hi, S_lo} nodes, padded boundary B pairs,
+    // padded step offsets; sum of the quadrature weights
+    float4* node4 = nullptr;
+    float2* b2 = nullptr;
+    int* poff = nullptr;
+    double wsum = 1.0;
     // direction tables
     DirInfo* info = nullptr;
     StepGeo* off = nullptr;
@@ -46,6 +51,10 @@ struct rt_ctx {
     unsigned long long* d_steps = nullptr;
     double* h_scal = nullptr;               // pinned
     unsigned long long* h_steps = nullptr;  // pinned
+    // per-sweep deltas of one Jacobi solve (device) and a pinned copy
+    double* dlt = nullptr;
+    double* h_dlt = nullptr;
+    int dlt_cap = 0;
     unsigned long long last_steps = 0;
 
     // profiling
@@ -100,13 +109,13 @@ void free_grid_buffers(rt_ctx* c)
     dfree(c->chi); dfree(c->eps); dfree(c->B); dfree(c->J); dfree(c->S);
     dfree(c->Jfs); dfree(c->Jn); dfree(c->Ja); dfree(c->Jb); dfree(c->r);
     dfree(c->lstar); dfree(c->coef); dfree(c->rdiag); dfree(c->partial);
-    dfree(c->chi32); dfree(c->S32); dfree(c->B32);
+    dfree(c->node4); dfree(c->b2);
     c->partial_groups = 0;
 }
 
 void free_tables(rt_ctx* c)
 {
-    dfree(c->info); dfree(c->off); dfree(c->bw); dfree(c->bw32);
+    dfree(c->info); dfree(c->off); dfree(c->bw); dfree(c->bw32); dfree(c->poff);
     dfree(c->d_mu); dfree(c->d_phi); dfree(c->d_w);
 }
 
@@ -133,7 +142,9 @@ int enter(rt_ctx* c)
 
 double default_cut(int precision)
 {
-    return precision == RT_FP64 ? 1e-17 : 1e-9;
+    // FP32 sweep: the cut is relative to S at the voxel (see fs32.cu); 2^-46
+    // keeps the truncation far below what 1/eps can amplify at eps = 1e-6.
+    return precision == RT_FP64 ? 1e-17 : 1.4210854715202004e-14;
 }
 
 // Number of z-blocks that walk the kSlots direction slots: enough blocks to
@@ -199,37 +210,45 @@ int set_field(rt_ctx* c, const double* src, double* dst, bool device, const char
     return RT_OK;
 }
 
-// Formal solution: source in c->S (already set), result J into Jout (device).
-int run_fs(rt_ctx* c, double* Jout, bool count_steps)
+View32 view32(rt_ctx* c)
 {
-    const bool bnd = c->g.top_bc || c->g.bottom_bc;
-    const int G = auto_groups(c);
+    View32 v;
+    v.g = c->g;
+    v.node = c->node4;
+    v.b2 = c->b2;
+    v.info = c->info;
+    v.off = c->off;
+    v.poff = c->poff;
+    v.bw = c->bw32;
+    v.smax = c->scal + 0;
+    v.partial = c->partial;
+    return v;
+}
+
+// Formal solution: source in c->S (already set), result J into Jout (device).
+// Pieces of one formal solution: per-problem preparation, the march itself,
+// and the reduction over direction slots plus (once per opacity) Lambda*.
+int fs_prepare(rt_ctx* c)
+{
     int rc = ensure_partial(c);
     if (rc) return rc;
-    if (count_steps) CK(cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned long long), c->stream));
-    const double cut = c->cut >= 0 ? c->cut : default_cut(c->precision);
-    if (c->profiling) CK(cudaEventRecord(c->ev[0], c->stream));
-    if (c->precision == RT_FP64) {
-        CK(launch_fs64(c->g, c->chi, c->S, c->B, c->info, c->off, c->bw, c->scal + 0, cut, G,
-                       c->partial, count_steps ? c->d_steps : nullptr, c->stream));
-    } else {
-        if (!c->chi32_valid) {
-            CK(launch_to_float(c->g.N, c->chi, c->chi32, c->stream));
-            CK(launch_to_float(c->g.N, c->B, c->B32, c->stream));
-            c->chi32_valid = true;
-            c->stats.launches += 2;
-        }
-        CK(launch_fs32(c->g, c->chi32, c->S32, c->B32, c->info, c->off, c->bw32, c->scal + 0, cut,
-                       G, c->partial, count_steps ? c->d_steps : nullptr, c->stream));
+    if (c->precision != RT_FP64 && !c->b2_valid) {
+        CK(launch_pack_b2(c->g, c->B, c->b2, c->stream));
+        c->b2_valid = true;
+        c->stats.launches += 1;
     }
-    if (c->profiling) {
-        CK(cudaEventRecord(c->ev[1], c->stream));
-        c->fs_pending = true;
-    }
-    c->stats.fs_launches += 1;
-    c->stats.launches += 2;
-    (void)bnd;
-    CK(launch_sum_groups(c->g.N, c->partial, Jout, c->stream));
+    return RT_OK;
+}
+
+double cut_of(const rt_ctx* c) { return c->cut >= 0 ? c->cut : default_cut(c->precision); }
+
+int fs_finish(rt_ctx* c, double* Jout)
+{
+    if (c->precision == RT_FP64)
+        CK(launch_sum_groups(c->g.N, c->partial, Jout, c->stream));
+    else
+        CK(launch_sum_groups_src(c->g.N, c->partial, c->S, c->wsum, Jout, c->stream));
+    c->stats.launches += 1;
     if (!c->lstar_valid) {
         CK(launch_lstar64(c->g, c->chi, c->info, c->off, c->bw, c->lstar, c->stream));
         c->lstar_valid = true;
@@ -237,6 +256,30 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
         c->stats.launches += 1;
         c->stats.lstar_launches += 1;
     }
+    return RT_OK;
+}
+
+int run_fs(rt_ctx* c, double* Jout, bool count_steps)
+{
+    const int G = auto_groups(c);
+    int rc = fs_prepare(c);
+    if (rc) return rc;
+    if (count_steps) CK(cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned long long), c->stream));
+    const double cut = cut_of(c);
+    if (c->profiling) CK(cudaEventRecord(c->ev[0], c->stream));
+    if (c->precision == RT_FP64) {
+        CK(launch_fs64(c->g, c->chi, c->S, c->B, c->info, c->off, c->bw, c->scal + 0, cut, G,
+                       c->partial, count_steps ? c->d_steps : nullptr, c->stream));
+    } else {
+        CK(launch_fs32d(view32(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
+    }
+    if (c->profiling) {
+        CK(cudaEventRecord(c->ev[1], c->stream));
+        c->fs_pending = true;
+    }
+    c->stats.fs_launches += 1;
+    c->stats.launches += 1;
+    if ((rc = fs_finish(c, Jout))) return rc;
     if (count_steps) {
         CK(cudaMemcpyAsync(c->h_steps, c->d_steps, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, c->stream));
@@ -248,16 +291,19 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
 int prepare_source(rt_ctx* c, const double* S_in, bool device)
 {
     const bool bnd = c->g.top_bc || c->g.bottom_bc;
-    float* s32 = c->precision == RT_FP64 ? nullptr : c->S32;
     CK(cudaMemsetAsync(c->scal + 0, 0, sizeof(double), c->stream));
     if (S_in) {
         CK(cudaMemcpyAsync(c->S, S_in, sizeof(double) * c->g.N, kind(device), c->stream));
-        CK(launch_absmax(c->g.N, c->S, bnd ? c->B : nullptr, c->scal + 0, s32, c->stream));
+        CK(launch_absmax(c->g.N, c->S, bnd ? c->B : nullptr, c->scal + 0, nullptr, c->stream));
     } else {
-        CK(launch_source(c->g.N, c->eps, c->B, c->J, c->S, s32, bnd ? c->B : nullptr, c->scal + 0,
-                         c->stream));
+        CK(launch_source(c->g.N, c->eps, c->B, c->J, c->S, nullptr, bnd ? c->B : nullptr,
+                         c->scal + 0, c->stream));
     }
     c->stats.launches += 1;
+    if (c->precision != RT_FP64) {
+        CK(launch_pack32(c->g, c->chi, c->S, c->node4, c->stream));
+        c->stats.launches += 1;
+    }
     return RT_OK;
 }
 
@@ -289,38 +335,64 @@ int ensure_coef(rt_ctx* c)
     return RT_OK;
 }
 
-// Jacobi solve from J_old (device) into J_new (device); J_fs device.
+int ensure_dlt(rt_ctx* c, int max_sweeps)
+{
+    if (c->dlt_cap >= max_sweeps) return RT_OK;
+    int cap = max_sweeps < 1024 ? 1024 : max_sweeps;
+    CK(dalloc(c->dlt, (size_t)cap));
+    if (c->h_dlt) cudaFreeHost(c->h_dlt);
+    c->h_dlt = nullptr;
+    CK(cudaMallocHost((void**)&c->h_dlt, sizeof(double) * cap));
+    c->dlt_cap = cap;
+    return RT_OK;
+}
+
+// Jacobi solve from J_old (device) into J_new (device); J_fs device.  Sweeps
+// are enqueued in growing chunks; a sweep that follows a converged one is a
+// no-op on the device, so checking once per chunk gives exactly the sweeps
+// of a check after every sweep.
 int run_os(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, double tol_inner,
            int max_sweeps, int* sweeps_out)
 {
     int rc = ensure_coef(c);
     if (rc) return rc;
+    if ((rc = ensure_dlt(c, max_sweeps))) return rc;
     CK(launch_os_rhs(c->g, c->coef, c->rdiag, Jfs, Jold, c->r, c->stream));
     c->stats.launches += 1;
-    const double* cur = Jold;
+    CK(cudaMemsetAsync(c->dlt, 0, sizeof(double) * max_sweeps, c->stream));
     double* bufs[2] = {c->Ja, c->Jb};
-    int n = 0;
-    for (; n < max_sweeps;) {
-        double* nxt = bufs[n & 1];
-        CK(cudaMemsetAsync(c->scal + 1, 0, sizeof(double), c->stream));
+    int launched = 0, done = -1, chunk = 2;
+    while (launched < max_sweeps && done < 0) {
+        const int n0 = launched;
+        const int n1 = launched + chunk < max_sweeps ? launched + chunk : max_sweeps;
         if (c->profiling) CK(cudaEventRecord(c->ev[2], c->stream));
-        CK(launch_jacobi(c->g, c->coef, c->r, cur, nxt, c->scal + 1, c->stream));
+        for (int n = n0; n < n1; ++n) {
+            const double* cur = n == 0 ? Jold : bufs[(n - 1) & 1];
+            CK(launch_jacobi(c->g, c->coef, c->r, cur, bufs[n & 1], c->dlt, n, tol_inner,
+                             c->stream));
+        }
         if (c->profiling) {
             CK(cudaEventRecord(c->ev[3], c->stream));
             c->jac_pending = true;
         }
-        c->stats.launches += 1;
-        c->stats.jacobi_launches += 1;
-        CK(cudaMemcpyAsync(c->h_scal + 1, c->scal + 1, sizeof(double), cudaMemcpyDeviceToHost,
-                           c->stream));
+        c->stats.launches += n1 - n0;
+        c->stats.jacobi_launches += n1 - n0;
+        CK(cudaMemcpyAsync(c->h_dlt + n0, c->dlt + n0, sizeof(double) * (n1 - n0),
+                           cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         harvest(c);
-        cur = nxt;
-        ++n;
-        if (*(c->h_scal + 1) < tol_inner) break;
+        for (int n = n0; n < n1; ++n)
+            if (c->h_dlt[n] < tol_inner) {
+                done = n;
+                break;
+            }
+        launched = n1;
+        if (chunk < 32) chunk *= 2;
     }
-    CK(cudaMemcpyAsync(Jnew, cur, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
-    if (sweeps_out) *sweeps_out = n;
+    const int sweeps = done >= 0 ? done + 1 : max_sweeps;
+    CK(cudaMemcpyAsync(Jnew, bufs[(sweeps - 1) & 1], sizeof(double) * c->g.N,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    if (sweeps_out) *sweeps_out = sweeps;
     return RT_OK;
 }
 
@@ -401,6 +473,189 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
     return RT_OK;
 }
 
+// ---- batched wavelengths ----------------------------------------------------
+
+}  // namespace
+
+struct rt_batch {
+    int device = 0;
+    int precision = RT_FP32_SWEEP;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::vector<rt_ctx*> ctx;       // one per wavelength, all on `stream`
+    std::vector<int> order;         // problems by decreasing size (fused launch order)
+    std::vector<int> iters;         // outer iterations done since the last reset
+    std::vector<double> delta;      // last outer delta
+    std::vector<char> converged;
+    View32* d_views = nullptr;      // device copies of the per-problem FP32 views
+    int* d_ids = nullptr;
+    long long* d_prefix = nullptr;
+    int* h_ids = nullptr;           // pinned
+    long long* h_prefix = nullptr;  // pinned
+    double* d_delta = nullptr;      // outer deltas [nprob]
+    double* h_delta = nullptr;      // pinned
+    unsigned long long* d_steps = nullptr;
+    unsigned long long* h_steps = nullptr;
+    int groups_req = 0;
+    bool profiling = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    rt_stats stats{};
+    std::string err;
+};
+
+namespace {
+
+int bfail(rt_batch* b, int code, const char* fmt, ...)
+{
+    if (b) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        b->err = buf;
+    }
+    return code;
+}
+
+#define BCK(call)                                                                       \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA,     \
+                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// Propagate a per-problem failure with the problem's message.
+int bpass(rt_batch* b, int p, int rc)
+{
+    if (rc == RT_OK) return RT_OK;
+    return bfail(b, rc, "problem %d: %s", p, b->ctx[p]->err.c_str());
+}
+
+int batch_groups(const rt_batch* b, const std::vector<int>& act)
+{
+    if (b->groups_req > 0) return b->groups_req < kSlots ? b->groups_req : kSlots;
+    long long blocks = 0;
+    for (int p : act) blocks += fs32_blocks(b->ctx[p]->g, 1);
+    int G = 1;
+    while (G < kSlots && blocks * G < 64LL * (b->num_sms > 0 ? b->num_sms : 152)) G *= 2;
+    return G;
+}
+
+void bharvest(rt_batch* b)
+{
+    float ms = 0.f;
+    if (b->profiling && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess)
+        b->stats.fs_ms += ms;
+}
+
+// Formal solutions of the active problems: FP32 sweep in one fused launch,
+// FP64 one launch per problem.
+int batch_fs(rt_batch* b, const std::vector<int>& act)
+{
+    int rc;
+    for (int p : act) {
+        rt_ctx* c = b->ctx[p];
+        if ((rc = bpass(b, p, prepare_source(c, nullptr, true)))) return rc;
+        if ((rc = bpass(b, p, fs_prepare(c)))) return rc;
+    }
+    const int G = batch_groups(b, act);
+    BCK(cudaMemsetAsync(b->d_steps, 0, sizeof(unsigned long long), b->stream));
+    if (b->profiling) BCK(cudaEventRecord(b->ev[0], b->stream));
+    if (b->precision == RT_FP32_SWEEP) {
+        long long total = 0;
+        int q = 0;
+        for (int p : b->order) {
+            if (b->converged[p]) continue;
+            b->h_ids[q] = p;
+            b->h_prefix[q] = total;
+            total += fs32_blocks(b->ctx[p]->g, G);
+            ++q;
+        }
+        b->h_prefix[q] = total;
+        BCK(cudaMemcpyAsync(b->d_ids, b->h_ids, sizeof(int) * q, cudaMemcpyHostToDevice, b->stream));
+        BCK(cudaMemcpyAsync(b->d_prefix, b->h_prefix, sizeof(long long) * (q + 1),
+                            cudaMemcpyHostToDevice, b->stream));
+        BCK(launch_fs32_batch(b->d_views, b->d_ids, b->d_prefix, q, total, G,
+                              cut_of(b->ctx[0]), b->d_steps, b->stream));
+        b->stats.fs_launches += 1;
+        b->stats.launches += 1;
+    } else {
+        for (int p : act) {
+            rt_ctx* c = b->ctx[p];
+            BCK(launch_fs64(c->g, c->chi, c->S, c->B, c->info, c->off, c->bw, c->scal + 0,
+                            cut_of(c), G, c->partial, b->d_steps, b->stream));
+            b->stats.fs_launches += 1;
+            b->stats.launches += 1;
+        }
+    }
+    if (b->profiling) BCK(cudaEventRecord(b->ev[1], b->stream));
+    for (int p : act)
+        if ((rc = bpass(b, p, fs_finish(b->ctx[p], b->ctx[p]->Jfs)))) return rc;
+    BCK(cudaMemcpyAsync(b->h_steps, b->d_steps, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        b->stream));
+    return RT_OK;
+}
+
+// Operator-splitting solves of the active problems; sweeps are enqueued in
+// chunks for every problem still iterating and checked with one host sync
+// per chunk (a sweep after a converged one is a device-side no-op).
+int batch_os(rt_batch* b, const std::vector<int>& act, double tol_inner, int max_sweeps)
+{
+    int rc;
+    std::vector<int> inner;
+    for (int p : act) {
+        rt_ctx* c = b->ctx[p];
+        if ((rc = bpass(b, p, ensure_coef(c)))) return rc;
+        if ((rc = bpass(b, p, ensure_dlt(c, max_sweeps)))) return rc;
+        BCK(launch_os_rhs(c->g, c->coef, c->rdiag, c->Jfs, c->J, c->r, b->stream));
+        BCK(cudaMemsetAsync(c->dlt, 0, sizeof(double) * max_sweeps, b->stream));
+        b->stats.launches += 1;
+        inner.push_back(p);
+    }
+    std::vector<int> sweeps(b->ctx.size(), max_sweeps);
+    int launched = 0, chunk = 2;
+    while (!inner.empty() && launched < max_sweeps) {
+        const int n0 = launched;
+        const int n1 = launched + chunk < max_sweeps ? launched + chunk : max_sweeps;
+        for (int p : inner) {
+            rt_ctx* c = b->ctx[p];
+            for (int n = n0; n < n1; ++n) {
+                const double* cur = n == 0 ? c->J : (n & 1 ? c->Ja : c->Jb);
+                double* nxt = n & 1 ? c->Jb : c->Ja;
+                BCK(launch_jacobi(c->g, c->coef, c->r, cur, nxt, c->dlt, n, tol_inner, b->stream));
+            }
+            BCK(cudaMemcpyAsync(c->h_dlt + n0, c->dlt + n0, sizeof(double) * (n1 - n0),
+                                cudaMemcpyDeviceToHost, b->stream));
+            b->stats.launches += n1 - n0;
+            b->stats.jacobi_launches += n1 - n0;
+        }
+        BCK(cudaStreamSynchronize(b->stream));
+        std::vector<int> still;
+        for (int p : inner) {
+            rt_ctx* c = b->ctx[p];
+            int done = -1;
+            for (int n = n0; n < n1; ++n)
+                if (c->h_dlt[n] < tol_inner) {
+                    done = n;
+                    break;
+                }
+            if (done >= 0) sweeps[p] = done + 1; else still.push_back(p);
+        }
+        inner.swap(still);
+        launched = n1;
+        if (chunk < 32) chunk *= 2;
+    }
+    for (int p : act) {
+        rt_ctx* c = b->ctx[p];
+        BCK(cudaMemcpyAsync(c->Jn, (sweeps[p] - 1) & 1 ? c->Jb : c->Ja, sizeof(double) * c->g.N,
+                            cudaMemcpyDeviceToDevice, b->stream));
+    }
+    return RT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -448,6 +703,8 @@ int rt_destroy(rt_ctx* c)
     dfree(c->d_steps);
     if (c->h_scal) cudaFreeHost(c->h_scal);
     if (c->h_steps) cudaFreeHost(c->h_steps);
+    if (c->h_dlt) cudaFreeHost(c->h_dlt);
+    dfree(c->dlt);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -477,11 +734,13 @@ int rt_set_grid(rt_ctx* c, int nx, int ny, int nz, double dx, double dy, double 
         return fail(c, RT_EINVAL, "spacings must be finite and > 0");
     if ((long long)nx * ny > (1LL << 30) || (long long)nx * ny * nz > (1LL << 40))
         return fail(c, RT_EINVAL, "grid too large");
+    if (c->precision != RT_FP64 && 4LL * nx * ny * nz >= (1LL << 31))
+        return fail(c, RT_EINVAL, "grid too large for the FP32-sweep form (4*nx*ny*nz >= 2^31)");
     CK(cudaStreamSynchronize(c->stream));
     free_grid_buffers(c);
     free_tables(c);
     c->have_grid = c->have_quad = c->have_chi = c->have_eps = c->have_B = false;
-    c->lstar_valid = c->coef_valid = c->chi32_valid = false;
+    c->lstar_valid = c->coef_valid = c->b2_valid = false;
     c->g.nx = nx; c->g.ny = ny; c->g.nz = nz;
     c->g.N = (long long)nx * ny * nz;
     c->g.ndir = 0;
@@ -492,7 +751,8 @@ int rt_set_grid(rt_ctx* c, int nx, int ny, int nz, double dx, double dy, double 
     CK(dalloc(c->Jb, N)); CK(dalloc(c->r, N)); CK(dalloc(c->rdiag, N));
     CK(dalloc(c->lstar, 27 * N)); CK(dalloc(c->coef, 27 * N));
     if (c->precision != RT_FP64) {
-        CK(dalloc(c->chi32, N)); CK(dalloc(c->S32, N)); CK(dalloc(c->B32, N));
+        CK(dalloc(c->node4, 4 * N));
+        CK(dalloc(c->b2, (size_t)8 * nx * ny));
     }
     c->have_grid = true;
     return RT_OK;
@@ -539,6 +799,12 @@ int rt_set_quadrature(rt_ctx* c, int ndir, const double* mu, const double* phi, 
     CK(launch_dir_tables(c->g, c->dx, c->dy, c->dz, c->d_mu, c->d_phi, c->d_w, c->info, c->off,
                          c->bw, c->bw32, c->stream));
     c->stats.launches += 1;
+    if (c->precision != RT_FP64) {
+        CK(dalloc(c->poff, T));
+        CK(launch_pad_offsets(c->g, c->info, c->off, c->poff, c->stream));
+        c->stats.launches += 1;
+    }
+    c->wsum = sw;
     CK(cudaStreamSynchronize(c->stream));
     c->have_quad = true;
     c->lstar_valid = c->coef_valid = false;
@@ -550,7 +816,7 @@ static int set_chi(rt_ctx* c, const double* chi, bool device)
     int rc = set_field(c, chi, c ? c->chi : nullptr, device, "chi", true, false);
     if (rc) return rc;
     c->have_chi = true;
-    c->lstar_valid = c->coef_valid = c->chi32_valid = false;
+    c->lstar_valid = c->coef_valid = false;
     return RT_OK;
 }
 
@@ -569,7 +835,7 @@ static int set_B(rt_ctx* c, const double* B, bool device)
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->J, c->B, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
     c->have_B = true;
-    c->chi32_valid = false;
+    c->b2_valid = false;
     return RT_OK;
 }
 
@@ -662,6 +928,18 @@ int rt_set_cutoff(rt_ctx* c, double cut)
     return RT_OK;
 }
 
+int rt_segment_weights(int precision, long long n, const double* x, double* w_cur, double* w_up,
+                       double* e, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !w_cur || !w_up || !e))) return RT_EINVAL;
+    if (precision != RT_FP64 && precision != RT_FP32_SWEEP) return RT_EINVAL;
+    if (n == 0) return RT_OK;
+    if (launch_seg_eval(n, precision == RT_FP32_SWEEP, x, w_cur, w_up, e, (cudaStream_t)stream) !=
+        cudaSuccess)
+        return RT_ECUDA;
+    return RT_OK;
+}
+
 int rt_set_profiling(rt_ctx* c, int on)
 {
     if (!c) return RT_EINVAL;
@@ -680,6 +958,221 @@ int rt_reset_stats(rt_ctx* c)
 {
     if (!c) return RT_EINVAL;
     c->stats = rt_stats{};
+    return RT_OK;
+}
+
+// ---- batched wavelengths (C ABI) --------------------------------------------
+
+int rt_batch_create(rt_batch** out, int device, int precision, int nprob, const rt_problem* probs,
+                    int top_mode, int bottom_mode, int ndir, const double* mu, const double* phi,
+                    const double* w)
+{
+    if (!out) return RT_EINVAL;
+    *out = nullptr;
+    if (nprob < 1 || !probs || (precision != RT_FP64 && precision != RT_FP32_SWEEP)) return RT_EINVAL;
+    rt_batch* b = new rt_batch();
+    b->device = device;
+    b->precision = precision;
+    *out = b;  // also on failure, for rt_batch_last_error; the caller destroys it
+    int rc = RT_OK;
+    auto bail = [&](int code) { return code; };
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return bail(bfail(b, RT_ECUDA, "device %d unavailable", device));
+    b->stream = b->own_stream;
+    for (int e = 0; e < 4; ++e) BCK(cudaEventCreate(&b->ev[e]));
+    b->ctx.assign(nprob, nullptr);
+    for (int p = 0; p < nprob; ++p) {
+        const rt_problem& q = probs[p];
+        rt_ctx* c = nullptr;
+        if ((rc = rt_create(&c, device, precision))) return bail(bfail(b, rc, "problem %d: context", p));
+        b->ctx[p] = c;
+        if ((rc = rt_set_stream(c, b->stream)) || (rc = rt_set_grid(c, q.nx, q.ny, q.nz, q.dx, q.dy, q.dz)) ||
+            (rc = rt_set_boundary(c, top_mode, bottom_mode)) ||
+            (rc = rt_set_quadrature(c, ndir, mu, phi, w)) || (rc = rt_set_opacity(c, q.chi)) ||
+            (rc = rt_set_epsilon(c, q.eps)) || (rc = rt_set_planck(c, q.B)) ||
+            (rc = ensure_partial(c)))
+            return bail(bpass(b, p, rc));
+    }
+    b->order.resize(nprob);
+    for (int p = 0; p < nprob; ++p) b->order[p] = p;
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](int x, int y) { return b->ctx[x]->g.N > b->ctx[y]->g.N; });
+    b->iters.assign(nprob, 0);
+    b->delta.assign(nprob, 0.0);
+    b->converged.assign(nprob, 0);
+    std::vector<View32> views(nprob);
+    for (int p = 0; p < nprob; ++p) views[p] = view32(b->ctx[p]);
+    BCK(cudaMalloc((void**)&b->d_views, sizeof(View32) * nprob));
+    BCK(cudaMemcpy(b->d_views, views.data(), sizeof(View32) * nprob, cudaMemcpyHostToDevice));
+    BCK(cudaMalloc((void**)&b->d_ids, sizeof(int) * nprob));
+    BCK(cudaMalloc((void**)&b->d_prefix, sizeof(long long) * (nprob + 1)));
+    BCK(cudaMalloc((void**)&b->d_delta, sizeof(double) * nprob));
+    BCK(cudaMalloc((void**)&b->d_steps, sizeof(unsigned long long)));
+    BCK(cudaMallocHost((void**)&b->h_ids, sizeof(int) * nprob));
+    BCK(cudaMallocHost((void**)&b->h_prefix, sizeof(long long) * (nprob + 1)));
+    BCK(cudaMallocHost((void**)&b->h_delta, sizeof(double) * nprob));
+    BCK(cudaMallocHost((void**)&b->h_steps, sizeof(unsigned long long)));
+    *out = b;
+    return RT_OK;
+}
+
+int rt_batch_destroy(rt_batch* b)
+{
+    if (!b) return RT_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (rt_ctx* c : b->ctx) rt_destroy(c);
+    if (b->d_views) cudaFree(b->d_views);
+    if (b->d_ids) cudaFree(b->d_ids);
+    if (b->d_prefix) cudaFree(b->d_prefix);
+    if (b->d_delta) cudaFree(b->d_delta);
+    if (b->d_steps) cudaFree(b->d_steps);
+    if (b->h_ids) cudaFreeHost(b->h_ids);
+    if (b->h_prefix) cudaFreeHost(b->h_prefix);
+    if (b->h_delta) cudaFreeHost(b->h_delta);
+    if (b->h_steps) cudaFreeHost(b->h_steps);
+    for (auto& e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->own_stream) cudaStreamDestroy(b->own_stream);
+    delete b;
+    return RT_OK;
+}
+
+const char* rt_batch_last_error(const rt_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int rt_batch_set_stream(rt_batch* b, void* stream)
+{
+    if (!b) return RT_EINVAL;
+    b->err.clear();
+    BCK(cudaSetDevice(b->device));
+    BCK(cudaStreamSynchronize(b->stream));
+    b->stream = stream ? (cudaStream_t)stream : b->own_stream;
+    for (size_t p = 0; p < b->ctx.size(); ++p) {
+        int rc = rt_set_stream(b->ctx[p], b->stream);
+        if (rc) return bpass(b, (int)p, rc);
+    }
+    return RT_OK;
+}
+
+int rt_batch_reset(rt_batch* b, int rebuild_lstar)
+{
+    if (!b) return RT_EINVAL;
+    b->err.clear();
+    BCK(cudaSetDevice(b->device));
+    for (size_t p = 0; p < b->ctx.size(); ++p) {
+        rt_ctx* c = b->ctx[p];
+        BCK(cudaMemcpyAsync(c->J, c->B, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice,
+                            b->stream));
+        if (rebuild_lstar) c->lstar_valid = c->coef_valid = false;
+        b->iters[p] = 0;
+        b->delta[p] = 0.0;
+        b->converged[p] = 0;
+    }
+    return RT_OK;
+}
+
+int rt_batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, int max_sweeps,
+                   int* iters, double* deltas, int* n_converged)
+{
+    if (!b) return RT_EINVAL;
+    b->err.clear();
+    BCK(cudaSetDevice(b->device));
+    if (max_iter < 1 || max_sweeps < 1 || !(tol >= 0) || !(tol_inner >= 0))
+        return bfail(b, RT_EINVAL, "bad iteration controls");
+    const int P = (int)b->ctx.size();
+    int rc;
+    for (int it = 0; it < max_iter; ++it) {
+        std::vector<int> act;
+        for (int p : b->order)
+            if (!b->converged[p] && b->iters[p] < max_iter) act.push_back(p);
+        if (act.empty()) break;
+        if ((rc = batch_fs(b, act))) return rc;
+        if ((rc = batch_os(b, act, tol_inner, max_sweeps))) return rc;
+        BCK(cudaMemsetAsync(b->d_delta, 0, sizeof(double) * P, b->stream));
+        for (int p : act) {
+            rt_ctx* c = b->ctx[p];
+            BCK(launch_rel_change(c->g.N, c->Jn, c->J, b->d_delta + p, b->stream));
+            b->stats.launches += 1;
+        }
+        BCK(cudaMemcpyAsync(b->h_delta, b->d_delta, sizeof(double) * P, cudaMemcpyDeviceToHost,
+                            b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
+        bharvest(b);
+        b->stats.steps += *b->h_steps;
+        for (int p : act) {
+            rt_ctx* c = b->ctx[p];
+            std::swap(c->J, c->Jn);
+            b->iters[p] += 1;
+            b->delta[p] = b->h_delta[p];
+            if (tol > 0 && b->h_delta[p] < tol) b->converged[p] = 1;
+        }
+    }
+    int nconv = 0;
+    for (int p = 0; p < P; ++p) {
+        if (iters) iters[p] = b->iters[p];
+        if (deltas) deltas[p] = b->delta[p];
+        nconv += b->converged[p];
+    }
+    if (n_converged) *n_converged = nconv;
+    if (tol > 0 && nconv < P)
+        return bfail(b, RT_ENOTCONV, "%d of %d problems not converged", P - nconv, P);
+    return RT_OK;
+}
+
+int rt_batch_get_J(rt_batch* b, int p, double* J)
+{
+    if (!b || !J || p < 0 || p >= (int)b->ctx.size()) return RT_EINVAL;
+    b->err.clear();
+    BCK(cudaSetDevice(b->device));
+    BCK(cudaStreamSynchronize(b->stream));
+    int rc = rt_get_J(b->ctx[p], J);
+    return bpass(b, p, rc);
+}
+
+int rt_batch_get_J_dev(rt_batch* b, int p, double* J)
+{
+    if (!b || !J || p < 0 || p >= (int)b->ctx.size()) return RT_EINVAL;
+    b->err.clear();
+    BCK(cudaSetDevice(b->device));
+    rt_ctx* c = b->ctx[p];
+    BCK(cudaMemcpyAsync(J, c->J, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, b->stream));
+    return RT_OK;
+}
+
+int rt_batch_set_direction_groups(rt_batch* b, int groups)
+{
+    if (!b) return RT_EINVAL;
+    if (groups < 0 || groups > kSlots) return bfail(b, RT_EINVAL, "groups must be in [0, %d]", kSlots);
+    b->groups_req = groups;
+    return RT_OK;
+}
+
+int rt_batch_set_profiling(rt_batch* b, int on)
+{
+    if (!b) return RT_EINVAL;
+    b->profiling = on != 0;
+    return RT_OK;
+}
+
+int rt_batch_get_stats(rt_batch* b, rt_stats* out)
+{
+    if (!b || !out) return RT_EINVAL;
+    rt_stats s = b->stats;
+    for (rt_ctx* c : b->ctx) {   // per-problem kernels (source, sums, Lambda*, OS set-up)
+        s.launches += c->stats.launches;
+        s.lstar_launches += c->stats.lstar_launches;
+    }
+    *out = s;
+    return RT_OK;
+}
+
+int rt_batch_reset_stats(rt_batch* b)
+{
+    if (!b) return RT_EINVAL;
+    b->stats = rt_stats{};
+    for (rt_ctx* c : b->ctx) c->stats = rt_stats{};
     return RT_OK;
 }
 

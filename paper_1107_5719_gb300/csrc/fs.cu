@@ -17,6 +17,7 @@
 // groups (grid z) are then summed in fixed order, so J is bit-reproducible
 // without atomics on floating-point data.
 #include "internal.h"
+#include "weights.cuh"
 
 #include <cmath>
 
@@ -77,41 +78,6 @@ __global__ void k_dir_tables(Geometry g, double dx, double dy, double dz,
     }
 }
 
-// Segment weights of the linear-in-tau source (exact integral of S(t)e^{-t}
-// over a segment of optical depth x):  w_cur = 1 - (1-e)/x on the
-// downstream node, w_up = (1-e)/x - e on the upstream node, e = exp(-x).
-// Below x = 1/4 the closed form cancels; there the Taylor series of e^{-x}
-// gives  w_cur = sum_{n>=1} (-1)^{n+1} x^n/(n+1)!  and
-//        w_up  = sum_{n>=1} (-1)^{n+1} n x^n/(n+1)!,  kept through x^12
-// (truncation < 3e-17 relative at x = 1/4).
-__device__ __forceinline__ void seg_weights64(double x, double& wc, double& wu, double& e)
-{
-    e = exp(-x);
-    if (x < 0.25) {
-        // a_n = (-1)^{n+1} / (n+1)!
-        constexpr double a1 = 1.0 / 2.0, a2 = -1.0 / 6.0, a3 = 1.0 / 24.0, a4 = -1.0 / 120.0,
-                         a5 = 1.0 / 720.0, a6 = -1.0 / 5040.0, a7 = 1.0 / 40320.0,
-                         a8 = -1.0 / 362880.0, a9 = 1.0 / 3628800.0, a10 = -1.0 / 39916800.0,
-                         a11 = 1.0 / 479001600.0, a12 = -1.0 / 6227020800.0;
-        double c = a12;
-        c = fma(c, x, a11); c = fma(c, x, a10); c = fma(c, x, a9); c = fma(c, x, a8);
-        c = fma(c, x, a7);  c = fma(c, x, a6);  c = fma(c, x, a5); c = fma(c, x, a4);
-        c = fma(c, x, a3);  c = fma(c, x, a2);  c = fma(c, x, a1);
-        wc = c * x;
-        double u = 12.0 * a12;
-        u = fma(u, x, 11.0 * a11); u = fma(u, x, 10.0 * a10); u = fma(u, x, 9.0 * a9);
-        u = fma(u, x, 8.0 * a8);   u = fma(u, x, 7.0 * a7);   u = fma(u, x, 6.0 * a6);
-        u = fma(u, x, 5.0 * a5);   u = fma(u, x, 4.0 * a4);   u = fma(u, x, 3.0 * a3);
-        u = fma(u, x, 2.0 * a2);   u = fma(u, x, a1);
-        wu = u * x;
-    } else {
-        const double om = 1.0 - e;
-        const double q = om / x;
-        wc = 1.0 - q;
-        wu = q - e;
-    }
-}
-
 struct Nodes {
     int a00, a10, a01, a11;
 };
@@ -157,11 +123,14 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
     const int t = blockIdx.x * kThreads + threadIdx.x;
     const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
     const bool active = t < nxy;
+    __shared__ double tab[kExpTable];
+    fill_exp_table(tab);
+    __syncthreads();
     unsigned long long nsteps = 0;
     if (active) {
         const int j0 = t / nx, i0 = t - j0 * nx;
         const long long v = (long long)k0 * nxy + t;
-        const double smax = *smax_p;
+        const int need = cut_need(*smax_p, cut);
         const double chi0 = chi[v], S0 = S[v];
         for (int slot = zb; slot < kSlots; slot += ZB) {
             double Jp = 0.0;
@@ -181,12 +150,12 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                     const double cb = bilin(chi + pb, n, b);
                     const double sb = bilin(S + pb, n, b);
                     double wc, wu, e;
-                    seg_weights64(di.hs * (ca + cb), wc, wu, e);
+                    seg_weights64(di.hs * (ca + cb), tab, wc, wu, e);
                     I = fma(T, fma(wc, sa, wu * sb), I);
                     T *= e;
                     ca = cb;
                     sa = sb;
-                    if (T * smax <= cut * fabs(I)) {
+                    if (cut_now(T, I, need)) {
                         early = true;
                         ++m;
                         break;
@@ -199,96 +168,6 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                 }
                 nsteps += (unsigned long long)m;
                 Jp = fma(di.w, I, Jp);
-            }
-            partial[(long long)slot * g.N + v] = Jp;
-        }
-    }
-    if (steps) add_steps(steps, nsteps);
-}
-
-// FP32 segment weights: same definitions as seg_weights64.  Below x = 3/4
-// the Taylor series is kept through x^10 (truncation < 5e-9 relative);
-// above it the closed form loses less than a factor 3 to cancellation.
-__device__ __forceinline__ void seg_weights32(float x, float& wc, float& wu, float& e)
-{
-    e = expf(-x);
-    if (x < 0.75f) {
-        constexpr float a1 = 1.0f / 2.0f, a2 = -1.0f / 6.0f, a3 = 1.0f / 24.0f,
-                        a4 = -1.0f / 120.0f, a5 = 1.0f / 720.0f, a6 = -1.0f / 5040.0f,
-                        a7 = 1.0f / 40320.0f, a8 = -1.0f / 362880.0f, a9 = 1.0f / 3628800.0f,
-                        a10 = -1.0f / 39916800.0f;
-        float c = a10;
-        c = fmaf(c, x, a9); c = fmaf(c, x, a8); c = fmaf(c, x, a7); c = fmaf(c, x, a6);
-        c = fmaf(c, x, a5); c = fmaf(c, x, a4); c = fmaf(c, x, a3); c = fmaf(c, x, a2);
-        c = fmaf(c, x, a1);
-        wc = c * x;
-        float u = 10.0f * a10;
-        u = fmaf(u, x, 9.0f * a9); u = fmaf(u, x, 8.0f * a8); u = fmaf(u, x, 7.0f * a7);
-        u = fmaf(u, x, 6.0f * a6); u = fmaf(u, x, 5.0f * a5); u = fmaf(u, x, 4.0f * a4);
-        u = fmaf(u, x, 3.0f * a3); u = fmaf(u, x, 2.0f * a2); u = fmaf(u, x, a1);
-        wu = u * x;
-    } else {
-        const float om = 1.0f - e;
-        const float q = __fdividef(om, x);
-        wc = 1.0f - q;
-        wu = q - e;
-    }
-}
-
-// FP32 march, FP64 accumulation of J over directions.
-__global__ void __launch_bounds__(kThreads)
-k_fs32(Geometry g, const float* __restrict__ chi, const float* __restrict__ S,
-       const float* __restrict__ B, const DirInfo* __restrict__ info,
-       const StepGeo* __restrict__ off, const float4* __restrict__ bw,
-       const double* __restrict__ smax_p, float cut, double* __restrict__ partial,
-       unsigned long long* __restrict__ steps)
-{
-    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
-    const int t = blockIdx.x * kThreads + threadIdx.x;
-    const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
-    const bool active = t < nxy;
-    unsigned long long nsteps = 0;
-    if (active) {
-        const int j0 = t / nx, i0 = t - j0 * nx;
-        const long long v = (long long)k0 * nxy + t;
-        const float smax = (float)*smax_p;
-        const float chi0 = chi[v], S0 = S[v];
-        for (int slot = zb; slot < kSlots; slot += ZB) {
-            double Jp = 0.0;
-            for (int d = slot; d < g.ndir; d += kSlots) {
-                const DirInfo di = info[d];
-                const int s = di.sgn;
-                const int M = s > 0 ? k0 : nz - 1 - k0;
-                const StepGeo* od = off + (long long)d * nz;
-                const float4* bd = bw + (long long)d * nz;
-                float I = 0.0f, T = 1.0f, ca = chi0, sa = S0;
-                bool early = false;
-                int m = 0;
-                for (; m < M; ++m) {
-                    const long long pb = (long long)(k0 - (m + 1) * s) * nxy;
-                    const Nodes n = nodes_of(i0, j0, od[m + 1], nx, ny);
-                    const float4 b = bd[m + 1];
-                    const float cb = bilin(chi + pb, n, b);
-                    const float sb = bilin(S + pb, n, b);
-                    float wc, wu, e;
-                    seg_weights32(di.hs32 * (ca + cb), wc, wu, e);
-                    I = fmaf(T, fmaf(wc, sa, wu * sb), I);
-                    T *= e;
-                    ca = cb;
-                    sa = sb;
-                    if (T * smax <= cut * fabsf(I)) {
-                        early = true;
-                        ++m;
-                        break;
-                    }
-                }
-                if (!early && (s > 0 ? g.top_bc : g.bottom_bc)) {
-                    const long long pb = (long long)(k0 - M * s) * nxy;
-                    const Nodes n = nodes_of(i0, j0, od[M], nx, ny);
-                    I = fmaf(T, bilin(B + pb, n, bd[M]), I);
-                }
-                nsteps += (unsigned long long)m;
-                Jp = fma(di.w, (double)I, Jp);
             }
             partial[(long long)slot * g.N + v] = Jp;
         }
@@ -318,10 +197,13 @@ k_lstar64(Geometry g, const double* __restrict__ chi, const DirInfo* __restrict_
           double* __restrict__ lstar)
 {
     __shared__ double lam[27][kThreads];
+    __shared__ double tab[kExpTable];
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int t = blockIdx.x * kThreads + threadIdx.x;
     const int k0 = blockIdx.y;
     for (int o = 0; o < 27; ++o) lam[o][threadIdx.x] = 0.0;
+    fill_exp_table(tab);
+    __syncthreads();
     if (t >= nxy) return;
     const int j0 = t / nx, i0 = t - j0 * nx;
     const long long v = (long long)k0 * nxy + t;
@@ -336,13 +218,13 @@ k_lstar64(Geometry g, const double* __restrict__ chi, const DirInfo* __restrict_
         const Bw4d b1 = bd[1];
         const double chi1 = bilin(chi + (long long)(k0 - s) * nxy, nodes_of(i0, j0, od[1], nx, ny), b1);
         double wc0, wu0, e0;
-        seg_weights64(di.hs * (chi0 + chi1), wc0, wu0, e0);
+        seg_weights64(di.hs * (chi0 + chi1), tab, wc0, wu0, e0);
         double c1 = wu0;
         if (M >= 2) {
             const double chi2 = bilin(chi + (long long)(k0 - 2 * s) * nxy,
                                       nodes_of(i0, j0, od[2], nx, ny), bd[2]);
             double wc1, wu1, e1;
-            seg_weights64(di.hs * (chi1 + chi2), wc1, wu1, e1);
+            seg_weights64(di.hs * (chi1 + chi2), tab, wc1, wu1, e1);
             c1 = fma(e0, wc1, wu0);
         }
         lam[13][threadIdx.x] += di.w * wc0;
@@ -353,6 +235,28 @@ k_lstar64(Geometry g, const double* __restrict__ chi, const DirInfo* __restrict_
         if (di.lo[3] >= 0) lam[di.lo[3]][threadIdx.x] += cw * b1.w;
     }
     for (int o = 0; o < 27; ++o) lstar[(long long)o * g.N + v] = lam[o][threadIdx.x];
+}
+
+// Diagnostic: the segment weights the marches use, at given optical depths.
+__global__ void k_seg_eval(long long n, int fp32, const double* __restrict__ x,
+                           double* __restrict__ wc, double* __restrict__ wu,
+                           double* __restrict__ e)
+{
+    __shared__ double tab[kExpTable];
+    fill_exp_table(tab);
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (fp32) {
+            float a, b, c;
+            seg_weights32((float)x[i], a, b, c);
+            wc[i] = a; wu[i] = b; e[i] = c;
+        } else {
+            double a, b, c;
+            seg_weights64(x[i], tab, a, b, c);
+            wc[i] = a; wu[i] = b; e[i] = c;
+        }
+    }
 }
 
 }  // namespace
@@ -377,18 +281,6 @@ cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_fs32(const Geometry& g, const float* chi, const float* S, const float* B,
-                        const DirInfo* info, const StepGeo* off, const float4* bw,
-                        const double* smax, double cut, int groups, double* partial,
-                        unsigned long long* steps, cudaStream_t st)
-{
-    const int nxy = g.nx * g.ny;
-    dim3 grid((nxy + kThreads - 1) / kThreads, g.nz, groups);
-    k_fs32<<<grid, kThreads, 0, st>>>(g, chi, S, B, info, off, bw, smax, (float)cut, partial,
-                                      steps);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_sum_groups(long long N, const double* partial, double* J,
                               cudaStream_t st)
 {
@@ -396,6 +288,16 @@ cudaError_t launch_sum_groups(long long N, const double* partial, double* J,
     long long blocks = (N + threads - 1) / threads;
     if (blocks > 65535LL * 16) blocks = 65535LL * 16;
     k_sum_groups<<<(unsigned)blocks, threads, 0, st>>>(N, partial, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_eval(long long n, int fp32, const double* x, double* wc, double* wu,
+                            double* e, cudaStream_t st)
+{
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_seg_eval<<<(unsigned)blocks, 256, 0, st>>>(n, fp32, x, wc, wu, e);
     return cudaGetLastError();
 }
 

@@ -56,11 +56,41 @@ cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, c
                         const double* smax, double cut, int groups, double* partial,
                         unsigned long long* steps, cudaStream_t st);
 
-// FP32-sweep formal solution (FP64 accumulation of J): same output layout.
-cudaError_t launch_fs32(const Geometry& g, const float* chi, const float* S, const float* B,
-                        const DirInfo* info, const StepGeo* off, const float4* bw,
-                        const double* smax, double cut, int groups, double* partial,
-                        unsigned long long* steps, cudaStream_t st);
+// ---- FP32-sweep form (fs32.cu) ---------------------------------------------
+// poff[d][m]: offset of the upstream node (x0, y0) of step m in the padded
+// [nz][2ny][2nx] layout, relative to the voxel's own padded index.
+cudaError_t launch_pad_offsets(const Geometry& g, const DirInfo* info, const StepGeo* off,
+                               int* poff, cudaStream_t st);
+// node[k][y][x] = {chi, S_hi, S_lo, 0} with periodic copies (planes 2ny x 2nx).
+cudaError_t launch_pack32(const Geometry& g, const double* chi, const double* S, float4* node,
+                          cudaStream_t st);
+// b2[plane][y][x] = {B_hi, B_lo} of the top (0) and bottom (1) planes, padded.
+cudaError_t launch_pack_b2(const Geometry& g, const double* B, float2* b2, cudaStream_t st);
+// Everything the FP32 march of one problem reads and writes.
+struct View32 {
+    Geometry g;
+    const float4* node;     // padded {chi, S_hi, S_lo, 0}
+    const float2* b2;       // padded boundary {B_hi, B_lo}
+    const DirInfo* info;
+    const StepGeo* off;
+    const int* poff;
+    const float4* bw;       // FP32 bilinear weights per (direction, step)
+    const double* smax;     // source bound of the cutoff
+    double* partial;        // [kSlots][N]
+};
+// FP32 march of I - S_0: partial[kSlots][N] of sum_d w_d (I_d - S_0).
+cudaError_t launch_fs32d(const View32& p, double cut, int groups, unsigned long long* steps,
+                         cudaStream_t st);
+// Blocks one problem takes in a batched launch with `groups` slot groups.
+long long fs32_blocks(const Geometry& g, int groups);
+// One launch over the active problems ids[0..nact) of views (device arrays);
+// prefix[q] = first block of active problem q, prefix[nact] = total_blocks.
+cudaError_t launch_fs32_batch(const View32* views, const int* ids, const long long* prefix,
+                              int nact, long long total_blocks, int groups, double cut,
+                              unsigned long long* steps, cudaStream_t st);
+// J[v] = wsum S[v] + sum_slot partial[slot][v].
+cudaError_t launch_sum_groups_src(long long N, const double* partial, const double* S,
+                                  double wsum, double* J, cudaStream_t st);
 
 // J[v] = sum_slot partial[slot][v] in slot order.
 cudaError_t launch_sum_groups(long long N, const double* partial, double* J,
@@ -70,6 +100,10 @@ cudaError_t launch_sum_groups(long long N, const double* partial, double* J,
 cudaError_t launch_lstar64(const Geometry& g, const double* chi, const DirInfo* info,
                            const StepGeo* off, const Bw4d* bw, double* lstar,
                            cudaStream_t st);
+
+// Diagnostic evaluation of the segment weights (FP64 or FP32 form).
+cudaError_t launch_seg_eval(long long n, int fp32, const double* x, double* wc, double* wu,
+                            double* e, cudaStream_t st);
 
 // ---- launchers (os.cu) -----------------------------------------------------
 // S = eps B + (1 - eps) J; smax = max(|S|, |B| if any Planck boundary).
@@ -88,9 +122,11 @@ cudaError_t launch_os_coef(const Geometry& g, const double* lstar, const double*
 // r[v] = J_fs[v] / diag_v - sum_o c[o][v] J_old[nb(v,o)]
 cudaError_t launch_os_rhs(const Geometry& g, const double* coef, const double* rdiag,
                           const double* J_fs, const double* J_old, double* r, cudaStream_t st);
-// Jn[v] = r[v] + sum_{o != 13} c[o][v] J[nb(v,o)];  *delta = max |Jn - J| / |Jn|
+// Sweep n: Jn[v] = r[v] + sum_{o != 13} c[o][v] J[nb(v,o)];  dlt[n] = max |Jn - J| / |Jn|;
+// no-op when n > 0 and dlt[n-1] < tol.
 cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r,
-                          const double* J, double* Jn, double* delta, cudaStream_t st);
+                          const double* J, double* Jn, double* dlt, int n, double tol,
+                          cudaStream_t st);
 // *delta = max |Jn - Jo| / |Jn|
 cudaError_t launch_rel_change(long long N, const double* Jn, const double* Jo, double* delta,
                               cudaStream_t st);

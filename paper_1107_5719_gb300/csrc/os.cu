@@ -165,10 +165,17 @@ k_os_rhs(Geometry g, const double* __restrict__ c, const double* __restrict__ rd
     r[v] = Jfs[v] * rdiag[v] - stencil<false>(g, c, Jold, i, j, k, v);
 }
 
+// Sweep n of a Jacobi solve.  dlt[n] receives max |Jn - J| / |Jn|; if the
+// previous sweep already met the tolerance (dlt[n-1] < tol) the sweep does
+// nothing, so a host loop may enqueue several sweeps per check without
+// changing the result.  dlt must be zeroed before sweep 0.
 __global__ void __launch_bounds__(kOsThreads)
 k_jacobi(Geometry g, const double* __restrict__ c, const double* __restrict__ r,
-         const double* __restrict__ J, double* __restrict__ Jn, double* __restrict__ delta)
+         const double* __restrict__ J, double* __restrict__ Jn, double* __restrict__ dlt, int n,
+         double tol)
 {
+    if (n > 0 && dlt[n - 1] < tol) return;
+    double* delta = dlt + n;
     const int nx = g.nx, nxy = nx * g.ny;
     const int t = blockIdx.x * kOsThreads + threadIdx.x;
     const int k = blockIdx.y;
@@ -243,10 +250,11 @@ cudaError_t launch_os_rhs(const Geometry& g, const double* coef, const double* r
 }
 
 cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r,
-                          const double* J, double* Jn, double* delta, cudaStream_t st)
+                          const double* J, double* Jn, double* dlt, int n, double tol,
+                          cudaStream_t st)
 {
     dim3 grid((g.nx * g.ny + kOsThreads - 1) / kOsThreads, g.nz);
-    k_jacobi<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, Jn, delta);
+    k_jacobi<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, Jn, dlt, n, tol);
     return cudaGetLastError();
 }
 

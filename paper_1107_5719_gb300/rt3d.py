@@ -48,6 +48,11 @@ class rt_stats(C.Structure):
                 ("lstar_launches", C.c_ulonglong)]
 
 
+class rt_problem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
+                ("dy", C.c_double), ("dz", C.c_double), ("chi", VP), ("eps", VP), ("B", VP)]
+
+
 # name -> (restype, argtypes); pointers to data are passed as void*
 _SIGS = {
     "rt_version": (C.c_char_p, []),
@@ -80,6 +85,21 @@ _SIGS = {
     "rt_set_profiling": (C.c_int, [VP, C.c_int]),
     "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
     "rt_reset_stats": (C.c_int, [VP]),
+    "rt_batch_create": (C.c_int, [C.POINTER(VP), C.c_int, C.c_int, C.c_int, C.POINTER(rt_problem),
+                                  C.c_int, C.c_int, C.c_int, VP, VP, VP]),
+    "rt_batch_destroy": (C.c_int, [VP]),
+    "rt_batch_last_error": (C.c_char_p, [VP]),
+    "rt_batch_set_stream": (C.c_int, [VP, VP]),
+    "rt_batch_reset": (C.c_int, [VP, C.c_int]),
+    "rt_batch_solve": (C.c_int, [VP, C.c_double, C.c_int, C.c_double, C.c_int, VP, VP,
+                                 C.POINTER(C.c_int)]),
+    "rt_batch_get_J": (C.c_int, [VP, C.c_int, VP]),
+    "rt_batch_get_J_dev": (C.c_int, [VP, C.c_int, VP]),
+    "rt_batch_set_direction_groups": (C.c_int, [VP, C.c_int]),
+    "rt_batch_set_profiling": (C.c_int, [VP, C.c_int]),
+    "rt_batch_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
+    "rt_batch_reset_stats": (C.c_int, [VP]),
+    "rt_segment_weights": (C.c_int, [C.c_int, C.c_longlong, VP, VP, VP, VP, VP]),
     "rt_formal_solution_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                              C.c_double, C.c_int, C.c_int, C.c_int, VP, VP, VP,
                                              VP, VP, VP, VP, VP]),
@@ -294,6 +314,13 @@ def rt_reset_stats(ctx):
     return _check(ctx, load().rt_reset_stats(ctx))
 
 
+def rt_segment_weights(precision, x, w_cur, w_up, e, stream=None):
+    """Diagnostic: device segment weights at optical depths x (CUDA tensors)."""
+    h = getattr(stream, "cuda_stream", stream)
+    return load().rt_segment_weights(precision, x.numel(), _dev(x), _dev(w_cur), _dev(w_up),
+                                     _dev(e), h)
+
+
 def rt_formal_solution_noalloc(nx, ny, nz, dx, dy, dz, top, bottom, mu, phi, w, chi, S, B, J_fs,
                                stream=None):
     """Allocation-free formal solution for callers that may not allocate
@@ -308,6 +335,93 @@ def rt_formal_solution_noalloc(nx, ny, nz, dx, dy, dz, top, bottom, mu, phi, w, 
                                              pw, _dev(chi), _dev(S), _dev(B), _dev(J_fs), h)
 
 
+def _bcheck(b, rc, allow=()):
+    if rc != RT_OK and rc not in allow:
+        raise RtError(rc, load().rt_batch_last_error(b).decode() if b else "")
+    return rc
+
+
+def rt_batch_create(problems, device=0, precision=RT_FP32_SWEEP):
+    """Batch of ``workloads.Problem``-like problems sharing quadrature and
+    boundary modes (taken from the first problem)."""
+    p0 = problems[0]
+    keep = []
+    arr = (rt_problem * len(problems))()
+    for i, p in enumerate(problems):
+        chi, pc = _host(p.chi)
+        eps, pe = _host(p.eps)
+        B, pb = _host(p.B)
+        keep += [chi, eps, B]
+        arr[i] = rt_problem(p.nx, p.ny, p.nz, p.dx, p.dy, p.dz, pc, pe, pb)
+    mu, pm = _host(p0.mu)
+    phi, pp = _host(p0.phi)
+    w, pw = _host(p0.w)
+    h = VP()
+    rc = load().rt_batch_create(C.byref(h), device, precision, len(problems), arr, p0.top_bc,
+                                p0.bottom_bc, len(mu), pm, pp, pw)
+    if rc != RT_OK:
+        msg = load().rt_batch_last_error(h.value).decode() if h.value else ""
+        if h.value:
+            load().rt_batch_destroy(h.value)
+        raise RtError(rc, msg)
+    return h.value
+
+
+def rt_batch_destroy(b):
+    return load().rt_batch_destroy(b)
+
+
+def rt_batch_last_error(b) -> str:
+    return load().rt_batch_last_error(b).decode()
+
+
+def rt_batch_set_stream(b, stream):
+    h = getattr(stream, "cuda_stream", stream)
+    return _bcheck(b, load().rt_batch_set_stream(b, h))
+
+
+def rt_batch_reset(b, rebuild_lstar=False):
+    return _bcheck(b, load().rt_batch_reset(b, 1 if rebuild_lstar else 0))
+
+
+def rt_batch_solve(b, nprob, tol=1e-8, max_iter=1000, tol_inner=1e-12, max_sweeps=1000):
+    """Returns dict(iters, deltas, n_converged, converged)."""
+    it = np.zeros(nprob, dtype=np.int32)
+    dl = np.zeros(nprob)
+    nc = C.c_int()
+    rc = _bcheck(b, load().rt_batch_solve(b, tol, max_iter, tol_inner, max_sweeps, it.ctypes.data,
+                                          dl.ctypes.data, C.byref(nc)), allow=(RT_ENOTCONV,))
+    return dict(iters=it, deltas=dl, n_converged=nc.value, converged=(rc == RT_OK))
+
+
+def rt_batch_get_J(b, p, shape):
+    J = np.empty(shape)
+    _bcheck(b, load().rt_batch_get_J(b, p, J.ctypes.data))
+    return J
+
+
+def rt_batch_get_J_dev(b, p, J):
+    return _bcheck(b, load().rt_batch_get_J_dev(b, p, _dev(J)))
+
+
+def rt_batch_set_direction_groups(b, groups):
+    return _bcheck(b, load().rt_batch_set_direction_groups(b, groups))
+
+
+def rt_batch_set_profiling(b, on=True):
+    return _bcheck(b, load().rt_batch_set_profiling(b, 1 if on else 0))
+
+
+def rt_batch_get_stats(b) -> dict:
+    s = rt_stats()
+    _bcheck(b, load().rt_batch_get_stats(b, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in rt_stats._fields_}
+
+
+def rt_batch_reset_stats(b):
+    return _bcheck(b, load().rt_batch_reset_stats(b))
+
+
 # ---- convenience ----------------------------------------------------------
 
 class Solver:
@@ -316,6 +430,7 @@ class Solver:
     def __init__(self, problem, device: int = 0, precision: int = RT_FP64, groups: int = 0,
                  cutoff: Optional[float] = None):
         self.p = problem
+        self.precision = precision
         self.ctx = rt_create(device, precision)
         self.shape = (problem.nz, problem.ny, problem.nx)
         rt_set_grid(self.ctx, problem.nx, problem.ny, problem.nz, problem.dx, problem.dy, problem.dz)

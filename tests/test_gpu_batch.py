@@ -1,0 +1,103 @@
+"""Batched wavelengths: many problems, one fused formal-solution launch per
+outer iteration (FP32 sweep), per-problem convergence.
+
+Each problem's iterates must be exactly those of solving it alone with the
+same precision (same arithmetic per voxel, fixed summation order), so J is
+compared bit for bit; problems of different grid sizes (an uneven batch)
+share the launch.  The FP64 batch is checked against the oracle.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1107_5719_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1107_5719_gb300 import build as B
+    B.build()
+    from paper_1107_5719_gb300 import rt3d
+    rt3d.load()
+    return rt3d
+
+
+def _uneven(n_theta=6, n_phi=4):
+    probs = []
+    for i, (nx, ny, nz) in enumerate([(9, 7, 6), (17, 9, 11), (5, 5, 5), (13, 11, 9), (3, 3, 4)]):
+        p = W.random_slab(nx, ny, nz, n_theta=n_theta, n_phi=n_phi, seed=200 + i,
+                          eps_range=(10 ** (-1 - i), 1.0))
+        probs.append(p)
+    return probs
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_batch_equals_individual_solves(R, precision):
+    probs = _uneven()
+    b = R.rt_batch_create(probs, precision=precision)
+    try:
+        r = R.rt_batch_solve(b, len(probs), tol=1e-9, max_iter=500)
+        assert r["converged"] and r["n_converged"] == len(probs)
+        for i, p in enumerate(probs):
+            J = R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx))
+            with R.Solver(p, precision=precision) as s:
+                ri = s.solve(tol=1e-9, max_iter=500)
+            assert ri["iters"] == r["iters"][i]
+            assert np.array_equal(J, ri["J"]), i
+        st = R.rt_batch_get_stats(b)
+        assert st["fs_launches"] == (max(r["iters"]) if precision == 1 else int(r["iters"].sum()))
+    finally:
+        R.rt_batch_destroy(b)
+
+
+def test_batch_fp64_matches_oracle(R, oracle_mod):
+    probs = _uneven(n_theta=4, n_phi=4)[:3]
+    b = R.rt_batch_create(probs, precision=0)
+    try:
+        r = R.rt_batch_solve(b, len(probs), tol=1e-9, max_iter=500, tol_inner=0.0, max_sweeps=10)
+        for i, p in enumerate(probs):
+            ro = oracle_mod.solve(p, tol=1e-9, max_iter=500, tol_inner=0.0, max_sweeps=10)
+            assert ro["iters"] == r["iters"][i]
+            J = R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx))
+            assert np.allclose(J, ro["J"], rtol=1e-12, atol=0)
+    finally:
+        R.rt_batch_destroy(b)
+
+
+def test_batch_reset_and_restart(R):
+    probs = _uneven()[:3]
+    b = R.rt_batch_create(probs, precision=1)
+    try:
+        r1 = R.rt_batch_solve(b, 3, tol=1e-9, max_iter=500)
+        J1 = [R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx)) for i, p in enumerate(probs)]
+        R.rt_batch_reset(b, rebuild_lstar=True)
+        r2 = R.rt_batch_solve(b, 3, tol=1e-9, max_iter=500)
+        J2 = [R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx)) for i, p in enumerate(probs)]
+        assert np.array_equal(r1["iters"], r2["iters"])
+        for a, c in zip(J1, J2):
+            assert np.array_equal(a, c)
+    finally:
+        R.rt_batch_destroy(b)
+
+
+def test_batch_wavelengths_of_one_slab(R):
+    """A small wavelength batch built like the 512-point one (65^3 slab
+    scaled per wavelength), reduced to 8 points on a 17^3 slab: the batch
+    converges every point and matches per-point FP32 solves."""
+    probs = W.batch_65(n_lambda=8, n=17, n_theta=8, n_phi=4)
+    b = R.rt_batch_create(probs, precision=1)
+    try:
+        r = R.rt_batch_solve(b, len(probs), tol=1e-8, max_iter=2000)
+        assert r["converged"]
+        for i in (0, 5):
+            with R.Solver(probs[i], precision=1) as s:
+                ri = s.solve(tol=1e-8, max_iter=2000)
+            J = R.rt_batch_get_J(b, i, ri["J"].shape)
+            assert np.array_equal(J, ri["J"])
+    finally:
+        R.rt_batch_destroy(b)

@@ -1,0 +1,117 @@
+"""GPU FP32-sweep ("precision") form.
+
+The march runs in FP32 on the deviation I - S_0 from the voxel's own
+source, with S held as an FP32 (hi, lo) pair; J, Lambda*, the operator
+splitting and the convergence test stay FP64 (Sect. 3.1: small eps needs
+double precision for the operator-splitting equations).  Checks: the
+formal solution against the FP64 oracle; Lambda* identical to the FP64
+path's; converged J against the FP64 path within 1e-6 relative, including
+strong scattering (eps = 1e-6), where a march that accumulates I itself in
+FP32 would be off by ~1e-3.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1107_5719_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FS_RTOL = 1e-6       # one formal solution, FP32 march
+CONV_RTOL = 1e-6     # converged J, FP32 sweep vs FP64
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1107_5719_gb300 import build as B
+    B.build()
+    from paper_1107_5719_gb300 import rt3d
+    rt3d.load()
+    return rt3d
+
+
+@pytest.mark.parametrize("shape,seed", [((17, 9, 6), 1), ((5, 5, 5), 2), ((3, 3, 4), 3),
+                                        ((4, 3, 2), 4), ((13, 11, 9), 5)])
+def test_fs32_matches_oracle(R, oracle_mod, shape, seed):
+    nx, ny, nz = shape
+    p = W.random_slab(nx, ny, nz, n_theta=6, n_phi=5, seed=seed, chi_decades=5.0)
+    rng = np.random.default_rng(seed)
+    S = 0.5 + 2.0 * rng.random(p.B.shape)
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        J, L = s.formal_solution(S)
+    Jo, Lo = oracle_mod.formal_solution(p, S)
+    assert np.allclose(J, Jo, rtol=FS_RTOL, atol=0)
+    # Lambda* is built in FP64 in both forms
+    scale = np.abs(Lo).reshape(27, -1).max(axis=0)
+    assert np.all(np.abs(L - Lo).reshape(27, -1).max(axis=0) <= 1e-12 * scale)
+
+
+def test_fs32_both_boundary_modes_and_spacings(R, oracle_mod):
+    p = W.random_slab(11, 7, 8, n_theta=4, n_phi=6, seed=9, top_bc=W.BC_PLANCK,
+                      bottom_bc=W.BC_ZERO, dx=0.6, dy=1.4, dz=0.8)
+    S = p.B * 0.7
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        J, _ = s.formal_solution(S, want_lstar=False)
+    Jo, _ = oracle_mod.formal_solution(p, S, lstar=False)
+    assert np.allclose(J, Jo, rtol=FS_RTOL, atol=0)
+
+
+def test_fs32_constant_source_is_exact_at_depth(R):
+    """S = B = const with a Planck inner boundary: I - S_0 = T_M (B - S_0) = 0
+    on every upward ray, so the FP32 march returns J = S exactly where the
+    downward rays are fully absorbed."""
+    p = W.slab_small(n_theta=8, n_phi=4)
+    S = np.ones_like(p.B)
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        J, _ = s.formal_solution(S, want_lstar=False)
+    assert np.allclose(J[-3:], 1.0, rtol=1e-15, atol=0)
+
+
+def test_fs32_deterministic(R):
+    p = W.random_slab(19, 8, 7, n_theta=8, n_phi=6, seed=12)
+    out = []
+    for groups in (0, 1, 4, 8):
+        with R.Solver(p, precision=R.RT_FP32_SWEEP, groups=groups) as s:
+            out.append(s.formal_solution(want_lstar=False)[0])
+    for J in out[1:]:
+        assert np.array_equal(J, out[0])
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-6])
+def test_fs32_converged_column_strong_scattering(R, eps):
+    """Horizontally uniform 3x3x129 column with the strong-scattering chi law
+    (tau 1e-4 .. 1e4): converged J of the FP32 sweep within 1e-6 of FP64."""
+    p = W.slab_precision(n=3, nzz=129, eps=eps, n_theta=16, n_phi=4)
+    with R.Solver(p, precision=R.RT_FP64) as s:
+        r64 = s.solve(tol=1e-10, max_iter=3000)
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        r32 = s.solve(tol=1e-10, max_iter=3000)
+    assert r64["converged"] and r32["converged"]
+    rel = np.abs(r32["J"] - r64["J"]) / r64["J"]
+    assert rel.max() < CONV_RTOL, rel.max()
+
+
+def test_fs32_converged_slab17(R):
+    p = W.slab_small()
+    with R.Solver(p, precision=R.RT_FP64) as s:
+        r64 = s.solve(tol=1e-10, max_iter=500)
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        r32 = s.solve(tol=1e-10, max_iter=500)
+    rel = np.abs(r32["J"] - r64["J"]) / r64["J"]
+    assert rel.max() < CONV_RTOL, rel.max()
+
+
+def test_fs32_slab65_sampled(R, oracle_mod):
+    """65^3 slab, 32x32 directions: the FP32-sweep J at sampled voxels
+    against the oracle."""
+    p = W.slab_65()
+    S = p.eps * p.B + (1 - p.eps) * p.B
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        J, _ = s.formal_solution(want_lstar=False)
+    rng = np.random.default_rng(6)
+    vox = rng.integers(0, p.nvox, 96)
+    Jo = oracle_mod.mean_intensity_at(p, S, vox)
+    assert np.allclose(J.ravel()[vox], Jo, rtol=FS_RTOL, atol=0)

@@ -291,3 +291,37 @@ def test_device_pointer_calls(R, oracle_mod):
         assert np.allclose(Jout.cpu().numpy(), ro["J"], rtol=1e-11, atol=0)
     finally:
         R.rt_destroy(ctx)
+
+
+def _weights_mp(x):
+    import mpmath
+    mpmath.mp.dps = 40
+    x = mpmath.mpf(x)
+    e = mpmath.exp(-x)
+    q = -mpmath.expm1(-x) / x
+    return float(1 - q), float(q - e), float(e)
+
+
+@pytest.mark.parametrize("precision,rtol", [(0, 4e-15), (1, 2e-6)])
+def test_device_segment_weights_against_high_precision(R, precision, rtol):
+    """The march's own segment weights and exp(-x) on the GPU against a
+    40-digit evaluation of their definition (mpmath)."""
+    pytest.importorskip("mpmath")
+    import torch
+    xs = np.concatenate([np.logspace(-10, np.log10(690.0), 400),
+                         [0.25 * (1 - 1e-15), 0.25, 0.75 * (1 - 1e-7), 0.75, 1.0, 2.0, 50.0]])
+    dev = torch.device("cuda:0")
+    x = torch.from_numpy(xs).to(dev)
+    wc, wu, e = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+    assert R.rt_segment_weights(precision, x, wc, wu, e) == 0
+    torch.cuda.synchronize()
+    wc, wu, e = wc.cpu().numpy(), wu.cpu().numpy(), e.cpu().numpy()
+    for i, xv in enumerate(xs):
+        if precision == 1:
+            xv = float(np.float32(xv))
+        rc, ru, re = _weights_mp(xv)
+        assert abs(wc[i] - rc) <= rtol * rc, (xv, wc[i], rc)
+        assert abs(wu[i] - ru) <= rtol * ru, (xv, wu[i], ru)
+        # FP32: rounding x*log2(e) to FP32 costs ~x*6e-8 of relative accuracy in e
+        etol = rtol * re if precision == 0 else 1.5e-7 * (1.0 + xv) * re + 1e-37
+        assert abs(e[i] - re) <= etol, (xv, e[i], re)
