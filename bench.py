@@ -42,6 +42,12 @@ FLOPS_PER_STEP_FP64 = 49
 # i.e. 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz).
 PEAK_FP64_TFLOPS = 1.25
 
+# The FP32-sweep iterate stops changing below a relative delta of ~1e-8
+# (rounding), so its outer tolerance is at least 5e-8, and Ng extrapolation
+# is skipped once delta < 1e-6 (it would amplify that rounding).
+TOL_FP32 = 5e-8
+NG_MIN_FP32 = 1e-6
+
 WORKLOADS = {
     "slab65": dict(desc="65^3 slab (x,y periodic), chi = 10^(-4+8k/64) exp(0.3 N(0,1)), "
                         "eps = 10^(-4U) per voxel, B = (1+k/64)^4, 32x32 directions, tol 1e-8",
@@ -60,8 +66,11 @@ def dist_env():
     return ws, rank, local
 
 
-def make_problem(name):
+def make_problem(name, lambdas=512):
     from paper_1107_5719_gb300 import workloads as W
+    if name == "batch":
+        # one wavelength of the batch stands for the per-wavelength cost
+        return W.batch_65(n_lambda=lambdas)[0]
     return getattr(W, WORKLOADS[name]["make"])()
 
 
@@ -135,7 +144,7 @@ def flush_l2(buf):
 
 
 def timed_solves(R, p, precision, dev, stream, flush, warmup, steps, max_iter, clk_id=None,
-                 groups=0):
+                 groups=0, ng=0, ng_min=0.0, tol=None):
     """Converged solves of problem `p` through the device API: every step
     re-sets the opacity (Lambda* rebuilt) and J = B, then iterates to
     convergence.  Returns per-step ms, iteration counts, profiling counters,
@@ -154,11 +163,14 @@ def timed_solves(R, p, precision, dev, stream, flush, warmup, steps, max_iter, c
         R.rt_set_epsilon_dev(ctx, eps)
         if groups:
             R.rt_set_direction_groups(ctx, groups)
+        if ng:
+            R.rt_set_ng(ctx, ng, ng_min)
+        tol_used = p.tol if tol is None else tol
 
         def step():
             R.rt_set_opacity_dev(ctx, chi)      # new opacity: Lambda* is rebuilt
             R.rt_set_planck_dev(ctx, Bt)        # J = B
-            it, delta, conv = R.rt_solve_dev(ctx, Jout, tol=p.tol, max_iter=max_iter)
+            it, delta, conv = R.rt_solve_dev(ctx, Jout, tol=tol_used, max_iter=max_iter)
             if not conv:
                 raise RuntimeError(f"solve did not converge in {it} iterations ({delta:.3e})")
             return it
@@ -204,7 +216,7 @@ def replicas_barrier():
         dist.barrier()
 
 
-def e2e_solves(R, p, precision, dev, steps, max_iter):
+def e2e_solves(R, p, precision, dev, steps, max_iter, ng=0):
     """Solves/s through the host-pointer API from pinned host buffers, with
     the host->device copies of chi, eps, B and the device->host copy of J in
     the timed region."""
@@ -220,6 +232,8 @@ def e2e_solves(R, p, precision, dev, steps, max_iter):
         R.rt_set_grid(ctx, p.nx, p.ny, p.nz, p.dx, p.dy, p.dz)
         R.rt_set_boundary(ctx, p.top_bc, p.bottom_bc)
         R.rt_set_quadrature(ctx, p.mu, p.phi, p.w)
+        if ng:
+            R.rt_set_ng(ctx, ng)
 
         def one():
             for f, t in ((lib.rt_set_opacity, chi_h), (lib.rt_set_epsilon, eps_h),
@@ -270,7 +284,7 @@ def run_ours(args):
     flush = torch.zeros(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MiB > L2
 
     r64 = timed_solves(R, p, R.RT_FP64, dev, stream, flush, args.warmup, args.steps,
-                       args.max_iter, clk_id=smi_id(dev))
+                       args.max_iter, clk_id=smi_id(dev), ng=args.ng)
     st = r64["stats"]
     my_ms = float(sum(r64["times"]))
     solves_per_s, total_ms = RP.weak_throughput(args.steps, my_ms)
@@ -294,8 +308,9 @@ def run_ours(args):
                 "share_of_step": round(st["fs_ms"] / my_ms, 4)}
 
     # the FP32-sweep form of the same workload on the same GPU
+    tol32 = max(p.tol, TOL_FP32)
     r32 = timed_solves(R, p, R.RT_FP32_SWEEP, dev, stream, flush, 1, args.fp32_steps,
-                       args.max_iter)
+                       args.max_iter, ng=args.ng, ng_min=NG_MIN_FP32, tol=tol32)
     st32 = r32["stats"]
     ms32 = float(sum(r32["times"]))
     fs32_ms = st32["fs_ms"] / max(st32["fs_launches"], 1)
@@ -305,12 +320,13 @@ def run_ours(args):
             "march_steps_per_s": round(st32["steps"] / (ms32 / 1e3), 1),
             "ms_per_fs_launch": round(fs32_ms, 4),
             "fs_steps_per_s": round(st32["steps"] / (st32["fs_ms"] / 1e3), 1),
+            "tol": tol32,
             "max_rel_dev_from_fp64_J": float(np.max(np.abs(r32["J"] - r64["J"]) / r64["J"])),
             "speedup_vs_fp64": round(my_ms / args.steps / (ms32 / args.fp32_steps), 3)}
 
     e2e = None
     if args.e2e_steps > 0:
-        v = e2e_solves(R, p, R.RT_FP64, dev, args.e2e_steps, args.max_iter)
+        v = e2e_solves(R, p, R.RT_FP64, dev, args.e2e_steps, args.max_iter, args.ng)
         e2e = {"value": round(RP.sum_over_ranks(v), 6), "unit": "solves/s",
                "h2d_bytes_per_step": 3 * p.nvox * 8, "d2h_bytes_per_step": p.nvox * 8,
                "steps": args.e2e_steps, "api": "rt_set_opacity/epsilon/planck + rt_solve (host)"}
@@ -324,7 +340,8 @@ def run_ours(args):
                    "nx": p.nx, "ny": p.ny, "nz": p.nz, "ndir": p.ndir, "tol": p.tol,
                    "precision": "FP64", "parallelism": f"replicas x{ws}",
                    "l2": "flushed between steps (512 MiB write)",
-                   "lstar": "rebuilt every step"},
+                   "lstar": "rebuilt every step",
+                   "ng_acceleration": f"every {args.ng} iterations" if args.ng else "off"},
         "voxel_dir_updates_per_s": round(vd_per_s, 1),
         "march_steps_per_s": round(steps_per_s, 1),
         "iters_per_solve": round(fs_per_solve, 3),
@@ -354,13 +371,15 @@ def run_batch(args, ws, rank, dev, R):
     probs_all = W.batch_65(n_lambda=nl)
     probs = [probs_all[i] for i in mine]
     b = R.rt_batch_create(probs, device=dev.index, precision=R.RT_FP32_SWEEP)
+    if args.ng:
+        R.rt_batch_set_ng(b, args.ng, NG_MIN_FP32)
     stream = torch.cuda.Stream(device=dev)
     R.rt_batch_set_stream(b, stream)
     flush = torch.zeros(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     try:
         def step():
             R.rt_batch_reset(b, rebuild_lstar=True)
-            r = R.rt_batch_solve(b, len(probs), tol=1e-8, max_iter=args.max_iter)
+            r = R.rt_batch_solve(b, len(probs), tol=TOL_FP32, max_iter=args.max_iter)
             if not r["converged"]:
                 raise RuntimeError("batch did not converge")
             return r
@@ -396,7 +415,7 @@ def run_batch(args, ws, rank, dev, R):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 march / f64 J, Lambda*, OS",
             "data": "synthetic",
             "config": {"workload": f"batch: {nl} wavelengths x 65^3 slab, chi x 10^(-2+4U), "
-                                   "eps 10^(-5+5U), 32x32 directions, tol 1e-8",
+                                   f"eps 10^(-5+5U), 32x32 directions, tol {TOL_FP32:g}",
                        "precision": "FP32 sweep", "parallelism": f"wavelength shards x{ws}",
                        "l2": "flushed between steps (512 MiB write)",
                        "lstar": "rebuilt every step"},
@@ -453,7 +472,7 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    p = make_problem(args.workload)
+    p = make_problem(args.workload, args.lambdas)
     iters = args.ref_iters
     sweeps = args.ref_sweeps
     vals = []
@@ -485,6 +504,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--ng", type=int, default=4,
+                    help="Ng acceleration period of the outer iteration (0 = off)")
     ap.add_argument("--lambdas", type=int, default=512, help="wavelengths of the batch workload")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

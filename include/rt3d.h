@@ -171,6 +171,19 @@ int rt_set_J(rt_ctx *ctx, const double *J);
  * the transmission cutoff are not counted). */
 int rt_last_step_count(rt_ctx *ctx, unsigned long long *steps);
 
+/* Ng acceleration of the outer iteration (the paper keeps it, with the
+ * set-up, in host code, Sect. 2): after every `period`-th iteration, once
+ * the four latest iterates x0 (newest) .. x3 are held, x0 is replaced by
+ * (1 - a - b) x0 + a x1 + b x2 with a, b minimising
+ * sum_i (d0 - a (d0 - d1) - b (d0 - d2))_i^2 / x0_i^2, d0 = x0 - x1,
+ * d1 = x1 - x2, d2 = x2 - x3 (second-order Ng extrapolation); the history
+ * then restarts.  The extrapolation is skipped while the previous
+ * iteration's delta is below min_delta (>= 0): once the iterates differ only
+ * by rounding noise (about 5e-8 relative for the FP32 sweep) the
+ * extrapolation would amplify that noise.  delta is measured against the
+ * extrapolated iterate.  period 0 (default) = off; otherwise >= 4. */
+int rt_set_ng(rt_ctx *ctx, int period, double min_delta);
+
 /* Tuning: the directions are summed into J in 8 fixed slots (direction d in
  * slot d mod 8, each slot in increasing d, then the slots in order), so J
  * is bit-reproducible and independent of this knob.  `groups` (1..8) sets
@@ -278,6 +291,8 @@ int rt_batch_get_J(rt_batch *batch, int p, double *J);
 int rt_batch_get_J_dev(rt_batch *batch, int p, double *J);
 /* As rt_set_direction_groups, for the fused launch (0 = auto). */
 int rt_batch_set_direction_groups(rt_batch *batch, int groups);
+/* As rt_set_ng, for every problem of the batch. */
+int rt_batch_set_ng(rt_batch *batch, int period, double min_delta);
 
 /* Counters of this context since the last rt_reset_stats: kernel launches,
  * formal-solution march launches and their device time, Jacobi sweeps and

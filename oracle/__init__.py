@@ -9,7 +9,9 @@ Sections of Hauschildt & Baron (2011) that each function follows:
   formal_solution     Sect. 2.2 (formal solution, J and Lambda*)
   intensity           Sect. 2.2 (intensity along one characteristic)
   os_step             Sect. 2.3 (operator splitting, Jordan iterations)
-  solve               Sect. 2 (outer iteration), Sect. 3.1 item 5 (S)
+  solve               Sect. 2 (outer iteration, optional Ng acceleration),
+                      Sect. 3.1 item 5 (S)
+  ng_step             Sect. 2 (Ng acceleration of the outer iteration)
   weights             segment weights of the linear-source integral
 """
 
@@ -66,6 +68,8 @@ def _configure(lib):
     lib.orc_solve.argtypes = [G, P, P, P, C.c_int, P, P, P, C.c_double, C.c_int,
                               C.c_double, C.c_int, C.c_int, P, P,
                               C.POINTER(C.c_int), P, C.POINTER(C.c_int), C.c_int]
+    lib.orc_solve_ng.argtypes = lib.orc_solve.argtypes + [C.c_int, C.c_double]
+    lib.orc_ng_step.argtypes = [C.c_long, P, P, P, P, P, P, P]
     return lib
 
 
@@ -163,10 +167,27 @@ def os_step(p, lstar, J_fs, J_old, tol_inner=1e-12, max_sweeps=1000):
     return Jn, ns.value
 
 
+def ng_step(x0, x1, x2, x3):
+    """Second-order Ng extrapolation of four iterates (x0 newest); returns
+    (x, a, b, singular)."""
+    lib = _load()
+    a0, p0 = _d(x0)
+    a1, p1 = _d(x1)
+    a2, p2 = _d(x2)
+    a3, p3 = _d(x3)
+    out = np.empty_like(a0)
+    a, b = C.c_double(), C.c_double()
+    rc = lib.orc_ng_step(a0.size, p0, p1, p2, p3, out.ctypes.data_as(C.POINTER(C.c_double)),
+                         C.byref(a), C.byref(b))
+    return out, a.value, b.value, bool(rc)
+
+
 def solve(p, tol=None, max_iter=500, tol_inner=1e-12, max_sweeps=1000, J0=None,
-          nthreads: int = 0, want_lstar: bool = False):
-    """Outer iteration.  Returns a dict with J, iters, deltas, sweeps,
-    converged (and lstar if asked)."""
+          nthreads: int = 0, want_lstar: bool = False, ng_period: int = 0,
+          ng_min_delta: float = 0.0):
+    """Outer iteration (Ng acceleration every ng_period iterations if > 0).
+    Returns a dict with J, iters, deltas, sweeps, converged (and lstar if
+    asked)."""
     lib = _load()
     g = _grid(p)
     chi, pc = _d(p.chi)
@@ -181,12 +202,13 @@ def solve(p, tol=None, max_iter=500, tol_inner=1e-12, max_sweeps=1000, J0=None,
     sweeps = np.zeros(max_iter, dtype=np.int32)
     iters = C.c_int()
     tol = p.tol if tol is None else tol
-    rc = lib.orc_solve(C.byref(g), pc, pe, pb, len(mu), pm, pp, pw, float(tol),
-                       int(max_iter), float(tol_inner), int(max_sweeps),
-                       1 if J0 is not None else 0, J.ctypes.data_as(C.POINTER(C.c_double)),
-                       L.ctypes.data_as(C.POINTER(C.c_double)) if want_lstar else None,
-                       C.byref(iters), deltas.ctypes.data_as(C.POINTER(C.c_double)),
-                       sweeps.ctypes.data_as(C.POINTER(C.c_int)), nthreads)
+    rc = lib.orc_solve_ng(C.byref(g), pc, pe, pb, len(mu), pm, pp, pw, float(tol),
+                          int(max_iter), float(tol_inner), int(max_sweeps),
+                          1 if J0 is not None else 0, J.ctypes.data_as(C.POINTER(C.c_double)),
+                          L.ctypes.data_as(C.POINTER(C.c_double)) if want_lstar else None,
+                          C.byref(iters), deltas.ctypes.data_as(C.POINTER(C.c_double)),
+                          sweeps.ctypes.data_as(C.POINTER(C.c_int)), nthreads, int(ng_period),
+                          float(ng_min_delta))
     if rc not in (OK, NOTCONV):
         raise ValueError(f"oracle solve rejected its input ({rc})")
     n = iters.value

@@ -66,6 +66,18 @@
  *   solution -> J_fs (Lambda* on the first pass); operator splitting ->
  *   J_new; delta = max_i |J_new_i - J_i| / |J_new_i|; stop when delta < tol
  *   or after max_iter.
+ *
+ *  Ng acceleration (the paper leaves it, with the set-up, to host code,
+ *   Sect. 2).  Second-order Ng extrapolation of the iterates: with the four
+ *   latest iterates x0 (newest) .. x3 and d0 = x0 - x1, d1 = x1 - x2,
+ *   d2 = x2 - x3, choose a, b minimising
+ *     sum_i w_i (d0 - a (d0 - d1) - b (d0 - d2))_i^2,   w_i = 1 / x0_i^2,
+ *   and replace x0 by (1 - a - b) x0 + a x1 + b x2.  In the outer loop it is
+ *   applied after every `ng_period`-th iteration once four iterates exist
+ *   since the last extrapolation, provided the previous iteration's delta
+ *   was at least `ng_min_delta` (extrapolating iterates whose differences
+ *   are down at rounding level only amplifies the rounding); delta is then
+ *   measured against the extrapolated iterate.
  */
 
 #include <math.h>
@@ -368,10 +380,48 @@ int orc_os_step(const orc_grid *g, const double *lstar, const double *eps,
     return ORC_OK;
 }
 
+/* Second-order Ng extrapolation (see header).  Returns 0, or 1 if the 2x2
+ * system is singular (x0 is then left unchanged). */
+int orc_ng_step(long N, const double *x0, const double *x1, const double *x2,
+                const double *x3, double *out, double *a_out, double *b_out)
+{
+    double a11 = 0, a12 = 0, a22 = 0, b1 = 0, b2 = 0;
+    for (long i = 0; i < N; ++i) {
+        double d0 = x0[i] - x1[i], d1 = x1[i] - x2[i], d2 = x2[i] - x3[i];
+        double q1 = d0 - d1, q2 = d0 - d2;
+        double w = 1.0 / (x0[i] * x0[i]);
+        a11 += w * q1 * q1;
+        a12 += w * q1 * q2;
+        a22 += w * q2 * q2;
+        b1 += w * d0 * q1;
+        b2 += w * d0 * q2;
+    }
+    double det = a11 * a22 - a12 * a12;
+    if (!(fabs(det) > 1e-300) || !(det == det)) {
+        for (long i = 0; i < N; ++i) out[i] = x0[i];
+        if (a_out) *a_out = 0.0;
+        if (b_out) *b_out = 0.0;
+        return 1;
+    }
+    double a = (b1 * a22 - b2 * a12) / det;
+    double b = (b2 * a11 - b1 * a12) / det;
+    for (long i = 0; i < N; ++i) out[i] = (1.0 - a - b) * x0[i] + a * x1[i] + b * x2[i];
+    if (a_out) *a_out = a;
+    if (b_out) *b_out = b;
+    return 0;
+}
+
 /* Outer iteration.  J_inout holds J^0 on entry if use_initial != 0 (else
  * J^0 = B) and the last iterate on exit.  deltas/sweeps (may be NULL) get
  * one entry per outer iteration.  Returns 0 on convergence, 3 if max_iter
  * was reached first (both leave J_inout valid). */
+int orc_solve_ng(const orc_grid *g, const double *chi, const double *eps,
+                 const double *B, int ndir, const double *mu, const double *phi,
+                 const double *w, double tol, int max_iter, double tol_inner,
+                 int max_sweeps, int use_initial, double *J_inout,
+                 double *lstar_out, int *iters_out, double *deltas, int *sweeps,
+                 int nthreads, int ng_period, double ng_min_delta);
+
 int orc_solve(const orc_grid *g, const double *chi, const double *eps,
               const double *B, int ndir, const double *mu, const double *phi,
               const double *w, double tol, int max_iter, double tol_inner,
@@ -379,28 +429,59 @@ int orc_solve(const orc_grid *g, const double *chi, const double *eps,
               double *lstar_out, int *iters_out, double *deltas, int *sweeps,
               int nthreads)
 {
+    return orc_solve_ng(g, chi, eps, B, ndir, mu, phi, w, tol, max_iter, tol_inner, max_sweeps,
+                        use_initial, J_inout, lstar_out, iters_out, deltas, sweeps, nthreads, 0,
+                        0.0);
+}
+
+/* Outer iteration with Ng acceleration every ng_period >= 4 iterations
+ * (0: none) while the previous delta >= ng_min_delta. */
+int orc_solve_ng(const orc_grid *g, const double *chi, const double *eps,
+                 const double *B, int ndir, const double *mu, const double *phi,
+                 const double *w, double tol, int max_iter, double tol_inner,
+                 int max_sweeps, int use_initial, double *J_inout,
+                 double *lstar_out, int *iters_out, double *deltas, int *sweeps,
+                 int nthreads, int ng_period, double ng_min_delta)
+{
+    if (ng_period != 0 && ng_period < 4) return ORC_EINVAL;
     if (check_grid(g) || check_dirs(ndir, mu) || max_iter < 1) return ORC_EINVAL;
     long N = (long)g->nx * g->ny * g->nz;
     double *J = malloc(sizeof(double) * N), *S = malloc(sizeof(double) * N);
     double *Jfs = malloc(sizeof(double) * N), *Jn = malloc(sizeof(double) * N);
     double *L = malloc(sizeof(double) * N * 27);
-    if (!J || !S || !Jfs || !Jn || !L) {
-        free(J); free(S); free(Jfs); free(Jn); free(L);
+    double *hist = malloc(sizeof(double) * N * 4);   /* ring of the last four iterates */
+    if (!J || !S || !Jfs || !Jn || !L || !hist) {
+        free(J); free(S); free(Jfs); free(Jn); free(L); free(hist);
         return ORC_ENOMEM;
     }
     for (long v = 0; v < N; ++v) J[v] = use_initial ? J_inout[v] : B[v];
-    int it, status = 3;
+    int it, status = 3, nhist = 0;
+    double prev_delta = 0.0;
+    memcpy(hist, J, sizeof(double) * N);
+    nhist = 1;
     for (it = 1; it <= max_iter; ++it) {
         for (long v = 0; v < N; ++v) S[v] = eps[v] * B[v] + (1.0 - eps[v]) * J[v];
         orc_formal_solution(g, chi, S, B, ndir, mu, phi, w, Jfs, it == 1 ? L : NULL, nthreads);
         int ns = 0;
         orc_os_step(g, L, eps, Jfs, J, Jn, tol_inner, max_sweeps, &ns);
+        if (ng_period) {
+            /* history: hist[k] holds the iterate k steps back (k = 0 newest) */
+            memmove(hist + N, hist, sizeof(double) * N * 3);
+            memcpy(hist, Jn, sizeof(double) * N);
+            if (nhist < 4) ++nhist;
+            if (nhist == 4 && it % ng_period == 0 && (it == 1 || prev_delta >= ng_min_delta)) {
+                orc_ng_step(N, hist, hist + N, hist + 2 * N, hist + 3 * N, Jn, NULL, NULL);
+                memcpy(hist, Jn, sizeof(double) * N);
+                nhist = 1;
+            }
+        }
         double delta = 0.0;
         for (long v = 0; v < N; ++v) {
             double rel = fabs(Jn[v] - J[v]) / fabs(Jn[v]);
             if (!(rel <= delta)) delta = rel;
         }
         memcpy(J, Jn, sizeof(double) * N);
+        prev_delta = delta;
         if (deltas) deltas[it - 1] = delta;
         if (sweeps) sweeps[it - 1] = ns;
         if (delta < tol) { status = 0; break; }
@@ -408,6 +489,6 @@ int orc_solve(const orc_grid *g, const double *chi, const double *eps,
     if (iters_out) *iters_out = it > max_iter ? max_iter : it;
     memcpy(J_inout, J, sizeof(double) * N);
     if (lstar_out) memcpy(lstar_out, L, sizeof(double) * N * 27);
-    free(J); free(S); free(Jfs); free(Jn); free(L);
+    free(J); free(S); free(Jfs); free(Jn); free(L); free(hist);
     return status;
 }

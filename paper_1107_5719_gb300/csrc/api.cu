@@ -57,6 +57,17 @@ struct rt_ctx {
     int dlt_cap = 0;
     unsigned long long last_steps = 0;
 
+    // Ng acceleration: period (0 = off), older iterates, reduction scratch
+    int ng_period = 0;
+    double ng_min_delta = 0.0;          // extrapolate only while the last delta >= this
+    double ng_last_delta = 0.0;         // delta of the previous iteration
+    int ng_count = 1;                   // iterates held, newest included
+    double* ng_old[3] = {nullptr, nullptr, nullptr};  // J_{n-1}, J_{n-2}, J_{n-3}
+    double* ng_part = nullptr;
+    double* ng_out = nullptr;           // device [5]
+    double* h_ng = nullptr;             // pinned [5]
+    int ng_applied = 0;
+
     // profiling
     rt_stats stats{};
     bool profiling = false;
@@ -104,12 +115,22 @@ cudaError_t dalloc(T*& p, size_t count)
     return cudaMalloc((void**)&p, count * sizeof(T));
 }
 
+void free_ng(rt_ctx* c)
+{
+    for (auto& p : c->ng_old) dfree(p);
+    dfree(c->ng_part);
+    dfree(c->ng_out);
+    if (c->h_ng) cudaFreeHost(c->h_ng);
+    c->h_ng = nullptr;
+}
+
 void free_grid_buffers(rt_ctx* c)
 {
     dfree(c->chi); dfree(c->eps); dfree(c->B); dfree(c->J); dfree(c->S);
     dfree(c->Jfs); dfree(c->Jn); dfree(c->Ja); dfree(c->Jb); dfree(c->r);
     dfree(c->lstar); dfree(c->coef); dfree(c->rdiag); dfree(c->partial);
     dfree(c->node4); dfree(c->b2);
+    free_ng(c);
     c->partial_groups = 0;
 }
 
@@ -421,6 +442,61 @@ int os_step(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, doub
     return RT_OK;
 }
 
+int ensure_ng(rt_ctx* c)
+{
+    if (c->ng_out) return RT_OK;
+    for (auto& p : c->ng_old) CK(dalloc(p, (size_t)c->g.N));
+    CK(dalloc(c->ng_part, (size_t)ng_partial_size()));
+    CK(dalloc(c->ng_out, 5));
+    CK(cudaMallocHost((void**)&c->h_ng, 5 * sizeof(double)));
+    return RT_OK;
+}
+
+// Ng bookkeeping after iteration `it` (1-based) produced J_new in c->Jn from
+// the previous iterate c->J: remember c->J, and when four iterates are held
+// and it is a multiple of the period, enqueue the weighted sums.  Returns
+// in *pending whether ng_finish must run after the next synchronisation.
+int ng_push(rt_ctx* c, int it, bool* pending)
+{
+    *pending = false;
+    if (!c->ng_period) return RT_OK;
+    int rc = ensure_ng(c);
+    if (rc) return rc;
+    double* t = c->ng_old[2];
+    c->ng_old[2] = c->ng_old[1];
+    c->ng_old[1] = c->ng_old[0];
+    c->ng_old[0] = t;
+    CK(cudaMemcpyAsync(c->ng_old[0], c->J, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    if (c->ng_count < 4) ++c->ng_count;
+    if (c->ng_count == 4 && it % c->ng_period == 0 &&
+        (it == 1 || c->ng_last_delta >= c->ng_min_delta)) {
+        CK(launch_ng_dots(c->g.N, c->Jn, c->ng_old[0], c->ng_old[1], c->ng_old[2], c->ng_part,
+                          c->ng_out, c->stream));
+        CK(cudaMemcpyAsync(c->h_ng, c->ng_out, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream));
+        c->stats.launches += 2;
+        *pending = true;
+    }
+    return RT_OK;
+}
+
+// After the sums are on the host: solve the 2x2 least-squares system and
+// replace J_new by the extrapolation (left unchanged if it is singular).
+int ng_finish(rt_ctx* c)
+{
+    const double* s = c->h_ng;  // a11 a12 a22 b1 b2
+    const double det = s[0] * s[2] - s[1] * s[1];
+    c->ng_count = 1;
+    if (!(std::fabs(det) > 1e-300) || det != det) return RT_OK;
+    const double a = (s[3] * s[2] - s[4] * s[1]) / det;
+    const double b = (s[4] * s[0] - s[3] * s[1]) / det;
+    CK(launch_ng_combine(c->g.N, c->Jn, c->ng_old[0], c->ng_old[1], a, b, c->Jn, c->stream));
+    c->stats.launches += 1;
+    c->ng_applied += 1;
+    return RT_OK;
+}
+
 int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps, double* J_out,
           int* iters, double* last_delta, double* deltas, int* sweeps, bool device)
 {
@@ -438,6 +514,12 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
         if ((rc = run_fs(c, c->Jfs, true))) return rc;
         int ns = 0;
         if ((rc = run_os(c, c->Jfs, c->J, c->Jn, tol_inner, max_sweeps, &ns))) return rc;
+        bool ng_pending = false;
+        if ((rc = ng_push(c, it + 1, &ng_pending))) return rc;
+        if (ng_pending) {
+            CK(cudaStreamSynchronize(c->stream));
+            if ((rc = ng_finish(c))) return rc;
+        }
         CK(cudaMemsetAsync(c->scal + 2, 0, sizeof(double), c->stream));
         CK(launch_rel_change(c->g.N, c->Jn, c->J, c->scal + 2, c->stream));
         c->stats.launches += 1;
@@ -447,6 +529,7 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
         harvest(c);
         total_steps += *c->h_steps;
         delta = c->h_scal[2];
+        c->ng_last_delta = delta;
         double* t = c->J;
         c->J = c->Jn;
         c->Jn = t;
@@ -834,6 +917,8 @@ static int set_B(rt_ctx* c, const double* B, bool device)
     int rc = set_field(c, B, c ? c->B : nullptr, device, "B", false, false);
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->J, c->B, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
+    c->ng_count = 1;
+    c->ng_last_delta = 0.0;
     c->have_B = true;
     c->b2_valid = false;
     return RT_OK;
@@ -901,6 +986,7 @@ int rt_set_J(rt_ctx* c, const double* J)
     if (!J) return fail(c, RT_EINVAL, "J is NULL");
     if ((rc = check_field(c, J, "J", false, false))) return rc;
     CK(cudaMemcpyAsync(c->J, J, sizeof(double) * c->g.N, cudaMemcpyHostToDevice, c->stream));
+    c->ng_count = 1;
     CK(cudaStreamSynchronize(c->stream));
     return RT_OK;
 }
@@ -937,6 +1023,26 @@ int rt_segment_weights(int precision, long long n, const double* x, double* w_cu
     if (launch_seg_eval(n, precision == RT_FP32_SWEEP, x, w_cur, w_up, e, (cudaStream_t)stream) !=
         cudaSuccess)
         return RT_ECUDA;
+    return RT_OK;
+}
+
+int rt_set_ng(rt_ctx* c, int period, double min_delta)
+{
+    if (!c) return RT_EINVAL;
+    if (period != 0 && period < 4) return fail(c, RT_EINVAL, "Ng period must be 0 (off) or >= 4");
+    if (!(min_delta >= 0)) return fail(c, RT_EINVAL, "Ng min_delta must be >= 0");
+    c->ng_period = period;
+    c->ng_min_delta = min_delta;
+    c->ng_count = 1;
+    return RT_OK;
+}
+
+int rt_batch_set_ng(rt_batch* b, int period, double min_delta)
+{
+    if (!b) return RT_EINVAL;
+    if (period != 0 && period < 4) return bfail(b, RT_EINVAL, "Ng period must be 0 (off) or >= 4");
+    if (!(min_delta >= 0)) return bfail(b, RT_EINVAL, "Ng min_delta must be >= 0");
+    for (rt_ctx* c : b->ctx) rt_set_ng(c, period, min_delta);
     return RT_OK;
 }
 
@@ -1065,6 +1171,8 @@ int rt_batch_reset(rt_batch* b, int rebuild_lstar)
         rt_ctx* c = b->ctx[p];
         BCK(cudaMemcpyAsync(c->J, c->B, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice,
                             b->stream));
+        c->ng_count = 1;
+        c->ng_last_delta = 0.0;
         if (rebuild_lstar) c->lstar_valid = c->coef_valid = false;
         b->iters[p] = 0;
         b->delta[p] = 0.0;
@@ -1090,6 +1198,17 @@ int rt_batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, int 
         if (act.empty()) break;
         if ((rc = batch_fs(b, act))) return rc;
         if ((rc = batch_os(b, act, tol_inner, max_sweeps))) return rc;
+        std::vector<int> ng_now;
+        for (int p : act) {
+            bool pend = false;
+            if ((rc = bpass(b, p, ng_push(b->ctx[p], b->iters[p] + 1, &pend)))) return rc;
+            if (pend) ng_now.push_back(p);
+        }
+        if (!ng_now.empty()) {
+            BCK(cudaStreamSynchronize(b->stream));
+            for (int p : ng_now)
+                if ((rc = bpass(b, p, ng_finish(b->ctx[p])))) return rc;
+        }
         BCK(cudaMemsetAsync(b->d_delta, 0, sizeof(double) * P, b->stream));
         for (int p : act) {
             rt_ctx* c = b->ctx[p];
@@ -1106,6 +1225,7 @@ int rt_batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, int 
             std::swap(c->J, c->Jn);
             b->iters[p] += 1;
             b->delta[p] = b->h_delta[p];
+            c->ng_last_delta = b->h_delta[p];
             if (tol > 0 && b->h_delta[p] < tol) b->converged[p] = 1;
         }
     }

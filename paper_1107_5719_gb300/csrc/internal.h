@@ -127,6 +127,14 @@ cudaError_t launch_os_rhs(const Geometry& g, const double* coef, const double* r
 cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r,
                           const double* J, double* Jn, double* dlt, int n, double tol,
                           cudaStream_t st);
+// Ng acceleration: out5 = the five weighted sums (fixed reduction order) of
+// iterates x0 (newest) .. x3; part is scratch of ng_partial_size() doubles.
+int ng_partial_size();
+cudaError_t launch_ng_dots(long long N, const double* x0, const double* x1, const double* x2,
+                           const double* x3, double* part, double* out5, cudaStream_t st);
+// out = (1 - a - b) x0 + a x1 + b x2 (out may alias x0).
+cudaError_t launch_ng_combine(long long N, const double* x0, const double* x1, const double* x2,
+                              double a, double b, double* out, cudaStream_t st);
 // *delta = max |Jn - Jo| / |Jn|
 cudaError_t launch_rel_change(long long N, const double* Jn, const double* Jo, double* delta,
                               cudaStream_t st);

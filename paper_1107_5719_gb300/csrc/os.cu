@@ -202,6 +202,66 @@ __global__ void k_rel_change(long long N, const double* __restrict__ Jn,
     block_max_to(m, delta);
 }
 
+// ---- Ng acceleration --------------------------------------------------------
+// Second-order Ng extrapolation of the outer iterates x0 (newest) .. x3:
+// the five weighted sums of the 2x2 least-squares system (weights 1/x0^2)
+// are reduced in a fixed order (fixed grid, fixed per-thread strides, fixed
+// tree), so the extrapolation is reproducible.
+constexpr int kNgBlocks = 1024, kNgThreads = 256;
+
+__global__ void __launch_bounds__(kNgThreads)
+k_ng_dots(long long N, const double* __restrict__ x0, const double* __restrict__ x1,
+          const double* __restrict__ x2, const double* __restrict__ x3, double* __restrict__ part)
+{
+    double s[5] = {0, 0, 0, 0, 0};
+    for (long long i = blockIdx.x * (long long)kNgThreads + threadIdx.x; i < N;
+         i += (long long)kNgBlocks * kNgThreads) {
+        const double d0 = x0[i] - x1[i], d1 = x1[i] - x2[i], d2 = x2[i] - x3[i];
+        const double q1 = d0 - d1, q2 = d0 - d2;
+        const double w = 1.0 / (x0[i] * x0[i]);
+        s[0] += w * q1 * q1;
+        s[1] += w * q1 * q2;
+        s[2] += w * q2 * q2;
+        s[3] += w * d0 * q1;
+        s[4] += w * d0 * q2;
+    }
+    __shared__ double sm[5][kNgThreads];
+    for (int k = 0; k < 5; ++k) sm[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int h = kNgThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int k = 0; k < 5; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kNgThreads)
+k_ng_sum(const double* __restrict__ part, double* __restrict__ out)
+{
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < kNgBlocks; b += kNgThreads)
+        for (int k = 0; k < 5; ++k) s[k] += part[b * 5 + k];
+    __shared__ double sm[5][kNgThreads];
+    for (int k = 0; k < 5; ++k) sm[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int h = kNgThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int k = 0; k < 5; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void k_ng_combine(long long N, const double* __restrict__ x0,
+                             const double* __restrict__ x1, const double* __restrict__ x2,
+                             double a, double b, double* __restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (1.0 - a - b) * x0[i] + a * x1[i] + b * x2[i];
+}
+
 unsigned grid_1d(long long N, int threads)
 {
     long long b = (N + threads - 1) / threads;
@@ -255,6 +315,23 @@ cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r
 {
     dim3 grid((g.nx * g.ny + kOsThreads - 1) / kOsThreads, g.nz);
     k_jacobi<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, Jn, dlt, n, tol);
+    return cudaGetLastError();
+}
+
+int ng_partial_size() { return kNgBlocks * 5; }
+
+cudaError_t launch_ng_dots(long long N, const double* x0, const double* x1, const double* x2,
+                           const double* x3, double* part, double* out5, cudaStream_t st)
+{
+    k_ng_dots<<<kNgBlocks, kNgThreads, 0, st>>>(N, x0, x1, x2, x3, part);
+    k_ng_sum<<<1, kNgThreads, 0, st>>>(part, out5);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ng_combine(long long N, const double* x0, const double* x1, const double* x2,
+                              double a, double b, double* out, cudaStream_t st)
+{
+    k_ng_combine<<<grid_1d(N, 256), 256, 0, st>>>(N, x0, x1, x2, a, b, out);
     return cudaGetLastError();
 }
 

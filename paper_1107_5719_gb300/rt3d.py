@@ -83,6 +83,8 @@ _SIGS = {
     "rt_set_direction_groups": (C.c_int, [VP, C.c_int]),
     "rt_set_cutoff": (C.c_int, [VP, C.c_double]),
     "rt_set_profiling": (C.c_int, [VP, C.c_int]),
+    "rt_set_ng": (C.c_int, [VP, C.c_int, C.c_double]),
+    "rt_batch_set_ng": (C.c_int, [VP, C.c_int, C.c_double]),
     "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
     "rt_reset_stats": (C.c_int, [VP]),
     "rt_batch_create": (C.c_int, [C.POINTER(VP), C.c_int, C.c_int, C.c_int, C.POINTER(rt_problem),
@@ -300,6 +302,14 @@ def rt_set_cutoff(ctx, cut):
     return _check(ctx, load().rt_set_cutoff(ctx, cut))
 
 
+def rt_set_ng(ctx, period, min_delta=0.0):
+    return _check(ctx, load().rt_set_ng(ctx, period, min_delta))
+
+
+def rt_batch_set_ng(b, period, min_delta=0.0):
+    return _bcheck(b, load().rt_batch_set_ng(b, period, min_delta))
+
+
 def rt_set_profiling(ctx, on=True):
     return _check(ctx, load().rt_set_profiling(ctx, 1 if on else 0))
 
@@ -428,7 +438,7 @@ class Solver:
     """One context holding one problem (a ``workloads.Problem``-like object)."""
 
     def __init__(self, problem, device: int = 0, precision: int = RT_FP64, groups: int = 0,
-                 cutoff: Optional[float] = None):
+                 cutoff: Optional[float] = None, ng_period: int = 0, ng_min_delta: float = 0.0):
         self.p = problem
         self.precision = precision
         self.ctx = rt_create(device, precision)
@@ -443,6 +453,8 @@ class Solver:
             rt_set_direction_groups(self.ctx, groups)
         if cutoff is not None:
             rt_set_cutoff(self.ctx, cutoff)
+        if ng_period:
+            rt_set_ng(self.ctx, ng_period, ng_min_delta)
 
     def formal_solution(self, S=None, want_lstar=True):
         return rt_formal_solution(self.ctx, S, self.shape, want_lstar)

@@ -149,6 +149,23 @@ def test_converged_solve_matches_oracle(R, oracle_mod, which):
     assert np.allclose(r["J"], ro["J"], rtol=RTOL, atol=0)
 
 
+@pytest.mark.parametrize("period,min_delta", [(4, 0.0), (5, 0.0), (4, 1e-5)])
+def test_ng_accelerated_solve_matches_oracle(R, oracle_mod, period, min_delta):
+    """Ng-accelerated outer iteration: same iteration count and J as the
+    oracle's Ng-accelerated iteration, and fewer iterations than plain."""
+    p = W.slab_small(n_theta=8, n_phi=8)
+    ro = oracle_mod.solve(p, tol=1e-8, max_iter=300, tol_inner=0.0, max_sweeps=12,
+                          ng_period=period, ng_min_delta=min_delta)
+    with R.Solver(p, ng_period=period, ng_min_delta=min_delta) as s:
+        r = s.solve(tol=1e-8, max_iter=300, tol_inner=0.0, max_sweeps=12)
+    assert r["converged"] and ro["converged"]
+    assert r["iters"] == ro["iters"]
+    assert np.allclose(r["J"], ro["J"], rtol=RTOL, atol=0)
+    with R.Solver(p) as s:
+        plain = s.solve(tol=1e-8, max_iter=300, tol_inner=0.0, max_sweeps=12)
+    assert r["iters"] < plain["iters"]
+
+
 def test_converged_solve_tolerance_driven_inner(R, oracle_mod):
     p = W.slab_small(n_theta=8, n_phi=8)
     ro = oracle_mod.solve(p, tol=1e-8, max_iter=300)

@@ -358,6 +358,53 @@ def test_converged_ali_equals_dense_solution(oracle_mod):
     assert np.allclose(r["J"].ravel(), ref, rtol=1e-11, atol=0)
 
 
+def test_ng_extrapolation_exact_for_two_geometric_modes(oracle_mod):
+    """If the error of the iterates is a sum of two geometric modes,
+    x_k = x* + A l1^k + C l2^k, second-order Ng extrapolation of the four
+    latest iterates returns x* exactly (the polynomial with roots l1, l2
+    annihilates both modes)."""
+    rng = np.random.default_rng(4)
+    n = 200
+    xs = 1.0 + rng.random(n)
+    A, Cm = rng.standard_normal(n), rng.standard_normal(n)
+    for l1, l2 in ((0.9, 0.5), (0.99, -0.3), (0.95, 0.8), (-0.7, 0.6)):
+        it = [xs + A * l1 ** k + Cm * l2 ** k for k in range(6)]
+        x, a, b, sing = oracle_mod.ng_step(it[5], it[4], it[3], it[2])
+        assert not sing
+        # coefficients of the polynomial with roots l1, l2 normalised to p(1) = 1
+        den = (1 - l1) * (1 - l2)
+        assert abs(a - (-(l1 + l2) / den)) < 1e-7 * abs(a)
+        assert abs(b - (l1 * l2 / den)) < 1e-7 * abs(b)
+        # the plain iterate is off by ~l1^5; the extrapolation by rounding only
+        assert np.max(np.abs(x - xs) / xs) < 1e-8, (l1, l2)
+        assert np.max(np.abs(it[5] - xs) / xs) > 1e-3
+
+
+def test_ng_accelerated_ali_reaches_the_same_fixed_point(oracle_mod):
+    p = W.random_slab(5, 5, 5, n_theta=4, n_phi=5, seed=31, eps_range=(1e-3, 1.0))
+    plain = oracle_mod.solve(p, tol=1e-13, max_iter=2000, tol_inner=1e-14, max_sweeps=2000)
+    ng = oracle_mod.solve(p, tol=1e-13, max_iter=2000, tol_inner=1e-14, max_sweeps=2000,
+                          ng_period=4)
+    assert plain["converged"] and ng["converged"]
+    assert ng["iters"] < plain["iters"]
+    assert np.allclose(ng["J"], plain["J"], rtol=1e-10, atol=0)
+
+
+def test_ng_threshold_switches_extrapolation_off(oracle_mod):
+    """With a minimum delta above every delta of the run, Ng never
+    extrapolates and the iteration is exactly the plain one."""
+    p = W.random_slab(5, 4, 6, n_theta=4, n_phi=4, seed=8, eps_range=(1e-2, 1.0))
+    plain = oracle_mod.solve(p, tol=1e-10, max_iter=500, tol_inner=0.0, max_sweeps=10)
+    off = oracle_mod.solve(p, tol=1e-10, max_iter=500, tol_inner=0.0, max_sweeps=10,
+                           ng_period=4, ng_min_delta=1e30)
+    assert off["iters"] == plain["iters"]
+    assert np.array_equal(off["J"], plain["J"])
+    on = oracle_mod.solve(p, tol=1e-10, max_iter=500, tol_inner=0.0, max_sweeps=10,
+                          ng_period=4, ng_min_delta=1e-6)
+    assert on["iters"] < plain["iters"]
+    assert np.allclose(on["J"], plain["J"], rtol=1e-8, atol=0)
+
+
 # ------------------------------------------------------------- physics
 
 def test_thermalisation_at_depth(oracle_mod):
@@ -436,6 +483,9 @@ _MUTANTS = {
                                    "Jn[v] = acc / (1.0 - lstar[13L * N + v]);"),
     "source_function_sign": ("S[v] = eps[v] * B[v] + (1.0 - eps[v]) * J[v];",
                              "S[v] = eps[v] * J[v] + (1.0 - eps[v]) * B[v];"),
+    "ng_coefficients_swapped": ("for (long i = 0; i < N; ++i) out[i] = (1.0 - a - b) * x0[i] + a * x1[i] + b * x2[i];",
+                                "for (long i = 0; i < N; ++i) out[i] = (1.0 - a - b) * x0[i] + b * x1[i] + a * x2[i];"),
+    "ng_unweighted_cross_term": ("a12 += w * q1 * q2;", "a12 += q1 * q2;"),
 }
 
 
@@ -450,6 +500,7 @@ def _pin_battery(mod):
         ("lstar", lambda: test_lstar_equals_brute_force_lambda(mod, (3, 4, 5), 12)),
         ("os_step", lambda: test_os_step_solves_its_linear_system(mod)),
         ("ali", lambda: test_converged_ali_equals_dense_solution(mod)),
+        ("ng", lambda: test_ng_extrapolation_exact_for_two_geometric_modes(mod)),
     ]
     for name, fn in pins:
         try:
