@@ -36,7 +36,10 @@ def _uneven(n_theta=6, n_phi=4):
     return probs
 
 
-TOL = {1: 5e-8, 0: 1e-9}   # FP32 sweep: its delta floor is ~1e-8
+# FP32 sweep: the iterate's delta floor is ~1e-8 with many directions and
+# higher with the few directions used here; equality with the individual
+# solves holds at any tolerance.
+TOL = {1: 1e-6, 0: 1e-9}
 
 
 @pytest.mark.parametrize("precision", [1, 0])
@@ -77,10 +80,10 @@ def test_batch_reset_and_restart(R):
     probs = _uneven()[:3]
     b = R.rt_batch_create(probs, precision=1)
     try:
-        r1 = R.rt_batch_solve(b, 3, tol=5e-8, max_iter=500)
+        r1 = R.rt_batch_solve(b, 3, tol=TOL[1], max_iter=500)
         J1 = [R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx)) for i, p in enumerate(probs)]
         R.rt_batch_reset(b, rebuild_lstar=True)
-        r2 = R.rt_batch_solve(b, 3, tol=5e-8, max_iter=500)
+        r2 = R.rt_batch_solve(b, 3, tol=TOL[1], max_iter=500)
         J2 = [R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx)) for i, p in enumerate(probs)]
         assert np.array_equal(r1["iters"], r2["iters"])
         for a, c in zip(J1, J2):
@@ -97,11 +100,11 @@ def test_batch_wavelengths_of_one_slab(R):
     b = R.rt_batch_create(probs, precision=1)
     try:
         R.rt_batch_set_ng(b, 4, 1e-6)
-        r = R.rt_batch_solve(b, len(probs), tol=5e-8, max_iter=2000)
+        r = R.rt_batch_solve(b, len(probs), tol=TOL[1], max_iter=2000)
         assert r["converged"]
         for i in (0, 5):
             with R.Solver(probs[i], precision=1, ng_period=4, ng_min_delta=1e-6) as s:
-                ri = s.solve(tol=5e-8, max_iter=2000)
+                ri = s.solve(tol=TOL[1], max_iter=2000)
             J = R.rt_batch_get_J(b, i, ri["J"].shape)
             assert np.array_equal(J, ri["J"])
     finally:

@@ -342,3 +342,33 @@ def test_device_segment_weights_against_high_precision(R, precision, rtol):
         # FP32: rounding x*log2(e) to FP32 costs ~x*6e-8 of relative accuracy in e
         etol = rtol * re if precision == 0 else 1.5e-7 * (1.0 + xv) * re + 1e-37
         assert abs(e[i] - re) <= etol, (xv, e[i], re)
+
+
+def test_not_converged_is_reported_and_outputs_stay_valid(R, oracle_mod):
+    """max_iter reached before tol: the C call returns RT_ENOTCONV, J and the
+    per-iteration deltas are still those of the iterations run."""
+    import ctypes as C
+    p = W.random_slab(7, 6, 5, n_theta=4, n_phi=4, seed=93, eps_range=(1e-3, 1e-2))
+    with R.Solver(p) as s:
+        lib = R.load()
+        J = np.empty(s.shape)
+        it, last = C.c_int(), C.c_double()
+        d = np.zeros(3)
+        rc = lib.rt_solve(s.ctx, 1e-12, 3, 0.0, 10, J.ctypes.data, C.byref(it), C.byref(last),
+                          d.ctypes.data, None)
+        assert rc == R.RT_ENOTCONV and it.value == 3 and last.value == d[-1] > 0
+        assert "not converged" in R.rt_last_error(s.ctx)
+    ro = oracle_mod.solve(p, tol=0.0, max_iter=3, tol_inner=0.0, max_sweeps=10)
+    assert np.allclose(J, ro["J"], rtol=RTOL, atol=0)
+
+
+def test_context_usable_after_invalid_call(R, oracle_mod):
+    p = W.random_slab(6, 5, 4, n_theta=4, n_phi=4, seed=94)
+    with R.Solver(p) as s:
+        bad = p.chi.copy()
+        bad[0, 0, 0] = -1.0
+        with pytest.raises(R.RtError):
+            R.rt_set_opacity(s.ctx, bad)
+        J, _ = s.formal_solution(p.B, want_lstar=False)
+    Jo, _ = oracle_mod.formal_solution(p, p.B, lstar=False)
+    assert np.allclose(J, Jo, rtol=RTOL, atol=0)
