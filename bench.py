@@ -41,6 +41,13 @@ FLOPS_PER_STEP_FP64 = 49
 # Peak FP64 of GB300 from the profiling recipe's figure (1.25 TFLOP/s,
 # i.e. 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz).
 PEAK_FP64_TFLOPS = 1.25
+# FP32 arithmetic of one step of the FP32-sweep march (closed-form branch,
+# FMA = 2): chi interpolation 7, source differences S(p) - S_0 20, optical
+# depth 2, weights 4 (plus 2 MUFU: ex2, rcp), the I - S_0 update 4 and its
+# TwoSum 6, optical-depth sum 1, transmission 1 (plus 1 MUFU ex2).
+FLOPS_PER_STEP_FP32 = 45
+# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
+PEAK_FP32_TFLOPS = 80.5
 
 # The FP32-sweep iterate stops changing below a relative delta of ~1e-8
 # (rounding), so its outer tolerance is at least 5e-8, and Ng extrapolation
@@ -323,6 +330,13 @@ def run_ours(args):
             "tol": tol32,
             "max_rel_dev_from_fp64_J": float(np.max(np.abs(r32["J"] - r64["J"]) / r64["J"])),
             "speedup_vs_fp64": round(my_ms / args.steps / (ms32 / args.fp32_steps), 3)}
+    if st32["fs_ms"] > 0:
+        ach32 = FLOPS_PER_STEP_FP32 * st32["steps"] / (st32["fs_ms"] / 1e3) / 1e12
+        fp32["roofline"] = {"kernel": "k_fs32d (FP32-sweep march)", "bound": "alu",
+                            "achieved": round(ach32, 3), "peak": PEAK_FP32_TFLOPS,
+                            "unit": "TFLOP/s", "frac": round(ach32 / PEAK_FP32_TFLOPS, 4),
+                            "flops_per_step": FLOPS_PER_STEP_FP32,
+                            "note": "ncu: limited by L1 throughput, not the FP32 pipe"}
 
     e2e = None
     if args.e2e_steps > 0:

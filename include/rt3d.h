@@ -81,7 +81,7 @@ typedef enum {
 } rt_status;
 
 enum { RT_FP64 = 0, RT_FP32_SWEEP = 1 };
-enum { RT_BC_ZERO = 0, RT_BC_PLANCK = 1 };
+enum { RT_BC_ZERO = 0, RT_BC_PLANCK = 1, RT_BC_DIFFUSION = 2 };
 
 typedef struct rt_ctx rt_ctx;
 
@@ -109,8 +109,12 @@ int rt_set_stream(rt_ctx *ctx, void *stream);
 int rt_set_grid(rt_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz);
 
 /* Incoming intensity at the top (entered by mu > 0) and bottom (mu < 0):
- * RT_BC_ZERO (I = 0, the outer boundary of Sect. 3.1) or RT_BC_PLANCK
- * (I = B interpolated at the entry point).  Default: ZERO top, PLANCK bottom. */
+ * RT_BC_ZERO (I = 0, the outer boundary of Sect. 3.1), RT_BC_PLANCK
+ * (I = B interpolated at the entry point) or, at the bottom only,
+ * RT_BC_DIFFUSION (the inner boundary's LTE diffusion, Sect. 3.1 item 4:
+ * I = B + |mu| dB/dtau, with dB/dtau taken at each bottom node as
+ * (B[nz-1] - B[nz-2]) / (dz (chi[nz-1] + chi[nz-2]) / 2) and interpolated
+ * like B).  Default: ZERO top, PLANCK bottom. */
 int rt_set_boundary(rt_ctx *ctx, int top_mode, int bottom_mode);
 
 /* Solid-angle quadrature: ndir directions, host arrays mu[ndir],

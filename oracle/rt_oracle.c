@@ -49,7 +49,11 @@
  *     I(p_m) = I(p_{m+1}) e + w_cur S(p_m) + w_up S(p_{m+1}),
  *     w_cur = 1 - (1-e)/x,   w_up = (1-e)/x - e,
  *   i.e. the exact integral of S(t) e^{-t} over the segment for a linear
- *   S(t).  I(p_M) = I_bc: 0 (zero mode) or B(p_M) (Planck mode).
+ *   S(t).  I(p_M) = I_bc: 0 (zero mode), B(p_M) (Planck mode), or at the
+ *   inner boundary B(p_M) + |mu| G(p_M) (LTE diffusion mode, Sect. 3.1
+ *   item 4: the diffusion approximation I = B + mu dB/dtau), where G is
+ *   dB/dtau at each bottom node, (B[nz-1] - B[nz-2]) / (dz (chi[nz-1] +
+ *   chi[nz-2]) / 2), interpolated bilinearly like B.
  *
  *  Lambda*.  I is linear in S.  Lambda_{i,j} = sum_d w_d dI_{i,d}/dS_j with
  *   the boundary intensity excluded; Lambda*_{i,o} = Lambda_{i,wrap(i+o)}
@@ -94,7 +98,8 @@
 typedef struct {
     int nx, ny, nz;
     double dx, dy, dz;
-    int top_bc, bottom_bc;      /* 0: I_bc = 0, 1: I_bc = B at the entry point */
+    int top_bc, bottom_bc;      /* 0: I_bc = 0, 1: I_bc = B at the entry point,
+                                   2 (bottom only): LTE diffusion, see below */
 } orc_grid;
 
 static long vidx(const orc_grid *g, long i, long j, long k)
@@ -168,6 +173,29 @@ static orc_dir dir_geometry(const orc_grid *g, double mu, double phi)
     return d;
 }
 
+/* dB/dtau at bottom node (i, j): vertical difference over the trapezoid
+ * optical depth between the two deepest planes. */
+static double diffusion_gradient(const orc_grid *g, const double *chi, const double *B,
+                                 long i, long j)
+{
+    long a = vidx(g, i, j, g->nz - 1), b = vidx(g, i, j, g->nz - 2);
+    return (B[a] - B[b]) / (g->dz * (chi[a] + chi[b]) / 2.0);
+}
+
+/* Bilinear value of the bottom-node gradient at (x, y). */
+static double diffusion_gradient_at(const orc_grid *g, const double *chi, const double *B,
+                                    double x, double y)
+{
+    double fx0 = floor(x), fy0 = floor(y);
+    double tx = x - fx0, ty = y - fy0;
+    long i0 = wrapi((long)fx0, g->nx), i1 = wrapi((long)fx0 + 1, g->nx);
+    long j0 = wrapi((long)fy0, g->ny), j1 = wrapi((long)fy0 + 1, g->ny);
+    return (1.0 - tx) * (1.0 - ty) * diffusion_gradient(g, chi, B, i0, j0)
+         + tx * (1.0 - ty) * diffusion_gradient(g, chi, B, i1, j0)
+         + (1.0 - tx) * ty * diffusion_gradient(g, chi, B, i0, j1)
+         + tx * ty * diffusion_gradient(g, chi, B, i1, j1);
+}
+
 static int steps_to_boundary(const orc_grid *g, const orc_dir *d, long k0)
 {
     return d->s > 0 ? (int)k0 : (int)(g->nz - 1 - k0);
@@ -185,6 +213,7 @@ double orc_intensity(const orc_grid *g, const double *chi, const double *S,
     double xM = (double)i0 - M * d.ax, yM = (double)j0 - M * d.ay;
     long kM = k0 - (long)M * d.s;
     double I = bc ? bilinear(g, B, kM, xM, yM) : 0.0;
+    if (bc == 2) I += fabs(mu) * diffusion_gradient_at(g, chi, B, xM, yM);
     for (int m = M - 1; m >= 0; --m) {
         double xa = (double)i0 - m * d.ax, ya = (double)j0 - m * d.ay;
         double xb = (double)i0 - (m + 1) * d.ax, yb = (double)j0 - (m + 1) * d.ay;
@@ -256,6 +285,7 @@ static void lstar_one(const orc_grid *g, const double *chi, double mu, double ph
 static int check_grid(const orc_grid *g)
 {
     if (!g || g->nx < 3 || g->ny < 3 || g->nz < 2) return ORC_EINVAL;
+    if (g->top_bc < 0 || g->top_bc > 1 || g->bottom_bc < 0 || g->bottom_bc > 2) return ORC_EINVAL;
     if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return ORC_EINVAL;
     return ORC_OK;
 }

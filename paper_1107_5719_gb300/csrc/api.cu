@@ -38,6 +38,10 @@ struct rt_ctx {
     // padded step offsets; sum of the quadrature weights
     float4* node4 = nullptr;
     float2* b2 = nullptr;
+    // LTE-diffusion inner boundary: dB/dtau of the bottom nodes (FP64, padded FP32)
+    double* gdiff = nullptr;
+    float* g2 = nullptr;
+    bool gdiff_valid = false;
     int* poff = nullptr;
     double wsum = 1.0;
     // direction tables
@@ -129,7 +133,7 @@ void free_grid_buffers(rt_ctx* c)
     dfree(c->chi); dfree(c->eps); dfree(c->B); dfree(c->J); dfree(c->S);
     dfree(c->Jfs); dfree(c->Jn); dfree(c->Ja); dfree(c->Jb); dfree(c->r);
     dfree(c->lstar); dfree(c->coef); dfree(c->rdiag); dfree(c->partial);
-    dfree(c->node4); dfree(c->b2);
+    dfree(c->node4); dfree(c->b2); dfree(c->gdiff); dfree(c->g2);
     free_ng(c);
     c->partial_groups = 0;
 }
@@ -237,6 +241,7 @@ View32 view32(rt_ctx* c)
     v.g = c->g;
     v.node = c->node4;
     v.b2 = c->b2;
+    v.g2 = c->g2;
     v.info = c->info;
     v.off = c->off;
     v.poff = c->poff;
@@ -253,6 +258,12 @@ int fs_prepare(rt_ctx* c)
 {
     int rc = ensure_partial(c);
     if (rc) return rc;
+    if (c->g.bottom_bc == RT_BC_DIFFUSION && !c->gdiff_valid) {
+        CK(launch_diffusion_grad(c->g, c->dz, c->chi, c->B, c->gdiff,
+                                 c->precision == RT_FP64 ? nullptr : c->g2, c->stream));
+        c->gdiff_valid = true;
+        c->stats.launches += 1;
+    }
     if (c->precision != RT_FP64 && !c->b2_valid) {
         CK(launch_pack_b2(c->g, c->B, c->b2, c->stream));
         c->b2_valid = true;
@@ -289,8 +300,8 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
     const double cut = cut_of(c);
     if (c->profiling) CK(cudaEventRecord(c->ev[0], c->stream));
     if (c->precision == RT_FP64) {
-        CK(launch_fs64(c->g, c->chi, c->S, c->B, c->info, c->off, c->bw, c->scal + 0, cut, G,
-                       c->partial, count_steps ? c->d_steps : nullptr, c->stream));
+        CK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->scal + 0,
+                       cut, G, c->partial, count_steps ? c->d_steps : nullptr, c->stream));
     } else {
         CK(launch_fs32d(view32(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
     }
@@ -668,8 +679,8 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
     } else {
         for (int p : act) {
             rt_ctx* c = b->ctx[p];
-            BCK(launch_fs64(c->g, c->chi, c->S, c->B, c->info, c->off, c->bw, c->scal + 0,
-                            cut_of(c), G, c->partial, b->d_steps, b->stream));
+            BCK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw,
+                            c->scal + 0, cut_of(c), G, c->partial, b->d_steps, b->stream));
             b->stats.fs_launches += 1;
             b->stats.launches += 1;
         }
@@ -833,9 +844,11 @@ int rt_set_grid(rt_ctx* c, int nx, int ny, int nz, double dx, double dy, double 
     CK(dalloc(c->S, N)); CK(dalloc(c->Jfs, N)); CK(dalloc(c->Jn, N)); CK(dalloc(c->Ja, N));
     CK(dalloc(c->Jb, N)); CK(dalloc(c->r, N)); CK(dalloc(c->rdiag, N));
     CK(dalloc(c->lstar, 27 * N)); CK(dalloc(c->coef, 27 * N));
+    CK(dalloc(c->gdiff, (size_t)nx * ny));
     if (c->precision != RT_FP64) {
         CK(dalloc(c->node4, 4 * N));
         CK(dalloc(c->b2, (size_t)8 * nx * ny));
+        CK(dalloc(c->g2, (size_t)4 * nx * ny));
     }
     c->have_grid = true;
     return RT_OK;
@@ -846,10 +859,11 @@ int rt_set_boundary(rt_ctx* c, int top_mode, int bottom_mode)
     int rc = enter(c);
     if (rc) return rc;
     if ((top_mode != RT_BC_ZERO && top_mode != RT_BC_PLANCK) ||
-        (bottom_mode != RT_BC_ZERO && bottom_mode != RT_BC_PLANCK))
-        return fail(c, RT_EINVAL, "boundary modes must be RT_BC_ZERO or RT_BC_PLANCK");
+        (bottom_mode != RT_BC_ZERO && bottom_mode != RT_BC_PLANCK && bottom_mode != RT_BC_DIFFUSION))
+        return fail(c, RT_EINVAL, "boundary modes: top ZERO or PLANCK, bottom ZERO, PLANCK or DIFFUSION");
     c->g.top_bc = top_mode;
     c->g.bottom_bc = bottom_mode;
+    c->gdiff_valid = false;
     return RT_OK;
 }
 
@@ -899,7 +913,7 @@ static int set_chi(rt_ctx* c, const double* chi, bool device)
     int rc = set_field(c, chi, c ? c->chi : nullptr, device, "chi", true, false);
     if (rc) return rc;
     c->have_chi = true;
-    c->lstar_valid = c->coef_valid = false;
+    c->lstar_valid = c->coef_valid = c->gdiff_valid = false;
     return RT_OK;
 }
 
@@ -920,7 +934,7 @@ static int set_B(rt_ctx* c, const double* B, bool device)
     c->ng_count = 1;
     c->ng_last_delta = 0.0;
     c->have_B = true;
-    c->b2_valid = false;
+    c->b2_valid = c->gdiff_valid = false;
     return RT_OK;
 }
 

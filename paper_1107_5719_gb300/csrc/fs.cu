@@ -62,7 +62,8 @@ __global__ void k_dir_tables(Geometry g, double dx, double dy, double dz,
         DirInfo di;
         di.hs = dz / (2.0 * amu);
         di.hs32 = (float)di.hs;
-        di.pad = 0.f;
+        di.amu = amu;
+        di.amu32 = (float)amu;
         di.w = w[d];
         di.sgn = m_u > 0.0 ? 1 : -1;
         // Lambda* offsets of the four nodes of p_1 (plane k0 - sgn).
@@ -114,7 +115,8 @@ __device__ __forceinline__ void add_steps(unsigned long long* steps, unsigned lo
 // are then added in slot order, so J does not depend on gridDim.z.
 __global__ void __launch_bounds__(kThreads)
 k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
-       const double* __restrict__ B, const DirInfo* __restrict__ info,
+       const double* __restrict__ B, const double* __restrict__ G,
+       const DirInfo* __restrict__ info,
        const StepGeo* __restrict__ off, const Bw4d* __restrict__ bw,
        const double* __restrict__ smax_p, double cut, double* __restrict__ partial,
        unsigned long long* __restrict__ steps)
@@ -161,10 +163,13 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                         break;
                     }
                 }
-                if (!early && (s > 0 ? g.top_bc : g.bottom_bc)) {
+                const int bc = s > 0 ? g.top_bc : g.bottom_bc;
+                if (!early && bc) {
                     const long long pb = (long long)(k0 - M * s) * nxy;
                     const Nodes n = nodes_of(i0, j0, od[M], nx, ny);
-                    I = fma(T, bilin(B + pb, n, bd[M]), I);
+                    double ibc = bilin(B + pb, n, bd[M]);
+                    if (bc == 2) ibc = fma(di.amu, bilin(G, n, bd[M]), ibc);  // B + |mu| dB/dtau
+                    I = fma(T, ibc, I);
                 }
                 nsteps += (unsigned long long)m;
                 Jp = fma(di.w, I, Jp);
@@ -237,6 +242,31 @@ k_lstar64(Geometry g, const double* __restrict__ chi, const DirInfo* __restrict_
     for (int o = 0; o < 27; ++o) lstar[(long long)o * g.N + v] = lam[o][threadIdx.x];
 }
 
+// dB/dtau at the bottom nodes for the LTE-diffusion inner boundary
+// (Sect. 3.1 item 4): vertical difference over the trapezoid optical depth
+// between the two deepest planes; also the padded FP32 copy.
+__global__ void k_diffusion_grad(Geometry g, double dz, const double* __restrict__ chi,
+                                 const double* __restrict__ B, double* __restrict__ G,
+                                 float* __restrict__ g2)
+{
+    const int nx = g.nx, ny = g.ny, nxy = nx * ny;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nxy; t += gridDim.x * blockDim.x) {
+        const long long a = (long long)(g.nz - 1) * nxy + t, b = (long long)(g.nz - 2) * nxy + t;
+        const double v = (B[a] - B[b]) / (dz * (chi[a] + chi[b]) / 2.0);
+        G[t] = v;
+        if (g2) {
+            const int i = t % nx, j = t / nx;
+            const long long W = 2LL * nx;
+            float* p = g2 + (long long)j * W + i;
+            const float f = (float)v;
+            p[0] = f;
+            p[nx] = f;
+            p[(long long)ny * W] = f;
+            p[(long long)ny * W + nx] = f;
+        }
+    }
+}
+
 // Diagnostic: the segment weights the marches use, at given optical depths.
 __global__ void k_seg_eval(long long n, int fp32, const double* __restrict__ x,
                            double* __restrict__ wc, double* __restrict__ wu,
@@ -271,13 +301,13 @@ cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz
 }
 
 cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, const double* B,
-                        const DirInfo* info, const StepGeo* off, const Bw4d* bw,
-                        const double* smax, double cut, int groups, double* partial,
-                        unsigned long long* steps, cudaStream_t st)
+                        const double* G, const DirInfo* info, const StepGeo* off,
+                        const Bw4d* bw, const double* smax, double cut, int groups,
+                        double* partial, unsigned long long* steps, cudaStream_t st)
 {
     const int nxy = g.nx * g.ny;
     dim3 grid((nxy + kThreads - 1) / kThreads, g.nz, groups);
-    k_fs64<<<grid, kThreads, 0, st>>>(g, chi, S, B, info, off, bw, smax, cut, partial, steps);
+    k_fs64<<<grid, kThreads, 0, st>>>(g, chi, S, B, G, info, off, bw, smax, cut, partial, steps);
     return cudaGetLastError();
 }
 
@@ -288,6 +318,14 @@ cudaError_t launch_sum_groups(long long N, const double* partial, double* J,
     long long blocks = (N + threads - 1) / threads;
     if (blocks > 65535LL * 16) blocks = 65535LL * 16;
     k_sum_groups<<<(unsigned)blocks, threads, 0, st>>>(N, partial, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diffusion_grad(const Geometry& g, double dz, const double* chi,
+                                  const double* B, double* G, float* g2, cudaStream_t st)
+{
+    const int nxy = g.nx * g.ny;
+    k_diffusion_grad<<<(nxy + 255) / 256, 256, 0, st>>>(g, dz, chi, B, G, g2);
     return cudaGetLastError();
 }
 

@@ -169,15 +169,22 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                 if (!early) {
                     // boundary term T_M (I_bc - S_0), added with its rounding error
                     float inc, inc_lo;
-                    if (s > 0 ? g.top_bc : g.bottom_bc) {
+                    const int bc = s > 0 ? g.top_bc : g.bottom_bc;
+                    if (bc) {
                         const StepGeo o = p.off[(long long)d * nz + M];
                         const float4 b = bd[M];
-                        const float2* pb = p.b2 + (s > 0 ? 0LL : P) + (j0 + o.oy) * W + (i0 + o.ox);
+                        const long long ip = (j0 + o.oy) * W + (i0 + o.ox);
+                        const float2* pb = p.b2 + (s > 0 ? 0LL : P) + ip;
                         const float2 c00 = pb[0], c10 = pb[1], c01 = pb[W], c11 = pb[W + 1];
                         const float h = b.x * (c00.x - s0h) + b.y * (c10.x - s0h) +
                                         b.z * (c01.x - s0h) + b.w * (c11.x - s0h);
                         const float l = b.x * c00.y + b.y * c10.y + b.z * c01.y + b.w * c11.y;
-                        const float ibc = h + (l - s0l);
+                        float ibc = h + (l - s0l);
+                        if (bc == 2) {   // + |mu| dB/dtau (LTE diffusion)
+                            const float* pg = p.g2 + ip;
+                            ibc = fmaf(di.amu32,
+                                       b.x * pg[0] + b.y * pg[1] + b.z * pg[W] + b.w * pg[W + 1], ibc);
+                        }
                         inc = T * ibc;
                         inc_lo = fmaf(T, ibc, -inc);
                     } else {

@@ -20,7 +20,8 @@ struct DirInfo {
     int sgn;        // +1: propagates to larger k (entered at the top), -1: from the bottom
     int lo[4];      // Lambda* offset index of the four bilinear nodes of p_1, -1 if none
     float hs32;     // hs in FP32 (sweep form)
-    float pad;
+    float amu32;    // |mu| in FP32
+    double amu;     // |mu| (LTE-diffusion boundary)
 };
 
 // Per-(direction, step m) lattice geometry.  The upstream point p_m of voxel
@@ -51,10 +52,16 @@ cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz
 
 // FP64 formal solution: partial[kSlots][N]; `groups` (1..kSlots) is the
 // number of z-blocks walking the slots (a tuning knob, no effect on J).
+// G[ny][nx]: dB/dtau at the bottom nodes (LTE-diffusion inner boundary),
+// read only when bottom_bc == 2 (may be null otherwise).
 cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, const double* B,
-                        const DirInfo* info, const StepGeo* off, const Bw4d* bw,
-                        const double* smax, double cut, int groups, double* partial,
-                        unsigned long long* steps, cudaStream_t st);
+                        const double* G, const DirInfo* info, const StepGeo* off,
+                        const Bw4d* bw, const double* smax, double cut, int groups,
+                        double* partial, unsigned long long* steps, cudaStream_t st);
+// G[j][i] = (B[nz-1] - B[nz-2]) / (dz (chi[nz-1] + chi[nz-2]) / 2), and its
+// padded FP32 copy g2[2ny][2nx] if g2 != null.
+cudaError_t launch_diffusion_grad(const Geometry& g, double dz, const double* chi,
+                                  const double* B, double* G, float* g2, cudaStream_t st);
 
 // ---- FP32-sweep form (fs32.cu) ---------------------------------------------
 // poff[d][m]: offset of the upstream node (x0, y0) of step m in the padded
@@ -71,6 +78,7 @@ struct View32 {
     Geometry g;
     const float4* node;     // padded {chi, S_hi, S_lo, 0}
     const float2* b2;       // padded boundary {B_hi, B_lo}
+    const float* g2;        // padded dB/dtau of the bottom nodes (diffusion boundary)
     const DirInfo* info;
     const StepGeo* off;
     const int* poff;

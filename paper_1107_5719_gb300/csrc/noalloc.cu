@@ -130,7 +130,8 @@ extern "C" int rt_formal_solution_noalloc(int nx, int ny, int nz, double dx, dou
     // The cutoff bound is a max-reduction: it must start from zero on every call.
     if (cudaMemsetAsync(smax, 0, sizeof(double), st)) return RT_ECUDA;
     if (launch_absmax(N, S, planck ? B : nullptr, smax, nullptr, st)) return RT_ECUDA;
-    if (launch_fs64(g, chi, S, B, info, off, bw, smax, 1e-17, G, partial, nullptr, st)) return RT_ECUDA;
+    if (launch_fs64(g, chi, S, B, nullptr, info, off, bw, smax, 1e-17, G, partial, nullptr, st))
+        return RT_ECUDA;
     if (launch_sum_groups(N, partial, J_fs, st)) return RT_ECUDA;
     return RT_OK;
 }

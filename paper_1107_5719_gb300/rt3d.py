@@ -21,7 +21,7 @@ import numpy as np
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_ETIMEOUT, RT_ESTATE, RT_ESCRATCH = range(8)
 RT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 RT_FP64, RT_FP32_SWEEP = 0, 1
-RT_BC_ZERO, RT_BC_PLANCK = 0, 1
+RT_BC_ZERO, RT_BC_PLANCK, RT_BC_DIFFUSION = 0, 1, 2
 
 _NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV",
           5: "RT_ETIMEOUT", 6: "RT_ESTATE", 7: "RT_ESCRATCH"}

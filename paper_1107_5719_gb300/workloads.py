@@ -29,6 +29,7 @@ import numpy as np
 
 BC_ZERO = 0     # incoming intensity 0 (outer boundary, Sect. 3.1 item 4)
 BC_PLANCK = 1   # incoming intensity B at the entry point (inner boundary)
+BC_DIFFUSION = 2  # inner boundary only: B + |mu| dB/dtau (LTE diffusion, Sect. 3.1 item 4)
 
 SEED_BASE = 1234
 

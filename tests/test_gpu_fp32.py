@@ -51,9 +51,10 @@ def test_fs32_matches_oracle(R, oracle_mod, shape, seed):
     assert np.all(np.abs(L - Lo).reshape(27, -1).max(axis=0) <= 1e-12 * scale)
 
 
-def test_fs32_both_boundary_modes_and_spacings(R, oracle_mod):
-    p = W.random_slab(11, 7, 8, n_theta=4, n_phi=6, seed=9, top_bc=W.BC_PLANCK,
-                      bottom_bc=W.BC_ZERO, dx=0.6, dy=1.4, dz=0.8)
+@pytest.mark.parametrize("top,bottom", [(W.BC_PLANCK, W.BC_ZERO), (W.BC_ZERO, W.BC_DIFFUSION)])
+def test_fs32_both_boundary_modes_and_spacings(R, oracle_mod, top, bottom):
+    p = W.random_slab(11, 7, 8, n_theta=4, n_phi=6, seed=9, top_bc=top,
+                      bottom_bc=bottom, dx=0.6, dy=1.4, dz=0.8)
     S = p.B * 0.7
     with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
         J, _ = s.formal_solution(S, want_lstar=False)

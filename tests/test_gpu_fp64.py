@@ -46,6 +46,8 @@ CASES = [
     dict(nx=13, ny=11, nz=7, seed=5, dx=0.7, dy=1.3, dz=0.9),
     dict(nx=12, ny=7, nz=9, seed=6, top_bc=W.BC_PLANCK, bottom_bc=W.BC_ZERO),
     dict(nx=6, ny=6, nz=8, seed=7, top_bc=W.BC_ZERO, bottom_bc=W.BC_ZERO, chi_decades=6.0),
+    dict(nx=10, ny=7, nz=6, seed=8, bottom_bc=W.BC_DIFFUSION),      # LTE-diffusion inner boundary
+    dict(nx=5, ny=4, nz=2, seed=9, top_bc=W.BC_PLANCK, bottom_bc=W.BC_DIFFUSION, dz=0.6),
 ]
 
 
@@ -174,6 +176,26 @@ def test_converged_solve_tolerance_driven_inner(R, oracle_mod):
     assert r["converged"] and r["iters"] == ro["iters"]
     assert np.array_equal(r["sweeps"], ro["sweeps"])
     assert np.allclose(r["J"], ro["J"], rtol=RTOL, atol=0)
+
+
+def test_converged_solve_with_diffusion_boundary(R, oracle_mod):
+    p = W.random_slab(9, 8, 10, n_theta=6, n_phi=4, seed=55, eps_range=(1e-3, 1.0),
+                      bottom_bc=W.BC_DIFFUSION)
+    ro = oracle_mod.solve(p, tol=1e-9, max_iter=400, tol_inner=0.0, max_sweeps=12)
+    with R.Solver(p) as s:
+        r = s.solve(tol=1e-9, max_iter=400, tol_inner=0.0, max_sweeps=12)
+    assert r["converged"] and ro["converged"] and r["iters"] == ro["iters"]
+    assert np.allclose(r["J"], ro["J"], rtol=RTOL, atol=0)
+
+
+def test_diffusion_boundary_rejected_at_the_top(R):
+    ctx = R.rt_create(0, R.RT_FP64)
+    try:
+        with pytest.raises(R.RtError) as e:
+            R.rt_set_boundary(ctx, R.RT_BC_DIFFUSION, R.RT_BC_PLANCK)
+        assert e.value.code == R.RT_EINVAL
+    finally:
+        R.rt_destroy(ctx)
 
 
 def test_pure_absorption_limit(R, oracle_mod):

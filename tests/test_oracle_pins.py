@@ -110,6 +110,29 @@ def test_pure_absorption_linear_chi_exact_tau(oracle_mod):
             assert abs(I - Iref) <= 2e-15 + 1e-14 * Iref
 
 
+def test_diffusion_boundary_exact_for_linear_planck(oracle_mod):
+    """Pure absorption, constant chi, B linear in optical depth,
+    B = a + c tau: the diffusion approximation I = B + |mu| dB/dtau is then
+    the exact upward intensity, so with the LTE-diffusion inner boundary
+    every upward ray at every depth gives B(tau_0) + |mu| c (the
+    linear-source march is exact for a linear source)."""
+    nx, ny, nz = 4, 3, 10
+    chi, a, c, dz = 0.7, 2.0, 0.45, 1.3
+    k = np.arange(nz, dtype=float)
+    tau = chi * dz * k
+    mu, phi, w = W.quadrature(8, 3)
+    p = _problem(nx, ny, nz, chi, (a + c * tau)[:, None, None], mu, phi, w, dz=dz,
+                 bottom=W.BC_DIFFUSION)
+    S = p.B.copy()
+    for d in range(len(mu)):
+        if mu[d] > 0:
+            continue
+        for k0 in range(nz):
+            I = oracle_mod.intensity(p, S, mu[d], phi[d], 1, 2, k0)
+            ref = a + c * tau[k0] + abs(mu[d]) * c
+            assert abs(I - ref) <= 1e-13 * ref, (d, k0, I, ref)
+
+
 # ------------------------------------- 1D rays with an exactly integrated source
 
 def _ray_reference(chi_k, S_k, k0, mu, dz, Ibc):
@@ -486,6 +509,10 @@ _MUTANTS = {
     "ng_coefficients_swapped": ("for (long i = 0; i < N; ++i) out[i] = (1.0 - a - b) * x0[i] + a * x1[i] + b * x2[i];",
                                 "for (long i = 0; i < N; ++i) out[i] = (1.0 - a - b) * x0[i] + b * x1[i] + a * x2[i];"),
     "ng_unweighted_cross_term": ("a12 += w * q1 * q2;", "a12 += q1 * q2;"),
+    "diffusion_without_mu": ("if (bc == 2) I += fabs(mu) * diffusion_gradient_at(g, chi, B, xM, yM);",
+                             "if (bc == 2) I += diffusion_gradient_at(g, chi, B, xM, yM);"),
+    "diffusion_gradient_sign": ("long a = vidx(g, i, j, g->nz - 1), b = vidx(g, i, j, g->nz - 2);",
+                                "long b = vidx(g, i, j, g->nz - 1), a = vidx(g, i, j, g->nz - 2);"),
 }
 
 
@@ -501,6 +528,7 @@ def _pin_battery(mod):
         ("os_step", lambda: test_os_step_solves_its_linear_system(mod)),
         ("ali", lambda: test_converged_ali_equals_dense_solution(mod)),
         ("ng", lambda: test_ng_extrapolation_exact_for_two_geometric_modes(mod)),
+        ("diffusion", lambda: test_diffusion_boundary_exact_for_linear_planck(mod)),
     ]
     for name, fn in pins:
         try:
