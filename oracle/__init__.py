@@ -8,7 +8,8 @@ baseline leg of the benchmark may import it; the GPU library never does.
 Sections of Hauschildt & Baron (2011) that each function follows:
   formal_solution     Sect. 2.2 (formal solution, J and Lambda*)
   intensity           Sect. 2.2 (intensity along one characteristic)
-  os_step             Sect. 2.3 (operator splitting, Jordan iterations)
+  os_step             Sect. 2.3 (operator splitting, Jordan iterations or
+                      red-black Gauss-Seidel)
   solve               Sect. 2 (outer iteration, optional Ng acceleration),
                       Sect. 3.1 item 5 (S)
   ng_step             Sect. 2 (Ng acceleration of the outer iteration)
@@ -69,6 +70,8 @@ def _configure(lib):
                               C.c_double, C.c_int, C.c_int, P, P,
                               C.POINTER(C.c_int), P, C.POINTER(C.c_int), C.c_int]
     lib.orc_solve_ng.argtypes = lib.orc_solve.argtypes + [C.c_int, C.c_double]
+    lib.orc_solve_os.argtypes = lib.orc_solve_ng.argtypes + [C.c_int]
+    lib.orc_os_step_method.argtypes = lib.orc_os_step.argtypes + [C.c_int]
     lib.orc_ng_step.argtypes = [C.c_long, P, P, P, P, P, P, P]
     return lib
 
@@ -150,8 +153,11 @@ def mean_intensity_at(p, S, voxels, nthreads: int = 0):
     return out
 
 
-def os_step(p, lstar, J_fs, J_old, tol_inner=1e-12, max_sweeps=1000):
-    """Return (J_new, sweeps)."""
+JACOBI, GAUSS_SEIDEL = 0, 1
+
+
+def os_step(p, lstar, J_fs, J_old, tol_inner=1e-12, max_sweeps=1000, method=JACOBI):
+    """Return (J_new, sweeps); method JACOBI or GAUSS_SEIDEL (red-black)."""
     lib = _load()
     g = _grid(p)
     L, pl = _d(lstar)
@@ -160,8 +166,9 @@ def os_step(p, lstar, J_fs, J_old, tol_inner=1e-12, max_sweeps=1000):
     Jo, po = _d(J_old)
     Jn = np.empty_like(Jo)
     ns = C.c_int()
-    rc = lib.orc_os_step(C.byref(g), pl, pe, pf, po, Jn.ctypes.data_as(C.POINTER(C.c_double)),
-                         float(tol_inner), int(max_sweeps), C.byref(ns))
+    rc = lib.orc_os_step_method(C.byref(g), pl, pe, pf, po,
+                                Jn.ctypes.data_as(C.POINTER(C.c_double)),
+                                float(tol_inner), int(max_sweeps), C.byref(ns), int(method))
     if rc:
         raise ValueError(f"oracle os_step rejected its input ({rc})")
     return Jn, ns.value
@@ -184,8 +191,9 @@ def ng_step(x0, x1, x2, x3):
 
 def solve(p, tol=None, max_iter=500, tol_inner=1e-12, max_sweeps=1000, J0=None,
           nthreads: int = 0, want_lstar: bool = False, ng_period: int = 0,
-          ng_min_delta: float = 0.0):
-    """Outer iteration (Ng acceleration every ng_period iterations if > 0).
+          ng_min_delta: float = 0.0, os_method: int = JACOBI):
+    """Outer iteration (Ng acceleration every ng_period iterations if > 0;
+    operator splitting by os_method, JACOBI or GAUSS_SEIDEL).
     Returns a dict with J, iters, deltas, sweeps, converged (and lstar if
     asked)."""
     lib = _load()
@@ -202,13 +210,13 @@ def solve(p, tol=None, max_iter=500, tol_inner=1e-12, max_sweeps=1000, J0=None,
     sweeps = np.zeros(max_iter, dtype=np.int32)
     iters = C.c_int()
     tol = p.tol if tol is None else tol
-    rc = lib.orc_solve_ng(C.byref(g), pc, pe, pb, len(mu), pm, pp, pw, float(tol),
+    rc = lib.orc_solve_os(C.byref(g), pc, pe, pb, len(mu), pm, pp, pw, float(tol),
                           int(max_iter), float(tol_inner), int(max_sweeps),
                           1 if J0 is not None else 0, J.ctypes.data_as(C.POINTER(C.c_double)),
                           L.ctypes.data_as(C.POINTER(C.c_double)) if want_lstar else None,
                           C.byref(iters), deltas.ctypes.data_as(C.POINTER(C.c_double)),
                           sweeps.ctypes.data_as(C.POINTER(C.c_int)), nthreads, int(ng_period),
-                          float(ng_min_delta))
+                          float(ng_min_delta), int(os_method))
     if rc not in (OK, NOTCONV):
         raise ValueError(f"oracle solve rejected its input ({rc})")
     n = iters.value

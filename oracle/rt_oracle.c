@@ -65,6 +65,15 @@
  *     (1 - Lambda* D) J_new = J_fs - Lambda* D J_old ,
  *   by Jacobi sweeps started from J_old, stopped when
  *   max_i |J^{n+1}_i - J^n_i| / |J^{n+1}_i| < tol_inner or after max_sweeps.
+ *   Gauss-Seidel variant (the paper's host code offers it beside the
+ *   Jordan method, Sect. 2.3) in red-black order: voxel (i,j,k) is red if
+ *   i+j+k is even, black otherwise.  One sweep first updates every red voxel
+ *   from the values at the start of the sweep, then every black voxel from
+ *   the new red and the old black values.  Within one colour the updates
+ *   are simultaneous (the 27-point stencil couples voxels of equal colour
+ *   through its edge offsets and, for odd nx or ny, across the periodic
+ *   seam), so the result does not depend on the visiting order.  The
+ *   stopping test is the Jacobi one, over all voxels of the sweep.
  *
  *  Outer iteration.  J^0 = B unless given; S = eps B + (1-eps) J; formal
  *   solution -> J_fs (Lambda* on the first pass); operator splitting ->
@@ -366,17 +375,42 @@ static long neighbour_index(const orc_grid *g, long v, int o)
     return vidx(g, wrapi(i0 + ox, g->nx), wrapi(j0 + oy, g->ny), kk);
 }
 
-/* Operator-splitting step, Jacobi ("Jordan") iterations from J_old. */
-int orc_os_step(const orc_grid *g, const double *lstar, const double *eps,
-                const double *J_fs, const double *J_old, double *J_new,
-                double tol_inner, int max_sweeps, int *sweeps_out)
+/* New value of voxel v from the current iterate X (all offsets but the
+ * centre), given the right-hand side rhs[v]. */
+static double os_update(const orc_grid *g, const double *lstar, const double *eps,
+                        const double *rhs, const double *X, long v, long N)
 {
-    if (check_grid(g) || max_sweeps < 1) return ORC_EINVAL;
+    double acc = rhs[v];
+    for (int o = 0; o < 27; ++o) {
+        if (o == 13) continue;
+        long j = neighbour_index(g, v, o);
+        if (j >= 0) acc += lstar[(long)o * N + v] * (1.0 - eps[j]) * X[j];
+    }
+    return acc / (1.0 - lstar[13L * N + v] * (1.0 - eps[v]));
+}
+
+static int colour_of(const orc_grid *g, long v)
+{
+    long i = v % g->nx, j = (v / g->nx) % g->ny, k = v / ((long)g->nx * g->ny);
+    return (int)((i + j + k) & 1);
+}
+
+/* Operator-splitting step from J_old: Jacobi ("Jordan") sweeps (method 0)
+ * or red-black Gauss-Seidel sweeps (method 1). */
+int orc_os_step_method(const orc_grid *g, const double *lstar, const double *eps,
+                       const double *J_fs, const double *J_old, double *J_new,
+                       double tol_inner, int max_sweeps, int *sweeps_out, int method)
+{
+    if (check_grid(g) || max_sweeps < 1 || method < 0 || method > 1) return ORC_EINVAL;
     long N = (long)g->nx * g->ny * g->nz;
     double *rhs = malloc(sizeof(double) * N);
     double *Jc = malloc(sizeof(double) * N);
     double *Jn = malloc(sizeof(double) * N);
-    if (!rhs || !Jc || !Jn) { free(rhs); free(Jc); free(Jn); return ORC_ENOMEM; }
+    double *upd = malloc(sizeof(double) * N);
+    if (!rhs || !Jc || !Jn || !upd) {
+        free(rhs); free(Jc); free(Jn); free(upd);
+        return ORC_ENOMEM;
+    }
     for (long v = 0; v < N; ++v) {
         double r = J_fs[v];
         for (int o = 0; o < 27; ++o) {
@@ -388,15 +422,20 @@ int orc_os_step(const orc_grid *g, const double *lstar, const double *eps,
     }
     int sweeps = 0;
     for (int n = 0; n < max_sweeps; ++n) {
+        if (method == 0) {
+            for (long v = 0; v < N; ++v) Jn[v] = os_update(g, lstar, eps, rhs, Jc, v, N);
+        } else {
+            /* red from the old values; then black from new red + old black */
+            memcpy(Jn, Jc, sizeof(double) * N);
+            for (int colour = 0; colour < 2; ++colour) {
+                for (long v = 0; v < N; ++v)
+                    if (colour_of(g, v) == colour) upd[v] = os_update(g, lstar, eps, rhs, Jn, v, N);
+                for (long v = 0; v < N; ++v)
+                    if (colour_of(g, v) == colour) Jn[v] = upd[v];
+            }
+        }
         double delta = 0.0;
         for (long v = 0; v < N; ++v) {
-            double acc = rhs[v];
-            for (int o = 0; o < 27; ++o) {
-                if (o == 13) continue;
-                long j = neighbour_index(g, v, o);
-                if (j >= 0) acc += lstar[(long)o * N + v] * (1.0 - eps[j]) * Jc[j];
-            }
-            Jn[v] = acc / (1.0 - lstar[13L * N + v] * (1.0 - eps[v]));
             double rel = fabs(Jn[v] - Jc[v]) / fabs(Jn[v]);
             if (!(rel <= delta)) delta = rel;     /* NaN propagates */
         }
@@ -406,8 +445,17 @@ int orc_os_step(const orc_grid *g, const double *lstar, const double *eps,
     }
     memcpy(J_new, Jc, sizeof(double) * N);
     if (sweeps_out) *sweeps_out = sweeps;
-    free(rhs); free(Jc); free(Jn);
+    free(rhs); free(Jc); free(Jn); free(upd);
     return ORC_OK;
+}
+
+/* Operator-splitting step, Jacobi ("Jordan") iterations from J_old. */
+int orc_os_step(const orc_grid *g, const double *lstar, const double *eps,
+                const double *J_fs, const double *J_old, double *J_new,
+                double tol_inner, int max_sweeps, int *sweeps_out)
+{
+    return orc_os_step_method(g, lstar, eps, J_fs, J_old, J_new, tol_inner, max_sweeps,
+                              sweeps_out, 0);
 }
 
 /* Second-order Ng extrapolation (see header).  Returns 0, or 1 if the 2x2
@@ -452,6 +500,13 @@ int orc_solve_ng(const orc_grid *g, const double *chi, const double *eps,
                  double *lstar_out, int *iters_out, double *deltas, int *sweeps,
                  int nthreads, int ng_period, double ng_min_delta);
 
+int orc_solve_os(const orc_grid *g, const double *chi, const double *eps,
+                 const double *B, int ndir, const double *mu, const double *phi,
+                 const double *w, double tol, int max_iter, double tol_inner,
+                 int max_sweeps, int use_initial, double *J_inout,
+                 double *lstar_out, int *iters_out, double *deltas, int *sweeps,
+                 int nthreads, int ng_period, double ng_min_delta, int os_method);
+
 int orc_solve(const orc_grid *g, const double *chi, const double *eps,
               const double *B, int ndir, const double *mu, const double *phi,
               const double *w, double tol, int max_iter, double tol_inner,
@@ -473,7 +528,22 @@ int orc_solve_ng(const orc_grid *g, const double *chi, const double *eps,
                  double *lstar_out, int *iters_out, double *deltas, int *sweeps,
                  int nthreads, int ng_period, double ng_min_delta)
 {
+    return orc_solve_os(g, chi, eps, B, ndir, mu, phi, w, tol, max_iter, tol_inner, max_sweeps,
+                        use_initial, J_inout, lstar_out, iters_out, deltas, sweeps, nthreads,
+                        ng_period, ng_min_delta, 0);
+}
+
+/* The same with the operator-splitting method chosen (0 Jacobi, 1 red-black
+ * Gauss-Seidel). */
+int orc_solve_os(const orc_grid *g, const double *chi, const double *eps,
+                 const double *B, int ndir, const double *mu, const double *phi,
+                 const double *w, double tol, int max_iter, double tol_inner,
+                 int max_sweeps, int use_initial, double *J_inout,
+                 double *lstar_out, int *iters_out, double *deltas, int *sweeps,
+                 int nthreads, int ng_period, double ng_min_delta, int os_method)
+{
     if (ng_period != 0 && ng_period < 4) return ORC_EINVAL;
+    if (os_method < 0 || os_method > 1) return ORC_EINVAL;
     if (check_grid(g) || check_dirs(ndir, mu) || max_iter < 1) return ORC_EINVAL;
     long N = (long)g->nx * g->ny * g->nz;
     double *J = malloc(sizeof(double) * N), *S = malloc(sizeof(double) * N);
@@ -493,7 +563,7 @@ int orc_solve_ng(const orc_grid *g, const double *chi, const double *eps,
         for (long v = 0; v < N; ++v) S[v] = eps[v] * B[v] + (1.0 - eps[v]) * J[v];
         orc_formal_solution(g, chi, S, B, ndir, mu, phi, w, Jfs, it == 1 ? L : NULL, nthreads);
         int ns = 0;
-        orc_os_step(g, L, eps, Jfs, J, Jn, tol_inner, max_sweeps, &ns);
+        orc_os_step_method(g, L, eps, Jfs, J, Jn, tol_inner, max_sweeps, &ns, os_method);
         if (ng_period) {
             /* history: hist[k] holds the iterate k steps back (k = 0 newest) */
             memmove(hist + N, hist, sizeof(double) * N * 3);

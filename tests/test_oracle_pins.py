@@ -366,6 +366,83 @@ def test_os_step_solves_its_linear_system(oracle_mod):
     assert np.allclose(Jn.ravel(), ref, rtol=1e-12, atol=0)
 
 
+def _os_dense(p, L, Jfs, Jold):
+    """(M, b) of the operator-splitting system M J_new = b in dense form."""
+    A = _dense_lstar(p, L)
+    Dg = np.diag(1 - p.eps.ravel())
+    return np.eye(p.nvox) - A @ Dg, Jfs.ravel() - A @ Dg @ Jold.ravel()
+
+
+def test_gauss_seidel_solves_its_linear_system(oracle_mod):
+    """Red-black Gauss-Seidel sweeps reach the same direct solution as the
+    Jacobi sweeps (Sect. 2.3), in fewer sweeps: the matrix 1 - Lambda* D is
+    an M-matrix (Lambda* >= 0, row sums < 1), for which the splitting that
+    takes the new values of the other colour converges at least as fast."""
+    p = W.random_slab(4, 5, 6, n_theta=4, n_phi=4, seed=21, eps_range=(1e-3, 1.0))
+    S = p.eps * p.B + (1 - p.eps) * p.B
+    Jfs, L = oracle_mod.formal_solution(p, S)
+    rng = np.random.default_rng(1)
+    Jold = p.B * (0.5 + rng.random(p.B.shape))
+    M, b = _os_dense(p, L, Jfs, Jold)
+    ref = np.linalg.solve(M, b)
+    Jj, nj = oracle_mod.os_step(p, L, Jfs, Jold, tol_inner=1e-14, max_sweeps=5000)
+    Jg, ng = oracle_mod.os_step(p, L, Jfs, Jold, tol_inner=1e-14, max_sweeps=5000,
+                                method=oracle_mod.GAUSS_SEIDEL)
+    assert np.allclose(Jg.ravel(), ref, rtol=1e-12, atol=0)
+    assert np.allclose(Jj.ravel(), ref, rtol=1e-12, atol=0)
+    assert 1 < ng < nj
+
+
+@pytest.mark.parametrize("shape,seed", [((4, 4, 3), 3), ((3, 5, 4), 4)])
+def test_gauss_seidel_sweep_equals_block_form(oracle_mod, shape, seed):
+    """One red-black sweep in the textbook block form: order the unknowns
+    red (i+j+k even) then black, split M = Dm - C (Dm its diagonal); then
+    x_r' = Dm_r^-1 (b_r + C_rr x_r + C_rb x_b),
+    x_b' = Dm_b^-1 (b_b + C_br x_r' + C_bb x_b).  Synthetic positive Lambda*
+    on all 27 offsets; shape (3, 5, 4) has odd periods, where equal colours
+    meet across the seam."""
+    nx, ny, nz = shape
+    p = W.random_slab(nx, ny, nz, n_theta=2, n_phi=1, seed=seed, eps_range=(1e-2, 1.0))
+    rng = np.random.default_rng(seed)
+    L = rng.random((27, nz, ny, nx)) * 0.03
+    L[:9, 0] = 0.0        # no plane above the top
+    L[18:, -1] = 0.0      # no plane below the bottom
+    Jfs = 1 + rng.random((nz, ny, nx))
+    Jold = 1 + rng.random((nz, ny, nx))
+    M, b = _os_dense(p, L, Jfs, Jold)
+    Dm = np.diag(M).copy()
+    Cm = np.diag(Dm) - M
+    kk, jj, ii = np.unravel_index(np.arange(p.nvox), (nz, ny, nx))
+    red = (ii + jj + kk) % 2 == 0
+    blk = ~red
+    x = Jold.ravel().copy()
+    xr = (b[red] + Cm[np.ix_(red, red)] @ x[red] + Cm[np.ix_(red, blk)] @ x[blk]) / Dm[red]
+    xb = (b[blk] + Cm[np.ix_(blk, red)] @ xr + Cm[np.ix_(blk, blk)] @ x[blk]) / Dm[blk]
+    ref = np.empty(p.nvox)
+    ref[red], ref[blk] = xr, xb
+    Jg, ns = oracle_mod.os_step(p, L, Jfs, Jold, tol_inner=0.0, max_sweeps=1,
+                                method=oracle_mod.GAUSS_SEIDEL)
+    assert ns == 1
+    assert np.allclose(Jg.ravel(), ref, rtol=1e-14, atol=0)
+    # the Jacobi sweep is the same block form with x_r' replaced by x_r
+    xbj = (b[blk] + Cm[np.ix_(blk, red)] @ x[red] + Cm[np.ix_(blk, blk)] @ x[blk]) / Dm[blk]
+    Jj, _ = oracle_mod.os_step(p, L, Jfs, Jold, tol_inner=0.0, max_sweeps=1)
+    assert np.allclose(Jj.ravel()[blk], xbj, rtol=1e-14, atol=0)
+    assert np.allclose(Jj.ravel()[red], xr, rtol=1e-14, atol=0)
+
+
+def test_gauss_seidel_ali_reaches_the_same_fixed_point(oracle_mod):
+    """The outer iteration with Gauss-Seidel operator splitting converges to
+    the same J as with Jacobi sweeps, with fewer inner sweeps."""
+    p = W.random_slab(5, 5, 5, n_theta=4, n_phi=5, seed=31, eps_range=(1e-2, 1.0))
+    rj = oracle_mod.solve(p, tol=1e-13, max_iter=400, tol_inner=1e-13, max_sweeps=2000)
+    rg = oracle_mod.solve(p, tol=1e-13, max_iter=400, tol_inner=1e-13, max_sweeps=2000,
+                          os_method=oracle_mod.GAUSS_SEIDEL)
+    assert rj["converged"] and rg["converged"]
+    assert np.allclose(rg["J"], rj["J"], rtol=1e-11, atol=0)
+    assert rg["sweeps"].sum() < rj["sweeps"].sum()
+
+
 def test_converged_ali_equals_dense_solution(oracle_mod):
     """The converged outer iteration is the unique fixed point
     J = Lambda (eps B + (1 - eps) J) + J_bc, solved directly with the
@@ -502,8 +579,13 @@ _MUTANTS = {
     "lstar_drops_upstream_term": ("if (m >= 1) c += T[m - 1] * wu[m - 1];", "(void)0;"),
     "os_forgets_destruction": ("r -= lstar[(long)o * N + v] * (1.0 - eps[j]) * J_old[j];",
                                "r -= lstar[(long)o * N + v] * J_old[j];"),
-    "os_diag_uses_neighbour_eps": ("Jn[v] = acc / (1.0 - lstar[13L * N + v] * (1.0 - eps[v]));",
-                                   "Jn[v] = acc / (1.0 - lstar[13L * N + v]);"),
+    "os_diag_uses_neighbour_eps": ("return acc / (1.0 - lstar[13L * N + v] * (1.0 - eps[v]));",
+                                   "return acc / (1.0 - lstar[13L * N + v]);"),
+    "gs_black_uses_old_red": ("upd[v] = os_update(g, lstar, eps, rhs, Jn, v, N);",
+                              "upd[v] = os_update(g, lstar, eps, rhs, Jc, v, N);"),
+    "gs_colour_ignores_depth": ("return (int)((i + j + k) & 1);", "return (int)((i + j) & 1);"),
+    "gs_sequential_within_colour": ("if (colour_of(g, v) == colour) upd[v] = os_update(g, lstar, eps, rhs, Jn, v, N);",
+                                    "if (colour_of(g, v) == colour) Jn[v] = upd[v] = os_update(g, lstar, eps, rhs, Jn, v, N);"),
     "source_function_sign": ("S[v] = eps[v] * B[v] + (1.0 - eps[v]) * J[v];",
                              "S[v] = eps[v] * J[v] + (1.0 - eps[v]) * B[v];"),
     "ng_coefficients_swapped": ("for (long i = 0; i < N; ++i) out[i] = (1.0 - a - b) * x0[i] + a * x1[i] + b * x2[i];",
@@ -526,6 +608,7 @@ def _pin_battery(mod):
         ("half_node", lambda: test_half_node_shift_splits_bilinearly(mod)),
         ("lstar", lambda: test_lstar_equals_brute_force_lambda(mod, (3, 4, 5), 12)),
         ("os_step", lambda: test_os_step_solves_its_linear_system(mod)),
+        ("gauss_seidel", lambda: test_gauss_seidel_sweep_equals_block_form(mod, (3, 5, 4), 4)),
         ("ali", lambda: test_converged_ali_equals_dense_solution(mod)),
         ("ng", lambda: test_ng_extrapolation_exact_for_two_geometric_modes(mod)),
         ("diffusion", lambda: test_diffusion_boundary_exact_for_linear_planck(mod)),
