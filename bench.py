@@ -338,6 +338,25 @@ def run_ours(args):
                             "flops_per_step": FLOPS_PER_STEP_FP32,
                             "note": "ncu: limited by L1 throughput, not the FP32 pipe"}
 
+    # the double-float form (FP64-accurate march on the FP32 pipes)
+    df64 = None
+    if args.df64_steps > 0:
+        rdf = timed_solves(R, p, R.RT_DF64, dev, stream, flush, 1, args.df64_steps,
+                           args.max_iter, ng=args.ng)
+        stdf = rdf["stats"]
+        msdf = float(sum(rdf["times"]))
+        fsdf_ms = stdf["fs_ms"] / max(stdf["fs_launches"], 1)
+        eq = FLOPS_PER_STEP_FP64 * stdf["steps"] / (stdf["fs_ms"] / 1e3) / 1e12 if stdf["fs_ms"] else 0.0
+        df64 = {"value": round(RP.weak_throughput(args.df64_steps, msdf)[0], 6), "unit": "solves/s",
+                "ms_per_step": round(msdf / args.df64_steps, 3),
+                "iters_per_solve": stdf["fs_launches"] / args.df64_steps,
+                "ms_per_fs_launch": round(fsdf_ms, 4),
+                "fs_steps_per_s": round(stdf["steps"] / (stdf["fs_ms"] / 1e3), 1) if stdf["fs_ms"] else None,
+                "fp64_equivalent_tflops": round(eq, 3),
+                "fp64_equivalent_frac_of_fp64_peak": round(eq / PEAK_FP64_TFLOPS, 3),
+                "max_rel_dev_from_fp64_J": float(np.max(np.abs(rdf["J"] - r64["J"]) / r64["J"])),
+                "speedup_vs_fp64": round(my_ms / args.steps / (msdf / args.df64_steps), 3)}
+
     e2e = None
     if args.e2e_steps > 0:
         v = e2e_solves(R, p, R.RT_FP64, dev, args.e2e_steps, args.max_iter, args.ng)
@@ -361,6 +380,7 @@ def run_ours(args):
         "iters_per_solve": round(fs_per_solve, 3),
         "roofline": roofline,
         "fp32_sweep": fp32,
+        "df64": df64,
         "gpu_launches": int(st["launches"]),
         "clocks": r64["clocks"],
         "e2e": e2e,
@@ -518,6 +538,7 @@ def main():
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--df64-steps", type=int, default=2)
     ap.add_argument("--ng", type=int, default=4,
                     help="Ng acceleration period of the outer iteration (0 = off)")
     ap.add_argument("--lambdas", type=int, default=512, help="wavelengths of the batch workload")

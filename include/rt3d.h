@@ -40,7 +40,10 @@
  *   intensity) runs in FP32 on FP32 copies of chi and S; J, Lambda*, the
  *   operator-splitting solve and the convergence test stay in FP64
  *   (Sect. 3.1: smaller eps needs double precision for the operator
- *   splitting equations).
+ *   splitting equations).  RT_DF64: the march runs in double-float
+ *   arithmetic (pairs of FP32 numbers, ~48 significant bits) on the FP32
+ *   pipes, to FP64-level accuracy; J, Lambda*, the operator splitting and
+ *   the convergence test are FP64.
  *
  *  Memory and ownership.  The caller owns every pointer it passes and
  *   every buffer it receives.  Host-pointer calls copy in and out and
@@ -80,16 +83,18 @@ typedef enum {
     RT_ESCRATCH = 7     /* too large for rt_formal_solution_noalloc's fixed scratch */
 } rt_status;
 
-enum { RT_FP64 = 0, RT_FP32_SWEEP = 1 };
+enum { RT_FP64 = 0, RT_FP32_SWEEP = 1, RT_DF64 = 2 };
 enum { RT_BC_ZERO = 0, RT_BC_PLANCK = 1, RT_BC_DIFFUSION = 2 };
+/* Operator-splitting methods (Sect. 2.3), see rt_set_os_method. */
+enum { RT_OS_JACOBI = 0, RT_OS_GAUSS_SEIDEL = 1 };
 
 typedef struct rt_ctx rt_ctx;
 
 /* Library version string (static storage). */
 const char *rt_version(void);
 
-/* Create a context on CUDA device `device` for precision RT_FP64 or
- * RT_FP32_SWEEP.  *ctx receives the handle (NULL on failure). */
+/* Create a context on CUDA device `device` for precision RT_FP64,
+ * RT_FP32_SWEEP or RT_DF64.  *ctx receives the handle (NULL on failure). */
 int rt_create(rt_ctx **ctx, int device, int precision);
 
 /* Free the context and every device buffer it owns.  NULL is accepted. */
@@ -187,6 +192,19 @@ int rt_last_step_count(rt_ctx *ctx, unsigned long long *steps);
  * extrapolation would amplify that noise.  delta is measured against the
  * extrapolated iterate.  period 0 (default) = off; otherwise >= 4. */
 int rt_set_ng(rt_ctx *ctx, int period, double min_delta);
+
+/* Operator-splitting method (Sect. 2.3 names the Jordan method and
+ * Gauss-Seidel iterations).  RT_OS_JACOBI (default): every sweep updates
+ * all voxels from the previous iterate.  RT_OS_GAUSS_SEIDEL: red-black
+ * order; voxel (i,j,k) is red if i+j+k is even; a sweep updates the red
+ * voxels from the iterate at its start, then the black voxels from the new
+ * red and the old black values (updates within a colour are simultaneous,
+ * so the result does not depend on thread order).  Both stop on the same
+ * test, max |J^{n+1} - J^n| / |J^{n+1}| < tol_inner, and solve the same
+ * system; the sweep counts reported are sweeps (two launches each for
+ * Gauss-Seidel).  Takes effect at the next operator-splitting step.
+ * RT_EINVAL for another value. */
+int rt_set_os_method(rt_ctx *ctx, int method);
 
 /* Tuning: the directions are summed into J in 8 fixed slots (direction d in
  * slot d mod 8, each slot in increasing d, then the slots in order), so J
@@ -297,6 +315,8 @@ int rt_batch_get_J_dev(rt_batch *batch, int p, double *J);
 int rt_batch_set_direction_groups(rt_batch *batch, int groups);
 /* As rt_set_ng, for every problem of the batch. */
 int rt_batch_set_ng(rt_batch *batch, int period, double min_delta);
+/* As rt_set_os_method, for every problem of the batch. */
+int rt_batch_set_os_method(rt_batch *batch, int method);
 
 /* Counters of this context since the last rt_reset_stats: kernel launches,
  * formal-solution march launches and their device time, Jacobi sweeps and

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt3d.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["fs.cu", "fs32.cu", "os.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["fs.cu", "fs32.cu", "fsdf.cu", "os.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
@@ -34,6 +34,7 @@ def nvcc() -> str:
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "weights.cuh"),
+              os.path.join(CSRC, "df.cuh"),
               os.path.join(INCLUDE, "rt3d.h")]
     return files
 

@@ -26,6 +26,7 @@ struct rt_ctx {
     double dx = 1, dy = 1, dz = 1;
     bool have_grid = false, have_quad = false, have_chi = false, have_eps = false, have_B = false;
     bool lstar_valid = false, coef_valid = false, b2_valid = false;
+    int os_method = RT_OS_JACOBI;
     int groups_req = 0;
     double cut = -1.0;
 
@@ -42,6 +43,9 @@ struct rt_ctx {
     double* gdiff = nullptr;
     float* g2 = nullptr;
     bool gdiff_valid = false;
+    // double-float march: df bilinear weights, df diffusion gradient
+    float4* bwdf = nullptr;
+    float2* g2df = nullptr;
     int* poff = nullptr;
     double wsum = 1.0;
     // direction tables
@@ -133,14 +137,14 @@ void free_grid_buffers(rt_ctx* c)
     dfree(c->chi); dfree(c->eps); dfree(c->B); dfree(c->J); dfree(c->S);
     dfree(c->Jfs); dfree(c->Jn); dfree(c->Ja); dfree(c->Jb); dfree(c->r);
     dfree(c->lstar); dfree(c->coef); dfree(c->rdiag); dfree(c->partial);
-    dfree(c->node4); dfree(c->b2); dfree(c->gdiff); dfree(c->g2);
+    dfree(c->node4); dfree(c->b2); dfree(c->gdiff); dfree(c->g2); dfree(c->g2df);
     free_ng(c);
     c->partial_groups = 0;
 }
 
 void free_tables(rt_ctx* c)
 {
-    dfree(c->info); dfree(c->off); dfree(c->bw); dfree(c->bw32); dfree(c->poff);
+    dfree(c->info); dfree(c->off); dfree(c->bw); dfree(c->bw32); dfree(c->poff); dfree(c->bwdf);
     dfree(c->d_mu); dfree(c->d_phi); dfree(c->d_w);
 }
 
@@ -167,9 +171,11 @@ int enter(rt_ctx* c)
 
 double default_cut(int precision)
 {
-    // FP32 sweep: the cut is relative to S at the voxel (see fs32.cu); 2^-46
-    // keeps the truncation far below what 1/eps can amplify at eps = 1e-6.
-    return precision == RT_FP64 ? 1e-17 : 1.4210854715202004e-14;
+    // FP32 sweep and double-float march: the cut is relative to S at the
+    // voxel (see fs32.cu); 2^-46 (2^-52) keeps the truncation far below what
+    // 1/eps can amplify at eps = 1e-6 (far below double-float rounding).
+    if (precision == RT_FP64) return 1e-17;
+    return precision == RT_DF64 ? 2.220446049250313e-16 : 1.4210854715202004e-14;
 }
 
 // Number of z-blocks that walk the kSlots direction slots: enough blocks to
@@ -251,6 +257,22 @@ View32 view32(rt_ctx* c)
     return v;
 }
 
+ViewDF viewdf(rt_ctx* c)
+{
+    ViewDF v;
+    v.g = c->g;
+    v.node = c->node4;
+    v.b2 = c->b2;
+    v.g2df = c->g2df;
+    v.info = c->info;
+    v.off = c->off;
+    v.poff = c->poff;
+    v.bw = c->bwdf;
+    v.smax = c->scal + 0;
+    v.partial = c->partial;
+    return v;
+}
+
 // Formal solution: source in c->S (already set), result J into Jout (device).
 // Pieces of one formal solution: per-problem preparation, the march itself,
 // and the reduction over direction slots plus (once per opacity) Lambda*.
@@ -260,9 +282,13 @@ int fs_prepare(rt_ctx* c)
     if (rc) return rc;
     if (c->g.bottom_bc == RT_BC_DIFFUSION && !c->gdiff_valid) {
         CK(launch_diffusion_grad(c->g, c->dz, c->chi, c->B, c->gdiff,
-                                 c->precision == RT_FP64 ? nullptr : c->g2, c->stream));
-        c->gdiff_valid = true;
+                                 c->precision == RT_FP32_SWEEP ? c->g2 : nullptr, c->stream));
         c->stats.launches += 1;
+        if (c->precision == RT_DF64) {
+            CK(launch_grad_df(c->g, c->gdiff, c->g2df, c->stream));
+            c->stats.launches += 1;
+        }
+        c->gdiff_valid = true;
     }
     if (c->precision != RT_FP64 && !c->b2_valid) {
         CK(launch_pack_b2(c->g, c->B, c->b2, c->stream));
@@ -302,6 +328,8 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
     if (c->precision == RT_FP64) {
         CK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->scal + 0,
                        cut, G, c->partial, count_steps ? c->d_steps : nullptr, c->stream));
+    } else if (c->precision == RT_DF64) {
+        CK(launch_fsdf(viewdf(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
     } else {
         CK(launch_fs32d(view32(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
     }
@@ -332,8 +360,11 @@ int prepare_source(rt_ctx* c, const double* S_in, bool device)
                          c->scal + 0, c->stream));
     }
     c->stats.launches += 1;
-    if (c->precision != RT_FP64) {
+    if (c->precision == RT_FP32_SWEEP) {
         CK(launch_pack32(c->g, c->chi, c->S, c->node4, c->stream));
+        c->stats.launches += 1;
+    } else if (c->precision == RT_DF64) {
+        CK(launch_packdf(c->g, c->chi, c->S, c->node4, c->stream));
         c->stats.launches += 1;
     }
     return RT_OK;
@@ -361,7 +392,8 @@ int formal_solution(rt_ctx* c, const double* S, double* Jfs_out, double* lstar_o
 int ensure_coef(rt_ctx* c)
 {
     if (c->coef_valid) return RT_OK;
-    CK(launch_os_coef(c->g, c->lstar, c->eps, c->coef, c->rdiag, c->stream));
+    CK(launch_os_coef(c->g, c->lstar, c->eps, c->coef, c->rdiag,
+                      c->os_method == RT_OS_GAUSS_SEIDEL, c->stream));
     c->coef_valid = true;
     c->stats.launches += 1;
     return RT_OK;
@@ -389,7 +421,8 @@ int run_os(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, doubl
     int rc = ensure_coef(c);
     if (rc) return rc;
     if ((rc = ensure_dlt(c, max_sweeps))) return rc;
-    CK(launch_os_rhs(c->g, c->coef, c->rdiag, Jfs, Jold, c->r, c->stream));
+    const bool gs = c->os_method == RT_OS_GAUSS_SEIDEL;
+    CK(launch_os_rhs(c->g, c->coef, c->rdiag, Jfs, Jold, c->r, gs, c->stream));
     c->stats.launches += 1;
     CK(cudaMemsetAsync(c->dlt, 0, sizeof(double) * max_sweeps, c->stream));
     double* bufs[2] = {c->Ja, c->Jb};
@@ -400,15 +433,19 @@ int run_os(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, doubl
         if (c->profiling) CK(cudaEventRecord(c->ev[2], c->stream));
         for (int n = n0; n < n1; ++n) {
             const double* cur = n == 0 ? Jold : bufs[(n - 1) & 1];
-            CK(launch_jacobi(c->g, c->coef, c->r, cur, bufs[n & 1], c->dlt, n, tol_inner,
-                             c->stream));
+            if (gs)
+                CK(launch_gs_sweep(c->g, c->coef, c->r, cur, bufs[n & 1], c->dlt, n, tol_inner,
+                                   c->stream));
+            else
+                CK(launch_jacobi(c->g, c->coef, c->r, cur, bufs[n & 1], c->dlt, n, tol_inner,
+                                 c->stream));
         }
         if (c->profiling) {
             CK(cudaEventRecord(c->ev[3], c->stream));
             c->jac_pending = true;
         }
-        c->stats.launches += n1 - n0;
-        c->stats.jacobi_launches += n1 - n0;
+        c->stats.launches += (gs ? 2 : 1) * (n1 - n0);
+        c->stats.jacobi_launches += (gs ? 2 : 1) * (n1 - n0);
         CK(cudaMemcpyAsync(c->h_dlt + n0, c->dlt + n0, sizeof(double) * (n1 - n0),
                            cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
@@ -679,8 +716,11 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
     } else {
         for (int p : act) {
             rt_ctx* c = b->ctx[p];
-            BCK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw,
-                            c->scal + 0, cut_of(c), G, c->partial, b->d_steps, b->stream));
+            if (b->precision == RT_DF64)
+                BCK(launch_fsdf(viewdf(c), cut_of(c), G, b->d_steps, b->stream));
+            else
+                BCK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw,
+                                c->scal + 0, cut_of(c), G, c->partial, b->d_steps, b->stream));
             b->stats.fs_launches += 1;
             b->stats.launches += 1;
         }
@@ -704,7 +744,8 @@ int batch_os(rt_batch* b, const std::vector<int>& act, double tol_inner, int max
         rt_ctx* c = b->ctx[p];
         if ((rc = bpass(b, p, ensure_coef(c)))) return rc;
         if ((rc = bpass(b, p, ensure_dlt(c, max_sweeps)))) return rc;
-        BCK(launch_os_rhs(c->g, c->coef, c->rdiag, c->Jfs, c->J, c->r, b->stream));
+        BCK(launch_os_rhs(c->g, c->coef, c->rdiag, c->Jfs, c->J, c->r,
+                          c->os_method == RT_OS_GAUSS_SEIDEL, b->stream));
         BCK(cudaMemsetAsync(c->dlt, 0, sizeof(double) * max_sweeps, b->stream));
         b->stats.launches += 1;
         inner.push_back(p);
@@ -719,12 +760,18 @@ int batch_os(rt_batch* b, const std::vector<int>& act, double tol_inner, int max
             for (int n = n0; n < n1; ++n) {
                 const double* cur = n == 0 ? c->J : (n & 1 ? c->Ja : c->Jb);
                 double* nxt = n & 1 ? c->Jb : c->Ja;
-                BCK(launch_jacobi(c->g, c->coef, c->r, cur, nxt, c->dlt, n, tol_inner, b->stream));
+                if (c->os_method == RT_OS_GAUSS_SEIDEL)
+                    BCK(launch_gs_sweep(c->g, c->coef, c->r, cur, nxt, c->dlt, n, tol_inner,
+                                        b->stream));
+                else
+                    BCK(launch_jacobi(c->g, c->coef, c->r, cur, nxt, c->dlt, n, tol_inner,
+                                      b->stream));
             }
             BCK(cudaMemcpyAsync(c->h_dlt + n0, c->dlt + n0, sizeof(double) * (n1 - n0),
                                 cudaMemcpyDeviceToHost, b->stream));
-            b->stats.launches += n1 - n0;
-            b->stats.jacobi_launches += n1 - n0;
+            const int per = c->os_method == RT_OS_GAUSS_SEIDEL ? 2 : 1;
+            b->stats.launches += per * (n1 - n0);
+            b->stats.jacobi_launches += per * (n1 - n0);
         }
         BCK(cudaStreamSynchronize(b->stream));
         std::vector<int> still;
@@ -760,7 +807,7 @@ int rt_create(rt_ctx** out, int device, int precision)
 {
     if (!out) return RT_EINVAL;
     *out = nullptr;
-    if (precision != RT_FP64 && precision != RT_FP32_SWEEP) return RT_EINVAL;
+    if (precision != RT_FP64 && precision != RT_FP32_SWEEP && precision != RT_DF64) return RT_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RT_ECUDA;
     rt_ctx* c = new rt_ctx();
@@ -842,14 +889,17 @@ int rt_set_grid(rt_ctx* c, int nx, int ny, int nz, double dx, double dy, double 
     const size_t N = (size_t)c->g.N;
     CK(dalloc(c->chi, N)); CK(dalloc(c->eps, N)); CK(dalloc(c->B, N)); CK(dalloc(c->J, N));
     CK(dalloc(c->S, N)); CK(dalloc(c->Jfs, N)); CK(dalloc(c->Jn, N)); CK(dalloc(c->Ja, N));
-    CK(dalloc(c->Jb, N)); CK(dalloc(c->r, N)); CK(dalloc(c->rdiag, N));
-    CK(dalloc(c->lstar, 27 * N)); CK(dalloc(c->coef, 27 * N));
+    // r, 1/diag and c sized for either storage (colour-split >= N)
+    const size_t Ns = (size_t)os_coef_stride(c->g, true);
+    CK(dalloc(c->Jb, N)); CK(dalloc(c->r, Ns)); CK(dalloc(c->rdiag, Ns));
+    CK(dalloc(c->lstar, 27 * N)); CK(dalloc(c->coef, 27 * Ns));
     CK(dalloc(c->gdiff, (size_t)nx * ny));
     if (c->precision != RT_FP64) {
         CK(dalloc(c->node4, 4 * N));
         CK(dalloc(c->b2, (size_t)8 * nx * ny));
         CK(dalloc(c->g2, (size_t)4 * nx * ny));
     }
+    if (c->precision == RT_DF64) CK(dalloc(c->g2df, (size_t)4 * nx * ny));
     c->have_grid = true;
     return RT_OK;
 }
@@ -899,6 +949,11 @@ int rt_set_quadrature(rt_ctx* c, int ndir, const double* mu, const double* phi, 
     if (c->precision != RT_FP64) {
         CK(dalloc(c->poff, T));
         CK(launch_pad_offsets(c->g, c->info, c->off, c->poff, c->stream));
+        c->stats.launches += 1;
+    }
+    if (c->precision == RT_DF64) {
+        CK(dalloc(c->bwdf, 2 * T));
+        CK(launch_bw_df((long long)T, c->bw, c->bwdf, c->stream));
         c->stats.launches += 1;
     }
     c->wsum = sw;
@@ -1051,6 +1106,27 @@ int rt_set_ng(rt_ctx* c, int period, double min_delta)
     return RT_OK;
 }
 
+int rt_set_os_method(rt_ctx* c, int method)
+{
+    if (!c) return RT_EINVAL;
+    if (method != RT_OS_JACOBI && method != RT_OS_GAUSS_SEIDEL)
+        return fail(c, RT_EINVAL, "unknown operator-splitting method");
+    if (method != c->os_method) {
+        c->os_method = method;
+        c->coef_valid = false;   // the storage of c, 1/diag, r differs
+    }
+    return RT_OK;
+}
+
+int rt_batch_set_os_method(rt_batch* b, int method)
+{
+    if (!b) return RT_EINVAL;
+    if (method != RT_OS_JACOBI && method != RT_OS_GAUSS_SEIDEL)
+        return bfail(b, RT_EINVAL, "unknown operator-splitting method");
+    for (rt_ctx* c : b->ctx) rt_set_os_method(c, method);
+    return RT_OK;
+}
+
 int rt_batch_set_ng(rt_batch* b, int period, double min_delta)
 {
     if (!b) return RT_EINVAL;
@@ -1089,7 +1165,9 @@ int rt_batch_create(rt_batch** out, int device, int precision, int nprob, const 
 {
     if (!out) return RT_EINVAL;
     *out = nullptr;
-    if (nprob < 1 || !probs || (precision != RT_FP64 && precision != RT_FP32_SWEEP)) return RT_EINVAL;
+    if (nprob < 1 || !probs ||
+        (precision != RT_FP64 && precision != RT_FP32_SWEEP && precision != RT_DF64))
+        return RT_EINVAL;
     rt_batch* b = new rt_batch();
     b->device = device;
     b->precision = precision;

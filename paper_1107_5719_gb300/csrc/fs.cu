@@ -64,6 +64,8 @@ __global__ void k_dir_tables(Geometry g, double dx, double dy, double dz,
         di.hs32 = (float)di.hs;
         di.amu = amu;
         di.amu32 = (float)amu;
+        di.hs32lo = (float)(di.hs - (double)di.hs32);
+        di.amu32lo = (float)(amu - (double)di.amu32);
         di.w = w[d];
         di.sgn = m_u > 0.0 ? 1 : -1;
         // Lambda* offsets of the four nodes of p_1 (plane k0 - sgn).

@@ -1,0 +1,311 @@
+// FP64-accurate formal solution in double-float arithmetic (precision
+// RT_DF64).  Same characteristics, interpolation, optical depths, segment
+// weights and cutoff as the FP64 march (Hauschildt & Baron 2011, Sect. 2.2),
+// but every quantity is an unevaluated pair of FP32 numbers (df.cuh), so the
+// march runs on the FP32 pipes, which issue 64x more operations per clock on
+// GB300 than the FP64 pipe.  Like the FP32 sweep it integrates I - S_0 (the
+// deviation from the source at the voxel), so that its ~1e-14 relative
+// rounding scales with I - S_0 and is not amplified by the near-singular
+// scattering problem at small eps.
+//
+// Layout: per node a float4 {chi_hi, chi_lo, S_hi, S_lo} in planes padded to
+// 2ny x 2nx by periodic copies (same addressing as the FP32 sweep); bilinear
+// weights per (direction, step) as two float4 (hi and lo parts); boundary B
+// and the LTE-diffusion gradient as padded float2 pairs.
+#include "df.cuh"
+#include "internal.h"
+
+namespace rt3d {
+
+namespace {
+
+constexpr int kThreadsDF = 128;
+constexpr int kExpTableDF = 256;
+
+// tab[j] = 2^{-j/256} and tab[256 + j] = 1 - 2^{-j/256} (the latter from
+// expm1, so accurate relative to itself), as double-float pairs (call from
+// all threads, then sync)
+__device__ __forceinline__ void fill_exp_table_df(dfl* tab)
+{
+    for (int j = threadIdx.x; j < kExpTableDF; j += blockDim.x) {
+        tab[j] = df_from_double(exp2(-(double)j / kExpTableDF));
+        tab[kExpTableDF + j] = df_from_double(-expm1(-(double)j * (0.693147180559945309417 / kExpTableDF)));
+    }
+}
+
+// e^{-x} and 1 - e^{-x} for 0.05 <= x <= 80 (Tang's table-driven method in
+// double-float): k = round(256 x / ln2), m = k >> 8, j = k & 255,
+// r = x - k ln2/256 (|r| <= 1.4e-3, ln2/256 split into three floats as in
+// Cody & Waite, the products formed exactly), p = e^{-r} - 1 =
+// -r + r^2/2 - r^3 (1/6 - r/24) (the cubic and quartic terms in FP32,
+// < 5e-10), and with t = 2^{-m} 2^{-j/256}:
+//   e = t + t p,   1 - e = (1 - t) - t p.
+// For m = 0 the factor 1 - t comes from its own table (1 - e would
+// otherwise inherit the table's rounding relative to e, which cancels);
+// for m >= 1, t <= 1/2 and 1 - t loses nothing.
+__device__ __forceinline__ void exp_neg_df(dfl x, const dfl* __restrict__ tab, dfl& e, dfl& om)
+{
+    constexpr float kInvL = 369.3299255371094f;          // 256 / ln 2 (rounding only)
+    constexpr float kL1 = 0.0027076061815023422f;         // ln2/256 = kL1 + kL2 + kL3
+    constexpr float kL2 = -7.440055516116928e-12f;
+    constexpr float kL3 = -3.4309311478864607e-19f;
+    const float k = rintf(x.h * kInvL);
+    dfl r = df_add(x, df_neg(two_prod(k, kL1)));
+    r = df_add(r, df_neg(two_prod(k, kL2)));
+    r = df_add_f(r, -k * kL3);
+    const dfl r2 = df_mul(r, r);
+    const float tail = r2.h * r.h * fmaf(-r.h, 1.0f / 24.0f, 1.0f / 6.0f);
+    const dfl p = df_add(df_neg(r), df_add_f(df_scale(r2, 0.5f), -tail));
+    const int ki = (int)k;
+    const int m = ki >> 8, j = ki & (kExpTableDF - 1);
+    const float sc = __int_as_float((127 - m) << 23);   // 2^-m, normal for x <= 80
+    const dfl t = df_scale(tab[j], sc);
+    const dfl tp = df_mul(t, p);
+    const dfl c = m == 0 ? tab[kExpTableDF + j] : df_add_f(df_neg(t), 1.0f);
+    e = df_add(t, tp);
+    om = df_sub(c, tp);
+}
+
+// Segment weights in double-float (same definitions as weights.cuh).
+__device__ __forceinline__ void seg_weights_df(dfl x, const dfl* __restrict__ tab, dfl& wc, dfl& wu,
+                                               dfl& e)
+{
+    if (x.h < 0.05f) {
+        // phi2 series: E = 1/2 + z/24 + z^2/720 + ..., O = x (1/6 + z/120 + z^2/5040 + ...);
+        // from z^2 on the terms are below 9e-9 and are summed in FP32.
+        const dfl z = df_mul(x, x);
+        const float zf = z.h;
+        const float rE = zf * zf * fmaf(zf, fmaf(zf, 1.0f / 3628800.0f, 1.0f / 40320.0f), 1.0f / 720.0f);
+        const float rO = zf * zf * fmaf(zf, 1.0f / 362880.0f, 1.0f / 5040.0f);
+        const dfl c24 = df_make(0.0416666679084301f, -1.2417634698280722e-09f);    // 1/24
+        const dfl c120 = df_make(0.008333333767950535f, -4.34617203337595e-10f);   // 1/120
+        const dfl c6 = df_make(0.1666666716337204f, -4.967053879312289e-09f);      // 1/6
+        dfl E = df_add_f(df_mul(z, c24), rE);
+        E = df_add_f(E, 0.5f);
+        dfl Op = df_add_f(df_mul(z, c120), rO);
+        Op = df_add(c6, Op);
+        const dfl O = df_mul(x, Op);
+        wc = df_mul(x, df_add(E, df_neg(O)));
+        e = df_add(df_add_f(df_neg(x), 1.0f), df_mul(x, wc));
+        wu = df_mul(df_mul(x, e), df_add(E, O));
+    } else {
+        dfl om;
+        if (x.h <= 80.0f) {
+            exp_neg_df(x, tab, e, om);
+        } else {
+            e = df_make(0.f, 0.f);
+            om = df_make(1.f, 0.f);
+        }
+        // q = om / x: FP32 quotient and two corrections from the residual
+        // (one leaves a relative error near 2^-44, amplified up to 40x in 1 - q)
+        const dfl q = df_div(om, x);
+        wc = df_add_f(df_neg(q), 1.0f);
+        wu = df_sub(q, e);
+    }
+}
+
+// Bilinear interpolation of a double-float field: sum of four df products
+// with the TwoProduct errors and cross terms gathered in one FP32 term.
+__device__ __forceinline__ dfl bilin_df(float4 wh, float4 wl, float ah, float al, float bh, float bl,
+                                        float ch, float cl, float dh, float dl)
+{
+    const dfl p0 = two_prod(wh.x, ah), p1 = two_prod(wh.y, bh), p2 = two_prod(wh.z, ch),
+              p3 = two_prod(wh.w, dh);
+    float err = p0.l + p1.l + p2.l + p3.l;
+    err = fmaf(wh.x, al, err); err = fmaf(wh.y, bl, err); err = fmaf(wh.z, cl, err);
+    err = fmaf(wh.w, dl, err);
+    err = fmaf(wl.x, ah, err); err = fmaf(wl.y, bh, err); err = fmaf(wl.z, ch, err);
+    err = fmaf(wl.w, dh, err);
+    dfl s = two_sum(p0.h, p1.h);
+    dfl t = two_sum(p2.h, p3.h);
+    dfl u = two_sum(s.h, t.h);
+    err += s.l + t.l + u.l;
+    return quick_two_sum(u.h, err);
+}
+
+__device__ __forceinline__ void add_steps_df(unsigned long long* steps, unsigned long long n)
+{
+    for (int s = 16; s > 0; s >>= 1) n += __shfl_down_sync(0xffffffffu, n, s);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(steps, n);
+}
+
+__global__ void __launch_bounds__(kThreadsDF)
+k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
+{
+    __shared__ dfl tab[2 * kExpTableDF];
+    fill_exp_table_df(tab);
+    __syncthreads();
+    const Geometry& g = p.g;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const int t = blockIdx.x * kThreadsDF + threadIdx.x;
+    const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
+    const bool active = t < nxy;
+    unsigned long long nsteps = 0;
+    if (active) {
+        const int j0 = t / nx, i0 = t - j0 * nx;
+        const long long v = (long long)k0 * nxy + t;
+        const long long W = 2LL * nx, P = 4LL * nxy;
+        const long long base = k0 * P + j0 * W + i0;
+        const float4 me = p.node[base];
+        const dfl chi0 = df_make(me.x, me.y), S0 = df_make(me.z, me.w);
+        // The rest of a characteristic changes I - S_0 by at most
+        // T * max|S - S_0| <= T * 2 smax: stop once that is below cut * S_0.
+        const float smax = (float)*p.smax;
+        const float tcut = smax > 0.f ? cut * S0.h / (2.0f * smax) : 0.f;
+        const float4* nb = p.node + base;
+        for (int slot = zb; slot < kSlots; slot += ZB) {
+            double Jp = 0.0;
+            for (int d = slot; d < g.ndir; d += kSlots) {
+                const DirInfo di = p.info[d];
+                const int s = di.sgn;
+                const int M = s > 0 ? k0 : nz - 1 - k0;
+                const int* od = p.poff + (long long)d * nz;
+                const float4* bd = p.bw + (long long)d * nz * 2;
+                const dfl hs = df_make(di.hs32, di.hs32lo);
+                dfl I = df_make(0.f, 0.f), T = df_make(1.f, 0.f), ca = chi0, da = df_make(0.f, 0.f);
+                bool early = false;
+                int m = 0;
+                for (; m < M; ++m) {
+                    const float4* q = nb + od[m + 1];
+                    const float4 wh = bd[2 * (m + 1)], wl = bd[2 * (m + 1) + 1];
+                    const float4 q00 = __ldg(q), q10 = __ldg(q + 1);
+                    const float4 q01 = __ldg(q + W), q11 = __ldg(q + W + 1);
+                    const dfl cb = bilin_df(wh, wl, q00.x, q00.y, q10.x, q10.y, q01.x, q01.y,
+                                            q11.x, q11.y);
+                    const dfl sb = bilin_df(wh, wl, q00.z, q00.w, q10.z, q10.w, q01.z, q01.w,
+                                            q11.z, q11.w);
+                    const dfl db = df_sub(sb, S0);
+                    const dfl x = df_mul(hs, df_add(ca, cb));
+                    dfl wc, wu, e;
+                    seg_weights_df(x, tab, wc, wu, e);
+                    I = df_add(I, df_mul(T, df_add(df_mul(wc, da), df_mul(wu, db))));
+                    T = df_mul(T, e);
+                    ca = cb;
+                    da = db;
+                    if (T.h <= tcut) {
+                        early = true;
+                        ++m;
+                        break;
+                    }
+                }
+                if (!early) {
+                    // boundary term T_M (I_bc - S_0)
+                    dfl ibc;
+                    const int bc = s > 0 ? g.top_bc : g.bottom_bc;
+                    if (bc) {
+                        const StepGeo o = p.off[(long long)d * nz + M];
+                        const float4 wh = bd[2 * M], wl = bd[2 * M + 1];
+                        const long long ip = (j0 + o.oy) * W + (i0 + o.ox);
+                        const float2* pb = p.b2 + (s > 0 ? 0LL : P) + ip;
+                        const float2 c00 = pb[0], c10 = pb[1], c01 = pb[W], c11 = pb[W + 1];
+                        ibc = bilin_df(wh, wl, c00.x, c00.y, c10.x, c10.y, c01.x, c01.y, c11.x, c11.y);
+                        if (bc == 2) {   // + |mu| dB/dtau (LTE diffusion)
+                            const float2* pg = p.g2df + ip;
+                            const float2 g00 = pg[0], g10 = pg[1], g01 = pg[W], g11 = pg[W + 1];
+                            const dfl gr = bilin_df(wh, wl, g00.x, g00.y, g10.x, g10.y, g01.x,
+                                                    g01.y, g11.x, g11.y);
+                            ibc = df_add(ibc, df_mul(df_make(di.amu32, di.amu32lo), gr));
+                        }
+                        ibc = df_sub(ibc, S0);
+                    } else {
+                        ibc = df_neg(S0);
+                    }
+                    I = df_add(I, df_mul(T, ibc));
+                }
+                nsteps += (unsigned long long)m;
+                Jp = fma(di.w, df_to_double(I), Jp);
+            }
+            p.partial[(long long)slot * g.N + v] = Jp;
+        }
+    }
+    if (steps) add_steps_df(steps, nsteps);
+}
+
+__global__ void k_packdf(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
+                         float4* __restrict__ node)
+{
+    const int nx = g.nx, ny = g.ny;
+    const long long W = 2LL * nx, P = 4LL * nx * ny;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(v % nx), j = (int)((v / nx) % ny);
+        const long long k = v / ((long long)nx * ny);
+        const dfl c = df_from_double(chi[v]), s = df_from_double(S[v]);
+        const float4 q = make_float4(c.h, c.l, s.h, s.l);
+        float4* pp = node + k * P + (long long)j * W + i;
+        pp[0] = q;
+        pp[nx] = q;
+        pp[(long long)ny * W] = q;
+        pp[(long long)ny * W + nx] = q;
+    }
+}
+
+// Bilinear weights of every (direction, step) as double-float: [hi4, lo4].
+__global__ void k_bw_df(long long n, const Bw4d* __restrict__ bw, float4* __restrict__ out)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const Bw4d b = bw[e];
+        const dfl x = df_from_double(b.x), y = df_from_double(b.y), z = df_from_double(b.z),
+                  w = df_from_double(b.w);
+        out[2 * e] = make_float4(x.h, y.h, z.h, w.h);
+        out[2 * e + 1] = make_float4(x.l, y.l, z.l, w.l);
+    }
+}
+
+// Padded double-float copy of the LTE-diffusion gradient G[ny][nx].
+__global__ void k_grad_df(Geometry g, const double* __restrict__ G, float2* __restrict__ out)
+{
+    const int nx = g.nx, ny = g.ny, nxy = nx * ny;
+    const long long W = 2LL * nx;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nxy; t += gridDim.x * blockDim.x) {
+        const int i = t % nx, j = t / nx;
+        const dfl d = df_from_double(G[t]);
+        const float2 q = make_float2(d.h, d.l);
+        float2* pp = out + (long long)j * W + i;
+        pp[0] = q;
+        pp[nx] = q;
+        pp[(long long)ny * W] = q;
+        pp[(long long)ny * W + nx] = q;
+    }
+}
+
+unsigned grid1d_df(long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b > 152LL * 32) b = 152LL * 32;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_packdf(const Geometry& g, const double* chi, const double* S, float4* node,
+                          cudaStream_t st)
+{
+    k_packdf<<<grid1d_df(g.N, 256), 256, 0, st>>>(g, chi, S, node);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bw_df(long long n, const Bw4d* bw, float4* out, cudaStream_t st)
+{
+    k_bw_df<<<grid1d_df(n, 256), 256, 0, st>>>(n, bw, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_df(const Geometry& g, const double* G, float2* out, cudaStream_t st)
+{
+    k_grad_df<<<grid1d_df((long long)g.nx * g.ny, 256), 256, 0, st>>>(g, G, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fsdf(const ViewDF& p, double cut, int groups, unsigned long long* steps,
+                        cudaStream_t st)
+{
+    const int nxy = p.g.nx * p.g.ny;
+    dim3 grid((nxy + kThreadsDF - 1) / kThreadsDF, p.g.nz, groups);
+    k_fsdf<<<grid, kThreadsDF, 0, st>>>(p, (float)cut, steps);
+    return cudaGetLastError();
+}
+
+}  // namespace rt3d

@@ -22,6 +22,8 @@ struct DirInfo {
     float hs32;     // hs in FP32 (sweep form)
     float amu32;    // |mu| in FP32
     double amu;     // |mu| (LTE-diffusion boundary)
+    float hs32lo;   // hs - hs32: hs as a double-float pair (RT_DF64 march)
+    float amu32lo;  // |mu| - amu32
 };
 
 // Per-(direction, step m) lattice geometry.  The upstream point p_m of voxel
@@ -96,6 +98,26 @@ long long fs32_blocks(const Geometry& g, int groups);
 cudaError_t launch_fs32_batch(const View32* views, const int* ids, const long long* prefix,
                               int nact, long long total_blocks, int groups, double cut,
                               unsigned long long* steps, cudaStream_t st);
+// ---- double-float march (fsdf.cu) -------------------------------------------
+struct ViewDF {
+    Geometry g;
+    const float4* node;     // padded {chi_hi, chi_lo, S_hi, S_lo}
+    const float2* b2;       // padded boundary {B_hi, B_lo}
+    const float2* g2df;     // padded LTE-diffusion gradient {hi, lo}
+    const DirInfo* info;
+    const StepGeo* off;
+    const int* poff;
+    const float4* bw;       // per (direction, step): hi4, lo4 of the bilinear weights
+    const double* smax;
+    double* partial;        // [kSlots][N] of sum_d w_d (I_d - S_0)
+};
+cudaError_t launch_packdf(const Geometry& g, const double* chi, const double* S, float4* node,
+                          cudaStream_t st);
+cudaError_t launch_bw_df(long long n, const Bw4d* bw, float4* out, cudaStream_t st);
+cudaError_t launch_grad_df(const Geometry& g, const double* G, float2* out, cudaStream_t st);
+cudaError_t launch_fsdf(const ViewDF& p, double cut, int groups, unsigned long long* steps,
+                        cudaStream_t st);
+
 // J[v] = wsum S[v] + sum_slot partial[slot][v].
 cudaError_t launch_sum_groups_src(long long N, const double* partial, const double* S,
                                   double wsum, double* J, cudaStream_t st);
@@ -125,11 +147,20 @@ cudaError_t launch_to_float(long long N, const double* x, float* y, cudaStream_t
 
 // Operator-splitting coefficients: c[o][v] = Lambda*_{v,o} (1 - eps_j) / diag_v,
 // rdiag[v] = 1 / diag_v, diag_v = 1 - Lambda*_{v,13} (1 - eps_v).
+// split: colour-split storage for red-black Gauss-Seidel (coef holds 27 *
+// os_coef_stride(g, split) doubles, rdiag and r os_coef_stride(g, split)).
+long long os_coef_stride(const Geometry& g, bool split);
 cudaError_t launch_os_coef(const Geometry& g, const double* lstar, const double* eps,
-                           double* coef, double* rdiag, cudaStream_t st);
+                           double* coef, double* rdiag, bool split, cudaStream_t st);
 // r[v] = J_fs[v] / diag_v - sum_o c[o][v] J_old[nb(v,o)]
 cudaError_t launch_os_rhs(const Geometry& g, const double* coef, const double* rdiag,
-                          const double* J_fs, const double* J_old, double* r, cudaStream_t st);
+                          const double* J_fs, const double* J_old, double* r, bool split,
+                          cudaStream_t st);
+// One red-black Gauss-Seidel sweep n (two launches), J -> Jn, same no-op
+// and dlt rules as launch_jacobi; coef, r colour-split.
+cudaError_t launch_gs_sweep(const Geometry& g, const double* coef, const double* r,
+                            const double* J, double* Jn, double* dlt, int n, double tol,
+                            cudaStream_t st);
 // Sweep n: Jn[v] = r[v] + sum_{o != 13} c[o][v] J[nb(v,o)];  dlt[n] = max |Jn - J| / |Jn|;
 // no-op when n > 0 and dlt[n-1] < tol.
 cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r,

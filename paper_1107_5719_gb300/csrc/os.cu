@@ -9,7 +9,16 @@
 //   r_v     = J_fs,v / diag_v - sum_o c_{v,o} J_old,nb(v,o)
 //   J^{n+1}_v = r_v + sum_{o != 13} c_{v,o} J^n_{nb(v,o)}
 // The coefficients are stored offset-major ([27][N]) so that a warp reads
-// 32 consecutive voxels of one offset (coalesced).  Max-reductions of
+// 32 consecutive voxels of one offset (coalesced).
+//
+// Red-black Gauss-Seidel (the other method of Sect. 2.3): voxel (i,j,k) is
+// red if i+j+k is even.  A sweep is two launches: the red voxels from the
+// iterate at the start of the sweep, then the black voxels from the new red
+// and the old black values; within a colour the updates are simultaneous,
+// so each launch reads only values no thread of it writes.  For this method
+// c, 1/diag and r are stored colour-split, [colour][nz][ny][h] with
+// h = ceil(nx/2) and the voxel at x = 2q + ((colour + j + k) & 1) at q, so
+// that a warp of one colour still reads 32 consecutive coefficients.  Max-reductions of
 // non-negative doubles use atomicMax on their bit patterns, which order
 // like the values; max is independent of the order, so results are
 // reproducible.
@@ -96,6 +105,22 @@ __device__ __forceinline__ int wrap1(int a, int n)
 
 constexpr int kOsThreads = 128;
 
+// Colour-split storage: h = ceil(nx/2) slots per row and colour.
+__device__ __host__ __forceinline__ int split_h(int nx) { return (nx + 1) >> 1; }
+
+__device__ __forceinline__ long long split_index(const Geometry& g, int i, int j, int k)
+{
+    const int col = (i + j + k) & 1;
+    return (((long long)col * g.nz + k) * g.ny + j) * split_h(g.nx) + (i >> 1);
+}
+
+// Coefficient storage size per offset: N ([27][N]) or the colour-split size.
+__device__ __host__ __forceinline__ long long coef_stride(const Geometry& g, bool split)
+{
+    return split ? 2LL * g.nz * g.ny * split_h(g.nx) : g.N;
+}
+
+template <bool SPLIT>
 __global__ void __launch_bounds__(kOsThreads)
 k_os_coef(Geometry g, const double* __restrict__ L, const double* __restrict__ eps,
           double* __restrict__ c, double* __restrict__ rdiag)
@@ -106,8 +131,10 @@ k_os_coef(Geometry g, const double* __restrict__ L, const double* __restrict__ e
     if (t >= nxy) return;
     const int j = t / nx, i = t - j * nx;
     const long long v = (long long)k * nxy + t;
+    const long long ci = SPLIT ? split_index(g, i, j, k) : v;
+    const long long cs = coef_stride(g, SPLIT);
     const double rd = 1.0 / (1.0 - L[13 * g.N + v] * (1.0 - eps[v]));
-    rdiag[v] = rd;
+    rdiag[ci] = rd;
     for (int o = 0; o < 27; ++o) {
         const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
         const int kk = k + oz;
@@ -116,7 +143,7 @@ k_os_coef(Geometry g, const double* __restrict__ L, const double* __restrict__ e
             const long long nb = (long long)kk * nxy + wrap1(j + oy, ny) * nx + wrap1(i + ox, nx);
             cv = L[o * g.N + v] * (1.0 - eps[nb]) * rd;
         }
-        c[o * g.N + v] = cv;
+        c[o * cs + ci] = cv;
     }
 }
 
@@ -125,7 +152,7 @@ k_os_coef(Geometry g, const double* __restrict__ L, const double* __restrict__ e
 template <bool SKIP_CENTRE>
 __device__ __forceinline__ double stencil(const Geometry& g, const double* __restrict__ c,
                                           const double* __restrict__ J, int i, int j, int k,
-                                          long long v)
+                                          long long v, long long cs)
 {
     const int nx = g.nx, ny = g.ny, nxy = nx * ny;
     const int xm = wrap1(i - 1, nx), xp = wrap1(i + 1, nx);
@@ -145,13 +172,14 @@ __device__ __forceinline__ double stencil(const Geometry& g, const double* __res
             for (int ox = 0; ox < 3; ++ox) {
                 const int o = oz * 9 + oy * 3 + ox;
                 if (SKIP_CENTRE && o == 13) continue;
-                acc = fma(__ldg(c + o * g.N + v), __ldg(Jr + xs[ox]), acc);
+                acc = fma(__ldg(c + o * cs + v), __ldg(Jr + xs[ox]), acc);
             }
         }
     }
     return acc;
 }
 
+template <bool SPLIT>
 __global__ void __launch_bounds__(kOsThreads)
 k_os_rhs(Geometry g, const double* __restrict__ c, const double* __restrict__ rdiag,
          const double* __restrict__ Jfs, const double* __restrict__ Jold, double* __restrict__ r)
@@ -162,7 +190,8 @@ k_os_rhs(Geometry g, const double* __restrict__ c, const double* __restrict__ rd
     if (t >= nxy) return;
     const int j = t / nx, i = t - j * nx;
     const long long v = (long long)k * nxy + t;
-    r[v] = Jfs[v] * rdiag[v] - stencil<false>(g, c, Jold, i, j, k, v);
+    const long long ci = SPLIT ? split_index(g, i, j, k) : v;
+    r[ci] = Jfs[v] * rdiag[ci] - stencil<false>(g, c, Jold, i, j, k, ci, coef_stride(g, SPLIT));
 }
 
 // Sweep n of a Jacobi solve.  dlt[n] receives max |Jn - J| / |Jn|; if the
@@ -183,11 +212,61 @@ k_jacobi(Geometry g, const double* __restrict__ c, const double* __restrict__ r,
     if (t < nxy) {
         const int j = t / nx, i = t - j * nx;
         const long long v = (long long)k * nxy + t;
-        const double jn = r[v] + stencil<true>(g, c, J, i, j, k, v);
+        const double jn = r[v] + stencil<true>(g, c, J, i, j, k, v, g.N);
         Jn[v] = jn;
         rel = nonneg((jn - J[v]) / jn);
     }
     block_max_to(rel, delta);
+}
+
+// Half of sweep n of a red-black Gauss-Seidel solve: the voxels of one
+// colour, from `same` for neighbours of that colour (the iterate at the
+// start of the sweep) and from `other` for the rest (the start iterate for
+// the red half, the new red values for the black half), written to `dst`.
+// dst == other in the black half: this launch reads only the other colour's
+// entries of it and writes only its own.  Same no-op rule as k_jacobi.
+__global__ void __launch_bounds__(kOsThreads)
+k_gs_half(Geometry g, const double* __restrict__ c, const double* __restrict__ r,
+          const double* __restrict__ same, const double* other, double* dst,
+          double* __restrict__ dlt, int n, double tol, int colour)
+{
+    if (n > 0 && dlt[n - 1] < tol) return;
+    const int nx = g.nx, ny = g.ny, nxy = nx * ny, h = split_h(nx);
+    const int t = blockIdx.x * kOsThreads + threadIdx.x;
+    const int k = blockIdx.y;
+    const int j = t / h, q = t - j * h;
+    const int i = 2 * q + ((colour + j + k) & 1);
+    double rel = 0.0;
+    if (j < ny && i < nx) {
+        const long long cs = coef_stride(g, true);
+        const long long ci = (((long long)colour * g.nz + k) * ny + j) * h + q;
+        const long long v = (long long)k * nxy + (long long)j * nx + i;
+        const int xm = wrap1(i - 1, nx), xp = wrap1(i + 1, nx);
+        const int ym = wrap1(j - 1, ny), yp = wrap1(j + 1, ny);
+        const int xs[3] = {xm, i, xp};
+        const int ys[3] = {ym, j, yp};
+        double acc = r[ci];
+#pragma unroll
+        for (int oz = 0; oz < 3; ++oz) {
+            const int kk = k + oz - 1;
+            if (kk < 0 || kk >= g.nz) continue;
+#pragma unroll
+            for (int oy = 0; oy < 3; ++oy) {
+                const long long row = (long long)kk * nxy + (long long)ys[oy] * nx;
+#pragma unroll
+                for (int ox = 0; ox < 3; ++ox) {
+                    const int o = oz * 9 + oy * 3 + ox;
+                    if (o == 13) continue;
+                    const int x = xs[ox];
+                    const double* src = ((x + ys[oy] + kk) & 1) == colour ? same : other;
+                    acc = fma(__ldg(c + o * cs + ci), __ldg(src + row + x), acc);
+                }
+            }
+        }
+        dst[v] = acc;
+        rel = nonneg((acc - same[v]) / acc);
+    }
+    block_max_to(rel, dlt + n);
 }
 
 __global__ void k_rel_change(long long N, const double* __restrict__ Jn,
@@ -293,19 +372,38 @@ cudaError_t launch_to_float(long long N, const double* x, float* y, cudaStream_t
     return cudaGetLastError();
 }
 
+long long os_coef_stride(const Geometry& g, bool split) { return coef_stride(g, split); }
+
 cudaError_t launch_os_coef(const Geometry& g, const double* lstar, const double* eps,
-                           double* coef, double* rdiag, cudaStream_t st)
+                           double* coef, double* rdiag, bool split, cudaStream_t st)
 {
     dim3 grid((g.nx * g.ny + kOsThreads - 1) / kOsThreads, g.nz);
-    k_os_coef<<<grid, kOsThreads, 0, st>>>(g, lstar, eps, coef, rdiag);
+    if (split)
+        k_os_coef<true><<<grid, kOsThreads, 0, st>>>(g, lstar, eps, coef, rdiag);
+    else
+        k_os_coef<false><<<grid, kOsThreads, 0, st>>>(g, lstar, eps, coef, rdiag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_os_rhs(const Geometry& g, const double* coef, const double* rdiag,
-                          const double* J_fs, const double* J_old, double* r, cudaStream_t st)
+                          const double* J_fs, const double* J_old, double* r, bool split,
+                          cudaStream_t st)
 {
     dim3 grid((g.nx * g.ny + kOsThreads - 1) / kOsThreads, g.nz);
-    k_os_rhs<<<grid, kOsThreads, 0, st>>>(g, coef, rdiag, J_fs, J_old, r);
+    if (split)
+        k_os_rhs<true><<<grid, kOsThreads, 0, st>>>(g, coef, rdiag, J_fs, J_old, r);
+    else
+        k_os_rhs<false><<<grid, kOsThreads, 0, st>>>(g, coef, rdiag, J_fs, J_old, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gs_sweep(const Geometry& g, const double* coef, const double* r,
+                            const double* J, double* Jn, double* dlt, int n, double tol,
+                            cudaStream_t st)
+{
+    dim3 grid((g.ny * split_h(g.nx) + kOsThreads - 1) / kOsThreads, g.nz);
+    k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, J, Jn, dlt, n, tol, 0);
+    k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, Jn, Jn, dlt, n, tol, 1);
     return cudaGetLastError();
 }
 

@@ -20,8 +20,9 @@ import numpy as np
 
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_ETIMEOUT, RT_ESTATE, RT_ESCRATCH = range(8)
 RT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
-RT_FP64, RT_FP32_SWEEP = 0, 1
+RT_FP64, RT_FP32_SWEEP, RT_DF64 = 0, 1, 2
 RT_BC_ZERO, RT_BC_PLANCK, RT_BC_DIFFUSION = 0, 1, 2
+RT_OS_JACOBI, RT_OS_GAUSS_SEIDEL = 0, 1
 
 _NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV",
           5: "RT_ETIMEOUT", 6: "RT_ESTATE", 7: "RT_ESCRATCH"}
@@ -85,6 +86,8 @@ _SIGS = {
     "rt_set_profiling": (C.c_int, [VP, C.c_int]),
     "rt_set_ng": (C.c_int, [VP, C.c_int, C.c_double]),
     "rt_batch_set_ng": (C.c_int, [VP, C.c_int, C.c_double]),
+    "rt_set_os_method": (C.c_int, [VP, C.c_int]),
+    "rt_batch_set_os_method": (C.c_int, [VP, C.c_int]),
     "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
     "rt_reset_stats": (C.c_int, [VP]),
     "rt_batch_create": (C.c_int, [C.POINTER(VP), C.c_int, C.c_int, C.c_int, C.POINTER(rt_problem),
@@ -310,6 +313,14 @@ def rt_batch_set_ng(b, period, min_delta=0.0):
     return _bcheck(b, load().rt_batch_set_ng(b, period, min_delta))
 
 
+def rt_set_os_method(ctx, method):
+    return _check(ctx, load().rt_set_os_method(ctx, method))
+
+
+def rt_batch_set_os_method(b, method):
+    return _bcheck(b, load().rt_batch_set_os_method(b, method))
+
+
 def rt_set_profiling(ctx, on=True):
     return _check(ctx, load().rt_set_profiling(ctx, 1 if on else 0))
 
@@ -438,7 +449,8 @@ class Solver:
     """One context holding one problem (a ``workloads.Problem``-like object)."""
 
     def __init__(self, problem, device: int = 0, precision: int = RT_FP64, groups: int = 0,
-                 cutoff: Optional[float] = None, ng_period: int = 0, ng_min_delta: float = 0.0):
+                 cutoff: Optional[float] = None, ng_period: int = 0, ng_min_delta: float = 0.0,
+                 os_method: int = RT_OS_JACOBI):
         self.p = problem
         self.precision = precision
         self.ctx = rt_create(device, precision)
@@ -455,6 +467,8 @@ class Solver:
             rt_set_cutoff(self.ctx, cutoff)
         if ng_period:
             rt_set_ng(self.ctx, ng_period, ng_min_delta)
+        if os_method != RT_OS_JACOBI:
+            rt_set_os_method(self.ctx, os_method)
 
     def formal_solution(self, S=None, want_lstar=True):
         return rt_formal_solution(self.ctx, S, self.shape, want_lstar)
