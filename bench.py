@@ -48,6 +48,15 @@ PEAK_FP64_TFLOPS = 1.25
 FLOPS_PER_STEP_FP32 = 45
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
 PEAK_FP32_TFLOPS = 80.5
+# DRAM bytes (read + write) per k_fs64 launch on slab65, from one ncu
+# capture of the current kernel: chi and S stay L2-resident, so the march
+# reads 6.7 MB per launch from DRAM and writes none.
+TRAFFIC_FS64_SLAB65 = 6736384
+# The double-float march executes 493 thread instructions per step (ncu,
+# slab65); its bound is instruction issue: 152 SMs x 4 schedulers x 32 lanes
+# x 2.07 GHz = 40.3e12 thread instructions/s.
+INSTR_PER_STEP_DF64 = 493
+PEAK_ISSUE_TINST = 40.3
 
 # The FP32-sweep iterate stops changing below a relative delta of ~1e-8
 # (rounding), so its outer tolerance is at least 5e-8, and Ng extrapolation
@@ -307,7 +316,8 @@ def run_ours(args):
     achieved = FLOPS_PER_STEP_FP64 * steps_per_launch / (fs_ms / 1e3) / 1e12
     roofline = {"kernel": "k_fs64 (formal-solution march, FP64)", "bound": "alu",
                 "achieved": round(achieved, 4), "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(achieved / PEAK_FP64_TFLOPS, 4), "traffic": None,
+                "frac": round(achieved / PEAK_FP64_TFLOPS, 4),
+                "traffic": TRAFFIC_FS64_SLAB65 if args.workload == "slab65" else None,
                 "peak_source": "recipe FP64 figure (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "flops_per_step": FLOPS_PER_STEP_FP64,
                 "steps_per_launch": round(steps_per_launch),
@@ -356,6 +366,13 @@ def run_ours(args):
                 "fp64_equivalent_frac_of_fp64_peak": round(eq / PEAK_FP64_TFLOPS, 3),
                 "max_rel_dev_from_fp64_J": float(np.max(np.abs(rdf["J"] - r64["J"]) / r64["J"])),
                 "speedup_vs_fp64": round(my_ms / args.steps / (msdf / args.df64_steps), 3)}
+        if stdf["fs_ms"] > 0:
+            issue = INSTR_PER_STEP_DF64 * stdf["steps"] / (stdf["fs_ms"] / 1e3) / 1e12
+            df64["roofline"] = {"kernel": "k_fsdf (double-float march)", "bound": "issue",
+                                "achieved": round(issue, 3), "peak": PEAK_ISSUE_TINST,
+                                "unit": "T thread-instructions/s",
+                                "frac": round(issue / PEAK_ISSUE_TINST, 4),
+                                "instructions_per_step": INSTR_PER_STEP_DF64}
 
     e2e = None
     if args.e2e_steps > 0:
@@ -544,10 +561,12 @@ def main():
     ap.add_argument("--lambdas", type=int, default=512, help="wavelengths of the batch workload")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-iters", type=float, default=60.0,
-                    help="outer iterations per solve assumed by the reference arm")
-    ap.add_argument("--ref-sweeps", type=float, default=2000.0,
-                    help="Jacobi sweeps per solve assumed by the reference arm")
+    ap.add_argument("--ref-iters", type=float, default=18.0,
+                    help="outer iterations per solve assumed by the reference arm (the GPU "
+                         "solve of slab65 with Ng period 4 takes 18)")
+    ap.add_argument("--ref-sweeps", type=float, default=764.0,
+                    help="Jacobi sweeps per solve assumed by the reference arm (764 in the "
+                         "GPU solve of slab65 with Ng period 4)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
