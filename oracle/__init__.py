@@ -6,7 +6,8 @@ arrays through ctypes.  Only the test suite, the smoke check and the CPU
 baseline leg of the benchmark may import it; the GPU library never does.
 
 Sections of Hauschildt & Baron (2011) that each function follows:
-  formal_solution     Sect. 2.2 (formal solution, J and Lambda*)
+  formal_solution     Sect. 2.2 (formal solution, J and Lambda*; long or
+                      short characteristics)
   intensity           Sect. 2.2 (intensity along one characteristic)
   os_step             Sect. 2.3 (operator splitting, Jordan iterations or
                       red-black Gauss-Seidel)
@@ -70,7 +71,8 @@ def _configure(lib):
                               C.c_double, C.c_int, C.c_int, P, P,
                               C.POINTER(C.c_int), P, C.POINTER(C.c_int), C.c_int]
     lib.orc_solve_ng.argtypes = lib.orc_solve.argtypes + [C.c_int, C.c_double]
-    lib.orc_solve_os.argtypes = lib.orc_solve_ng.argtypes + [C.c_int]
+    lib.orc_solve_ex.argtypes = lib.orc_solve_ng.argtypes + [C.c_int, C.c_int]
+    lib.orc_formal_solution_sc.argtypes = lib.orc_formal_solution.argtypes
     lib.orc_os_step_method.argtypes = lib.orc_os_step.argtypes + [C.c_int]
     lib.orc_ng_step.argtypes = [C.c_long, P, P, P, P, P, P, P]
     return lib
@@ -112,8 +114,9 @@ def intensity(p, S, mu, phi, i, j, k) -> float:
     return lib.orc_intensity(C.byref(g), pc, ps, pb, float(mu), float(phi), i, j, k)
 
 
-def formal_solution(p, S, lstar: bool = True, nthreads: int = 0):
-    """Return (J_fs, Lambda* [27][nz][ny][nx] or None) for source S."""
+def formal_solution(p, S, lstar: bool = True, nthreads: int = 0, method: int = 0):
+    """Return (J_fs, Lambda* [27][nz][ny][nx] or None) for source S; method
+    LONG (long characteristics) or SHORT (short characteristics)."""
     lib = _load()
     g = _grid(p)
     chi, pc = _d(p.chi)
@@ -124,10 +127,10 @@ def formal_solution(p, S, lstar: bool = True, nthreads: int = 0):
     w, pw = _d(p.w)
     J = np.empty((p.nz, p.ny, p.nx))
     L = np.empty((27, p.nz, p.ny, p.nx)) if lstar else None
-    rc = lib.orc_formal_solution(C.byref(g), pc, ps, pb, len(mu), pm, pp, pw,
-                                 J.ctypes.data_as(C.POINTER(C.c_double)),
-                                 L.ctypes.data_as(C.POINTER(C.c_double)) if lstar else None,
-                                 nthreads)
+    fn = lib.orc_formal_solution_sc if method == SHORT else lib.orc_formal_solution
+    rc = fn(C.byref(g), pc, ps, pb, len(mu), pm, pp, pw,
+            J.ctypes.data_as(C.POINTER(C.c_double)),
+            L.ctypes.data_as(C.POINTER(C.c_double)) if lstar else None, nthreads)
     if rc:
         raise ValueError(f"oracle formal_solution rejected its input ({rc})")
     return J, L
@@ -154,6 +157,7 @@ def mean_intensity_at(p, S, voxels, nthreads: int = 0):
 
 
 JACOBI, GAUSS_SEIDEL = 0, 1
+LONG, SHORT = 0, 1
 
 
 def os_step(p, lstar, J_fs, J_old, tol_inner=1e-12, max_sweeps=1000, method=JACOBI):
@@ -191,9 +195,10 @@ def ng_step(x0, x1, x2, x3):
 
 def solve(p, tol=None, max_iter=500, tol_inner=1e-12, max_sweeps=1000, J0=None,
           nthreads: int = 0, want_lstar: bool = False, ng_period: int = 0,
-          ng_min_delta: float = 0.0, os_method: int = JACOBI):
+          ng_min_delta: float = 0.0, os_method: int = JACOBI, fs_method: int = 0):
     """Outer iteration (Ng acceleration every ng_period iterations if > 0;
-    operator splitting by os_method, JACOBI or GAUSS_SEIDEL).
+    operator splitting by os_method, JACOBI or GAUSS_SEIDEL; formal solution
+    by fs_method, LONG or SHORT characteristics).
     Returns a dict with J, iters, deltas, sweeps, converged (and lstar if
     asked)."""
     lib = _load()
@@ -210,13 +215,13 @@ def solve(p, tol=None, max_iter=500, tol_inner=1e-12, max_sweeps=1000, J0=None,
     sweeps = np.zeros(max_iter, dtype=np.int32)
     iters = C.c_int()
     tol = p.tol if tol is None else tol
-    rc = lib.orc_solve_os(C.byref(g), pc, pe, pb, len(mu), pm, pp, pw, float(tol),
+    rc = lib.orc_solve_ex(C.byref(g), pc, pe, pb, len(mu), pm, pp, pw, float(tol),
                           int(max_iter), float(tol_inner), int(max_sweeps),
                           1 if J0 is not None else 0, J.ctypes.data_as(C.POINTER(C.c_double)),
                           L.ctypes.data_as(C.POINTER(C.c_double)) if want_lstar else None,
                           C.byref(iters), deltas.ctypes.data_as(C.POINTER(C.c_double)),
                           sweeps.ctypes.data_as(C.POINTER(C.c_int)), nthreads, int(ng_period),
-                          float(ng_min_delta), int(os_method))
+                          float(ng_min_delta), int(os_method), int(fs_method))
     if rc not in (OK, NOTCONV):
         raise ValueError(f"oracle solve rejected its input ({rc})")
     n = iters.value

@@ -55,6 +55,20 @@
  *   dB/dtau at each bottom node, (B[nz-1] - B[nz-2]) / (dz (chi[nz-1] +
  *   chi[nz-2]) / 2), interpolated bilinearly like B.
  *
+ *  Short characteristics (the O(1)-per-pair alternative; the paper's own
+ *   boundary-started tracking is also O(1) per pair, Sect. 2.2).  Per
+ *   direction the planes are taken in the order of propagation; on the plane
+ *   where the direction enters, I = I_bc at each node (as above, evaluated at
+ *   the node); on every other plane k each node takes the intensity from its
+ *   upstream point p = (i - ax, j - ay) on the preceding plane k - s only:
+ *     I(i,j,k) = I(p) e + w_cur S(i,j,k) + w_up S(p),
+ *     dtau = ds (chi(p) + chi(i,j,k)) / 2,
+ *   with I(p), chi(p), S(p) bilinear in that plane (whose intensities are
+ *   complete).  Its Lambda* (same definition as below) has, per direction,
+ *   the diagonal w_cur and, at the four nodes c of p, b_c (w_up + e w_cur(c)),
+ *   w_cur(c) being the weight of c's own segment (0 where c lies on the
+ *   entry plane): I(p) depends on S(c) only through c's own last segment.
+ *
  *  Lambda*.  I is linear in S.  Lambda_{i,j} = sum_d w_d dI_{i,d}/dS_j with
  *   the boundary intensity excluded; Lambda*_{i,o} = Lambda_{i,wrap(i+o)}
  *   for the 27 offsets o in {-1,0,1}^3 (index o = (oz+1)*9+(oy+1)*3+(ox+1));
@@ -339,6 +353,108 @@ int orc_formal_solution(const orc_grid *g, const double *chi, const double *S,
     return ORC_OK;
 }
 
+/* ---- Short characteristics (see header) ---------------------------------- */
+
+/* Intensity on the entry plane of a direction, at node (i, j, k). */
+static double sc_entry_intensity(const orc_grid *g, const double *chi, const double *B,
+                                 int bc, double amu, long i, long j, long k)
+{
+    if (!bc) return 0.0;
+    double I = B[vidx(g, i, j, k)];
+    if (bc == 2) I += amu * diffusion_gradient(g, chi, B, i, j);
+    return I;
+}
+
+/* w_cur and e of the last segment into node (i, j, k), whose upstream
+ * point lies on plane k - s. */
+static void sc_segment(const orc_grid *g, const double *chi, const orc_dir *d, long i, long j,
+                       long k, double *wc, double *wu, double *e)
+{
+    double x = (double)i - d->ax, y = (double)j - d->ay;
+    double dtau = d->ds * (bilinear(g, chi, k - d->s, x, y) + chi[vidx(g, i, j, k)]) / 2.0;
+    orc_weights(dtau, wc, wu);
+    *e = exp(-dtau);
+}
+
+/* Lambda* row of voxel (i0, j0, k0) for one direction (see header). */
+static void sc_lstar_one(const orc_grid *g, const double *chi, double mu, double phi,
+                         double wd, long i0, long j0, long k0, double *lrow /*[27]*/)
+{
+    orc_dir d = dir_geometry(g, mu, phi);
+    long kin = d.s > 0 ? 0 : g->nz - 1;
+    if (k0 == kin) return;                 /* I = I_bc there: no dependence on S */
+    long ku = k0 - d.s;
+    double wc, wu, e;
+    sc_segment(g, chi, &d, i0, j0, k0, &wc, &wu, &e);
+    lrow[13] += wd * wc;
+    double x = (double)i0 - d.ax, y = (double)j0 - d.ay;
+    double fx0 = floor(x), fy0 = floor(y);
+    double tx = x - fx0, ty = y - fy0;
+    long nodes_x[2] = {(long)fx0, (long)fx0 + 1}, nodes_y[2] = {(long)fy0, (long)fy0 + 1};
+    double bx[2] = {1.0 - tx, tx}, by[2] = {1.0 - ty, ty};
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+            long ic = wrapi(nodes_x[a], g->nx), jc = wrapi(nodes_y[b], g->ny);
+            double wcc = 0.0, wuc, ec;
+            if (ku != kin) sc_segment(g, chi, &d, ic, jc, ku, &wcc, &wuc, &ec);
+            int o = neighbour_offset(g, nodes_x[a], nodes_y[b], ku, i0, j0, k0);
+            if (o >= 0) lrow[o] += wd * bx[a] * by[b] * (wu + e * wcc);
+        }
+}
+
+/* Short-characteristics formal solution: J_out[N] and, if lstar_out !=
+ * NULL, its Lambda* [27][N].  Directions are summed in index order. */
+int orc_formal_solution_sc(const orc_grid *g, const double *chi, const double *S,
+                           const double *B, int ndir, const double *mu,
+                           const double *phi, const double *w, double *J_out,
+                           double *lstar_out, int nthreads)
+{
+    if (check_grid(g) || check_dirs(ndir, mu)) return ORC_EINVAL;
+    long nxy = (long)g->nx * g->ny, N = nxy * g->nz;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    double *I = malloc(sizeof(double) * N);
+    if (!I) return ORC_ENOMEM;
+    for (long v = 0; v < N; ++v) J_out[v] = 0.0;
+    for (int dd = 0; dd < ndir; ++dd) {
+        orc_dir d = dir_geometry(g, mu[dd], phi[dd]);
+        int bc = d.s > 0 ? g->top_bc : g->bottom_bc;
+        long kin = d.s > 0 ? 0 : g->nz - 1;
+        for (long n = 0; n < g->nz; ++n) {
+            long k = d.s > 0 ? n : g->nz - 1 - n;
+#pragma omp parallel for schedule(static)
+            for (long t = 0; t < nxy; ++t) {
+                long i = t % g->nx, j = t / g->nx, v = vidx(g, i, j, k);
+                if (k == kin) {
+                    I[v] = sc_entry_intensity(g, chi, B, bc, fabs(mu[dd]), i, j, k);
+                    continue;
+                }
+                long ku = k - d.s;
+                double x = (double)i - d.ax, y = (double)j - d.ay;
+                double wc, wu, e;
+                sc_segment(g, chi, &d, i, j, k, &wc, &wu, &e);
+                I[v] = bilinear(g, I, ku, x, y) * e + wc * S[v] + wu * bilinear(g, S, ku, x, y);
+            }
+        }
+        for (long v = 0; v < N; ++v) J_out[v] += w[dd] * I[v];
+    }
+    free(I);
+    if (lstar_out) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (long v = 0; v < N; ++v) {
+            long i0 = v % g->nx, j0 = (v / g->nx) % g->ny, k0 = v / nxy;
+            double row[27] = {0};
+            for (int dd = 0; dd < ndir; ++dd)
+                sc_lstar_one(g, chi, mu[dd], phi[dd], w[dd], i0, j0, k0, row);
+            for (int o = 0; o < 27; ++o) lstar_out[(long)o * N + v] = row[o];
+        }
+    }
+    return ORC_OK;
+}
+
 /* Mean intensity at a sample of voxels only (full-size spot checks). */
 int orc_mean_intensity_at(const orc_grid *g, const double *chi, const double *S,
                           const double *B, int ndir, const double *mu,
@@ -500,12 +616,13 @@ int orc_solve_ng(const orc_grid *g, const double *chi, const double *eps,
                  double *lstar_out, int *iters_out, double *deltas, int *sweeps,
                  int nthreads, int ng_period, double ng_min_delta);
 
-int orc_solve_os(const orc_grid *g, const double *chi, const double *eps,
+int orc_solve_ex(const orc_grid *g, const double *chi, const double *eps,
                  const double *B, int ndir, const double *mu, const double *phi,
                  const double *w, double tol, int max_iter, double tol_inner,
                  int max_sweeps, int use_initial, double *J_inout,
                  double *lstar_out, int *iters_out, double *deltas, int *sweeps,
-                 int nthreads, int ng_period, double ng_min_delta, int os_method);
+                 int nthreads, int ng_period, double ng_min_delta, int os_method,
+                 int fs_method);
 
 int orc_solve(const orc_grid *g, const double *chi, const double *eps,
               const double *B, int ndir, const double *mu, const double *phi,
@@ -528,22 +645,24 @@ int orc_solve_ng(const orc_grid *g, const double *chi, const double *eps,
                  double *lstar_out, int *iters_out, double *deltas, int *sweeps,
                  int nthreads, int ng_period, double ng_min_delta)
 {
-    return orc_solve_os(g, chi, eps, B, ndir, mu, phi, w, tol, max_iter, tol_inner, max_sweeps,
+    return orc_solve_ex(g, chi, eps, B, ndir, mu, phi, w, tol, max_iter, tol_inner, max_sweeps,
                         use_initial, J_inout, lstar_out, iters_out, deltas, sweeps, nthreads,
-                        ng_period, ng_min_delta, 0);
+                        ng_period, ng_min_delta, 0, 0);
 }
 
-/* The same with the operator-splitting method chosen (0 Jacobi, 1 red-black
- * Gauss-Seidel). */
-int orc_solve_os(const orc_grid *g, const double *chi, const double *eps,
+/* The same with the operator-splitting method (0 Jacobi, 1 red-black
+ * Gauss-Seidel) and the formal solution (0 long characteristics, 1 short
+ * characteristics) chosen. */
+int orc_solve_ex(const orc_grid *g, const double *chi, const double *eps,
                  const double *B, int ndir, const double *mu, const double *phi,
                  const double *w, double tol, int max_iter, double tol_inner,
                  int max_sweeps, int use_initial, double *J_inout,
                  double *lstar_out, int *iters_out, double *deltas, int *sweeps,
-                 int nthreads, int ng_period, double ng_min_delta, int os_method)
+                 int nthreads, int ng_period, double ng_min_delta, int os_method,
+                 int fs_method)
 {
     if (ng_period != 0 && ng_period < 4) return ORC_EINVAL;
-    if (os_method < 0 || os_method > 1) return ORC_EINVAL;
+    if (os_method < 0 || os_method > 1 || fs_method < 0 || fs_method > 1) return ORC_EINVAL;
     if (check_grid(g) || check_dirs(ndir, mu) || max_iter < 1) return ORC_EINVAL;
     long N = (long)g->nx * g->ny * g->nz;
     double *J = malloc(sizeof(double) * N), *S = malloc(sizeof(double) * N);
@@ -561,7 +680,11 @@ int orc_solve_os(const orc_grid *g, const double *chi, const double *eps,
     nhist = 1;
     for (it = 1; it <= max_iter; ++it) {
         for (long v = 0; v < N; ++v) S[v] = eps[v] * B[v] + (1.0 - eps[v]) * J[v];
-        orc_formal_solution(g, chi, S, B, ndir, mu, phi, w, Jfs, it == 1 ? L : NULL, nthreads);
+        if (fs_method == 1)
+            orc_formal_solution_sc(g, chi, S, B, ndir, mu, phi, w, Jfs, it == 1 ? L : NULL,
+                                   nthreads);
+        else
+            orc_formal_solution(g, chi, S, B, ndir, mu, phi, w, Jfs, it == 1 ? L : NULL, nthreads);
         int ns = 0;
         orc_os_step_method(g, L, eps, Jfs, J, Jn, tol_inner, max_sweeps, &ns, os_method);
         if (ng_period) {

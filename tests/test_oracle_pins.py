@@ -157,10 +157,13 @@ def _ray_reference(chi_k, S_k, k0, mu, dz, Ibc):
     return float(I)
 
 
-def test_horizontally_uniform_slab_equals_exact_1d_rays(oracle_mod):
+@pytest.mark.parametrize("method", [0, 1], ids=["long", "short"])
+def test_horizontally_uniform_slab_equals_exact_1d_rays(oracle_mod, method):
     """Horizontally uniform chi and S: every (x,y) column gives the same J,
     equal to the exactly integrated 1D plane-parallel rays on the same
-    z-grid and mu set (Sect. 3.1: the test slab is plane parallel)."""
+    z-grid and mu set (Sect. 3.1: the test slab is plane parallel).  Holds
+    for long and short characteristics alike (interpolating a uniform plane
+    is exact)."""
     nx, ny, nz = 5, 4, 13
     k = np.arange(nz, dtype=float)
     chi_k = 10.0 ** (-3.0 + 5.0 * k / (nz - 1))
@@ -169,7 +172,7 @@ def test_horizontally_uniform_slab_equals_exact_1d_rays(oracle_mod):
     mu, phi, w = W.quadrature(8, 3)
     p = _problem(nx, ny, nz, chi_k[:, None, None], B_k[:, None, None], mu, phi, w, dz=1.0)
     S = np.broadcast_to(S_k[:, None, None], (nz, ny, nx)).copy()
-    J, _ = oracle_mod.formal_solution(p, S, lstar=False)
+    J, _ = oracle_mod.formal_solution(p, S, lstar=False, method=method)
     assert np.max(np.abs(J - J[:, :1, :1])) <= 1e-14 * np.max(np.abs(J))
     for k0 in range(nz):
         Jref = 0.0
@@ -281,7 +284,7 @@ def test_mirror_symmetry(oracle_mod):
 
 # ------------------------------------------------------ brute-force Lambda
 
-def _brute_lambda(oracle_mod, p):
+def _brute_lambda(oracle_mod, p, method=0):
     N = p.nvox
     q = W.Problem(p.nx, p.ny, p.nz, p.chi, p.eps, p.B, p.mu, p.phi, p.w,
                   dx=p.dx, dy=p.dy, dz=p.dz, top_bc=W.BC_ZERO, bottom_bc=W.BC_ZERO)
@@ -289,7 +292,8 @@ def _brute_lambda(oracle_mod, p):
     for j in range(N):
         S = np.zeros(N)
         S[j] = 1.0
-        J, _ = oracle_mod.formal_solution(q, S.reshape(p.nz, p.ny, p.nx), lstar=False)
+        J, _ = oracle_mod.formal_solution(q, S.reshape(p.nz, p.ny, p.nx), lstar=False,
+                                          method=method)
         Lam[:, j] = J.ravel()
     return Lam
 
@@ -332,6 +336,76 @@ def test_lstar_equals_brute_force_lambda(oracle_mod, shape, seed):
     assert np.all(Lf >= 0.0)
     assert np.all(Lf.sum(axis=0) <= Lam.sum(axis=1) * (1 + 1e-14) + 1e-15)
     assert np.all(Lam.sum(axis=1) <= 1.0 + 1e-14)
+
+
+# ------------------------------------------------- short characteristics
+
+def _lattice_direction_problem(top, bottom):
+    """Directions whose per-plane shift (ax, ay) is a lattice vector, so that
+    the upstream point of every node is itself a node."""
+    p = W.random_slab(7, 6, 8, n_theta=2, n_phi=1, seed=5, top_bc=top, bottom_bc=bottom)
+    r2, r3, r5 = math.sqrt(2.0), math.sqrt(3.0), math.sqrt(5.0)
+    p.mu = np.array([1 / r2, -1 / r2, 1 / r3, -1 / r5, 1.0, -1 / r2, -1 / r3])
+    p.phi = np.array([0.0, math.pi / 2, math.pi / 4, math.pi, 0.3, 1.5 * math.pi,
+                      1.25 * math.pi])
+    p.w = np.full(7, 1.0 / 7.0)
+    return p
+
+
+@pytest.mark.parametrize("bc", [(0, 1), (1, 0), (0, 2)])
+def test_short_characteristics_equal_long_on_lattice_directions(oracle_mod, bc):
+    """When every upstream point is a lattice node, interpolating the
+    intensity there is exact, so the short-characteristics J and Lambda*
+    equal the long-characteristics ones for arbitrary 3D chi and S."""
+    p = _lattice_direction_problem(*bc)
+    S = 0.5 + np.random.default_rng(1).random(p.B.shape)
+    Jl, Ll = oracle_mod.formal_solution(p, S)
+    Js, Ls = oracle_mod.formal_solution(p, S, method=oracle_mod.SHORT)
+    assert np.allclose(Js, Jl, rtol=1e-13, atol=0)
+    assert np.max(np.abs(Ls - Ll)) <= 1e-14
+
+
+@pytest.mark.parametrize("shape,seed", [((4, 4, 4), 14), ((3, 5, 4), 15)])
+def test_short_lstar_equals_brute_force_lambda(oracle_mod, shape, seed):
+    """The short-characteristics Lambda* equals the matching elements of its
+    full Lambda, built column by column from unit-source formal solutions;
+    J is linear in S with that Lambda."""
+    nx, ny, nz = shape
+    p = W.random_slab(nx, ny, nz, n_theta=4, n_phi=5, seed=seed)
+    J, L = oracle_mod.formal_solution(p, p.B, method=oracle_mod.SHORT)
+    Lam = _brute_lambda(oracle_mod, p, method=oracle_mod.SHORT)
+    N = p.nvox
+    Lf = L.reshape(27, N)
+    for v in range(N):
+        for o in range(27):
+            j = _neighbour(p, v, o)
+            if j < 0:
+                assert Lf[o, v] == 0.0
+            else:
+                assert abs(Lf[o, v] - Lam[v, j]) <= 1e-14 * max(abs(Lam[v, j]), 1e-3), (v, o)
+    rng = np.random.default_rng(seed)
+    S2 = rng.random((nz, ny, nx)) * 3.0
+    J2, _ = oracle_mod.formal_solution(p, S2, lstar=False, method=oracle_mod.SHORT)
+    J0, _ = oracle_mod.formal_solution(p, np.zeros_like(S2), lstar=False,
+                                       method=oracle_mod.SHORT)
+    assert np.allclose(J2.ravel(), Lam @ S2.ravel() + J0.ravel(), rtol=1e-13, atol=1e-15)
+    assert np.all(Lf >= 0.0) and np.all(Lam.sum(axis=1) <= 1.0 + 1e-14)
+
+
+def test_short_characteristics_converged_ali_equals_dense_solution(oracle_mod):
+    """Outer iteration with the short-characteristics formal solution: the
+    fixed point J = Lambda_sc (eps B + (1 - eps) J) + J_bc, solved directly."""
+    p = W.random_slab(5, 5, 5, n_theta=4, n_phi=5, seed=31, eps_range=(1e-2, 1.0))
+    r = oracle_mod.solve(p, tol=1e-14, max_iter=400, tol_inner=1e-14, max_sweeps=2000,
+                         fs_method=oracle_mod.SHORT)
+    assert r["converged"]
+    Lam = _brute_lambda(oracle_mod, p, method=oracle_mod.SHORT)
+    J0, _ = oracle_mod.formal_solution(p, np.zeros_like(p.B), lstar=False,
+                                       method=oracle_mod.SHORT)
+    eps = p.eps.ravel()
+    A = np.eye(p.nvox) - Lam * (1 - eps)[None, :]
+    ref = np.linalg.solve(A, Lam @ (eps * p.B.ravel()) + J0.ravel())
+    assert np.allclose(r["J"].ravel(), ref, rtol=1e-11, atol=0)
 
 
 # ------------------------------------------- operator splitting and ALI
@@ -581,6 +655,12 @@ _MUTANTS = {
                                "r -= lstar[(long)o * N + v] * J_old[j];"),
     "os_diag_uses_neighbour_eps": ("return acc / (1.0 - lstar[13L * N + v] * (1.0 - eps[v]));",
                                    "return acc / (1.0 - lstar[13L * N + v]);"),
+    "sc_upstream_on_own_plane": ("long ku = k - d.s;\n                double x = (double)i - d.ax",
+                                 "long ku = k;\n                double x = (double)i - d.ax"),
+    "sc_no_attenuation": ("I[v] = bilinear(g, I, ku, x, y) * e + wc * S[v]",
+                          "I[v] = bilinear(g, I, ku, x, y) + wc * S[v]"),
+    "sc_lstar_drops_corner_segment": ("if (o >= 0) lrow[o] += wd * bx[a] * by[b] * (wu + e * wcc);",
+                                      "if (o >= 0) lrow[o] += wd * bx[a] * by[b] * wu;"),
     "gs_black_uses_old_red": ("upd[v] = os_update(g, lstar, eps, rhs, Jn, v, N);",
                               "upd[v] = os_update(g, lstar, eps, rhs, Jc, v, N);"),
     "gs_colour_ignores_depth": ("return (int)((i + j + k) & 1);", "return (int)((i + j) & 1);"),
@@ -607,6 +687,8 @@ def _pin_battery(mod):
         ("geometry", lambda: test_single_direction_unit_source_geometry(mod, +1, 0.0, (1, 0))),
         ("half_node", lambda: test_half_node_shift_splits_bilinearly(mod)),
         ("lstar", lambda: test_lstar_equals_brute_force_lambda(mod, (3, 4, 5), 12)),
+        ("short", lambda: test_short_characteristics_equal_long_on_lattice_directions(mod, (0, 1))),
+        ("short_lstar", lambda: test_short_lstar_equals_brute_force_lambda(mod, (3, 5, 4), 15)),
         ("os_step", lambda: test_os_step_solves_its_linear_system(mod)),
         ("gauss_seidel", lambda: test_gauss_seidel_sweep_equals_block_form(mod, (3, 5, 4), 4)),
         ("ali", lambda: test_converged_ali_equals_dense_solution(mod)),
