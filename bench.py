@@ -160,7 +160,7 @@ def flush_l2(buf):
 
 
 def timed_solves(R, p, precision, dev, stream, flush, warmup, steps, max_iter, clk_id=None,
-                 groups=0, ng=0, ng_min=0.0, tol=None):
+                 groups=0, ng=0, ng_min=0.0, tol=None, fs_method=0):
     """Converged solves of problem `p` through the device API: every step
     re-sets the opacity (Lambda* rebuilt) and J = B, then iterates to
     convergence.  Returns per-step ms, iteration counts, profiling counters,
@@ -181,6 +181,8 @@ def timed_solves(R, p, precision, dev, stream, flush, warmup, steps, max_iter, c
             R.rt_set_direction_groups(ctx, groups)
         if ng:
             R.rt_set_ng(ctx, ng, ng_min)
+        if fs_method:
+            R.rt_set_fs_method(ctx, fs_method)
         tol_used = p.tol if tol is None else tol
 
         def step():
@@ -374,6 +376,24 @@ def run_ours(args):
                                 "frac": round(issue / PEAK_ISSUE_TINST, 4),
                                 "instructions_per_step": INSTR_PER_STEP_DF64}
 
+    # the short-characteristics formal solution (O(1) per pair, FP64): a
+    # different discretisation of the same problem, reported beside it
+    short = None
+    if args.sc_steps > 0:
+        rsc = timed_solves(R, p, R.RT_FP64, dev, stream, flush, 1, args.sc_steps,
+                           args.max_iter, ng=args.ng, fs_method=R.RT_FS_SHORT)
+        stsc = rsc["stats"]
+        mssc = float(sum(rsc["times"]))
+        short = {"value": round(RP.weak_throughput(args.sc_steps, mssc)[0], 6), "unit": "solves/s",
+                 "ms_per_step": round(mssc / args.sc_steps, 3),
+                 "iters_per_solve": stsc["fs_launches"] / args.sc_steps,
+                 "ms_per_fs_launch": round(stsc["fs_ms"] / max(stsc["fs_launches"], 1), 4),
+                 "pairs_per_s_fs": round(stsc["fs_launches"] * pairs / (stsc["fs_ms"] / 1e3), 1)
+                 if stsc["fs_ms"] else None,
+                 "max_rel_diff_from_long_J": float(np.max(np.abs(rsc["J"] - r64["J"]) / r64["J"])),
+                 "median_rel_diff_from_long_J": float(np.median(np.abs(rsc["J"] - r64["J"]) / r64["J"])),
+                 "note": "different discretisation (I interpolated on each plane)"}
+
     e2e = None
     if args.e2e_steps > 0:
         v = e2e_solves(R, p, R.RT_FP64, dev, args.e2e_steps, args.max_iter, args.ng)
@@ -398,6 +418,7 @@ def run_ours(args):
         "roofline": roofline,
         "fp32_sweep": fp32,
         "df64": df64,
+        "short_characteristics": short,
         "gpu_launches": int(st["launches"]),
         "clocks": r64["clocks"],
         "e2e": e2e,
@@ -556,6 +577,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--df64-steps", type=int, default=2)
+    ap.add_argument("--sc-steps", type=int, default=2)
     ap.add_argument("--ng", type=int, default=4,
                     help="Ng acceleration period of the outer iteration (0 = off)")
     ap.add_argument("--lambdas", type=int, default=512, help="wavelengths of the batch workload")

@@ -87,6 +87,8 @@ enum { RT_FP64 = 0, RT_FP32_SWEEP = 1, RT_DF64 = 2 };
 enum { RT_BC_ZERO = 0, RT_BC_PLANCK = 1, RT_BC_DIFFUSION = 2 };
 /* Operator-splitting methods (Sect. 2.3), see rt_set_os_method. */
 enum { RT_OS_JACOBI = 0, RT_OS_GAUSS_SEIDEL = 1 };
+/* Formal-solution methods, see rt_set_fs_method. */
+enum { RT_FS_LONG = 0, RT_FS_SHORT = 1 };
 
 typedef struct rt_ctx rt_ctx;
 
@@ -192,6 +194,25 @@ int rt_last_step_count(rt_ctx *ctx, unsigned long long *steps);
  * extrapolation would amplify that noise.  delta is measured against the
  * extrapolated iterate.  period 0 (default) = off; otherwise >= 4. */
 int rt_set_ng(rt_ctx *ctx, int period, double min_delta);
+
+/* Formal-solution method.  RT_FS_LONG (default): the long characteristic
+ * of every (voxel, direction), integrated back to the boundary plane it
+ * entered through, O(nz) steps per pair.  RT_FS_SHORT: short
+ * characteristics, O(1) per pair (the paper's own tracking of
+ * characteristics started on the boundary planes is O(1) per pair too,
+ * Sect. 2.2): per direction the planes are swept in the order of
+ * propagation and each node takes the intensity from its upstream point on
+ * the preceding plane only, I = I(p) e + w_cur S + w_up S(p) with I(p),
+ * chi(p), S(p) bilinear in that plane; on the entry plane I = I_bc at the
+ * node.  A different discretisation: J differs from the long
+ * characteristics by the interpolation of I (it agrees exactly where every
+ * upstream point is a lattice node, and on horizontally uniform slabs).
+ * Lambda* is that of the chosen method (per direction the diagonal w_cur
+ * and, at the nodes c of p, b_c (w_up + e w_cur(c))).  RT_FS_SHORT needs
+ * precision RT_FP64 (RT_EINVAL otherwise); its working memory is
+ * min(ndir, 1024) * N doubles, allocated at the first formal solution.
+ * Changing the method invalidates Lambda*. */
+int rt_set_fs_method(rt_ctx *ctx, int method);
 
 /* Operator-splitting method (Sect. 2.3 names the Jordan method and
  * Gauss-Seidel iterations).  RT_OS_JACOBI (default): every sweep updates

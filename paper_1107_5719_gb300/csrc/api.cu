@@ -27,6 +27,9 @@ struct rt_ctx {
     bool have_grid = false, have_quad = false, have_chi = false, have_eps = false, have_B = false;
     bool lstar_valid = false, coef_valid = false, b2_valid = false;
     int os_method = RT_OS_JACOBI;
+    int fs_method = RT_FS_LONG;
+    double *scpart = nullptr, *scplanes = nullptr;   // short characteristics
+    size_t scpart_n = 0, scplanes_n = 0;
     int groups_req = 0;
     double cut = -1.0;
 
@@ -138,6 +141,8 @@ void free_grid_buffers(rt_ctx* c)
     dfree(c->Jfs); dfree(c->Jn); dfree(c->Ja); dfree(c->Jb); dfree(c->r);
     dfree(c->lstar); dfree(c->coef); dfree(c->rdiag); dfree(c->partial);
     dfree(c->node4); dfree(c->b2); dfree(c->gdiff); dfree(c->g2); dfree(c->g2df);
+    dfree(c->scpart); dfree(c->scplanes);
+    c->scpart_n = c->scplanes_n = 0;
     free_ng(c);
     c->partial_groups = 0;
 }
@@ -188,6 +193,26 @@ int auto_groups(const rt_ctx* c)
     int G = 1;
     while (G < kSlots && blocks * G < target) G *= 2;
     return G;
+}
+
+// Buffers of the short-characteristics march (sized by grid and directions).
+int ensure_sc(rt_ctx* c)
+{
+    const size_t np = (size_t)sc_chunk(c->g) * (size_t)c->g.N;
+    if (c->scpart_n < np) {
+        dfree(c->scpart);
+        c->scpart_n = 0;
+        CK(dalloc(c->scpart, np));
+        c->scpart_n = np;
+    }
+    const size_t ns = sc_scratch_planes(c->g);
+    if (ns && c->scplanes_n < ns) {
+        dfree(c->scplanes);
+        c->scplanes_n = 0;
+        CK(dalloc(c->scplanes, ns));
+        c->scplanes_n = ns;
+    }
+    return RT_OK;
 }
 
 int ensure_partial(rt_ctx* c)
@@ -317,8 +342,41 @@ int fs_finish(rt_ctx* c, double* Jout)
     return RT_OK;
 }
 
+// Short-characteristics formal solution (FP64 only): J straight from the
+// march's ordered reduction, Lambda* from its own kernel once per opacity.
+int run_fs_short(rt_ctx* c, double* Jout, bool count_steps)
+{
+    int rc = fs_prepare(c);
+    if (rc) return rc;
+    if ((rc = ensure_sc(c))) return rc;
+    if (count_steps) CK(cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned long long), c->stream));
+    if (c->profiling) CK(cudaEventRecord(c->ev[0], c->stream));
+    CK(launch_sc64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->scpart,
+                   c->scplanes, Jout, count_steps ? c->d_steps : nullptr, c->stream));
+    if (c->profiling) {
+        CK(cudaEventRecord(c->ev[1], c->stream));
+        c->fs_pending = true;
+    }
+    const int chunks = (c->g.ndir + sc_chunk(c->g) - 1) / sc_chunk(c->g);
+    c->stats.fs_launches += 1;
+    c->stats.launches += 2 * chunks;
+    if (!c->lstar_valid) {
+        CK(launch_lstar_sc64(c->g, c->chi, c->info, c->off, c->bw, c->lstar, c->stream));
+        c->lstar_valid = true;
+        c->coef_valid = false;
+        c->stats.launches += 1;
+        c->stats.lstar_launches += 1;
+    }
+    if (count_steps) {
+        CK(cudaMemcpyAsync(c->h_steps, c->d_steps, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, c->stream));
+    }
+    return RT_OK;
+}
+
 int run_fs(rt_ctx* c, double* Jout, bool count_steps)
 {
+    if (c->fs_method == RT_FS_SHORT) return run_fs_short(c, Jout, count_steps);
     const int G = auto_groups(c);
     int rc = fs_prepare(c);
     if (rc) return rc;
@@ -1103,6 +1161,20 @@ int rt_set_ng(rt_ctx* c, int period, double min_delta)
     c->ng_period = period;
     c->ng_min_delta = min_delta;
     c->ng_count = 1;
+    return RT_OK;
+}
+
+int rt_set_fs_method(rt_ctx* c, int method)
+{
+    if (!c) return RT_EINVAL;
+    if (method != RT_FS_LONG && method != RT_FS_SHORT)
+        return fail(c, RT_EINVAL, "unknown formal-solution method");
+    if (method == RT_FS_SHORT && c->precision != RT_FP64)
+        return fail(c, RT_EINVAL, "short characteristics need precision RT_FP64");
+    if (method != c->fs_method) {
+        c->fs_method = method;
+        c->lstar_valid = c->coef_valid = false;   // Lambda* differs between methods
+    }
     return RT_OK;
 }
 

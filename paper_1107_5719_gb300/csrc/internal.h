@@ -65,6 +65,22 @@ cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, c
 cudaError_t launch_diffusion_grad(const Geometry& g, double dz, const double* chi,
                                   const double* B, double* G, float* g2, cudaStream_t st);
 
+// ---- short characteristics (sc.cu) -----------------------------------------
+// Directions per march launch (the [directions][N] partial buffer holds
+// sc_chunk(g) slices) and the global plane scratch it needs (doubles; 0 when
+// two planes of I fit in shared memory).
+int sc_chunk(const Geometry& g);
+size_t sc_scratch_planes(const Geometry& g);
+// J[N] = sum_d w_d I_d of the short-characteristics march; part holds
+// sc_chunk(g) * N doubles, gplanes sc_scratch_planes(g) doubles (or null).
+cudaError_t launch_sc64(const Geometry& g, const double* chi, const double* S, const double* B,
+                        const double* G, const DirInfo* info, const StepGeo* off,
+                        const Bw4d* bw, double* part, double* gplanes, double* J,
+                        unsigned long long* steps, cudaStream_t st);
+// Lambda* [27][N] of the short characteristics.
+cudaError_t launch_lstar_sc64(const Geometry& g, const double* chi, const DirInfo* info,
+                              const StepGeo* off, const Bw4d* bw, double* lstar, cudaStream_t st);
+
 // ---- FP32-sweep form (fs32.cu) ---------------------------------------------
 // poff[d][m]: offset of the upstream node (x0, y0) of step m in the padded
 // [nz][2ny][2nx] layout, relative to the voxel's own padded index.

@@ -23,6 +23,7 @@ RT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 RT_FP64, RT_FP32_SWEEP, RT_DF64 = 0, 1, 2
 RT_BC_ZERO, RT_BC_PLANCK, RT_BC_DIFFUSION = 0, 1, 2
 RT_OS_JACOBI, RT_OS_GAUSS_SEIDEL = 0, 1
+RT_FS_LONG, RT_FS_SHORT = 0, 1
 
 _NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV",
           5: "RT_ETIMEOUT", 6: "RT_ESTATE", 7: "RT_ESCRATCH"}
@@ -87,6 +88,7 @@ _SIGS = {
     "rt_set_ng": (C.c_int, [VP, C.c_int, C.c_double]),
     "rt_batch_set_ng": (C.c_int, [VP, C.c_int, C.c_double]),
     "rt_set_os_method": (C.c_int, [VP, C.c_int]),
+    "rt_set_fs_method": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_os_method": (C.c_int, [VP, C.c_int]),
     "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
     "rt_reset_stats": (C.c_int, [VP]),
@@ -317,6 +319,10 @@ def rt_set_os_method(ctx, method):
     return _check(ctx, load().rt_set_os_method(ctx, method))
 
 
+def rt_set_fs_method(ctx, method):
+    return _check(ctx, load().rt_set_fs_method(ctx, method))
+
+
 def rt_batch_set_os_method(b, method):
     return _bcheck(b, load().rt_batch_set_os_method(b, method))
 
@@ -450,7 +456,7 @@ class Solver:
 
     def __init__(self, problem, device: int = 0, precision: int = RT_FP64, groups: int = 0,
                  cutoff: Optional[float] = None, ng_period: int = 0, ng_min_delta: float = 0.0,
-                 os_method: int = RT_OS_JACOBI):
+                 os_method: int = RT_OS_JACOBI, fs_method: int = RT_FS_LONG):
         self.p = problem
         self.precision = precision
         self.ctx = rt_create(device, precision)
@@ -469,6 +475,8 @@ class Solver:
             rt_set_ng(self.ctx, ng_period, ng_min_delta)
         if os_method != RT_OS_JACOBI:
             rt_set_os_method(self.ctx, os_method)
+        if fs_method != RT_FS_LONG:
+            rt_set_fs_method(self.ctx, fs_method)
 
     def formal_solution(self, S=None, want_lstar=True):
         return rt_formal_solution(self.ctx, S, self.shape, want_lstar)
