@@ -15,6 +15,7 @@ Sections of Hauschildt & Baron (2011) that each function follows:
                       Sect. 3.1 item 5 (S)
   ng_step             Sect. 2 (Ng acceleration of the outer iteration)
   weights             segment weights of the linear-source integral
+  weights_parabolic   segment weights of the parabolic-source integral
 """
 
 from __future__ import annotations
@@ -38,7 +39,7 @@ OK, EINVAL, ENOMEM, NOTCONV = 0, 1, 2, 3
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
-                ("top_bc", C.c_int), ("bottom_bc", C.c_int)]
+                ("top_bc", C.c_int), ("bottom_bc", C.c_int), ("src_order", C.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -59,6 +60,8 @@ def _configure(lib):
     G = C.POINTER(Grid)
     lib.orc_weights.argtypes = [C.c_double, P, P]
     lib.orc_weights.restype = None
+    lib.orc_weights_parabolic.argtypes = [C.c_double, C.c_double, P, P, P]
+    lib.orc_weights_parabolic.restype = None
     lib.orc_intensity.argtypes = [G, P, P, P, C.c_double, C.c_double,
                                   C.c_long, C.c_long, C.c_long]
     lib.orc_intensity.restype = C.c_double
@@ -93,7 +96,8 @@ def _d(a):
 
 
 def _grid(p) -> Grid:
-    return Grid(p.nx, p.ny, p.nz, p.dx, p.dy, p.dz, p.top_bc, p.bottom_bc)
+    return Grid(p.nx, p.ny, p.nz, p.dx, p.dy, p.dz, p.top_bc, p.bottom_bc,
+                getattr(p, "src_order", 0))
 
 
 def weights(x: float):
@@ -102,6 +106,15 @@ def weights(x: float):
     a, b = C.c_double(), C.c_double()
     lib.orc_weights(float(x), C.byref(a), C.byref(b))
     return a.value, b.value
+
+
+def weights_parabolic(a: float, b: float):
+    """(P_up, P_cur, P_down) of a segment with optical depth a whose
+    downstream neighbour segment has optical depth b."""
+    lib = _load()
+    u, c, d = C.c_double(), C.c_double(), C.c_double()
+    lib.orc_weights_parabolic(float(a), float(b), C.byref(u), C.byref(c), C.byref(d))
+    return u.value, c.value, d.value
 
 
 def intensity(p, S, mu, phi, i, j, k) -> float:

@@ -55,6 +55,22 @@
  *   dB/dtau at each bottom node, (B[nz-1] - B[nz-2]) / (dz (chi[nz-1] +
  *   chi[nz-2]) / 2), interpolated bilinearly like B.
  *
+ *  Parabolic source (second-order variant, src_order = 1; the paper names
+ *   no order).  On segment m (from p_{m+1} to p_m, optical depth a = dtau_m)
+ *   S is the quadratic in t (optical depth measured upstream from p_m)
+ *   through (a, S(p_{m+1})), (0, S(p_m)) and (-b, S(p_{m-1})), b = dtau_{m-1}
+ *   the optical depth of the next segment downstream.  With the moments
+ *   E_n = int_0^a t^n e^{-t} dt and the Lagrange basis of those nodes, the
+ *   segment adds  P_up S(p_{m+1}) + P_cur S(p_m) + P_down S(p_{m-1}):
+ *     P_up   = (E2 + b E1) / (a (a + b)),
+ *     P_cur  = (a b E0 - (b - a) E1 - E2) / (a b),
+ *     P_down = (E2 - a E1) / (b (a + b)),
+ *   exact for S quadratic in t.  For m = 0 the downstream point p_{-1} =
+ *   (i0 + ax, j0 + ay, k0 + s) is used when plane k0 + s exists (b from the
+ *   trapezoid rule like every dtau); otherwise segment 0 keeps the linear
+ *   weights.  Lambda* then also has entries on plane k0 + s and may have
+ *   negative entries.
+ *
  *  Short characteristics (the O(1)-per-pair alternative; the paper's own
  *   boundary-started tracking is also O(1) per pair, Sect. 2.2).  Per
  *   direction the planes are taken in the order of propagation; on the plane
@@ -123,6 +139,7 @@ typedef struct {
     double dx, dy, dz;
     int top_bc, bottom_bc;      /* 0: I_bc = 0, 1: I_bc = B at the entry point,
                                    2 (bottom only): LTE diffusion, see below */
+    int src_order;              /* 0: linear source, 1: parabolic (long characteristics) */
 } orc_grid;
 
 static long vidx(const orc_grid *g, long i, long j, long k)
@@ -177,6 +194,40 @@ void orc_weights(double x, double *w_cur, double *w_up)
     }
 }
 
+/* Moments E_n = int_0^a t^n e^{-t} dt, n = 0, 1, 2: below a = 1 the
+ * series E_n = sum_{k>=0} (-1)^k a^{n+k+1} / (k! (n+k+1)) (40 terms), above
+ * it E_0 = 1 - e^{-a}, E_1 = 1 - e^{-a} (1 + a), E_2 = 2 - e^{-a} (a^2 + 2a + 2). */
+static void exp_moments(double a, double E[3])
+{
+    if (a < 1.0) {
+        for (int n = 0; n < 3; ++n) {
+            double sum = 0.0, ak = 1.0, fact = 1.0;   /* a^k, k! */
+            for (int k = 0; k < 40; ++k) {
+                if (k > 0) { ak *= a; fact *= (double)k; }
+                double sgn = (k % 2) ? -1.0 : 1.0;
+                sum += sgn * ak * pow(a, n + 1) / (fact * (double)(n + k + 1));
+            }
+            E[n] = sum;
+        }
+    } else {
+        double e = exp(-a);
+        E[0] = -expm1(-a);
+        E[1] = 1.0 - e * (1.0 + a);
+        E[2] = 2.0 - e * (a * a + 2.0 * a + 2.0);
+    }
+}
+
+/* Parabolic segment weights (see header): a the segment's optical depth, b
+ * the next downstream segment's. */
+void orc_weights_parabolic(double a, double b, double *p_up, double *p_cur, double *p_down)
+{
+    double E[3];
+    exp_moments(a, E);
+    *p_up = (E[2] + b * E[1]) / (a * (a + b));
+    *p_cur = (a * b * E[0] - (b - a) * E[1] - E[2]) / (a * b);
+    *p_down = (E[2] - a * E[1]) / (b * (a + b));
+}
+
 /* Geometry of one direction. */
 typedef struct {
     int s;          /* +1: propagates to larger k (came from the top); -1 */
@@ -219,6 +270,16 @@ static double diffusion_gradient_at(const orc_grid *g, const double *chi, const 
          + tx * ty * diffusion_gradient(g, chi, B, i1, j1);
 }
 
+/* Incoming intensity at the entry point (xM, yM) of plane kM for boundary
+ * mode bc (0: none, 1: B, 2: B + |mu| dB/dtau). */
+static double boundary_intensity(const orc_grid *g, const double *chi, const double *B, int bc,
+                                 double mu, long kM, double xM, double yM)
+{
+    double I = bc ? bilinear(g, B, kM, xM, yM) : 0.0;
+    if (bc == 2) I += fabs(mu) * diffusion_gradient_at(g, chi, B, xM, yM);
+    return I;
+}
+
 static int steps_to_boundary(const orc_grid *g, const orc_dir *d, long k0)
 {
     return d->s > 0 ? (int)k0 : (int)(g->nz - 1 - k0);
@@ -226,17 +287,21 @@ static int steps_to_boundary(const orc_grid *g, const orc_dir *d, long k0)
 
 /* Intensity at voxel (i0,j0,k0) in direction (mu,phi): textbook
  * back-to-front recursion along the characteristic. */
+static double intensity_parabolic(const orc_grid *g, const double *chi, const double *S,
+                                  const double *B, double mu, double phi,
+                                  long i0, long j0, long k0);
+
 double orc_intensity(const orc_grid *g, const double *chi, const double *S,
                      const double *B, double mu, double phi,
                      long i0, long j0, long k0)
 {
+    if (g->src_order == 1) return intensity_parabolic(g, chi, S, B, mu, phi, i0, j0, k0);
     orc_dir d = dir_geometry(g, mu, phi);
     int M = steps_to_boundary(g, &d, k0);
     int bc = d.s > 0 ? g->top_bc : g->bottom_bc;
     double xM = (double)i0 - M * d.ax, yM = (double)j0 - M * d.ay;
     long kM = k0 - (long)M * d.s;
-    double I = bc ? bilinear(g, B, kM, xM, yM) : 0.0;
-    if (bc == 2) I += fabs(mu) * diffusion_gradient_at(g, chi, B, xM, yM);
+    double I = boundary_intensity(g, chi, B, bc, mu, kM, xM, yM);
     for (int m = M - 1; m >= 0; --m) {
         double xa = (double)i0 - m * d.ax, ya = (double)j0 - m * d.ay;
         double xb = (double)i0 - (m + 1) * d.ax, yb = (double)j0 - (m + 1) * d.ay;
@@ -248,6 +313,81 @@ double orc_intensity(const orc_grid *g, const double *chi, const double *S,
         orc_weights(dtau, &wc, &wu);
         I = I * exp(-dtau) + wc * S_a + wu * S_b;
     }
+    return I;
+}
+
+/* Point p_m of the characteristic of voxel (i0, j0, k0) (m = -1 is the
+ * downstream point): its plane and lattice position. */
+static void char_point(const orc_dir *d, long i0, long j0, long k0, int m, long *k,
+                       double *x, double *y)
+{
+    *x = (double)i0 - m * d->ax;
+    *y = (double)j0 - m * d->ay;
+    *k = k0 - (long)m * d->s;
+}
+
+/* Optical depths dtau_m, m = -1..M-1, of the segments of the characteristic
+ * (dtau_{-1} only if plane k0 + s exists; has_down says whether it does). */
+static void segment_depths(const orc_grid *g, const double *chi, const orc_dir *d, long i0,
+                           long j0, long k0, int M, double *dtau /*[M+1], index m+1*/,
+                           int *has_down)
+{
+    long kd = k0 + d->s;
+    *has_down = kd >= 0 && kd < g->nz;
+    for (int m = *has_down ? -1 : 0; m < M; ++m) {
+        long ka, kb;
+        double xa, ya, xb, yb;
+        char_point(d, i0, j0, k0, m, &ka, &xa, &ya);
+        char_point(d, i0, j0, k0, m + 1, &kb, &xb, &yb);
+        dtau[m + 1] = d->ds * (bilinear(g, chi, ka, xa, ya) + bilinear(g, chi, kb, xb, yb)) / 2.0;
+    }
+}
+
+/* Weights (on S(p_{m+1}), S(p_m), S(p_{m-1})) of segment m under the
+ * parabolic source; segment 0 falls back to the linear weights when there
+ * is no downstream plane. */
+static void parabolic_segment(const double *dtau, int m, int has_down, double *wu, double *wc,
+                              double *wd)
+{
+    if (m == 0 && !has_down) {
+        orc_weights(dtau[1], wc, wu);
+        *wd = 0.0;
+    } else {
+        orc_weights_parabolic(dtau[m + 1], dtau[m], wu, wc, wd);
+    }
+}
+
+/* Intensity under the parabolic source: back-to-front recursion
+ * I(p_m) = I(p_{m+1}) e^{-dtau_m} + P_up S(p_{m+1}) + P_cur S(p_m) + P_down S(p_{m-1}). */
+static double intensity_parabolic(const orc_grid *g, const double *chi, const double *S,
+                                  const double *B, double mu, double phi,
+                                  long i0, long j0, long k0)
+{
+    orc_dir d = dir_geometry(g, mu, phi);
+    int M = steps_to_boundary(g, &d, k0);
+    int bc = d.s > 0 ? g->top_bc : g->bottom_bc;
+    long kM;
+    double xM, yM;
+    char_point(&d, i0, j0, k0, M, &kM, &xM, &yM);
+    double I = boundary_intensity(g, chi, B, bc, mu, kM, xM, yM);
+    double *dtau = malloc(sizeof(double) * (M + 1));
+    int has_down;
+    segment_depths(g, chi, &d, i0, j0, k0, M, dtau, &has_down);
+    for (int m = M - 1; m >= 0; --m) {
+        double wu, wc, wd, Sm1 = 0.0;
+        parabolic_segment(dtau, m, has_down, &wu, &wc, &wd);
+        long ka, kb, kc;
+        double xa, ya, xb, yb, xc, yc;
+        char_point(&d, i0, j0, k0, m, &ka, &xa, &ya);
+        char_point(&d, i0, j0, k0, m + 1, &kb, &xb, &yb);
+        if (wd != 0.0) {
+            char_point(&d, i0, j0, k0, m - 1, &kc, &xc, &yc);
+            Sm1 = bilinear(g, S, kc, xc, yc);
+        }
+        I = I * exp(-dtau[m + 1]) + wu * bilinear(g, S, kb, xb, yb) + wc * bilinear(g, S, ka, xa, ya)
+          + wd * Sm1;
+    }
+    free(dtau);
     return I;
 }
 
@@ -268,9 +408,16 @@ static int neighbour_offset(const orc_grid *g, long a, long b, long kk,
  * S(p_m) in I is c_m = T_m w_cur(m) [m < M] + T_{m-1} w_up(m-1) [m >= 1],
  * T_m = prod_{l<m} exp(-dtau_l); c_m is shared among the four bilinear
  * nodes of p_m and kept where the node is a nearest neighbour. */
+static void lstar_one_parabolic(const orc_grid *g, const double *chi, double mu, double phi,
+                                double wdir, long i0, long j0, long k0, double *lrow);
+
 static void lstar_one(const orc_grid *g, const double *chi, double mu, double phi,
                       double wd, long i0, long j0, long k0, double *lrow /*[27]*/)
 {
+    if (g->src_order == 1) {
+        lstar_one_parabolic(g, chi, mu, phi, wd, i0, j0, k0, lrow);
+        return;
+    }
     orc_dir d = dir_geometry(g, mu, phi);
     int M = steps_to_boundary(g, &d, k0);
     if (M == 0) return;
@@ -305,10 +452,55 @@ static void lstar_one(const orc_grid *g, const double *chi, double mu, double ph
     free(T); free(wc); free(wu);
 }
 
+/* Lambda* under the parabolic source: the coefficient of S(p_j) in I(p_0)
+ * is c_j = T_{j-1} P_up(j-1) + T_j P_cur(j) + T_{j+1} P_down(j+1) over the
+ * segments that exist (T_m = prod_{l<m} e^{-dtau_l}); j runs from -1 (the
+ * downstream point) to M; c_j is shared among the bilinear nodes of p_j and
+ * kept where they are nearest neighbours. */
+static void lstar_one_parabolic(const orc_grid *g, const double *chi, double mu, double phi,
+                                double wdir, long i0, long j0, long k0, double *lrow)
+{
+    orc_dir d = dir_geometry(g, mu, phi);
+    int M = steps_to_boundary(g, &d, k0);
+    if (M == 0) return;
+    double *dtau = malloc(sizeof(double) * (M + 1));
+    double *T = malloc(sizeof(double) * (M + 1));
+    double *wu = malloc(sizeof(double) * M), *wc = malloc(sizeof(double) * M);
+    double *wdn = malloc(sizeof(double) * M);
+    int has_down;
+    segment_depths(g, chi, &d, i0, j0, k0, M, dtau, &has_down);
+    T[0] = 1.0;
+    for (int m = 0; m < M; ++m) {
+        parabolic_segment(dtau, m, has_down, &wu[m], &wc[m], &wdn[m]);
+        T[m + 1] = T[m] * exp(-dtau[m + 1]);
+    }
+    for (int j = -1; j <= M; ++j) {
+        double c = 0.0;
+        if (j >= 1) c += T[j - 1] * wu[j - 1];
+        if (j >= 0 && j < M) c += T[j] * wc[j];
+        if (j + 1 < M) c += T[j + 1] * wdn[j + 1];
+        if (c == 0.0) continue;
+        long km;
+        double x, y;
+        char_point(&d, i0, j0, k0, j, &km, &x, &y);
+        double fx0 = floor(x), fy0 = floor(y);
+        double tx = x - fx0, ty = y - fy0;
+        long nodes_x[2] = {(long)fx0, (long)fx0 + 1}, nodes_y[2] = {(long)fy0, (long)fy0 + 1};
+        double bx[2] = {1.0 - tx, tx}, by[2] = {1.0 - ty, ty};
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                int o = neighbour_offset(g, nodes_x[a], nodes_y[b], km, i0, j0, k0);
+                if (o >= 0) lrow[o] += wdir * c * bx[a] * by[b];
+            }
+    }
+    free(dtau); free(T); free(wu); free(wc); free(wdn);
+}
+
 static int check_grid(const orc_grid *g)
 {
     if (!g || g->nx < 3 || g->ny < 3 || g->nz < 2) return ORC_EINVAL;
     if (g->top_bc < 0 || g->top_bc > 1 || g->bottom_bc < 0 || g->bottom_bc > 2) return ORC_EINVAL;
+    if (g->src_order < 0 || g->src_order > 1) return ORC_EINVAL;
     if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return ORC_EINVAL;
     return ORC_OK;
 }
@@ -409,7 +601,7 @@ int orc_formal_solution_sc(const orc_grid *g, const double *chi, const double *S
                            const double *phi, const double *w, double *J_out,
                            double *lstar_out, int nthreads)
 {
-    if (check_grid(g) || check_dirs(ndir, mu)) return ORC_EINVAL;
+    if (check_grid(g) || check_dirs(ndir, mu) || g->src_order != 0) return ORC_EINVAL;
     long nxy = (long)g->nx * g->ny, N = nxy * g->nz;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);

@@ -54,6 +54,7 @@ class Problem:
     bottom_bc: int = BC_PLANCK
     tol: float = 1e-8
     name: str = ""
+    src_order: int = 0      # 0: linear source on each segment, 1: parabolic
 
     @property
     def nvox(self) -> int:

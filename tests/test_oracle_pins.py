@@ -287,7 +287,8 @@ def test_mirror_symmetry(oracle_mod):
 def _brute_lambda(oracle_mod, p, method=0):
     N = p.nvox
     q = W.Problem(p.nx, p.ny, p.nz, p.chi, p.eps, p.B, p.mu, p.phi, p.w,
-                  dx=p.dx, dy=p.dy, dz=p.dz, top_bc=W.BC_ZERO, bottom_bc=W.BC_ZERO)
+                  dx=p.dx, dy=p.dy, dz=p.dz, top_bc=W.BC_ZERO, bottom_bc=W.BC_ZERO,
+                  src_order=p.src_order)
     Lam = np.empty((N, N))
     for j in range(N):
         S = np.zeros(N)
@@ -336,6 +337,97 @@ def test_lstar_equals_brute_force_lambda(oracle_mod, shape, seed):
     assert np.all(Lf >= 0.0)
     assert np.all(Lf.sum(axis=0) <= Lam.sum(axis=1) * (1 + 1e-14) + 1e-15)
     assert np.all(Lam.sum(axis=1) <= 1.0 + 1e-14)
+
+
+# ------------------------------------------------------- parabolic source
+
+def _parabolic_mp(a, b):
+    """(P_up, P_cur, P_down) from 40-digit quadrature of the Lagrange basis
+    through t = a, 0, -b against e^{-t} on [0, a]."""
+    mpmath.mp.dps = 40
+    a, b = mpmath.mpf(a), mpmath.mpf(b)
+    Lu = lambda t: t * (t + b) / (a * (a + b))
+    L0 = lambda t: (a - t) * (t + b) / (a * b)
+    Ld = lambda t: t * (t - a) / (b * (a + b))
+    return [float(mpmath.quad(lambda t: L(t) * mpmath.exp(-t), [0, a])) for L in (Lu, L0, Ld)]
+
+
+@pytest.mark.parametrize("a", [1e-7, 3e-3, 0.2, 0.9999, 1.0, 2.5, 40.0, 800.0])
+@pytest.mark.parametrize("b", [1e-6, 0.05, 1.0, 30.0])
+def test_parabolic_weights_match_high_precision(oracle_mod, a, b):
+    """Parabolic weights: 40-digit quadrature of each Lagrange basis
+    polynomial against e^{-t}; they sum to 1 - e^{-a} and integrate t and t^2
+    exactly."""
+    w = oracle_mod.weights_parabolic(a, b)
+    ref = _parabolic_mp(a, b)
+    for x, r in zip(w, ref):
+        assert abs(x - r) <= 1e-13 * abs(r) + 1e-300, (a, b, w, ref)
+    E0 = -math.expm1(-a)
+    assert abs(sum(w) - E0) <= 1e-14 * sum(abs(x) for x in w)
+
+
+def test_parabolic_source_exact_for_quadratic_source(oracle_mod):
+    """Horizontally uniform slab, chi rising with depth, pure absorption,
+    zero boundaries, S quadratic in the (trapezoid) vertical optical depth
+    tau: along every ray the optical depth is (tau - tau_0)/|mu|, so S is
+    quadratic in it and the parabolic source integrates it exactly on
+    unequal segments (all voxels with a downstream plane in both
+    propagation senses, i.e. not the top and bottom planes), while the
+    linear source does not."""
+    nx, ny, nz = 4, 3, 9
+    dz = 1.0
+    k = np.arange(nz, dtype=float)
+    chi_k = 0.2 * 10.0 ** (1.5 * k / (nz - 1))
+    tau = np.concatenate([[0.0], np.cumsum(dz * (chi_k[1:] + chi_k[:-1]) / 2.0)])
+    al, be, ga = 1.0, 0.8, 0.6
+    S_k = al + be * tau + ga * tau ** 2
+    mu, phi, w = W.quadrature(6, 2)
+    p = _problem(nx, ny, nz, chi_k[:, None, None], S_k[:, None, None], mu, phi, w, dz=dz,
+                 top=W.BC_ZERO, bottom=W.BC_ZERO)
+    p.src_order = 1
+    S = np.broadcast_to(S_k[:, None, None], (nz, ny, nx)).copy()
+    mpmath.mp.dps = 30
+    for k0 in range(1, nz - 1):
+        for d in range(len(mu)):
+            amu = abs(mu[d])
+            tb = tau[0] if mu[d] > 0 else tau[-1]       # depth of the entry plane
+            t_M = abs(tau[k0] - tb) / amu
+            sgn = 1.0 if mu[d] > 0 else -1.0
+            # along the ray t = |tau0 - tau| / |mu|: tau = tau0 - sgn |mu| t
+            f = lambda t: (al + be * (tau[k0] - sgn * amu * t) + ga * (tau[k0] - sgn * amu * t) ** 2) \
+                * mpmath.exp(-t)
+            ref = float(mpmath.quad(f, [0, t_M]))
+            I = oracle_mod.intensity(p, S, mu[d], phi[d], 1, 1, k0)
+            assert abs(I - ref) <= 1e-13 * ref, (k0, d, I, ref)
+    p.src_order = 0
+    I_lin = oracle_mod.intensity(p, S, mu[0], phi[0], 1, 1, nz // 2)
+    p.src_order = 1
+    I_par = oracle_mod.intensity(p, S, mu[0], phi[0], 1, 1, nz // 2)
+    assert abs(I_lin - I_par) > 1e-6 * abs(I_par)
+
+
+@pytest.mark.parametrize("shape,seed", [((4, 4, 4), 16), ((3, 5, 4), 17)])
+def test_parabolic_lstar_equals_brute_force_lambda(oracle_mod, shape, seed):
+    """The parabolic-source Lambda* equals the matching elements of its full
+    Lambda (unit-source formal solutions), including the downstream plane."""
+    nx, ny, nz = shape
+    p = W.random_slab(nx, ny, nz, n_theta=4, n_phi=5, seed=seed)
+    p.src_order = 1
+    J, L = oracle_mod.formal_solution(p, p.B)
+    q = W.Problem(p.nx, p.ny, p.nz, p.chi, p.eps, p.B, p.mu, p.phi, p.w, src_order=1,
+                  top_bc=W.BC_ZERO, bottom_bc=W.BC_ZERO)
+    Lam = _brute_lambda(oracle_mod, q)
+    N = p.nvox
+    Lf = L.reshape(27, N)
+    for v in range(N):
+        for o in range(27):
+            j = _neighbour(p, v, o)
+            if j < 0:
+                assert Lf[o, v] == 0.0
+            else:
+                assert abs(Lf[o, v] - Lam[v, j]) <= 1e-14 * max(abs(Lam[v, j]), 1e-3), (v, o)
+    # the downstream plane carries entries (negative ones among them)
+    assert np.any(Lf[18:] != 0.0) and np.any(Lf[:9] != 0.0) and np.any(Lf < 0.0)
 
 
 # ------------------------------------------------- short characteristics
@@ -655,6 +747,11 @@ _MUTANTS = {
                                "r -= lstar[(long)o * N + v] * J_old[j];"),
     "os_diag_uses_neighbour_eps": ("return acc / (1.0 - lstar[13L * N + v] * (1.0 - eps[v]));",
                                    "return acc / (1.0 - lstar[13L * N + v]);"),
+    "parabolic_up_down_swapped": ("*p_up = (E[2] + b * E[1]) / (a * (a + b));",
+                                  "*p_up = (E[2] - a * E[1]) / (b * (a + b));"),
+    "parabolic_downstream_depth_from_upstream": ("orc_weights_parabolic(dtau[m + 1], dtau[m], wu, wc, wd);",
+                                                 "orc_weights_parabolic(dtau[m + 1], dtau[m + 1], wu, wc, wd);"),
+    "parabolic_lstar_drops_downstream": ("if (j + 1 < M) c += T[j + 1] * wdn[j + 1];", "(void)0;"),
     "sc_upstream_on_own_plane": ("long ku = k - d.s;\n                double x = (double)i - d.ax",
                                  "long ku = k;\n                double x = (double)i - d.ax"),
     "sc_no_attenuation": ("I[v] = bilinear(g, I, ku, x, y) * e + wc * S[v]",
@@ -688,6 +785,9 @@ def _pin_battery(mod):
         ("half_node", lambda: test_half_node_shift_splits_bilinearly(mod)),
         ("lstar", lambda: test_lstar_equals_brute_force_lambda(mod, (3, 4, 5), 12)),
         ("short", lambda: test_short_characteristics_equal_long_on_lattice_directions(mod, (0, 1))),
+        ("parabolic", lambda: test_parabolic_weights_match_high_precision(mod, 0.2, 0.05)),
+        ("parabolic_exact", lambda: test_parabolic_source_exact_for_quadratic_source(mod)),
+        ("parabolic_lstar", lambda: test_parabolic_lstar_equals_brute_force_lambda(mod, (3, 5, 4), 17)),
         ("short_lstar", lambda: test_short_lstar_equals_brute_force_lambda(mod, (3, 5, 4), 15)),
         ("os_step", lambda: test_os_step_solves_its_linear_system(mod)),
         ("gauss_seidel", lambda: test_gauss_seidel_sweep_equals_block_form(mod, (3, 5, 4), 4)),
