@@ -160,7 +160,7 @@ def flush_l2(buf):
 
 
 def timed_solves(R, p, precision, dev, stream, flush, warmup, steps, max_iter, clk_id=None,
-                 groups=0, ng=0, ng_min=0.0, tol=None, fs_method=0):
+                 groups=0, ng=0, ng_min=0.0, tol=None, fs_method=0, src_order=0):
     """Converged solves of problem `p` through the device API: every step
     re-sets the opacity (Lambda* rebuilt) and J = B, then iterates to
     convergence.  Returns per-step ms, iteration counts, profiling counters,
@@ -183,6 +183,8 @@ def timed_solves(R, p, precision, dev, stream, flush, warmup, steps, max_iter, c
             R.rt_set_ng(ctx, ng, ng_min)
         if fs_method:
             R.rt_set_fs_method(ctx, fs_method)
+        if src_order:
+            R.rt_set_source_order(ctx, src_order)
         tol_used = p.tol if tol is None else tol
 
         def step():
@@ -394,6 +396,23 @@ def run_ours(args):
                  "median_rel_diff_from_long_J": float(np.median(np.abs(rsc["J"] - r64["J"]) / r64["J"])),
                  "note": "different discretisation (I interpolated on each plane)"}
 
+    # the parabolic-source variant of the FP64 march (second-order source)
+    para = None
+    if args.para_steps > 0:
+        rpa = timed_solves(R, p, R.RT_FP64, dev, stream, flush, 1, args.para_steps,
+                           args.max_iter, ng=args.ng, src_order=R.RT_SRC_PARABOLIC)
+        stpa = rpa["stats"]
+        mspa = float(sum(rpa["times"]))
+        para = {"value": round(RP.weak_throughput(args.para_steps, mspa)[0], 6), "unit": "solves/s",
+                "ms_per_step": round(mspa / args.para_steps, 3),
+                "iters_per_solve": stpa["fs_launches"] / args.para_steps,
+                "ms_per_fs_launch": round(stpa["fs_ms"] / max(stpa["fs_launches"], 1), 4),
+                "fs_steps_per_s": round(stpa["steps"] / (stpa["fs_ms"] / 1e3), 1)
+                if stpa["fs_ms"] else None,
+                "max_rel_diff_from_linear_J": float(np.max(np.abs(rpa["J"] - r64["J"]) / r64["J"])),
+                "median_rel_diff_from_linear_J": float(np.median(np.abs(rpa["J"] - r64["J"]) / r64["J"])),
+                "note": "different discretisation (second-order source)"}
+
     e2e = None
     if args.e2e_steps > 0:
         v = e2e_solves(R, p, R.RT_FP64, dev, args.e2e_steps, args.max_iter, args.ng)
@@ -419,6 +438,7 @@ def run_ours(args):
         "fp32_sweep": fp32,
         "df64": df64,
         "short_characteristics": short,
+        "parabolic_source": para,
         "gpu_launches": int(st["launches"]),
         "clocks": r64["clocks"],
         "e2e": e2e,
@@ -578,6 +598,7 @@ def main():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--df64-steps", type=int, default=2)
     ap.add_argument("--sc-steps", type=int, default=2)
+    ap.add_argument("--para-steps", type=int, default=1)
     ap.add_argument("--ng", type=int, default=4,
                     help="Ng acceleration period of the outer iteration (0 = off)")
     ap.add_argument("--lambdas", type=int, default=512, help="wavelengths of the batch workload")

@@ -89,6 +89,8 @@ enum { RT_BC_ZERO = 0, RT_BC_PLANCK = 1, RT_BC_DIFFUSION = 2 };
 enum { RT_OS_JACOBI = 0, RT_OS_GAUSS_SEIDEL = 1 };
 /* Formal-solution methods, see rt_set_fs_method. */
 enum { RT_FS_LONG = 0, RT_FS_SHORT = 1 };
+/* Source interpolation along a characteristic, see rt_set_source_order. */
+enum { RT_SRC_LINEAR = 0, RT_SRC_PARABOLIC = 1 };
 
 typedef struct rt_ctx rt_ctx;
 
@@ -213,6 +215,22 @@ int rt_set_ng(rt_ctx *ctx, int period, double min_delta);
  * min(ndir, 1024) * N doubles, allocated at the first formal solution.
  * Changing the method invalidates Lambda*. */
 int rt_set_fs_method(rt_ctx *ctx, int method);
+
+/* Source interpolation on each segment of a characteristic (the paper
+ * names no order).  RT_SRC_LINEAR (default): S linear in optical depth
+ * between the segment's end points.  RT_SRC_PARABOLIC: S quadratic through
+ * the segment's two end points and the next point downstream, in optical
+ * depth t measured upstream from the segment's downstream end (nodes at
+ * t = a, 0, -b; a, b the optical depths of the segment and of the next one
+ * downstream); with E_n = int_0^a t^n e^{-t} dt the segment adds
+ * P_up S_up + P_cur S_cur + P_down S_down, P_up = (E2 + b E1)/(a(a+b)),
+ * P_cur = (a b E0 - (b-a) E1 - E2)/(a b), P_down = (E2 - a E1)/(b(a+b)).
+ * The last segment into a voxel uses the point one plane beyond the voxel
+ * when that plane exists, else the linear weights.  Lambda* then also
+ * couples to the downstream plane and may have negative entries.  Needs
+ * precision RT_FP64 and RT_FS_LONG (RT_EINVAL otherwise); changing it
+ * invalidates Lambda*. */
+int rt_set_source_order(rt_ctx *ctx, int order);
 
 /* Operator-splitting method (Sect. 2.3 names the Jordan method and
  * Gauss-Seidel iterations).  RT_OS_JACOBI (default): every sweep updates

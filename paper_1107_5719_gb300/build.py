@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt3d.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["fs.cu", "fs32.cu", "fsdf.cu", "sc.cu", "os.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["fs.cu", "fs32.cu", "fsdf.cu", "sc.cu", "para.cu", "os.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -28,6 +28,8 @@ struct rt_ctx {
     bool lstar_valid = false, coef_valid = false, b2_valid = false;
     int os_method = RT_OS_JACOBI;
     int fs_method = RT_FS_LONG;
+    int src_order = RT_SRC_LINEAR;
+    DownGeo* dn = nullptr;   // downstream-point table (FP64 contexts)
     double *scpart = nullptr, *scplanes = nullptr;   // short characteristics
     size_t scpart_n = 0, scplanes_n = 0;
     int groups_req = 0;
@@ -150,6 +152,7 @@ void free_grid_buffers(rt_ctx* c)
 void free_tables(rt_ctx* c)
 {
     dfree(c->info); dfree(c->off); dfree(c->bw); dfree(c->bw32); dfree(c->poff); dfree(c->bwdf);
+    dfree(c->dn);
     dfree(c->d_mu); dfree(c->d_phi); dfree(c->d_w);
 }
 
@@ -333,7 +336,10 @@ int fs_finish(rt_ctx* c, double* Jout)
         CK(launch_sum_groups_src(c->g.N, c->partial, c->S, c->wsum, Jout, c->stream));
     c->stats.launches += 1;
     if (!c->lstar_valid) {
-        CK(launch_lstar64(c->g, c->chi, c->info, c->off, c->bw, c->lstar, c->stream));
+        if (c->src_order == RT_SRC_PARABOLIC)
+            CK(launch_lstar64p(c->g, c->chi, c->info, c->off, c->bw, c->dn, c->lstar, c->stream));
+        else
+            CK(launch_lstar64(c->g, c->chi, c->info, c->off, c->bw, c->lstar, c->stream));
         c->lstar_valid = true;
         c->coef_valid = false;
         c->stats.launches += 1;
@@ -383,7 +389,11 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
     if (count_steps) CK(cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned long long), c->stream));
     const double cut = cut_of(c);
     if (c->profiling) CK(cudaEventRecord(c->ev[0], c->stream));
-    if (c->precision == RT_FP64) {
+    if (c->precision == RT_FP64 && c->src_order == RT_SRC_PARABOLIC) {
+        CK(launch_fs64p(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->dn,
+                        c->scal + 0, cut, G, c->partial, count_steps ? c->d_steps : nullptr,
+                        c->stream));
+    } else if (c->precision == RT_FP64) {
         CK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->scal + 0,
                        cut, G, c->partial, count_steps ? c->d_steps : nullptr, c->stream));
     } else if (c->precision == RT_DF64) {
@@ -1008,6 +1018,10 @@ int rt_set_quadrature(rt_ctx* c, int ndir, const double* mu, const double* phi, 
         CK(dalloc(c->poff, T));
         CK(launch_pad_offsets(c->g, c->info, c->off, c->poff, c->stream));
         c->stats.launches += 1;
+    } else {
+        CK(dalloc(c->dn, (size_t)ndir));
+        CK(launch_down_tables(c->g, c->dx, c->dy, c->dz, c->d_mu, c->d_phi, c->dn, c->stream));
+        c->stats.launches += 1;
     }
     if (c->precision == RT_DF64) {
         CK(dalloc(c->bwdf, 2 * T));
@@ -1171,9 +1185,25 @@ int rt_set_fs_method(rt_ctx* c, int method)
         return fail(c, RT_EINVAL, "unknown formal-solution method");
     if (method == RT_FS_SHORT && c->precision != RT_FP64)
         return fail(c, RT_EINVAL, "short characteristics need precision RT_FP64");
+    if (method == RT_FS_SHORT && c->src_order != RT_SRC_LINEAR)
+        return fail(c, RT_EINVAL, "short characteristics take the linear source only");
     if (method != c->fs_method) {
         c->fs_method = method;
         c->lstar_valid = c->coef_valid = false;   // Lambda* differs between methods
+    }
+    return RT_OK;
+}
+
+int rt_set_source_order(rt_ctx* c, int order)
+{
+    if (!c) return RT_EINVAL;
+    if (order != RT_SRC_LINEAR && order != RT_SRC_PARABOLIC)
+        return fail(c, RT_EINVAL, "unknown source order");
+    if (order == RT_SRC_PARABOLIC && (c->precision != RT_FP64 || c->fs_method != RT_FS_LONG))
+        return fail(c, RT_EINVAL, "the parabolic source needs RT_FP64 and long characteristics");
+    if (order != c->src_order) {
+        c->src_order = order;
+        c->lstar_valid = c->coef_valid = false;
     }
     return RT_OK;
 }

@@ -56,6 +56,20 @@ __device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.h, -a.l}; }
 
 __device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
 
+// a + b with the low parts added once (Dekker's add, 11 operations against
+// 20): the error is bounded by ~2^-47 (|a| + |b|) instead of 2^-47 |a + b|.
+// Used wherever that bound is already the rounding level of the operands
+// (sums of like-signed terms, differences of quantities that each carry a
+// 2^-48 representation error).
+__device__ __forceinline__ dfl df_add_s(dfl a, dfl b)
+{
+    dfl s = two_sum(a.h, b.h);
+    s.l += a.l + b.l;
+    return quick_two_sum(s.h, s.l);
+}
+
+__device__ __forceinline__ dfl df_sub_s(dfl a, dfl b) { return df_add_s(a, df_neg(b)); }
+
 // a + b with b a float
 __device__ __forceinline__ dfl df_add_f(dfl a, float b)
 {
@@ -95,6 +109,21 @@ __device__ __forceinline__ dfl df_div(dfl a, dfl b)
     const float q2 = res.h * r;
     const dfl q = quick_two_sum(q1, q2);
     const dfl res2 = df_sub(a, df_mul(b, q));
+    return df_add_f(q, res2.h * r);
+}
+
+// As df_div with the residuals formed by df_sub_s: each residual is
+// a - b q with |a - b q| ~ 2^-23 |a|, formed to ~2^-48 |a|, so every
+// correction still gains ~23 bits.
+__device__ __forceinline__ dfl df_div_s(dfl a, dfl b)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b.h));
+    const float q1 = a.h * r;
+    const dfl res = df_sub_s(a, df_mul_f(b, q1));
+    const float q2 = res.h * r;
+    const dfl q = quick_two_sum(q1, q2);
+    const dfl res2 = df_sub_s(a, df_mul(b, q));
     return df_add_f(q, res2.h * r);
 }
 

@@ -8,6 +8,11 @@
 // rounding scales with I - S_0 and is not amplified by the near-singular
 // scattering problem at small eps.
 //
+// Sums use Dekker's add (df_add_s): its error bound, ~2^-47 times the sum of
+// the operands' magnitudes, is the level at which the operands themselves
+// are known (chi, S, the table entries and the bilinear weights each carry
+// a 2^-48 representation error), so the accurate add would buy nothing.
+//
 // Layout: per node a float4 {chi_hi, chi_lo, S_hi, S_lo} in planes padded to
 // 2ny x 2nx by periodic copies (same addressing as the FP32 sweep); bilinear
 // weights per (direction, step) as two float4 (hi and lo parts); boundary B
@@ -50,20 +55,20 @@ __device__ __forceinline__ void exp_neg_df(dfl x, const dfl* __restrict__ tab, d
     constexpr float kL2 = -7.440055516116928e-12f;
     constexpr float kL3 = -3.4309311478864607e-19f;
     const float k = rintf(x.h * kInvL);
-    dfl r = df_add(x, df_neg(two_prod(k, kL1)));
-    r = df_add(r, df_neg(two_prod(k, kL2)));
+    dfl r = df_add_s(x, df_neg(two_prod(k, kL1)));
+    r = df_add_s(r, df_neg(two_prod(k, kL2)));
     r = df_add_f(r, -k * kL3);
     const dfl r2 = df_mul(r, r);
     const float tail = r2.h * r.h * fmaf(-r.h, 1.0f / 24.0f, 1.0f / 6.0f);
-    const dfl p = df_add(df_neg(r), df_add_f(df_scale(r2, 0.5f), -tail));
+    const dfl p = df_add_s(df_neg(r), df_add_f(df_scale(r2, 0.5f), -tail));
     const int ki = (int)k;
     const int m = ki >> 8, j = ki & (kExpTableDF - 1);
     const float sc = __int_as_float((127 - m) << 23);   // 2^-m, normal for x <= 80
     const dfl t = df_scale(tab[j], sc);
     const dfl tp = df_mul(t, p);
     const dfl c = m == 0 ? tab[kExpTableDF + j] : df_add_f(df_neg(t), 1.0f);
-    e = df_add(t, tp);
-    om = df_sub(c, tp);
+    e = df_add_s(t, tp);
+    om = df_sub_s(c, tp);
 }
 
 // Segment weights in double-float (same definitions as weights.cuh).
@@ -83,11 +88,11 @@ __device__ __forceinline__ void seg_weights_df(dfl x, const dfl* __restrict__ ta
         dfl E = df_add_f(df_mul(z, c24), rE);
         E = df_add_f(E, 0.5f);
         dfl Op = df_add_f(df_mul(z, c120), rO);
-        Op = df_add(c6, Op);
+        Op = df_add_s(c6, Op);
         const dfl O = df_mul(x, Op);
-        wc = df_mul(x, df_add(E, df_neg(O)));
-        e = df_add(df_add_f(df_neg(x), 1.0f), df_mul(x, wc));
-        wu = df_mul(df_mul(x, e), df_add(E, O));
+        wc = df_mul(x, df_add_s(E, df_neg(O)));
+        e = df_add_s(df_add_f(df_neg(x), 1.0f), df_mul(x, wc));
+        wu = df_mul(df_mul(x, e), df_add_s(E, O));
     } else {
         dfl om;
         if (x.h <= 80.0f) {
@@ -98,9 +103,9 @@ __device__ __forceinline__ void seg_weights_df(dfl x, const dfl* __restrict__ ta
         }
         // q = om / x: FP32 quotient and two corrections from the residual
         // (one leaves a relative error near 2^-44, amplified up to 40x in 1 - q)
-        const dfl q = df_div(om, x);
+        const dfl q = df_div_s(om, x);
         wc = df_add_f(df_neg(q), 1.0f);
-        wu = df_sub(q, e);
+        wu = df_sub_s(q, e);
     }
 }
 
@@ -174,11 +179,11 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
                                             q11.x, q11.y);
                     const dfl sb = bilin_df(wh, wl, q00.z, q00.w, q10.z, q10.w, q01.z, q01.w,
                                             q11.z, q11.w);
-                    const dfl db = df_sub(sb, S0);
-                    const dfl x = df_mul(hs, df_add(ca, cb));
+                    const dfl db = df_sub_s(sb, S0);
+                    const dfl x = df_mul(hs, df_add_s(ca, cb));
                     dfl wc, wu, e;
                     seg_weights_df(x, tab, wc, wu, e);
-                    I = df_add(I, df_mul(T, df_add(df_mul(wc, da), df_mul(wu, db))));
+                    I = df_add_s(I, df_mul(T, df_add_s(df_mul(wc, da), df_mul(wu, db))));
                     T = df_mul(T, e);
                     ca = cb;
                     da = db;
@@ -204,13 +209,13 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
                             const float2 g00 = pg[0], g10 = pg[1], g01 = pg[W], g11 = pg[W + 1];
                             const dfl gr = bilin_df(wh, wl, g00.x, g00.y, g10.x, g10.y, g01.x,
                                                     g01.y, g11.x, g11.y);
-                            ibc = df_add(ibc, df_mul(df_make(di.amu32, di.amu32lo), gr));
+                            ibc = df_add_s(ibc, df_mul(df_make(di.amu32, di.amu32lo), gr));
                         }
-                        ibc = df_sub(ibc, S0);
+                        ibc = df_sub_s(ibc, S0);
                     } else {
                         ibc = df_neg(S0);
                     }
-                    I = df_add(I, df_mul(T, ibc));
+                    I = df_add_s(I, df_mul(T, ibc));
                 }
                 nsteps += (unsigned long long)m;
                 Jp = fma(di.w, df_to_double(I), Jp);

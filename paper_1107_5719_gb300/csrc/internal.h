@@ -40,6 +40,15 @@ struct alignas(32) Bw4d {
     double x, y, z, w;
 };
 
+// Downstream point p_{-1} = (i0 + ax, j0 + ay) of a direction (parabolic
+// source): lattice offset, bilinear weights, and the Lambda* offset index of
+// its four nodes on plane k0 + s (-1 where not a nearest neighbour).
+struct alignas(32) DownGeo {
+    Bw4d b;
+    int ox, oy;
+    int ld[4];
+};
+
 struct Geometry {
     int nx, ny, nz, ndir;
     long long N;            // nx * ny * nz
@@ -64,6 +73,18 @@ cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, c
 // padded FP32 copy g2[2ny][2nx] if g2 != null.
 cudaError_t launch_diffusion_grad(const Geometry& g, double dz, const double* chi,
                                   const double* B, double* G, float* g2, cudaStream_t st);
+
+// ---- parabolic source (para.cu) --------------------------------------------
+cudaError_t launch_down_tables(const Geometry& g, double dx, double dy, double dz,
+                               const double* mu, const double* phi, DownGeo* dn, cudaStream_t st);
+// As launch_fs64 with the parabolic source.
+cudaError_t launch_fs64p(const Geometry& g, const double* chi, const double* S, const double* B,
+                         const double* G, const DirInfo* info, const StepGeo* off,
+                         const Bw4d* bw, const DownGeo* dn, const double* smax, double cut,
+                         int groups, double* partial, unsigned long long* steps, cudaStream_t st);
+cudaError_t launch_lstar64p(const Geometry& g, const double* chi, const DirInfo* info,
+                            const StepGeo* off, const Bw4d* bw, const DownGeo* dn, double* lstar,
+                            cudaStream_t st);
 
 // ---- short characteristics (sc.cu) -----------------------------------------
 // Directions per march launch (the [directions][N] partial buffer holds

@@ -24,6 +24,7 @@ RT_FP64, RT_FP32_SWEEP, RT_DF64 = 0, 1, 2
 RT_BC_ZERO, RT_BC_PLANCK, RT_BC_DIFFUSION = 0, 1, 2
 RT_OS_JACOBI, RT_OS_GAUSS_SEIDEL = 0, 1
 RT_FS_LONG, RT_FS_SHORT = 0, 1
+RT_SRC_LINEAR, RT_SRC_PARABOLIC = 0, 1
 
 _NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV",
           5: "RT_ETIMEOUT", 6: "RT_ESTATE", 7: "RT_ESCRATCH"}
@@ -89,6 +90,7 @@ _SIGS = {
     "rt_batch_set_ng": (C.c_int, [VP, C.c_int, C.c_double]),
     "rt_set_os_method": (C.c_int, [VP, C.c_int]),
     "rt_set_fs_method": (C.c_int, [VP, C.c_int]),
+    "rt_set_source_order": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_os_method": (C.c_int, [VP, C.c_int]),
     "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
     "rt_reset_stats": (C.c_int, [VP]),
@@ -323,6 +325,10 @@ def rt_set_fs_method(ctx, method):
     return _check(ctx, load().rt_set_fs_method(ctx, method))
 
 
+def rt_set_source_order(ctx, order):
+    return _check(ctx, load().rt_set_source_order(ctx, order))
+
+
 def rt_batch_set_os_method(b, method):
     return _bcheck(b, load().rt_batch_set_os_method(b, method))
 
@@ -477,6 +483,8 @@ class Solver:
             rt_set_os_method(self.ctx, os_method)
         if fs_method != RT_FS_LONG:
             rt_set_fs_method(self.ctx, fs_method)
+        if getattr(problem, "src_order", 0):
+            rt_set_source_order(self.ctx, problem.src_order)
 
     def formal_solution(self, S=None, want_lstar=True):
         return rt_formal_solution(self.ctx, S, self.shape, want_lstar)
