@@ -52,10 +52,10 @@ PEAK_FP32_TFLOPS = 80.5
 # capture of the current kernel: chi and S stay L2-resident, so the march
 # reads 6.7 MB per launch from DRAM and writes none.
 TRAFFIC_FS64_SLAB65 = 6736384
-# The double-float march executes 493 thread instructions per step (ncu,
+# The double-float march executes 398 thread instructions per step (ncu,
 # slab65); its bound is instruction issue: 152 SMs x 4 schedulers x 32 lanes
 # x 2.07 GHz = 40.3e12 thread instructions/s.
-INSTR_PER_STEP_DF64 = 493
+INSTR_PER_STEP_DF64 = 398
 PEAK_ISSUE_TINST = 40.3
 
 # The FP32-sweep iterate stops changing below a relative delta of ~1e-8
@@ -413,6 +413,51 @@ def run_ours(args):
                 "median_rel_diff_from_linear_J": float(np.median(np.abs(rpa["J"] - r64["J"]) / r64["J"])),
                 "note": "different discretisation (second-order source)"}
 
+    # precision form at eps = 1e-6 (strong scattering) on a 9x9x129 column
+    # with 32x8 directions: FP32 sweep to its tolerance, then double-float
+    # iterations with Ng from that J, each against the FP64 fixed point
+    precision = None
+    if args.precision_check:
+        import time as _t
+        from paper_1107_5719_gb300 import workloads as W
+        pc = W.slab_precision(n=9, nzz=129, n_theta=32, n_phi=8)
+
+        def _solve(prec, tol, ngmin=0.0, then=None):
+            ctx = R.rt_create(dev.index, prec)
+            try:
+                R.rt_set_grid(ctx, pc.nx, pc.ny, pc.nz, pc.dx, pc.dy, pc.dz)
+                R.rt_set_boundary(ctx, pc.top_bc, pc.bottom_bc)
+                R.rt_set_quadrature(ctx, pc.mu, pc.phi, pc.w)
+                R.rt_set_opacity(ctx, pc.chi)
+                R.rt_set_epsilon(ctx, pc.eps)
+                R.rt_set_planck(ctx, pc.B)
+                R.rt_set_ng(ctx, 4, ngmin)
+                t0 = _t.time()
+                r = R.rt_solve(ctx, (pc.nz, pc.ny, pc.nx), tol=tol, max_iter=5000)
+                out = [(r, _t.time() - t0)]
+                if then is not None:
+                    R.rt_set_precision(ctx, then[0])
+                    R.rt_set_ng(ctx, 4, 0.0)
+                    t0 = _t.time()
+                    out.append((R.rt_solve(ctx, (pc.nz, pc.ny, pc.nx), tol=then[1], max_iter=500),
+                                _t.time() - t0))
+                return out
+            finally:
+                R.rt_destroy(ctx)
+
+        (c64, t64), = _solve(R.RT_FP64, 1e-11)
+        (c32, t32), (cfin, tfin) = _solve(R.RT_FP32_SWEEP, TOL_FP32, NG_MIN_FP32,
+                                          then=(R.RT_DF64, 1e-8))
+        err = lambda r: float(np.max(np.abs(r["J"] - c64["J"]) / c64["J"]))
+        precision = {"workload": "9x9x129 column, strong-scattering chi law, eps = 1e-6, "
+                                 "32x8 directions",
+                     "fp64": {"iters": c64["iters"], "s": round(t64, 2), "tol": 1e-11},
+                     "fp32_sweep": {"iters": c32["iters"], "s": round(t32, 2), "tol": TOL_FP32,
+                                    "max_rel_err_vs_fp64": err(c32)},
+                     "fp32_then_df64": {"iters": cfin["iters"], "s": round(tfin, 2), "tol": 1e-8,
+                                        "max_rel_err_vs_fp64": err(cfin)},
+                     "target": 1e-6}
+
     e2e = None
     if args.e2e_steps > 0:
         v = e2e_solves(R, p, R.RT_FP64, dev, args.e2e_steps, args.max_iter, args.ng)
@@ -439,6 +484,7 @@ def run_ours(args):
         "df64": df64,
         "short_characteristics": short,
         "parabolic_source": para,
+        "precision_eps1e-6": precision,
         "gpu_launches": int(st["launches"]),
         "clocks": r64["clocks"],
         "e2e": e2e,
@@ -599,6 +645,8 @@ def main():
     ap.add_argument("--df64-steps", type=int, default=2)
     ap.add_argument("--sc-steps", type=int, default=2)
     ap.add_argument("--para-steps", type=int, default=1)
+    ap.add_argument("--no-precision-check", dest="precision_check", action="store_false",
+                    help="skip the eps = 1e-6 precision comparison")
     ap.add_argument("--ng", type=int, default=4,
                     help="Ng acceleration period of the outer iteration (0 = off)")
     ap.add_argument("--lambdas", type=int, default=512, help="wavelengths of the batch workload")

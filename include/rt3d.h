@@ -216,6 +216,16 @@ int rt_set_ng(rt_ctx *ctx, int period, double min_delta);
  * Changing the method invalidates Lambda*. */
 int rt_set_fs_method(rt_ctx *ctx, int method);
 
+/* Switch a context between RT_FP32_SWEEP and RT_DF64 (either direction;
+ * RT_EINVAL for RT_FP64 on either side).  Everything else is kept: J, Lambda*,
+ * the OS coefficients, all settings; the Ng history restarts.  Typical use:
+ * iterate with the FP32 sweep to its tolerance (about 5e-8; its iterate then
+ * sits near its ~1e-8 rounding floor), then switch to RT_DF64 and continue
+ * with Ng on to the final tolerance: the FP64-accurate iterates let Ng
+ * remove the slowly converging error that small eps leaves behind.
+ * Allocates the double-float tables on the first switch to RT_DF64. */
+int rt_set_precision(rt_ctx *ctx, int precision);
+
 /* Source interpolation on each segment of a characteristic (the paper
  * names no order).  RT_SRC_LINEAR (default): S linear in optical depth
  * between the segment's end points.  RT_SRC_PARABOLIC: S quadratic through
@@ -341,6 +351,12 @@ int rt_batch_set_stream(rt_batch *batch, void *stream);
 /* Restart every problem from J = B; rebuild_lstar != 0 also rebuilds
  * Lambda* (and the OS coefficients) at the next iteration. */
 int rt_batch_reset(rt_batch *batch, int rebuild_lstar);
+/* Switch every problem between RT_FP32_SWEEP and RT_DF64 (rt_set_precision)
+ * and start a new stage from the current iterates: iteration counts, deltas
+ * and convergence flags restart, J and Lambda* are kept.  The FP32 stage runs
+ * as one fused launch per iteration, the double-float stage as one launch per
+ * problem. */
+int rt_batch_set_precision(rt_batch *batch, int precision);
 /* Iterate until every problem has delta < tol or max_iter iterations.
  * iters[nprob], deltas[nprob] (host, may be NULL) receive each problem's
  * iteration count and last delta; *n_converged the number converged.

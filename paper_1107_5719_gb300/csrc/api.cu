@@ -1194,6 +1194,30 @@ int rt_set_fs_method(rt_ctx* c, int method)
     return RT_OK;
 }
 
+int rt_set_precision(rt_ctx* c, int precision)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if (precision == c->precision) return RT_OK;
+    const bool ok = (precision == RT_FP32_SWEEP || precision == RT_DF64) &&
+                    (c->precision == RT_FP32_SWEEP || c->precision == RT_DF64);
+    if (!ok) return fail(c, RT_EINVAL, "precision switches only between RT_FP32_SWEEP and RT_DF64");
+    if (precision == RT_DF64) {
+        // buffers the double-float march needs beyond the FP32 sweep's
+        if (c->have_grid && !c->g2df) CK(dalloc(c->g2df, (size_t)4 * c->g.nx * c->g.ny));
+        if (c->have_quad && !c->bwdf) {
+            const long long T = (long long)c->g.ndir * c->g.nz;
+            CK(dalloc(c->bwdf, (size_t)(2 * T)));
+            CK(launch_bw_df(T, c->bw, c->bwdf, c->stream));
+            c->stats.launches += 1;
+        }
+    }
+    c->precision = precision;
+    c->gdiff_valid = false;    // the gradient's packed copy differs between the forms
+    c->ng_count = 1;           // restart the Ng history with iterates of the new form
+    return RT_OK;
+}
+
 int rt_set_source_order(rt_ctx* c, int order)
 {
     if (!c) return RT_EINVAL;
@@ -1372,6 +1396,26 @@ int rt_batch_reset(rt_batch* b, int rebuild_lstar)
         b->delta[p] = 0.0;
         b->converged[p] = 0;
     }
+    return RT_OK;
+}
+
+int rt_batch_set_precision(rt_batch* b, int precision)
+{
+    if (!b) return RT_EINVAL;
+    b->err.clear();
+    BCK(cudaSetDevice(b->device));
+    if (precision == b->precision) return RT_OK;
+    if (!((precision == RT_FP32_SWEEP || precision == RT_DF64) &&
+          (b->precision == RT_FP32_SWEEP || b->precision == RT_DF64)))
+        return bfail(b, RT_EINVAL, "precision switches only between RT_FP32_SWEEP and RT_DF64");
+    for (size_t p = 0; p < b->ctx.size(); ++p) {
+        const int rc = rt_set_precision(b->ctx[p], precision);
+        if (rc) return bfail(b, rc, "problem %zu: %s", p, rt_last_error(b->ctx[p]));
+        b->iters[p] = 0;        // a new stage: counts, deltas and convergence restart
+        b->delta[p] = 0.0;
+        b->converged[p] = 0;
+    }
+    b->precision = precision;
     return RT_OK;
 }
 

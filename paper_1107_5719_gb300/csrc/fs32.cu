@@ -181,8 +181,10 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                         const float l = b.x * c00.y + b.y * c10.y + b.z * c01.y + b.w * c11.y;
                         float ibc = h + (l - s0l);
                         if (bc == 2) {   // + |mu| dB/dtau (LTE diffusion)
+                            // |mu| read here, not kept live through the march
+                            // loop (that cost the loop 13%)
                             const float* pg = p.g2 + ip;
-                            ibc = fmaf(di.amu32,
+                            ibc = fmaf(__ldg(&p.info[d].amu32),
                                        b.x * pg[0] + b.y * pg[1] + b.z * pg[W] + b.w * pg[W + 1], ibc);
                         }
                         inc = T * ibc;

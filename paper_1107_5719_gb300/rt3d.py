@@ -91,6 +91,8 @@ _SIGS = {
     "rt_set_os_method": (C.c_int, [VP, C.c_int]),
     "rt_set_fs_method": (C.c_int, [VP, C.c_int]),
     "rt_set_source_order": (C.c_int, [VP, C.c_int]),
+    "rt_set_precision": (C.c_int, [VP, C.c_int]),
+    "rt_batch_set_precision": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_os_method": (C.c_int, [VP, C.c_int]),
     "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
     "rt_reset_stats": (C.c_int, [VP]),
@@ -327,6 +329,14 @@ def rt_set_fs_method(ctx, method):
 
 def rt_set_source_order(ctx, order):
     return _check(ctx, load().rt_set_source_order(ctx, order))
+
+
+def rt_set_precision(ctx, precision):
+    return _check(ctx, load().rt_set_precision(ctx, precision))
+
+
+def rt_batch_set_precision(b, precision):
+    return _bcheck(b, load().rt_batch_set_precision(b, precision))
 
 
 def rt_batch_set_os_method(b, method):

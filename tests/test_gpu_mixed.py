@@ -1,0 +1,93 @@
+"""Switching a context between the FP32 sweep and the double-float march
+(rt_set_precision): the strong-scattering column (eps = 1e-6) solved with
+the FP32 sweep to its tolerance stands ~4e-6 from the FP64 fixed point
+(the outer iteration contracts slowly); a few double-float iterations with
+Ng on bring it within 1e-6."""
+
+import numpy as np
+import pytest
+
+from paper_1107_5719_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1107_5719_gb300 import build as B
+    B.build()
+    from paper_1107_5719_gb300 import rt3d
+    rt3d.load()
+    return rt3d
+
+
+def test_fp32_then_double_float_reaches_1e6(R):
+    p = W.slab_precision(n=9, nzz=129, n_theta=32, n_phi=8)
+    with R.Solver(p, precision=R.RT_FP64, ng_period=4) as s:
+        r64 = s.solve(tol=1e-11, max_iter=5000)
+    assert r64["converged"]
+    with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+        r32 = s.solve(tol=5e-8, max_iter=5000)
+        assert r32["converged"]
+        err32 = np.max(np.abs(r32["J"] - r64["J"]) / r64["J"])
+        R.rt_set_precision(s.ctx, R.RT_DF64)
+        R.rt_set_ng(s.ctx, 4, 0.0)
+        rdf = s.solve(tol=1e-8, max_iter=200)
+        assert rdf["converged"]
+        errdf = np.max(np.abs(rdf["J"] - r64["J"]) / r64["J"])
+    assert err32 > 1e-6          # the stopping error the finish removes
+    assert errdf < 1e-6, (err32, errdf)
+    assert rdf["iters"] < 0.05 * r32["iters"]
+
+
+def test_precision_switch_round_trip(R):
+    """After a switch the formal solution is the one of a context created in
+    that precision, bit for bit, in both directions."""
+    p = W.random_slab(13, 11, 7, n_theta=6, n_phi=5, seed=5, bottom_bc=W.BC_DIFFUSION)
+    S = p.B * 1.1
+    ref = {}
+    for prec in (R.RT_FP32_SWEEP, R.RT_DF64):
+        with R.Solver(p, precision=prec) as s:
+            ref[prec] = s.formal_solution(S)
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        for prec in (R.RT_DF64, R.RT_FP32_SWEEP, R.RT_DF64):
+            R.rt_set_precision(s.ctx, prec)
+            J, L = s.formal_solution(S)
+            assert np.array_equal(J, ref[prec][0])
+            assert np.array_equal(L, ref[prec][1])
+        with pytest.raises(R.RtError):
+            R.rt_set_precision(s.ctx, R.RT_FP64)
+    with R.Solver(p, precision=R.RT_FP64) as s:
+        with pytest.raises(R.RtError):
+            R.rt_set_precision(s.ctx, R.RT_DF64)
+
+
+def test_batch_fp32_then_double_float_equals_single(R):
+    """The batch's two stages (fused FP32 launches, then per-problem
+    double-float launches) give each problem the iterates of solving it
+    alone with the same two stages."""
+    probs = [W.slab_precision(n=7, nzz=33, eps=e, n_theta=8, n_phi=4, seed=70 + i)
+             for i, e in enumerate((1e-6, 1e-4, 1e-2))]
+    b = R.rt_batch_create(probs, precision=R.RT_FP32_SWEEP)
+    try:
+        R.rt_batch_set_ng(b, 4, 1e-6)
+        r1 = R.rt_batch_solve(b, len(probs), tol=5e-8, max_iter=3000)
+        assert r1["converged"]
+        R.rt_batch_set_precision(b, R.RT_DF64)
+        R.rt_batch_set_ng(b, 4, 0.0)
+        r2 = R.rt_batch_solve(b, len(probs), tol=1e-8, max_iter=500)
+        assert r2["converged"]
+        Jb = [R.rt_batch_get_J(b, i, (q.nz, q.ny, q.nx)) for i, q in enumerate(probs)]
+    finally:
+        R.rt_batch_destroy(b)
+    for i, q in enumerate(probs):
+        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+            a = s.solve(tol=5e-8, max_iter=3000)
+            R.rt_set_precision(s.ctx, R.RT_DF64)
+            R.rt_set_ng(s.ctx, 4, 0.0)
+            c = s.solve(tol=1e-8, max_iter=500)
+        assert a["iters"] == r1["iters"][i] and c["iters"] == r2["iters"][i]
+        assert np.array_equal(c["J"], Jb[i])
