@@ -80,7 +80,8 @@ typedef enum {
     RT_ENOTCONV = 4,    /* max_iter reached before delta < tol (outputs valid) */
     RT_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
     RT_ESTATE = 6,      /* the call needs data that was not set yet */
-    RT_ESCRATCH = 7     /* too large for rt_formal_solution_noalloc's fixed scratch */
+    RT_ESCRATCH = 7,    /* too large for rt_formal_solution_noalloc's fixed scratch */
+    RT_EBOUNDS = 8      /* checked build: a kernel found an index outside its buffer */
 } rt_status;
 
 enum { RT_FP64 = 0, RT_FP32_SWEEP = 1, RT_DF64 = 2 };
@@ -372,6 +373,20 @@ int rt_batch_set_direction_groups(rt_batch *batch, int groups);
 int rt_batch_set_ng(rt_batch *batch, int period, double min_delta);
 /* As rt_set_os_method, for every problem of the batch. */
 int rt_batch_set_os_method(rt_batch *batch, int method);
+
+/* Checked build (librt3d_checked.so, compiled with RT_CHECKED): the gathers
+ * of the formal-solution marches and of the operator-splitting stencils test
+ * every index against its buffer; the first index found outside is recorded
+ * on the device and the access skipped, and the call that launched the
+ * kernel returns RT_EBOUNDS naming the index, the limit and the kernel site
+ * (1 FP64 march, 2 its Lambda*, 3 FP32 sweep, 4 double-float march, 5 short
+ * characteristics, 6 their Lambda*, 7 parabolic march, 8 its Lambda*,
+ * 9 Jacobi stencil, 10 Gauss-Seidel stencil).  Results of such a call are
+ * not valid.  rt_checked_build() says which library is loaded;
+ * rt_bounds_selftest(ctx) runs one guard on an index never dereferenced
+ * (site 99): RT_EBOUNDS in the checked build, RT_OK otherwise. */
+int rt_checked_build(void);
+int rt_bounds_selftest(rt_ctx *ctx);
 
 /* Counters of this context since the last rt_reset_stats: kernel launches,
  * formal-solution march launches and their device time, Jacobi sweeps and

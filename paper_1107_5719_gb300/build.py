@@ -17,6 +17,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librt3d.so")
+# The checked build (-DRT_CHECKED): bounds tests on every gathered index of
+# the marches and stencils, reported as RT_EBOUNDS; loaded instead of LIB
+# when RT3D_CHECKED=1.
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "librt3d_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["fs.cu", "fs32.cu", "fsdf.cu", "sc.cu", "para.cu", "os.cu", "api.cu", "noalloc.cu"]
@@ -39,23 +44,34 @@ def _deps():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link librt3d.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    cc = nvcc()
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile and link librt3d.so (or librt3d_checked.so); returns its path."""
+    return build_many([checked], force, verbose, extra_flags)[0]
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
+
+def build_many(variants=(False, True), force: bool = False, verbose: bool = False,
+               extra_flags=()) -> list:
+    """Compile the requested variants (False: normal, True: checked) with all
+    translation units of all variants in one parallel pool."""
+    cc = nvcc()
+    todo = [v for v in variants if force or not up_to_date(LIB_CHECKED if v else LIB)]
+    jobs = []
+    for v in todo:
+        os.makedirs(BUILD_CHECKED if v else BUILD, exist_ok=True)
+        jobs += [(v, src) for src in SOURCES]
+
+    def compile_one(job):
+        v, src = job
+        obj = os.path.join(BUILD_CHECKED if v else BUILD, os.path.splitext(src)[0] + ".o")
+        cmd = [cc, *ARCH, *FLAGS, *extra_flags, *(["-DRT_CHECKED"] if v else []),
+               "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -65,16 +81,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    with ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for v in todo:
+        lib = LIB_CHECKED if v else LIB
+        mine = [o for (vv, _), o in zip(jobs, objs) if vv == v]
+        tmp = lib + f".{os.getpid()}.tmp"
+        r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *mine], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
+    return [LIB_CHECKED if v else LIB for v in variants]
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build_many(force="--force" in sys.argv, verbose="-v" in sys.argv))

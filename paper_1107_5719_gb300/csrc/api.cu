@@ -27,6 +27,7 @@ struct rt_ctx {
     bool have_grid = false, have_quad = false, have_chi = false, have_eps = false, have_B = false;
     bool lstar_valid = false, coef_valid = false, b2_valid = false;
     int os_method = RT_OS_JACOBI;
+    unsigned long long* berr = nullptr;   // checked builds: out-of-bounds record
     int fs_method = RT_FS_LONG;
     int src_order = RT_SRC_LINEAR;
     DownGeo* dn = nullptr;   // downstream-point table (FP64 contexts)
@@ -436,6 +437,25 @@ int prepare_source(rt_ctx* c, const double* S_in, bool device)
         c->stats.launches += 1;
     }
     return RT_OK;
+}
+
+// Checked builds: report (and clear) the first out-of-bounds index the
+// kernels recorded since the last check.  Normal builds: nothing to do.
+int check_bounds(rt_ctx* c, int rc)
+{
+#ifdef RT_CHECKED
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (cudaMemcpy(h, c->berr, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(c, RT_ECUDA, "reading the bounds record failed");
+    if (h[0]) {
+        cudaMemset(c->berr, 0, sizeof(h));
+        return fail(c, RT_EBOUNDS, "index %lld outside [0, %lld) at site %llu",
+                    (long long)h[2], (long long)h[3], h[1]);
+    }
+#else
+    (void)c;
+#endif
+    return rc;
 }
 
 int formal_solution(rt_ctx* c, const double* S, double* Jfs_out, double* lstar_out, bool device)
@@ -897,6 +917,14 @@ int rt_create(rt_ctx** out, int device, int precision)
     c->stream = c->own_stream;
     c->g.top_bc = RT_BC_ZERO;
     c->g.bottom_bc = RT_BC_PLANCK;
+#ifdef RT_CHECKED
+    if (cudaMalloc((void**)&c->berr, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->berr, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        rt_destroy(c);
+        return RT_ECUDA;
+    }
+#endif
+    c->g.berr = c->berr;
     *out = c;
     return RT_OK;
 }
@@ -910,6 +938,7 @@ int rt_destroy(rt_ctx* c)
     free_tables(c);
     dfree(c->scal);
     dfree(c->d_steps);
+    dfree(c->berr);
     if (c->h_scal) cudaFreeHost(c->h_scal);
     if (c->h_steps) cudaFreeHost(c->h_steps);
     if (c->h_dlt) cudaFreeHost(c->h_dlt);
@@ -1074,38 +1103,38 @@ int rt_set_planck_dev(rt_ctx* c, const double* B) { return set_B(c, B, true); }
 
 int rt_formal_solution(rt_ctx* c, const double* S, double* J_fs, double* lstar)
 {
-    return formal_solution(c, S, J_fs, lstar, false);
+    return check_bounds(c, formal_solution(c, S, J_fs, lstar, false));
 }
 
 int rt_formal_solution_dev(rt_ctx* c, const double* S, double* J_fs, double* lstar)
 {
-    return formal_solution(c, S, J_fs, lstar, true);
+    return check_bounds(c, formal_solution(c, S, J_fs, lstar, true));
 }
 
 int rt_os_step(rt_ctx* c, const double* J_fs, const double* J_old, double* J_new, double tol_inner,
                int max_sweeps, int* sweeps)
 {
-    return os_step(c, J_fs, J_old, J_new, tol_inner, max_sweeps, sweeps, false);
+    return check_bounds(c, os_step(c, J_fs, J_old, J_new, tol_inner, max_sweeps, sweeps, false));
 }
 
 int rt_os_step_dev(rt_ctx* c, const double* J_fs, const double* J_old, double* J_new,
                    double tol_inner, int max_sweeps, int* sweeps)
 {
-    return os_step(c, J_fs, J_old, J_new, tol_inner, max_sweeps, sweeps, true);
+    return check_bounds(c, os_step(c, J_fs, J_old, J_new, tol_inner, max_sweeps, sweeps, true));
 }
 
 int rt_solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps, double* J_out,
              int* iters, double* last_delta, double* deltas, int* sweeps)
 {
-    return solve(c, tol, max_iter, tol_inner, max_sweeps, J_out, iters, last_delta, deltas, sweeps,
-                 false);
+    return check_bounds(c, solve(c, tol, max_iter, tol_inner, max_sweeps, J_out, iters, last_delta,
+                                 deltas, sweeps, false));
 }
 
 int rt_solve_dev(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
                  double* J_out, int* iters, double* last_delta, double* deltas, int* sweeps)
 {
-    return solve(c, tol, max_iter, tol_inner, max_sweeps, J_out, iters, last_delta, deltas, sweeps,
-                 true);
+    return check_bounds(c, solve(c, tol, max_iter, tol_inner, max_sweeps, J_out, iters, last_delta,
+                                 deltas, sweeps, true));
 }
 
 int rt_get_J(rt_ctx* c, double* J)
@@ -1419,8 +1448,41 @@ int rt_batch_set_precision(rt_batch* b, int precision)
     return RT_OK;
 }
 
+static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, int max_sweeps,
+                       int* iters, double* deltas, int* n_converged);
+
 int rt_batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, int max_sweeps,
                    int* iters, double* deltas, int* n_converged)
+{
+    int rc = batch_solve(b, tol, max_iter, tol_inner, max_sweeps, iters, deltas, n_converged);
+    if (!b) return rc;
+    for (size_t p = 0; p < b->ctx.size(); ++p) {
+        const int r2 = check_bounds(b->ctx[p], RT_OK);
+        if (r2) return bfail(b, r2, "problem %zu: %s", p, rt_last_error(b->ctx[p]));
+    }
+    return rc;
+}
+
+int rt_checked_build(void)
+{
+#ifdef RT_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int rt_bounds_selftest(rt_ctx* c)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    CK(launch_bounds_selftest(c->g, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return check_bounds(c, RT_OK);
+}
+
+static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, int max_sweeps,
+                       int* iters, double* deltas, int* n_converged)
 {
     if (!b) return RT_EINVAL;
     b->err.clear();

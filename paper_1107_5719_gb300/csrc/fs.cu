@@ -98,6 +98,10 @@ __device__ __forceinline__ Nodes nodes_of(int i0, int j0, StepGeo o, int nx, int
     return Nodes{y0 * nx + x0, y0 * nx + x1, y1 * nx + x0, y1 * nx + x1};
 }
 
+// Extremes of the four node indices (checked builds test both).
+__device__ __forceinline__ int nodes_min(Nodes n) { return min(min(n.a00, n.a10), min(n.a01, n.a11)); }
+__device__ __forceinline__ int nodes_max(Nodes n) { return max(max(n.a00, n.a10), max(n.a01, n.a11)); }
+
 template <typename T, typename V4>
 __device__ __forceinline__ T bilin(const T* __restrict__ p, Nodes n, V4 b)
 {
@@ -150,6 +154,8 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                 for (; m < M; ++m) {
                     const long long pb = (long long)(k0 - (m + 1) * s) * nxy;
                     const Nodes n = nodes_of(i0, j0, od[m + 1], nx, ny);
+                    RT_GUARD(g, pb + nodes_min(n), g.N, kSiteFs64) { early = true; break; }
+                    RT_GUARD(g, pb + nodes_max(n), g.N, kSiteFs64) { early = true; break; }
                     const Bw4d b = bd[m + 1];
                     const double cb = bilin(chi + pb, n, b);
                     const double sb = bilin(S + pb, n, b);
@@ -166,7 +172,14 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                     }
                 }
                 const int bc = s > 0 ? g.top_bc : g.bottom_bc;
+                bool bc_ok = true;
                 if (!early && bc) {
+                    const long long pb = (long long)(k0 - M * s) * nxy;
+                    const Nodes n = nodes_of(i0, j0, od[M], nx, ny);
+                    RT_GUARD(g, pb + nodes_max(n), g.N, kSiteFs64) bc_ok = false;
+                    RT_GUARD(g, pb + nodes_min(n), g.N, kSiteFs64) bc_ok = false;
+                }
+                if (!early && bc && bc_ok) {
                     const long long pb = (long long)(k0 - M * s) * nxy;
                     const Nodes n = nodes_of(i0, j0, od[M], nx, ny);
                     double ibc = bilin(B + pb, n, bd[M]);
@@ -223,13 +236,18 @@ k_lstar64(Geometry g, const double* __restrict__ chi, const DirInfo* __restrict_
         const StepGeo* od = off + (long long)d * nz;
         const Bw4d* bd = bw + (long long)d * nz;
         const Bw4d b1 = bd[1];
-        const double chi1 = bilin(chi + (long long)(k0 - s) * nxy, nodes_of(i0, j0, od[1], nx, ny), b1);
+        const Nodes n1 = nodes_of(i0, j0, od[1], nx, ny);
+        RT_GUARD(g, (long long)(k0 - s) * nxy + nodes_max(n1), g.N, kSiteLstar64) continue;
+        RT_GUARD(g, (long long)(k0 - s) * nxy + nodes_min(n1), g.N, kSiteLstar64) continue;
+        const double chi1 = bilin(chi + (long long)(k0 - s) * nxy, n1, b1);
         double wc0, wu0, e0;
         seg_weights64(di.hs * (chi0 + chi1), tab, wc0, wu0, e0);
         double c1 = wu0;
         if (M >= 2) {
-            const double chi2 = bilin(chi + (long long)(k0 - 2 * s) * nxy,
-                                      nodes_of(i0, j0, od[2], nx, ny), bd[2]);
+            const Nodes n2 = nodes_of(i0, j0, od[2], nx, ny);
+            RT_GUARD(g, (long long)(k0 - 2 * s) * nxy + nodes_max(n2), g.N, kSiteLstar64) continue;
+            RT_GUARD(g, (long long)(k0 - 2 * s) * nxy + nodes_min(n2), g.N, kSiteLstar64) continue;
+            const double chi2 = bilin(chi + (long long)(k0 - 2 * s) * nxy, n2, bd[2]);
             double wc1, wu1, e1;
             seg_weights64(di.hs * (chi1 + chi2), tab, wc1, wu1, e1);
             c1 = fma(e0, wc1, wu0);
@@ -310,6 +328,19 @@ cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, c
     const int nxy = g.nx * g.ny;
     dim3 grid((nxy + kThreads - 1) / kThreads, g.nz, groups);
     k_fs64<<<grid, kThreads, 0, st>>>(g, chi, S, B, G, info, off, bw, smax, cut, partial, steps);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_bounds_selftest(Geometry g)
+{
+    RT_GUARD(g, g.N, g.N, kSiteSelfTest) return;
+}
+}  // namespace
+
+cudaError_t launch_bounds_selftest(const Geometry& g, cudaStream_t st)
+{
+    k_bounds_selftest<<<1, 1, 0, st>>>(g);
     return cudaGetLastError();
 }
 

@@ -138,6 +138,8 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                 bool early = false;
                 int m = 0;
                 for (; m < M; ++m) {
+                    RT_GUARD(g, base + od[m + 1], 4 * g.N, kSiteFs32) { early = true; break; }
+                    RT_GUARD(g, base + od[m + 1] + W + 1, 4 * g.N, kSiteFs32) { early = true; break; }
                     const float4* q = nb + od[m + 1];
                     const float4 b = bd[m + 1];
                     const float4 q00 = __ldg(q), q10 = __ldg(q + 1);
@@ -173,7 +175,8 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                     if (bc) {
                         const StepGeo o = p.off[(long long)d * nz + M];
                         const float4 b = bd[M];
-                        const long long ip = (j0 + o.oy) * W + (i0 + o.ox);
+                        long long ip = (j0 + o.oy) * W + (i0 + o.ox);
+                        RT_GUARD(g, ip, P - W - 1, kSiteFs32) ip = 0;   // record, read a safe node
                         const float2* pb = p.b2 + (s > 0 ? 0LL : P) + ip;
                         const float2 c00 = pb[0], c10 = pb[1], c01 = pb[W], c11 = pb[W + 1];
                         const float h = b.x * (c00.x - s0h) + b.y * (c10.x - s0h) +

@@ -171,6 +171,8 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
                 bool early = false;
                 int m = 0;
                 for (; m < M; ++m) {
+                    RT_GUARD(g, base + od[m + 1], 4 * g.N, kSiteFsdf) { early = true; break; }
+                    RT_GUARD(g, base + od[m + 1] + W + 1, 4 * g.N, kSiteFsdf) { early = true; break; }
                     const float4* q = nb + od[m + 1];
                     const float4 wh = bd[2 * (m + 1)], wl = bd[2 * (m + 1) + 1];
                     const float4 q00 = __ldg(q), q10 = __ldg(q + 1);
@@ -200,7 +202,8 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
                     if (bc) {
                         const StepGeo o = p.off[(long long)d * nz + M];
                         const float4 wh = bd[2 * M], wl = bd[2 * M + 1];
-                        const long long ip = (j0 + o.oy) * W + (i0 + o.ox);
+                        long long ip = (j0 + o.oy) * W + (i0 + o.ox);
+                        RT_GUARD(g, ip, P - W - 1, kSiteFsdf) ip = 0;   // record, read a safe node
                         const float2* pb = p.b2 + (s > 0 ? 0LL : P) + ip;
                         const float2 c00 = pb[0], c10 = pb[1], c01 = pb[W], c11 = pb[W + 1];
                         ibc = bilin_df(wh, wl, c00.x, c00.y, c10.x, c10.y, c01.x, c01.y, c11.x, c11.y);

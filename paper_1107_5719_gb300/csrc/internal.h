@@ -52,8 +52,43 @@ struct alignas(32) DownGeo {
 struct Geometry {
     int nx, ny, nz, ndir;
     long long N;            // nx * ny * nz
-    int top_bc, bottom_bc;  // 0 zero, 1 Planck
+    int top_bc, bottom_bc;  // 0 zero, 1 Planck, 2 (bottom) LTE diffusion
+    // Checked builds only: device record {hit, site, index, limit} of the
+    // first gathered index found outside its buffer (null: no record).
+    unsigned long long* berr;
 };
+
+// Checked builds (compiled with -DRT_CHECKED into librt3d_checked.so): the
+// gathers of the marches and of the operator-splitting stencils test each
+// index against its buffer before the access.  The first index found
+// outside is recorded in g.berr and the access is skipped (RT_GUARD runs
+// its statement: leave the characteristic, skip the voxel), so the kernel
+// runs to its end and the host reports RT_EBOUNDS instead of the GPU
+// faulting.  In normal builds RT_GUARD compiles to nothing.
+#ifdef RT_CHECKED
+__device__ __forceinline__ bool rt_in_bounds(const Geometry& g, long long i, long long n, int site)
+{
+    if (i >= 0 && i < n) return true;
+    if (g.berr && atomicCAS(g.berr, 0ull, 1ull) == 0ull) {
+        g.berr[1] = (unsigned long long)site;
+        g.berr[2] = (unsigned long long)i;
+        g.berr[3] = (unsigned long long)n;
+    }
+    return false;
+}
+#define RT_GUARD(g, i, n, site) if (!rt_in_bounds((g), (long long)(i), (long long)(n), (site)))
+#else
+#define RT_GUARD(g, i, n, site) if (false)
+#endif
+// Sites named in the RT_EBOUNDS message.
+enum {
+    kSiteFs64 = 1, kSiteLstar64 = 2, kSiteFs32 = 3, kSiteFsdf = 4, kSiteSc = 5,
+    kSiteLstarSc = 6, kSiteFs64p = 7, kSiteLstar64p = 8, kSiteStencil = 9, kSiteGs = 10,
+    kSiteSelfTest = 99
+};
+// Launch one guard on an index that is never dereferenced (index = limit),
+// so that a checked build records site kSiteSelfTest (a no-op otherwise).
+cudaError_t launch_bounds_selftest(const Geometry& g, cudaStream_t st);
 
 // ---- launchers (fs.cu) -----------------------------------------------------
 cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz,

@@ -172,6 +172,8 @@ __device__ __forceinline__ double stencil(const Geometry& g, const double* __res
             for (int ox = 0; ox < 3; ++ox) {
                 const int o = oz * 9 + oy * 3 + ox;
                 if (SKIP_CENTRE && o == 13) continue;
+                RT_GUARD(g, (Jr - J) + xs[ox], g.N, kSiteStencil) continue;
+                RT_GUARD(g, o * cs + v, 27 * cs, kSiteStencil) continue;
                 acc = fma(__ldg(c + o * cs + v), __ldg(Jr + xs[ox]), acc);
             }
         }
@@ -258,6 +260,8 @@ k_gs_half(Geometry g, const double* __restrict__ c, const double* __restrict__ r
                     const int o = oz * 9 + oy * 3 + ox;
                     if (o == 13) continue;
                     const int x = xs[ox];
+                    RT_GUARD(g, row + x, g.N, kSiteGs) continue;
+                    RT_GUARD(g, o * cs + ci, 27 * cs, kSiteGs) continue;
                     const double* src = ((x + ys[oy] + kk) & 1) == colour ? same : other;
                     acc = fma(__ldg(c + o * cs + ci), __ldg(src + row + x), acc);
                 }

@@ -43,6 +43,9 @@ __device__ __forceinline__ NodesP nodes_p(int i0, int j0, int ox, int oy, int nx
     return NodesP{y0 * nx + x0, y0 * nx + x1, y1 * nx + x0, y1 * nx + x1};
 }
 
+__device__ __forceinline__ int nmin_p(NodesP n) { return min(min(n.a00, n.a10), min(n.a01, n.a11)); }
+__device__ __forceinline__ int nmax_p(NodesP n) { return max(max(n.a00, n.a10), max(n.a01, n.a11)); }
+
 __device__ __forceinline__ double bilin_p(const double* __restrict__ f, NodesP n, Bw4d b)
 {
     return b.x * __ldg(f + n.a00) + b.y * __ldg(f + n.a10) + b.z * __ldg(f + n.a01) +
@@ -165,7 +168,9 @@ k_fs64p(Geometry g, const double* __restrict__ chi, const double* __restrict__ S
                 double xprev = 0.0, sprev = 0.0;
                 if (down) {
                     const DownGeo q = dn[d];
-                    const NodesP n = nodes_p(i0, j0, q.ox, q.oy, nx, ny);
+                    NodesP n = nodes_p(i0, j0, q.ox, q.oy, nx, ny);
+                    RT_GUARD(g, nmax_p(n), nxy, kSiteFs64p) n = NodesP{0, 0, 0, 0};
+                    RT_GUARD(g, nmin_p(n), nxy, kSiteFs64p) n = NodesP{0, 0, 0, 0};
                     const long long pd = (long long)kd * nxy;
                     xprev = di.hs * (chi0 + bilin_p(chi + pd, n, q.b));
                     sprev = bilin_p(S + pd, n, q.b);
@@ -177,6 +182,8 @@ k_fs64p(Geometry g, const double* __restrict__ chi, const double* __restrict__ S
                     const long long pb = (long long)(k0 - (m + 1) * s) * nxy;
                     const StepGeo o = od[m + 1];
                     const NodesP n = nodes_p(i0, j0, o.ox, o.oy, nx, ny);
+                    RT_GUARD(g, pb + nmax_p(n), g.N, kSiteFs64p) { early = true; break; }
+                    RT_GUARD(g, pb + nmin_p(n), g.N, kSiteFs64p) { early = true; break; }
                     const Bw4d b = bd[m + 1];
                     const double cb = bilin_p(chi + pb, n, b);
                     const double sb = bilin_p(S + pb, n, b);

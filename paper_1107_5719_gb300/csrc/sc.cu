@@ -102,6 +102,8 @@ k_sc64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
         for (int t = threadIdx.x; t < nxy; t += kScThreads) {
             const int j = t / nx, i = t - j * nx;
             const Corners c = corners_of(i, j, o, nx, ny);
+            RT_GUARD(g, max(max(c.a00, c.a10), max(c.a01, c.a11)), nxy, kSiteSc) continue;
+            RT_GUARD(g, min(min(c.a00, c.a10), min(c.a01, c.a11)), nxy, kSiteSc) continue;
             const double Iu = bilin4(prev, c, b);
             const double cu = bilin4_ldg(chiu, c, b);
             const double su = bilin4_ldg(Su, c, b);
@@ -159,6 +161,8 @@ k_lstar_sc64(Geometry g, const double* __restrict__ chi, const DirInfo* __restri
         const StepGeo o = off[(long long)d * nz + 1];
         const Bw4d b = bw[(long long)d * nz + 1];
         const Corners c = corners_of(i0, j0, o, nx, ny);
+        RT_GUARD(g, max(max(c.a00, c.a10), max(c.a01, c.a11)), nxy, kSiteLstarSc) continue;
+        RT_GUARD(g, min(min(c.a00, c.a10), min(c.a01, c.a11)), nxy, kSiteLstarSc) continue;
         const double* chiu = chi + (long long)ku * nxy;
         double wc, wu, e;
         seg_weights64(di.hs * (bilin4_ldg(chiu, c, b) + chi0), tab, wc, wu, e);

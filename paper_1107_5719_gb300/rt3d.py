@@ -18,7 +18,8 @@ from typing import Optional
 
 import numpy as np
 
-RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_ETIMEOUT, RT_ESTATE, RT_ESCRATCH = range(8)
+(RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTCONV, RT_ETIMEOUT, RT_ESTATE, RT_ESCRATCH,
+ RT_EBOUNDS) = range(9)
 RT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 RT_FP64, RT_FP32_SWEEP, RT_DF64 = 0, 1, 2
 RT_BC_ZERO, RT_BC_PLANCK, RT_BC_DIFFUSION = 0, 1, 2
@@ -27,10 +28,13 @@ RT_FS_LONG, RT_FS_SHORT = 0, 1
 RT_SRC_LINEAR, RT_SRC_PARABOLIC = 0, 1
 
 _NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOTCONV",
-          5: "RT_ETIMEOUT", 6: "RT_ESTATE", 7: "RT_ESCRATCH"}
+          5: "RT_ETIMEOUT", 6: "RT_ESTATE", 7: "RT_ESCRATCH", 8: "RT_EBOUNDS"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librt3d.so")
+# RT3D_CHECKED=1 loads the checked build (bounds tests in the kernels,
+# RT_EBOUNDS on a bad index) instead.
+LIB_PATH_CHECKED = os.path.join(_HERE, "librt3d_checked.so")
 _lib = None
 _lock = threading.Lock()
 
@@ -92,6 +96,8 @@ _SIGS = {
     "rt_set_fs_method": (C.c_int, [VP, C.c_int]),
     "rt_set_source_order": (C.c_int, [VP, C.c_int]),
     "rt_set_precision": (C.c_int, [VP, C.c_int]),
+    "rt_checked_build": (C.c_int, []),
+    "rt_bounds_selftest": (C.c_int, [VP]),
     "rt_batch_set_precision": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_os_method": (C.c_int, [VP, C.c_int]),
     "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
@@ -122,7 +128,7 @@ def load(path: Optional[str] = None):
     global _lib
     with _lock:
         if _lib is None:
-            p = path or LIB_PATH
+            p = path or (LIB_PATH_CHECKED if os.environ.get("RT3D_CHECKED") == "1" else LIB_PATH)
             if not os.path.exists(p):
                 raise ImportError(f"{p} is missing: build it with paper_1107_5719_gb300.build.build()")
             lib = C.CDLL(p)
@@ -333,6 +339,15 @@ def rt_set_source_order(ctx, order):
 
 def rt_set_precision(ctx, precision):
     return _check(ctx, load().rt_set_precision(ctx, precision))
+
+
+def rt_checked_build() -> bool:
+    return bool(load().rt_checked_build())
+
+
+def rt_bounds_selftest(ctx):
+    """Raw status: RT_EBOUNDS from the checked build, RT_OK otherwise."""
+    return load().rt_bounds_selftest(ctx)
 
 
 def rt_batch_set_precision(b, precision):

@@ -62,3 +62,48 @@ def test_weak_throughput_two_gloo_ranks():
 def test_single_process_is_identity():
     thr, ms = RP.weak_throughput(4, 500.0)
     assert ms == 500.0 and thr == 8.0
+
+
+def _failing_worker(rank, ws, port, out):
+    """Rank 1 fails on the host before the timing reduction and leaves;
+    rank 0 must get an error from its collective within the group's
+    timeout instead of waiting forever."""
+    import datetime
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=ws,
+                            timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        out[rank] = "left"
+        raise SystemExit(3)          # host-side failure: never joins the reduction
+    try:
+        RP.weak_throughput(1, 100.0)
+        out[rank] = "no error"
+    except Exception as e:           # gloo reports the lost peer or the timeout
+        out[rank] = "error: " + type(e).__name__
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:
+            pass
+
+
+def test_rank_failure_surfaces_as_an_error():
+    import socket
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert procs[1].exitcode == 3
+    assert out[1] == "left"
+    assert str(out[0]).startswith("error"), out[0]
+    assert procs[0].exitcode == 0
