@@ -54,10 +54,17 @@ def test_binding_covers_every_declared_symbol(lib):
 
 
 def test_library_is_built_for_sm_103a(lib):
-    out = subprocess.run(["cuobjdump", "--list-elf", lib], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+    from paper_1107_5719_gb300 import build as B
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_checked_library_exports_the_same_symbols(lib):
+    from paper_1107_5719_gb300 import build as B
+    path = B.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (rt_[A-Za-z0-9_]+)$", out, flags=re.M))
+    assert not (_declared() - exported)
 
 
 def test_no_gpu_fails_loudly(lib):
