@@ -395,6 +395,15 @@ def run_ours(args):
                  "max_rel_diff_from_long_J": float(np.max(np.abs(rsc["J"] - r64["J"]) / r64["J"])),
                  "median_rel_diff_from_long_J": float(np.median(np.abs(rsc["J"] - r64["J"]) / r64["J"])),
                  "note": "different discretisation (I interpolated on each plane)"}
+        rscd = timed_solves(R, p, R.RT_DF64, dev, stream, flush, 1, args.sc_steps,
+                            args.max_iter, ng=args.ng, fs_method=R.RT_FS_SHORT)
+        stscd = rscd["stats"]
+        msscd = float(sum(rscd["times"]))
+        short["double_float"] = {
+            "value": round(RP.weak_throughput(args.sc_steps, msscd)[0], 6), "unit": "solves/s",
+            "ms_per_step": round(msscd / args.sc_steps, 3),
+            "ms_per_fs_launch": round(stscd["fs_ms"] / max(stscd["fs_launches"], 1), 4),
+            "max_rel_dev_from_fp64_short_J": float(np.max(np.abs(rscd["J"] - rsc["J"]) / rsc["J"]))}
 
     # the parabolic-source variant of the FP64 march (second-order source)
     para = None

@@ -211,10 +211,12 @@ int rt_set_ng(rt_ctx *ctx, int period, double min_delta);
  * characteristics by the interpolation of I (it agrees exactly where every
  * upstream point is a lattice node, and on horizontally uniform slabs).
  * Lambda* is that of the chosen method (per direction the diagonal w_cur
- * and, at the nodes c of p, b_c (w_up + e w_cur(c))).  RT_FS_SHORT needs
- * precision RT_FP64 (RT_EINVAL otherwise); its working memory is
- * min(ndir, 1024) * N doubles, allocated at the first formal solution.
- * Changing the method invalidates Lambda*. */
+ * and, at the nodes c of p, b_c (w_up + e w_cur(c))).  RT_FS_SHORT runs in
+ * precision RT_FP64 or RT_DF64 (the latter in double-float arithmetic,
+ * carrying D = I - S from plane to plane: D = e D(p) + (1 - w_cur)(S(p) - S));
+ * RT_EINVAL for RT_FP32_SWEEP.  Its working memory is min(ndir, 1024) * N
+ * doubles, allocated at the first formal solution.  Changing the method
+ * invalidates Lambda*. */
 int rt_set_fs_method(rt_ctx *ctx, int method);
 
 /* Switch a context between RT_FP32_SWEEP and RT_DF64 (either direction;

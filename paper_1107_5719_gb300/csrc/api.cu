@@ -358,8 +358,12 @@ int run_fs_short(rt_ctx* c, double* Jout, bool count_steps)
     if ((rc = ensure_sc(c))) return rc;
     if (count_steps) CK(cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned long long), c->stream));
     if (c->profiling) CK(cudaEventRecord(c->ev[0], c->stream));
-    CK(launch_sc64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->scpart,
-                   c->scplanes, Jout, count_steps ? c->d_steps : nullptr, c->stream));
+    if (c->precision == RT_DF64)
+        CK(launch_scdf(viewdf(c), c->S, c->wsum, c->scpart, (float2*)c->scplanes, Jout,
+                       count_steps ? c->d_steps : nullptr, c->stream));
+    else
+        CK(launch_sc64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->scpart,
+                       c->scplanes, Jout, count_steps ? c->d_steps : nullptr, c->stream));
     if (c->profiling) {
         CK(cudaEventRecord(c->ev[1], c->stream));
         c->fs_pending = true;
@@ -1212,8 +1216,8 @@ int rt_set_fs_method(rt_ctx* c, int method)
     if (!c) return RT_EINVAL;
     if (method != RT_FS_LONG && method != RT_FS_SHORT)
         return fail(c, RT_EINVAL, "unknown formal-solution method");
-    if (method == RT_FS_SHORT && c->precision != RT_FP64)
-        return fail(c, RT_EINVAL, "short characteristics need precision RT_FP64");
+    if (method == RT_FS_SHORT && c->precision != RT_FP64 && c->precision != RT_DF64)
+        return fail(c, RT_EINVAL, "short characteristics need precision RT_FP64 or RT_DF64");
     if (method == RT_FS_SHORT && c->src_order != RT_SRC_LINEAR)
         return fail(c, RT_EINVAL, "short characteristics take the linear source only");
     if (method != c->fs_method) {
@@ -1231,6 +1235,8 @@ int rt_set_precision(rt_ctx* c, int precision)
     const bool ok = (precision == RT_FP32_SWEEP || precision == RT_DF64) &&
                     (c->precision == RT_FP32_SWEEP || c->precision == RT_DF64);
     if (!ok) return fail(c, RT_EINVAL, "precision switches only between RT_FP32_SWEEP and RT_DF64");
+    if (precision == RT_FP32_SWEEP && c->fs_method == RT_FS_SHORT)
+        return fail(c, RT_EINVAL, "short characteristics have no FP32-sweep form");
     if (precision == RT_DF64) {
         // buffers the double-float march needs beyond the FP32 sweep's
         if (c->have_grid && !c->g2df) CK(dalloc(c->g2df, (size_t)4 * c->g.nx * c->g.ny));

@@ -278,6 +278,122 @@ __global__ void k_grad_df(Geometry g, const double* __restrict__ G, float2* __re
     }
 }
 
+// ---- short characteristics in double-float ---------------------------------
+// The plane sweep of the short characteristics (one block per direction,
+// two planes in shared memory, one barrier per plane) in double-float,
+// carried in the difference form D = I - S at every node:
+//   D(i,j,k) = e D(p) + (1 - w_cur) (S(p) - S(i,j,k)),
+// which is I = I(p) e + w_cur S + w_up S(p) rewritten with w_up + e =
+// 1 - w_cur, D(p) bilinear in the preceding plane's D; on the entry plane
+// D = I_bc - S.  Rounding then scales with D and with the source step
+// S(p) - S rather than with S.  Each block writes w_d D for every voxel to
+// its slice of the [directions][N] buffer; J = (sum_d w_d) S + the ordered
+// sum of the slices.
+constexpr int kScThreadsDF = 256;
+
+struct CornersDF {
+    int a00, a10, a01, a11;
+};
+
+__device__ __forceinline__ CornersDF corners_df(int i, int j, StepGeo o, int nx, int ny)
+{
+    int x0 = i + o.ox;
+    x0 -= x0 >= nx ? nx : 0;
+    const int x1 = x0 + 1 == nx ? 0 : x0 + 1;
+    int y0 = j + o.oy;
+    y0 -= y0 >= ny ? ny : 0;
+    const int y1 = y0 + 1 == ny ? 0 : y0 + 1;
+    return CornersDF{y0 * nx + x0, y0 * nx + x1, y1 * nx + x0, y1 * nx + x1};
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(kScThreadsDF)
+k_scdf(ViewDF p, int d0, double* __restrict__ part, float2* gplanes,
+       unsigned long long* __restrict__ steps)
+{
+    extern __shared__ float2 splanes_df[];
+    __shared__ dfl tab[2 * kExpTableDF];
+    fill_exp_table_df(tab);
+    const Geometry& g = p.g;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const long long W = 2LL * nx, P = 4LL * nxy;
+    const int d = d0 + blockIdx.x;
+    float2* pl = SMEM ? splanes_df : gplanes + (long long)blockIdx.x * 2 * nxy;
+    const DirInfo di = p.info[d];
+    const int s = di.sgn;
+    const int kin = s > 0 ? 0 : nz - 1;
+    const int bc = s > 0 ? g.top_bc : g.bottom_bc;
+    const StepGeo o = p.off[(long long)d * nz + 1];
+    const int po = p.poff[(long long)d * nz + 1];
+    const float4 wh = p.bw[2 * ((long long)d * nz + 1)], wl = p.bw[2 * ((long long)d * nz + 1) + 1];
+    const dfl hs = df_make(di.hs32, di.hs32lo);
+    double* out = part + (long long)blockIdx.x * g.N;
+    for (int t = threadIdx.x; t < nxy; t += kScThreadsDF) {
+        const int j = t / nx, i = t - j * nx;
+        const long long ip = (long long)j * W + i;
+        const float4 me = p.node[(long long)kin * P + ip];
+        dfl ibc = df_make(0.f, 0.f);
+        if (bc) {
+            const float2 bb = p.b2[(s > 0 ? 0LL : P) + ip];
+            ibc = df_make(bb.x, bb.y);
+            if (bc == 2) {
+                const float2 gg = p.g2df[ip];
+                ibc = df_add_s(ibc, df_mul(df_make(di.amu32, di.amu32lo), df_make(gg.x, gg.y)));
+            }
+        }
+        const dfl D = df_sub_s(ibc, df_make(me.z, me.w));
+        pl[t] = make_float2(D.h, D.l);
+        out[(long long)kin * nxy + t] = di.w * df_to_double(D);
+    }
+    __syncthreads();   // also publishes tab
+    int cur = 0;
+    for (int n = 1; n < nz; ++n) {
+        const int k = s > 0 ? n : nz - 1 - n;
+        const float2* prev = pl + cur * nxy;
+        float2* next = pl + (cur ^ 1) * nxy;
+        for (int t = threadIdx.x; t < nxy; t += kScThreadsDF) {
+            const int j = t / nx, i = t - j * nx;
+            const long long ip = (long long)j * W + i;
+            const CornersDF c = corners_df(i, j, o, nx, ny);
+            RT_GUARD(g, max(max(c.a00, c.a10), max(c.a01, c.a11)), nxy, kSiteSc) continue;
+            RT_GUARD(g, min(min(c.a00, c.a10), min(c.a01, c.a11)), nxy, kSiteSc) continue;
+            // po is relative to the node's own padded index and includes the
+            // step to plane ku
+            RT_GUARD(g, (long long)k * P + ip + po, 4 * g.N - W - 1, kSiteSc) continue;
+            const float4 me = p.node[(long long)k * P + ip];
+            const float4* q = p.node + (long long)k * P + ip + po;
+            const float4 q00 = __ldg(q), q10 = __ldg(q + 1), q01 = __ldg(q + W), q11 = __ldg(q + W + 1);
+            const dfl cu = bilin_df(wh, wl, q00.x, q00.y, q10.x, q10.y, q01.x, q01.y, q11.x, q11.y);
+            const dfl su = bilin_df(wh, wl, q00.z, q00.w, q10.z, q10.w, q01.z, q01.w, q11.z, q11.w);
+            const float2 e00 = prev[c.a00], e10 = prev[c.a10], e01 = prev[c.a01], e11 = prev[c.a11];
+            const dfl Du = bilin_df(wh, wl, e00.x, e00.y, e10.x, e10.y, e01.x, e01.y, e11.x, e11.y);
+            const dfl x = df_mul(hs, df_add_s(cu, df_make(me.x, me.y)));
+            dfl wc, wu, e;
+            seg_weights_df(x, tab, wc, wu, e);
+            const dfl dS = df_sub_s(su, df_make(me.z, me.w));
+            const dfl D = df_add_s(df_mul(e, Du), df_mul(df_add_f(df_neg(wc), 1.0f), dS));
+            next[t] = make_float2(D.h, D.l);
+            out[(long long)k * nxy + t] = di.w * df_to_double(D);
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    if (steps && threadIdx.x == 0) atomicAdd(steps, (unsigned long long)(nz - 1) * nxy);
+}
+
+// J[v] = (accumulate ? J[v] : wsum S[v]) + sum over q < nd of part[q][v].
+__global__ void k_scdf_reduce(long long N, int nd, const double* __restrict__ part,
+                              const double* __restrict__ S, double wsum, double* __restrict__ J,
+                              int accumulate)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+        double acc = accumulate ? J[v] : wsum * S[v];
+        for (int q = 0; q < nd; ++q) acc += part[(long long)q * N + v];
+        J[v] = acc;
+    }
+}
+
 unsigned grid1d_df(long long n, int threads)
 {
     long long b = (n + threads - 1) / threads;
@@ -315,5 +431,30 @@ cudaError_t launch_fsdf(const ViewDF& p, double cut, int groups, unsigned long l
     k_fsdf<<<grid, kThreadsDF, 0, st>>>(p, (float)cut, steps);
     return cudaGetLastError();
 }
+
+cudaError_t launch_scdf(const ViewDF& p, const double* S, double wsum, double* part,
+                        float2* gplanes, double* J, unsigned long long* steps, cudaStream_t st)
+{
+    const Geometry& g = p.g;
+    const int chunk = sc_chunk(g);
+    const size_t shm = 2 * sizeof(float2) * (size_t)g.nx * g.ny;
+    const bool smem = shm <= 200 * 1024;
+    if (smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_scdf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)shm);
+        if (e != cudaSuccess) return e;
+    }
+    for (int d0 = 0; d0 < g.ndir; d0 += chunk) {
+        const int nd = g.ndir - d0 < chunk ? g.ndir - d0 : chunk;
+        if (smem)
+            k_scdf<true><<<nd, kScThreadsDF, shm, st>>>(p, d0, part, gplanes, steps);
+        else
+            k_scdf<false><<<nd, kScThreadsDF, 0, st>>>(p, d0, part, gplanes, steps);
+        k_scdf_reduce<<<grid1d_df(g.N, 256), 256, 0, st>>>(g.N, nd, part, S, wsum, J, d0 > 0);
+    }
+    return cudaGetLastError();
+}
+
+bool scdf_planes_in_smem(const Geometry& g) { return 2 * sizeof(float2) * (size_t)g.nx * g.ny <= 200 * 1024; }
 
 }  // namespace rt3d

@@ -183,6 +183,12 @@ struct ViewDF {
     const double* smax;
     double* partial;        // [kSlots][N] of sum_d w_d (I_d - S_0)
 };
+// Double-float short characteristics (context in RT_DF64): J[N] = wsum S +
+// sum_d w_d (I_d - S); part as for launch_sc64, gplanes 2 * sc_chunk(g) *
+// nx * ny float2 when scdf_planes_in_smem(g) is false (else null).
+cudaError_t launch_scdf(const ViewDF& p, const double* S, double wsum, double* part,
+                        float2* gplanes, double* J, unsigned long long* steps, cudaStream_t st);
+bool scdf_planes_in_smem(const Geometry& g);
 cudaError_t launch_packdf(const Geometry& g, const double* chi, const double* S, float4* node,
                           cudaStream_t st);
 cudaError_t launch_bw_df(long long n, const Bw4d* bw, float4* out, cudaStream_t st);

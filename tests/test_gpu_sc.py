@@ -41,14 +41,16 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "{nx}x{ny}x{nz}".format(**c))
-def test_sc_formal_solution_matches_oracle(R, oracle_mod, case):
+def test_sc_formal_solution_matches_oracle(R, oracle_mod, case, prec):
     kw = dict(case)
     p = W.random_slab(kw.pop("nx"), kw.pop("ny"), kw.pop("nz"), n_theta=6, n_phi=5,
                       seed=kw.pop("seed"), **kw)
     rng = np.random.default_rng(0)
     S = 0.5 + rng.random(p.B.shape) * 2.0
-    with R.Solver(p, fs_method=R.RT_FS_SHORT) as s:
+    precision = R.RT_DF64 if prec == "df64" else R.RT_FP64
+    with R.Solver(p, precision=precision, fs_method=R.RT_FS_SHORT) as s:
         J, L = s.formal_solution(S)
         steps = R.rt_last_step_count(s.ctx)
     Jo, Lo = oracle_mod.formal_solution(p, S, method=oracle_mod.SHORT)
@@ -57,12 +59,14 @@ def test_sc_formal_solution_matches_oracle(R, oracle_mod, case):
     assert steps == p.ndir * (p.nz - 1) * p.nx * p.ny
 
 
-def test_sc_more_directions_than_one_launch(R, oracle_mod):
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_sc_more_directions_than_one_launch(R, oracle_mod, prec):
     """1100 directions: two launches of the march, their sums added in order."""
     p = W.random_slab(5, 4, 3, n_theta=44, n_phi=25, seed=10)
     assert p.ndir > 1024
     S = p.B * 1.3
-    with R.Solver(p, fs_method=R.RT_FS_SHORT) as s:
+    precision = R.RT_DF64 if prec == "df64" else R.RT_FP64
+    with R.Solver(p, precision=precision, fs_method=R.RT_FS_SHORT) as s:
         J, L = s.formal_solution(S)
     Jo, Lo = oracle_mod.formal_solution(p, S, method=oracle_mod.SHORT)
     assert np.allclose(J, Jo, rtol=RTOL, atol=0)
@@ -85,10 +89,14 @@ def test_sc_switching_methods_and_errors(R, oracle_mod):
     with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
         with pytest.raises(R.RtError):
             R.rt_set_fs_method(s.ctx, R.RT_FS_SHORT)
+    with R.Solver(p, precision=R.RT_DF64, fs_method=R.RT_FS_SHORT) as s:
+        with pytest.raises(R.RtError):
+            R.rt_set_precision(s.ctx, R.RT_FP32_SWEEP)    # no FP32 short characteristics
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
 @pytest.mark.parametrize("which", ["slab17", "random"])
-def test_sc_converged_solve_matches_oracle(R, oracle_mod, which):
+def test_sc_converged_solve_matches_oracle(R, oracle_mod, which, prec):
     if which == "slab17":
         p = W.slab_small(n_theta=8, n_phi=8)
     else:
@@ -96,18 +104,21 @@ def test_sc_converged_solve_matches_oracle(R, oracle_mod, which):
                           bottom_bc=W.BC_DIFFUSION)
     ro = oracle_mod.solve(p, tol=1e-8, max_iter=300, tol_inner=0.0, max_sweeps=12,
                           ng_period=4, fs_method=oracle_mod.SHORT)
-    with R.Solver(p, ng_period=4, fs_method=R.RT_FS_SHORT) as s:
+    precision = R.RT_DF64 if prec == "df64" else R.RT_FP64
+    with R.Solver(p, precision=precision, ng_period=4, fs_method=R.RT_FS_SHORT) as s:
         r = s.solve(tol=1e-8, max_iter=300, tol_inner=0.0, max_sweeps=12)
     assert r["converged"] and ro["converged"] and r["iters"] == ro["iters"]
     assert np.allclose(r["J"], ro["J"], rtol=RTOL, atol=0)
 
 
-def test_sc_slab65_full_grid(R, oracle_mod):
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_sc_slab65_full_grid(R, oracle_mod, prec):
     """The 65^3 slab with 1024 directions, every voxel: J of one formal
     solution and its reproducibility."""
     p = W.slab_65()
     S = p.B.copy()
-    with R.Solver(p, fs_method=R.RT_FS_SHORT) as s:
+    precision = R.RT_DF64 if prec == "df64" else R.RT_FP64
+    with R.Solver(p, precision=precision, fs_method=R.RT_FS_SHORT) as s:
         J1, _ = s.formal_solution(S, want_lstar=False)
         J2, _ = s.formal_solution(S, want_lstar=False)
     assert np.array_equal(J1, J2)
