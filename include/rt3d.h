@@ -220,8 +220,10 @@ int rt_set_ng(rt_ctx *ctx, int period, double min_delta);
 int rt_set_fs_method(rt_ctx *ctx, int method);
 
 /* Switch a context between RT_FP32_SWEEP and RT_DF64 (either direction;
- * RT_EINVAL for RT_FP64 on either side).  Everything else is kept: J, Lambda*,
- * the OS coefficients, all settings; the Ng history restarts.  Typical use:
+ * RT_EINVAL for RT_FP64 on either side).  J and all settings are kept; the
+ * Ng history restarts; Lambda* and the OS coefficients are rebuilt by the
+ * new form at its first formal solution (the FP32-sweep form builds Lambda*
+ * in FP64, the double-float form in double-float).  Typical use:
  * iterate with the FP32 sweep to its tolerance (about 5e-8; its iterate then
  * sits near its ~1e-8 rounding floor), then switch to RT_DF64 and continue
  * with Ng on to the final tolerance: the FP64-accurate iterates let Ng

@@ -339,6 +339,8 @@ int fs_finish(rt_ctx* c, double* Jout)
     if (!c->lstar_valid) {
         if (c->src_order == RT_SRC_PARABOLIC)
             CK(launch_lstar64p(c->g, c->chi, c->info, c->off, c->bw, c->dn, c->lstar, c->stream));
+        else if (c->precision == RT_DF64)
+            CK(launch_lstar_df(viewdf(c), false, c->lstar, c->stream));
         else
             CK(launch_lstar64(c->g, c->chi, c->info, c->off, c->bw, c->lstar, c->stream));
         c->lstar_valid = true;
@@ -372,7 +374,10 @@ int run_fs_short(rt_ctx* c, double* Jout, bool count_steps)
     c->stats.fs_launches += 1;
     c->stats.launches += 2 * chunks;
     if (!c->lstar_valid) {
-        CK(launch_lstar_sc64(c->g, c->chi, c->info, c->off, c->bw, c->lstar, c->stream));
+        if (c->precision == RT_DF64)
+            CK(launch_lstar_df(viewdf(c), true, c->lstar, c->stream));
+        else
+            CK(launch_lstar_sc64(c->g, c->chi, c->info, c->off, c->bw, c->lstar, c->stream));
         c->lstar_valid = true;
         c->coef_valid = false;
         c->stats.launches += 1;
@@ -1249,6 +1254,7 @@ int rt_set_precision(rt_ctx* c, int precision)
     }
     c->precision = precision;
     c->gdiff_valid = false;    // the gradient's packed copy differs between the forms
+    c->lstar_valid = c->coef_valid = false;   // Lambda* is rebuilt by the new form's kernel
     c->ng_count = 1;           // restart the Ng history with iterates of the new form
     return RT_OK;
 }

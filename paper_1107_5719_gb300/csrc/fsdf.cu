@@ -394,6 +394,116 @@ __global__ void k_scdf_reduce(long long N, int nd, const double* __restrict__ pa
     }
 }
 
+// ---- Lambda* in double-float ------------------------------------------------
+// The same elements as the FP64 kernels (long characteristics: w_cur(0) at
+// p_0, w_up(0) + e_0 w_cur(1) shared among the nodes of p_1; short
+// characteristics: w_cur at the voxel, b_c (w_up + e w_cur(c)) at the nodes c
+// of p), evaluated in double-float and summed over the directions in a
+// double-float accumulator per element.
+constexpr int kLsThreadsDF = 128;
+
+__device__ __forceinline__ void lam_add(float2* cell, dfl v)
+{
+    const dfl a = df_add_s(df_make(cell->x, cell->y), v);
+    *cell = make_float2(a.h, a.l);
+}
+
+__device__ __forceinline__ dfl bw_df(float hi, float lo) { return df_make(hi, lo); }
+
+template <bool SHORT>
+__global__ void __launch_bounds__(kLsThreadsDF)
+k_lstar_df(ViewDF p, double* __restrict__ lstar)
+{
+    __shared__ float2 lam[27][kLsThreadsDF];
+    __shared__ dfl tab[2 * kExpTableDF];
+    for (int q = 0; q < 27; ++q) lam[q][threadIdx.x] = make_float2(0.f, 0.f);
+    fill_exp_table_df(tab);
+    __syncthreads();
+    const Geometry& g = p.g;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const long long W = 2LL * nx, P = 4LL * nxy;
+    const int t = blockIdx.x * kLsThreadsDF + threadIdx.x;
+    const int k0 = blockIdx.y;
+    if (t >= nxy) return;
+    const int j0 = t / nx, i0 = t - j0 * nx;
+    const long long v = (long long)k0 * nxy + t;
+    const long long base = k0 * P + (long long)j0 * W + i0;
+    const float4 me = p.node[base];
+    const dfl chi0 = df_make(me.x, me.y);
+    for (int d = 0; d < g.ndir; ++d) {
+        const DirInfo di = p.info[d];
+        const int s = di.sgn;
+        const int M = s > 0 ? k0 : nz - 1 - k0;
+        if (M == 0) continue;
+        const int* od = p.poff + (long long)d * nz;
+        const float4* bd = p.bw + 2LL * d * nz;
+        const dfl hs = df_make(di.hs32, di.hs32lo);
+        const dfl wd = df_from_double(di.w);
+        const float4 wh = bd[2], wl = bd[3];     // step 1
+        RT_GUARD(g, base + od[1], 4 * g.N - W - 1, SHORT ? kSiteLstarSc : kSiteLstar64) continue;
+        const float4* q = p.node + base + od[1];
+        const float4 q00 = __ldg(q), q10 = __ldg(q + 1), q01 = __ldg(q + W), q11 = __ldg(q + W + 1);
+        const dfl chi1 = bilin_df(wh, wl, q00.x, q00.y, q10.x, q10.y, q01.x, q01.y, q11.x, q11.y);
+        dfl wc0, wu0, e0;
+        seg_weights_df(df_mul(hs, df_add_s(chi0, chi1)), tab, wc0, wu0, e0);
+        lam_add(&lam[13][threadIdx.x], df_mul(wd, wc0));
+        const dfl bq[4] = {bw_df(wh.x, wl.x), bw_df(wh.y, wl.y), bw_df(wh.z, wl.z), bw_df(wh.w, wl.w)};
+        if (!SHORT) {
+            dfl c1 = wu0;
+            if (M >= 2) {
+                RT_GUARD(g, base + od[2], 4 * g.N - W - 1, kSiteLstar64) continue;
+                const float4* r = p.node + base + od[2];
+                const float4 r00 = __ldg(r), r10 = __ldg(r + 1), r01 = __ldg(r + W), r11 = __ldg(r + W + 1);
+                const dfl chi2 = bilin_df(bd[4], bd[5], r00.x, r00.y, r10.x, r10.y, r01.x, r01.y,
+                                          r11.x, r11.y);
+                dfl wc1, wu1, e1;
+                seg_weights_df(df_mul(hs, df_add_s(chi1, chi2)), tab, wc1, wu1, e1);
+                c1 = df_add_s(wu0, df_mul(e0, wc1));
+            }
+            const dfl cw = df_mul(wd, c1);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (di.lo[c] >= 0) lam_add(&lam[di.lo[c]][threadIdx.x], df_mul(cw, bq[c]));
+        } else {
+            // corner c of p: its own last segment comes from plane k0 - 2s
+            const int kin = s > 0 ? 0 : nz - 1;
+            const bool deeper = k0 - s != kin;
+            const float4 qc[4] = {q00, q10, q01, q11};
+            const StepGeo o = p.off[(long long)d * nz + 1];
+            int xc0 = i0 + o.ox, yc0 = j0 + o.oy;
+            xc0 -= xc0 >= nx ? nx : 0;
+            yc0 -= yc0 >= ny ? ny : 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (di.lo[c] < 0) continue;
+                dfl wcc = df_make(0.f, 0.f);
+                if (deeper) {
+                    // c's own padded index (unpadded coordinates, wrapped),
+                    // then its upstream nodes at the same relative offset
+                    int xc = xc0 + (c & 1), yc = yc0 + (c >> 1);
+                    xc -= xc >= nx ? nx : 0;
+                    yc -= yc >= ny ? ny : 0;
+                    const long long ic = (long long)(k0 - s) * P + (long long)yc * W + xc + od[1];
+                    RT_GUARD(g, ic, 4 * g.N - W - 1, kSiteLstarSc) continue;
+                    const float4* r = p.node + ic;
+                    const float4 r00 = __ldg(r), r10 = __ldg(r + 1), r01 = __ldg(r + W), r11 = __ldg(r + W + 1);
+                    const dfl chic = bilin_df(wh, wl, r00.x, r00.y, r10.x, r10.y, r01.x, r01.y,
+                                              r11.x, r11.y);
+                    dfl wuc, ec;
+                    seg_weights_df(df_mul(hs, df_add_s(df_make(qc[c].x, qc[c].y), chic)), tab, wcc,
+                                   wuc, ec);
+                }
+                lam_add(&lam[di.lo[c]][threadIdx.x],
+                        df_mul(df_mul(wd, bq[c]), df_add_s(wu0, df_mul(e0, wcc))));
+            }
+        }
+    }
+    for (int q = 0; q < 27; ++q) {
+        const float2 a = lam[q][threadIdx.x];
+        lstar[(long long)q * g.N + v] = (double)a.x + (double)a.y;
+    }
+}
+
 unsigned grid1d_df(long long n, int threads)
 {
     long long b = (n + threads - 1) / threads;
@@ -456,5 +566,15 @@ cudaError_t launch_scdf(const ViewDF& p, const double* S, double wsum, double* p
 }
 
 bool scdf_planes_in_smem(const Geometry& g) { return 2 * sizeof(float2) * (size_t)g.nx * g.ny <= 200 * 1024; }
+
+cudaError_t launch_lstar_df(const ViewDF& p, bool short_chars, double* lstar, cudaStream_t st)
+{
+    dim3 grid((p.g.nx * p.g.ny + kLsThreadsDF - 1) / kLsThreadsDF, p.g.nz);
+    if (short_chars)
+        k_lstar_df<true><<<grid, kLsThreadsDF, 0, st>>>(p, lstar);
+    else
+        k_lstar_df<false><<<grid, kLsThreadsDF, 0, st>>>(p, lstar);
+    return cudaGetLastError();
+}
 
 }  // namespace rt3d

@@ -189,6 +189,9 @@ struct ViewDF {
 cudaError_t launch_scdf(const ViewDF& p, const double* S, double wsum, double* part,
                         float2* gplanes, double* J, unsigned long long* steps, cudaStream_t st);
 bool scdf_planes_in_smem(const Geometry& g);
+// Lambda* [27][N] in double-float from the packed nodes (long or short
+// characteristics).
+cudaError_t launch_lstar_df(const ViewDF& p, bool short_chars, double* lstar, cudaStream_t st);
 cudaError_t launch_packdf(const Geometry& g, const double* chi, const double* S, float4* node,
                           cudaStream_t st);
 cudaError_t launch_bw_df(long long n, const Bw4d* bw, float4* out, cudaStream_t st);
