@@ -50,8 +50,8 @@ FLOPS_PER_STEP_FP32 = 45
 PEAK_FP32_TFLOPS = 80.5
 # DRAM bytes (read + write) per k_fs64 launch on slab65, from one ncu
 # capture of the current kernel: chi and S stay L2-resident, so the march
-# reads 6.7 MB per launch from DRAM and writes none.
-TRAFFIC_FS64_SLAB65 = 6736384
+# reads 6.4 MB per launch from DRAM and writes none.
+TRAFFIC_FS64_SLAB65 = 6427648
 # The double-float march executes 398 thread instructions per step (ncu,
 # slab65); its bound is instruction issue: 152 SMs x 4 schedulers x 32 lanes
 # x 2.07 GHz = 40.3e12 thread instructions/s.
@@ -467,6 +467,42 @@ def run_ours(args):
                                         "max_rel_err_vs_fp64": err(cfin)},
                      "target": 1e-6}
 
+    # FP32-batched form on the same GPU: a batch of wavelength points (each
+    # its own chi scale and eps) in one fused launch per outer iteration
+    batched = None
+    if args.batch_lambdas > 0:
+        from paper_1107_5719_gb300 import workloads as W
+        probs = W.batch_65(n_lambda=args.batch_lambdas)
+        bt = R.rt_batch_create(probs, device=dev.index, precision=R.RT_FP32_SWEEP)
+        try:
+            R.rt_batch_set_ng(bt, args.ng, NG_MIN_FP32)
+            R.rt_batch_set_stream(bt, stream)
+            R.rt_batch_solve(bt, len(probs), tol=TOL_FP32, max_iter=2)     # warm-up
+            R.rt_batch_reset(bt, rebuild_lstar=True)
+            R.rt_batch_reset_stats(bt)
+            R.rt_batch_set_profiling(bt, True)
+            with torch.cuda.stream(stream):
+                flush_l2(flush)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rb = R.rt_batch_solve(bt, len(probs), tol=TOL_FP32, max_iter=args.max_iter)
+            e1.record(stream)
+            e1.synchronize()
+            msb = e0.elapsed_time(e1)
+            stb = R.rt_batch_get_stats(bt)
+        finally:
+            R.rt_batch_destroy(bt)
+        vb = RP.weak_throughput(len(probs), msb)[0]
+        batched = {"value": round(vb, 6), "unit": "wavelength-solves/s",
+                   "workload": f"{len(probs)} wavelengths x 65^3, chi x 10^(-2+4U), "
+                               f"eps 10^(-5+5U), 32x32 directions, tol {TOL_FP32:g}",
+                   "converged": bool(rb["converged"]), "s": round(msb / 1e3, 2),
+                   "iters_mean": float(np.mean(rb["iters"])), "iters_max": int(np.max(rb["iters"])),
+                   "fused_fs_ms_per_launch": round(stb["fs_ms"] / max(stb["fs_launches"], 1), 3),
+                   "vs_fp64_plain": round(vb / solves_per_s, 3)}
+
     e2e = None
     if args.e2e_steps > 0:
         v = e2e_solves(R, p, R.RT_FP64, dev, args.e2e_steps, args.max_iter, args.ng)
@@ -494,6 +530,7 @@ def run_ours(args):
         "short_characteristics": short,
         "parabolic_source": para,
         "precision_eps1e-6": precision,
+        "fp32_batched": batched,
         "gpu_launches": int(st["launches"]),
         "clocks": r64["clocks"],
         "e2e": e2e,
@@ -654,6 +691,8 @@ def main():
     ap.add_argument("--df64-steps", type=int, default=2)
     ap.add_argument("--sc-steps", type=int, default=2)
     ap.add_argument("--para-steps", type=int, default=1)
+    ap.add_argument("--batch-lambdas", type=int, default=16,
+                    help="wavelengths of the FP32-batched companion (0 = skip)")
     ap.add_argument("--no-precision-check", dest="precision_check", action="store_false",
                     help="skip the eps = 1e-6 precision comparison")
     ap.add_argument("--ng", type=int, default=4,
