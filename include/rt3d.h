@@ -231,6 +231,19 @@ int rt_set_fs_method(rt_ctx *ctx, int method);
  * Allocates the double-float tables on the first switch to RT_DF64. */
 int rt_set_precision(rt_ctx *ctx, int precision);
 
+/* Automatic double-float finishing stage for RT_FP32_SWEEP contexts:
+ * within rt_solve, once an iteration's delta falls below delta_switch (and
+ * not yet below tol), the iteration continues in double-float with Ng
+ * applied regardless of its delta threshold, down to tol; when the solve
+ * returns (converged or not) the context is back in the FP32 sweep with its
+ * Ng threshold.  The FP32 sweep's iterate stops improving near delta 1e-8
+ * and its Ng must stop near 1e-6; at small eps the remaining iterations
+ * converge slowly, which the double-float stage with Ng avoids.  0 (default)
+ * = off.  The batch version applies it per problem: problems still in the
+ * FP32 sweep share the fused launch, those in their finishing stage run one
+ * launch each. */
+int rt_set_df_finish(rt_ctx *ctx, double delta_switch);
+
 /* Source interpolation on each segment of a characteristic (the paper
  * names no order).  RT_SRC_LINEAR (default): S linear in optical depth
  * between the segment's end points.  RT_SRC_PARABOLIC: S quadratic through
@@ -362,6 +375,8 @@ int rt_batch_reset(rt_batch *batch, int rebuild_lstar);
  * as one fused launch per iteration, the double-float stage as one launch per
  * problem. */
 int rt_batch_set_precision(rt_batch *batch, int precision);
+/* As rt_set_df_finish, for every problem of the batch. */
+int rt_batch_set_df_finish(rt_batch *batch, double delta_switch);
 /* Iterate until every problem has delta < tol or max_iter iterations.
  * iters[nprob], deltas[nprob] (host, may be NULL) receive each problem's
  * iteration count and last delta; *n_converged the number converged.

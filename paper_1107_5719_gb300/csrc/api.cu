@@ -27,6 +27,7 @@ struct rt_ctx {
     bool have_grid = false, have_quad = false, have_chi = false, have_eps = false, have_B = false;
     bool lstar_valid = false, coef_valid = false, b2_valid = false;
     int os_method = RT_OS_JACOBI;
+    double df_switch = 0.0;   // FP32 sweep: continue in double-float once delta < this
     unsigned long long* berr = nullptr;   // checked builds: out-of-bounds record
     int fs_method = RT_FS_LONG;
     int src_order = RT_SRC_LINEAR;
@@ -642,6 +643,32 @@ int ng_finish(rt_ctx* c)
     return RT_OK;
 }
 
+// Switch between the FP32 sweep and the double-float march (see rt_set_precision).
+int switch_precision(rt_ctx* c, int precision)
+{
+    if (precision == c->precision) return RT_OK;
+    const bool ok = (precision == RT_FP32_SWEEP || precision == RT_DF64) &&
+                    (c->precision == RT_FP32_SWEEP || c->precision == RT_DF64);
+    if (!ok) return fail(c, RT_EINVAL, "precision switches only between RT_FP32_SWEEP and RT_DF64");
+    if (precision == RT_FP32_SWEEP && c->fs_method == RT_FS_SHORT)
+        return fail(c, RT_EINVAL, "short characteristics have no FP32-sweep form");
+    if (precision == RT_DF64) {
+        // buffers the double-float march needs beyond the FP32 sweep's
+        if (c->have_grid && !c->g2df) CK(dalloc(c->g2df, (size_t)4 * c->g.nx * c->g.ny));
+        if (c->have_quad && !c->bwdf) {
+            const long long T = (long long)c->g.ndir * c->g.nz;
+            CK(dalloc(c->bwdf, (size_t)(2 * T)));
+            CK(launch_bw_df(T, c->bw, c->bwdf, c->stream));
+            c->stats.launches += 1;
+        }
+    }
+    c->precision = precision;
+    c->gdiff_valid = false;    // the gradient's packed copy differs between the forms
+    c->lstar_valid = c->coef_valid = false;   // Lambda* is rebuilt by the new form's kernel
+    c->ng_count = 1;           // restart the Ng history with iterates of the new form
+    return RT_OK;
+}
+
 int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps, double* J_out,
           int* iters, double* last_delta, double* deltas, int* sweeps, bool device)
 {
@@ -650,6 +677,21 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
     if ((rc = need_all(c))) return rc;
     if (max_iter < 1 || max_sweeps < 1 || !(tol >= 0) || !(tol_inner >= 0))
         return fail(c, RT_EINVAL, "bad iteration controls");
+    // double-float finishing stage: the context returns to its form and Ng
+    // threshold when the solve ends, whichever way it ends
+    struct FinishGuard {
+        rt_ctx* c;
+        int precision;
+        double ng_min;
+        bool on;
+        ~FinishGuard()
+        {
+            if (on) {
+                switch_precision(c, precision);
+                c->ng_min_delta = ng_min;
+            }
+        }
+    } guard{c, c->precision, c->ng_min_delta, false};
     int it = 0;
     double delta = 0.0;
     bool converged = false;
@@ -684,6 +726,11 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
         if (tol > 0 && delta < tol) {
             converged = true;
             break;
+        }
+        if (!guard.on && c->df_switch > 0 && c->precision == RT_FP32_SWEEP && delta < c->df_switch) {
+            if ((rc = switch_precision(c, RT_DF64))) return rc;
+            c->ng_min_delta = 0.0;
+            guard.on = true;
         }
     }
     c->last_steps = total_steps;
@@ -793,23 +840,36 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
     BCK(cudaMemsetAsync(b->d_steps, 0, sizeof(unsigned long long), b->stream));
     if (b->profiling) BCK(cudaEventRecord(b->ev[0], b->stream));
     if (b->precision == RT_FP32_SWEEP) {
+        // one fused launch over the problems still in the FP32 sweep (act is
+        // in launch order); those in their double-float finishing stage run
+        // one launch each
         long long total = 0;
         int q = 0;
-        for (int p : b->order) {
-            if (b->converged[p]) continue;
+        for (int p : act) {
+            if (b->ctx[p]->precision != RT_FP32_SWEEP) continue;
             b->h_ids[q] = p;
             b->h_prefix[q] = total;
             total += fs32_blocks(b->ctx[p]->g, G);
             ++q;
         }
         b->h_prefix[q] = total;
-        BCK(cudaMemcpyAsync(b->d_ids, b->h_ids, sizeof(int) * q, cudaMemcpyHostToDevice, b->stream));
-        BCK(cudaMemcpyAsync(b->d_prefix, b->h_prefix, sizeof(long long) * (q + 1),
-                            cudaMemcpyHostToDevice, b->stream));
-        BCK(launch_fs32_batch(b->d_views, b->d_ids, b->d_prefix, q, total, G,
-                              cut_of(b->ctx[0]), b->d_steps, b->stream));
-        b->stats.fs_launches += 1;
-        b->stats.launches += 1;
+        if (q > 0) {
+            BCK(cudaMemcpyAsync(b->d_ids, b->h_ids, sizeof(int) * q, cudaMemcpyHostToDevice,
+                                b->stream));
+            BCK(cudaMemcpyAsync(b->d_prefix, b->h_prefix, sizeof(long long) * (q + 1),
+                                cudaMemcpyHostToDevice, b->stream));
+            BCK(launch_fs32_batch(b->d_views, b->d_ids, b->d_prefix, q, total, G,
+                                  cut_of(b->ctx[0]), b->d_steps, b->stream));
+            b->stats.fs_launches += 1;
+            b->stats.launches += 1;
+        }
+        for (int p : act) {
+            rt_ctx* c = b->ctx[p];
+            if (c->precision != RT_DF64) continue;
+            BCK(launch_fsdf(viewdf(c), cut_of(c), G, b->d_steps, b->stream));
+            b->stats.fs_launches += 1;
+            b->stats.launches += 1;
+        }
     } else {
         for (int p : act) {
             rt_ctx* c = b->ctx[p];
@@ -1236,26 +1296,23 @@ int rt_set_precision(rt_ctx* c, int precision)
 {
     int rc = enter(c);
     if (rc) return rc;
-    if (precision == c->precision) return RT_OK;
-    const bool ok = (precision == RT_FP32_SWEEP || precision == RT_DF64) &&
-                    (c->precision == RT_FP32_SWEEP || c->precision == RT_DF64);
-    if (!ok) return fail(c, RT_EINVAL, "precision switches only between RT_FP32_SWEEP and RT_DF64");
-    if (precision == RT_FP32_SWEEP && c->fs_method == RT_FS_SHORT)
-        return fail(c, RT_EINVAL, "short characteristics have no FP32-sweep form");
-    if (precision == RT_DF64) {
-        // buffers the double-float march needs beyond the FP32 sweep's
-        if (c->have_grid && !c->g2df) CK(dalloc(c->g2df, (size_t)4 * c->g.nx * c->g.ny));
-        if (c->have_quad && !c->bwdf) {
-            const long long T = (long long)c->g.ndir * c->g.nz;
-            CK(dalloc(c->bwdf, (size_t)(2 * T)));
-            CK(launch_bw_df(T, c->bw, c->bwdf, c->stream));
-            c->stats.launches += 1;
-        }
-    }
-    c->precision = precision;
-    c->gdiff_valid = false;    // the gradient's packed copy differs between the forms
-    c->lstar_valid = c->coef_valid = false;   // Lambda* is rebuilt by the new form's kernel
-    c->ng_count = 1;           // restart the Ng history with iterates of the new form
+    return switch_precision(c, precision);
+}
+
+
+int rt_set_df_finish(rt_ctx* c, double delta_switch)
+{
+    if (!c) return RT_EINVAL;
+    if (!(delta_switch >= 0)) return fail(c, RT_EINVAL, "delta_switch must be >= 0");
+    c->df_switch = delta_switch;
+    return RT_OK;
+}
+
+int rt_batch_set_df_finish(rt_batch* b, double delta_switch)
+{
+    if (!b) return RT_EINVAL;
+    if (!(delta_switch >= 0)) return bfail(b, RT_EINVAL, "delta_switch must be >= 0");
+    for (rt_ctx* c : b->ctx) c->df_switch = delta_switch;
     return RT_OK;
 }
 
@@ -1503,6 +1560,8 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
         return bfail(b, RT_EINVAL, "bad iteration controls");
     const int P = (int)b->ctx.size();
     int rc;
+    std::vector<char> switched(P, 0);   // problems in their double-float finishing stage
+    std::vector<double> ng_min0(P, 0.0);
     for (int it = 0; it < max_iter; ++it) {
         std::vector<int> act;
         for (int p : b->order)
@@ -1538,9 +1597,24 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
             b->iters[p] += 1;
             b->delta[p] = b->h_delta[p];
             c->ng_last_delta = b->h_delta[p];
-            if (tol > 0 && b->h_delta[p] < tol) b->converged[p] = 1;
+            if (tol > 0 && b->h_delta[p] < tol) {
+                b->converged[p] = 1;
+            } else if (c->df_switch > 0 && c->precision == RT_FP32_SWEEP &&
+                       b->precision == RT_FP32_SWEEP && b->h_delta[p] < c->df_switch) {
+                // double-float finishing stage for this problem
+                if ((rc = bpass(b, p, switch_precision(c, RT_DF64)))) return rc;
+                switched[p] = 1;
+                ng_min0[p] = c->ng_min_delta;
+                c->ng_min_delta = 0.0;
+            }
         }
     }
+    for (int p = 0; p < P; ++p)
+        if (switched[p]) {
+            rt_ctx* c = b->ctx[p];
+            switch_precision(c, RT_FP32_SWEEP);
+            c->ng_min_delta = ng_min0[p];
+        }
     int nconv = 0;
     for (int p = 0; p < P; ++p) {
         if (iters) iters[p] = b->iters[p];

@@ -96,6 +96,8 @@ _SIGS = {
     "rt_set_fs_method": (C.c_int, [VP, C.c_int]),
     "rt_set_source_order": (C.c_int, [VP, C.c_int]),
     "rt_set_precision": (C.c_int, [VP, C.c_int]),
+    "rt_set_df_finish": (C.c_int, [VP, C.c_double]),
+    "rt_batch_set_df_finish": (C.c_int, [VP, C.c_double]),
     "rt_checked_build": (C.c_int, []),
     "rt_bounds_selftest": (C.c_int, [VP]),
     "rt_batch_set_precision": (C.c_int, [VP, C.c_int]),
@@ -352,6 +354,14 @@ def rt_bounds_selftest(ctx):
 
 def rt_batch_set_precision(b, precision):
     return _bcheck(b, load().rt_batch_set_precision(b, precision))
+
+
+def rt_set_df_finish(ctx, delta_switch):
+    return _check(ctx, load().rt_set_df_finish(ctx, delta_switch))
+
+
+def rt_batch_set_df_finish(b, delta_switch):
+    return _bcheck(b, load().rt_batch_set_df_finish(b, delta_switch))
 
 
 def rt_batch_set_os_method(b, method):

@@ -91,3 +91,47 @@ def test_batch_fp32_then_double_float_equals_single(R):
             c = s.solve(tol=1e-8, max_iter=500)
         assert a["iters"] == r1["iters"][i] and c["iters"] == r2["iters"][i]
         assert np.array_equal(c["J"], Jb[i])
+
+
+def test_automatic_double_float_finish(R):
+    """rt_set_df_finish: the FP32-sweep solve switches itself to double-float
+    once delta < 1e-6 and reaches a tolerance below the FP32 noise floor, in
+    fewer iterations than the FP32 sweep needs for 5e-8; afterwards the
+    context is an FP32-sweep context again."""
+    p = W.slab_precision(n=9, nzz=129, n_theta=32, n_phi=8)
+    with R.Solver(p, precision=R.RT_FP64, ng_period=4) as s:
+        r64 = s.solve(tol=1e-11, max_iter=5000)
+    with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+        r32 = s.solve(tol=5e-8, max_iter=5000)
+    S = p.B * 1.1
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        Jref, _ = s.formal_solution(S)
+    with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+        R.rt_set_df_finish(s.ctx, 1e-6)
+        r = s.solve(tol=1e-8, max_iter=5000)
+        J, _ = s.formal_solution(S)                 # back in the FP32 sweep
+    assert r["converged"]
+    err = np.max(np.abs(r["J"] - r64["J"]) / r64["J"])
+    assert err < 1e-6, err
+    assert r["iters"] < r32["iters"]
+    assert np.array_equal(J, Jref)
+
+
+def test_batch_automatic_finish_equals_single(R):
+    probs = [W.slab_precision(n=7, nzz=33, eps=e, n_theta=8, n_phi=4, seed=80 + i)
+             for i, e in enumerate((1e-6, 1e-4, 1e-2))]
+    b = R.rt_batch_create(probs, precision=R.RT_FP32_SWEEP)
+    try:
+        R.rt_batch_set_ng(b, 4, 1e-6)
+        R.rt_batch_set_df_finish(b, 1e-6)
+        rb = R.rt_batch_solve(b, len(probs), tol=1e-8, max_iter=3000)
+        assert rb["converged"]
+        Jb = [R.rt_batch_get_J(b, i, (q.nz, q.ny, q.nx)) for i, q in enumerate(probs)]
+    finally:
+        R.rt_batch_destroy(b)
+    for i, q in enumerate(probs):
+        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+            R.rt_set_df_finish(s.ctx, 1e-6)
+            r = s.solve(tol=1e-8, max_iter=3000)
+        assert r["iters"] == rb["iters"][i]
+        assert np.array_equal(r["J"], Jb[i])
