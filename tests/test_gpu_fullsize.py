@@ -42,3 +42,20 @@ def test_slab129_formal_solution_sampled(R, case, prec, rtol):
         J, _ = s.formal_solution(S, want_lstar=False)
     Js = J.ravel()[vox]
     assert np.allclose(Js, Jo, rtol=rtol, atol=0), np.max(np.abs(Js - Jo) / Jo)
+
+
+def test_uneven_batch_largest_grid_sampled(R, oracle_mod):
+    """The largest grid of the uneven batch, 257 x 257 x 129 with 64x64
+    directions (one wavelength of it), FP32 sweep and double-float march,
+    J at sampled voxels against the oracle."""
+    q = W.batch_uneven(sizes=((257, 257, 129, 1),))[0]
+    rng = np.random.default_rng(23)
+    S = 0.5 + rng.random(q.chi.shape)
+    ks = np.concatenate([np.arange(0, q.nz, 4), rng.integers(0, q.nz, 15)])
+    vox = ks * q.nx * q.ny + rng.integers(0, q.nx * q.ny, ks.shape[0])
+    Jo = oracle_mod.mean_intensity_at(q, S, vox)
+    for precision, rtol in ((R.RT_DF64, 1e-12), (R.RT_FP32_SWEEP, 1e-6)):
+        with R.Solver(q, precision=precision) as s:
+            J, _ = s.formal_solution(S, want_lstar=False)
+        Js = J.ravel()[vox]
+        assert np.allclose(Js, Jo, rtol=rtol, atol=0), (precision, np.max(np.abs(Js - Jo) / Jo))
