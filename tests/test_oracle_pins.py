@@ -110,12 +110,18 @@ def test_pure_absorption_linear_chi_exact_tau(oracle_mod):
             assert abs(I - Iref) <= 2e-15 + 1e-14 * Iref
 
 
-def test_diffusion_boundary_exact_for_linear_planck(oracle_mod):
+@pytest.mark.parametrize("variant", ["linear", "parabolic", "short"])
+def test_diffusion_boundary_exact_for_linear_planck(oracle_mod, variant):
+    _diffusion_pin(oracle_mod, variant)
+
+
+def _diffusion_pin(oracle_mod, variant="linear"):
     """Pure absorption, constant chi, B linear in optical depth,
     B = a + c tau: the diffusion approximation I = B + |mu| dB/dtau is then
     the exact upward intensity, so with the LTE-diffusion inner boundary
-    every upward ray at every depth gives B(tau_0) + |mu| c (the
-    linear-source march is exact for a linear source)."""
+    every upward ray at every depth gives B(tau_0) + |mu| c: the linear and
+    the parabolic source integrate a linear source exactly, and the short
+    characteristics interpolate a horizontally uniform plane exactly."""
     nx, ny, nz = 4, 3, 10
     chi, a, c, dz = 0.7, 2.0, 0.45, 1.3
     k = np.arange(nz, dtype=float)
@@ -123,7 +129,16 @@ def test_diffusion_boundary_exact_for_linear_planck(oracle_mod):
     mu, phi, w = W.quadrature(8, 3)
     p = _problem(nx, ny, nz, chi, (a + c * tau)[:, None, None], mu, phi, w, dz=dz,
                  bottom=W.BC_DIFFUSION)
+    p.src_order = 1 if variant == "parabolic" else 0
     S = p.B.copy()
+    if variant == "short":
+        # J from the upward directions only: zero weight on the downward ones
+        up = mu < 0
+        p.w = np.where(up, w, 0.0) / np.sum(w[up])
+        J, _ = oracle_mod.formal_solution(p, S, lstar=False, method=oracle_mod.SHORT)
+        ref = a + c * tau + np.sum(p.w * np.abs(mu)) * c
+        assert np.allclose(J[:, 0, 0], ref, rtol=1e-13, atol=0)
+        return
     for d in range(len(mu)):
         if mu[d] > 0:
             continue
@@ -793,7 +808,7 @@ def _pin_battery(mod):
         ("gauss_seidel", lambda: test_gauss_seidel_sweep_equals_block_form(mod, (3, 5, 4), 4)),
         ("ali", lambda: test_converged_ali_equals_dense_solution(mod)),
         ("ng", lambda: test_ng_extrapolation_exact_for_two_geometric_modes(mod)),
-        ("diffusion", lambda: test_diffusion_boundary_exact_for_linear_planck(mod)),
+        ("diffusion", lambda: _diffusion_pin(mod)),
     ]
     for name, fn in pins:
         try:
