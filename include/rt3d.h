@@ -231,6 +231,14 @@ int rt_set_fs_method(rt_ctx *ctx, int method);
  * Allocates the double-float tables on the first switch to RT_DF64. */
 int rt_set_precision(rt_ctx *ctx, int precision);
 
+/* Operator-splitting steps as CUDA graphs (default on): the right-hand side
+ * and the sweep loop of one step form one graph whose WHILE node runs the
+ * sweeps and their convergence test on the device, so the host launches it
+ * and synchronises once per step instead of once per chunk of sweeps.
+ * Results are identical either way (same kernels, same sweep count).
+ * on = 0 selects the host-driven loop. */
+int rt_set_graphs(rt_ctx *ctx, int on);
+
 /* Automatic double-float finishing stage for RT_FP32_SWEEP contexts:
  * within rt_solve, once an iteration's delta falls below delta_switch (and
  * not yet below tol), the iteration continues in double-float with Ng

@@ -28,6 +28,20 @@ struct rt_ctx {
     bool lstar_valid = false, coef_valid = false, b2_valid = false;
     int os_method = RT_OS_JACOBI;
     double df_switch = 0.0;   // FP32 sweep: continue in double-float once delta < this
+    // operator-splitting step as a CUDA graph with the sweep loop in a WHILE
+    // node (two cached instances: J_old alternates between two buffers)
+    struct OsGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const double* jold = nullptr;
+        const double* jfs = nullptr;
+        const double* dlt = nullptr;
+        int max_sweeps = 0, method = -1;
+        double tol = -1.0;
+    } osg[2];
+    int osg_next = 0;
+    int* d_nsw = nullptr;     // the graph's sweep counter
+    bool use_graphs = true;
     unsigned long long* berr = nullptr;   // checked builds: out-of-bounds record
     int fs_method = RT_FS_LONG;
     int src_order = RT_SRC_LINEAR;
@@ -139,8 +153,18 @@ void free_ng(rt_ctx* c)
     c->h_ng = nullptr;
 }
 
+void free_os_graphs(rt_ctx* c)
+{
+    for (auto& e : c->osg) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (e.graph) cudaGraphDestroy(e.graph);
+        e = rt_ctx::OsGraph{};
+    }
+}
+
 void free_grid_buffers(rt_ctx* c)
 {
+    free_os_graphs(c);
     dfree(c->chi); dfree(c->eps); dfree(c->B); dfree(c->J); dfree(c->S);
     dfree(c->Jfs); dfree(c->Jn); dfree(c->Ja); dfree(c->Jb); dfree(c->r);
     dfree(c->lstar); dfree(c->coef); dfree(c->rdiag); dfree(c->partial);
@@ -501,6 +525,7 @@ int ensure_dlt(rt_ctx* c, int max_sweeps)
 {
     if (c->dlt_cap >= max_sweeps) return RT_OK;
     int cap = max_sweeps < 1024 ? 1024 : max_sweeps;
+    free_os_graphs(c);          // they hold the old dlt pointer
     CK(dalloc(c->dlt, (size_t)cap));
     if (c->h_dlt) cudaFreeHost(c->h_dlt);
     c->h_dlt = nullptr;
@@ -513,11 +538,132 @@ int ensure_dlt(rt_ctx* c, int max_sweeps)
 // are enqueued in growing chunks; a sweep that follows a converged one is a
 // no-op on the device, so checking once per chunk gives exactly the sweeps
 // of a check after every sweep.
+// The operator-splitting step as one CUDA graph: right-hand side, zeroed
+// deltas, J_old copied to the sweep buffer read first, a zeroed sweep
+// counter, then a WHILE node whose body runs two sweeps and the loop test on
+// the device.  The host launches it once and reads the deltas once, instead
+// of synchronising after every chunk of sweeps.  Results are those of the
+// host loop: same kernels, same no-op rule after convergence.
+int build_os_graph(rt_ctx* c, rt_ctx::OsGraph& e, const double* Jfs, const double* Jold,
+                   double tol, int max_sweeps)
+{
+    const bool gs = c->os_method == RT_OS_GAUSS_SEIDEL;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t err = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    std::vector<cudaGraphNode_t> deps;
+    if (err == cudaSuccess)
+        err = cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+        // prologue; every call is attempted so that the capture is always ended
+        cudaError_t e1 = launch_os_rhs(c->g, c->coef, c->rdiag, Jfs, Jold, c->r, gs, c->stream);
+        cudaError_t e2 = cudaMemsetAsync(c->dlt, 0, sizeof(double) * (max_sweeps + 2), c->stream);
+        cudaError_t e3 = cudaMemcpyAsync(c->Jb, Jold, sizeof(double) * c->g.N,
+                                         cudaMemcpyDeviceToDevice, c->stream);
+        cudaError_t e4 = cudaMemsetAsync(c->d_nsw, 0, sizeof(int), c->stream);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* dp = nullptr;
+        size_t nd = 0;
+        cudaError_t e5 = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, nullptr, &dp, nullptr, &nd);
+        if (e5 == cudaSuccess) deps.assign(dp, dp + nd);
+        cudaGraph_t out = nullptr;
+        cudaError_t e6 = cudaStreamEndCapture(c->stream, &out);
+        for (cudaError_t x : {e1, e2, e3, e4, e5, e6})
+            if (err == cudaSuccess && x != cudaSuccess) err = x;
+    }
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t cn;
+    if (err == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        err = cudaGraphAddNode(&cn, g, deps.data(), nullptr, deps.size(), &cp);
+    }
+    if (err == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        err = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+        if (err == cudaSuccess) {
+            cudaError_t e1 = launch_sweep_pass(c->g, c->coef, c->r, c->Ja, c->Jb, c->dlt, c->d_nsw,
+                                               max_sweeps, tol, gs, h, c->stream);
+            cudaGraph_t out = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(c->stream, &out);
+            err = e1 != cudaSuccess ? e1 : e2;
+        }
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, g, 0);
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(c, RT_ECUDA, "building the operator-splitting graph: %s", cudaGetErrorString(err));
+    }
+    e.graph = g;
+    e.exec = exec;
+    e.jold = Jold;
+    e.jfs = Jfs;
+    e.dlt = c->dlt;
+    e.max_sweeps = max_sweeps;
+    e.method = c->os_method;
+    e.tol = tol;
+    return RT_OK;
+}
+
+int run_os_graph(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, double tol_inner,
+                 int max_sweeps, int* sweeps_out)
+{
+    int rc;
+    if ((rc = ensure_dlt(c, max_sweeps + 2))) return rc;
+    if (!c->d_nsw) CK(cudaMalloc((void**)&c->d_nsw, sizeof(int)));
+    rt_ctx::OsGraph* e = nullptr;
+    for (auto& x : c->osg)
+        if (x.exec && x.jold == Jold && x.jfs == Jfs && x.dlt == c->dlt &&
+            x.max_sweeps == max_sweeps && x.tol == tol_inner && x.method == c->os_method)
+            e = &x;
+    if (!e) {
+        e = &c->osg[c->osg_next];
+        c->osg_next ^= 1;
+        if (e->exec) cudaGraphExecDestroy(e->exec);
+        if (e->graph) cudaGraphDestroy(e->graph);
+        *e = rt_ctx::OsGraph{};
+        if ((rc = build_os_graph(c, *e, Jfs, Jold, tol_inner, max_sweeps))) return rc;
+    }
+    if (c->profiling) CK(cudaEventRecord(c->ev[2], c->stream));
+    CK(cudaGraphLaunch(e->exec, c->stream));
+    if (c->profiling) {
+        CK(cudaEventRecord(c->ev[3], c->stream));
+        c->jac_pending = true;
+    }
+    CK(cudaMemcpyAsync(c->h_dlt, c->dlt, sizeof(double) * max_sweeps, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    harvest(c);
+    int sweeps = max_sweeps;
+    for (int n = 0; n < max_sweeps; ++n)
+        if (c->h_dlt[n] < tol_inner) {
+            sweeps = n + 1;
+            break;
+        }
+    // sweep n wrote Ja for even n, Jb for odd n
+    CK(cudaMemcpyAsync(Jnew, (sweeps - 1) & 1 ? c->Jb : c->Ja, sizeof(double) * c->g.N,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    const int per = c->os_method == RT_OS_GAUSS_SEIDEL ? 2 : 1;
+    const int passes = (sweeps + 1) / 2;
+    c->stats.launches += 1 + passes * (2 * per + 1);
+    c->stats.jacobi_launches += passes * 2 * per;
+    if (sweeps_out) *sweeps_out = sweeps;
+    return RT_OK;
+}
+
 int run_os(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, double tol_inner,
            int max_sweeps, int* sweeps_out)
 {
     int rc = ensure_coef(c);
     if (rc) return rc;
+    if (c->use_graphs) return run_os_graph(c, Jfs, Jold, Jnew, tol_inner, max_sweeps, sweeps_out);
     if ((rc = ensure_dlt(c, max_sweeps))) return rc;
     const bool gs = c->os_method == RT_OS_GAUSS_SEIDEL;
     CK(launch_os_rhs(c->g, c->coef, c->rdiag, Jfs, Jold, c->r, gs, c->stream));
@@ -1008,6 +1154,8 @@ int rt_destroy(rt_ctx* c)
     dfree(c->scal);
     dfree(c->d_steps);
     dfree(c->berr);
+    if (c->d_nsw) cudaFree(c->d_nsw);
+    c->d_nsw = nullptr;
     if (c->h_scal) cudaFreeHost(c->h_scal);
     if (c->h_steps) cudaFreeHost(c->h_steps);
     if (c->h_dlt) cudaFreeHost(c->h_dlt);
@@ -1299,6 +1447,13 @@ int rt_set_precision(rt_ctx* c, int precision)
     return switch_precision(c, precision);
 }
 
+
+int rt_set_graphs(rt_ctx* c, int on)
+{
+    if (!c) return RT_EINVAL;
+    c->use_graphs = on != 0;
+    return RT_OK;
+}
 
 int rt_set_df_finish(rt_ctx* c, double delta_switch)
 {

@@ -242,6 +242,13 @@ cudaError_t launch_os_rhs(const Geometry& g, const double* coef, const double* r
 cudaError_t launch_gs_sweep(const Geometry& g, const double* coef, const double* r,
                             const double* J, double* Jn, double* dlt, int n, double tol,
                             cudaStream_t st);
+// One pass of the device-side sweep loop (body of a CUDA graph WHILE node):
+// sweeps *nsw (b1 -> b0) and *nsw + 1 (b0 -> b1), Jacobi or Gauss-Seidel,
+// then *nsw += 2 and the loop condition h = (*nsw < max_sweeps and the last
+// sweep's dlt >= tol).  Same no-op rule and dlt layout as the host loop.
+cudaError_t launch_sweep_pass(const Geometry& g, const double* coef, const double* r, double* b0,
+                              double* b1, double* dlt, int* nsw, int max_sweeps, double tol,
+                              bool gs, cudaGraphConditionalHandle h, cudaStream_t st);
 // Sweep n: Jn[v] = r[v] + sum_{o != 13} c[o][v] J[nb(v,o)];  dlt[n] = max |Jn - J| / |Jn|;
 // no-op when n > 0 and dlt[n-1] < tol.
 cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r,

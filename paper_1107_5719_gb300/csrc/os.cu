@@ -200,11 +200,18 @@ k_os_rhs(Geometry g, const double* __restrict__ c, const double* __restrict__ rd
 // previous sweep already met the tolerance (dlt[n-1] < tol) the sweep does
 // nothing, so a host loop may enqueue several sweeps per check without
 // changing the result.  dlt must be zeroed before sweep 0.
+//
+// With nsw != null the sweep index is *nsw + n (a device-side counter: the
+// sweep loop of a CUDA graph), and sweeps at or past max_sweeps do nothing.
 __global__ void __launch_bounds__(kOsThreads)
 k_jacobi(Geometry g, const double* __restrict__ c, const double* __restrict__ r,
          const double* __restrict__ J, double* __restrict__ Jn, double* __restrict__ dlt, int n,
-         double tol)
+         double tol, const int* __restrict__ nsw, int max_sweeps)
 {
+    if (nsw) {
+        n += *nsw;
+        if (n >= max_sweeps) return;
+    }
     if (n > 0 && dlt[n - 1] < tol) return;
     double* delta = dlt + n;
     const int nx = g.nx, nxy = nx * g.ny;
@@ -230,8 +237,13 @@ k_jacobi(Geometry g, const double* __restrict__ c, const double* __restrict__ r,
 __global__ void __launch_bounds__(kOsThreads)
 k_gs_half(Geometry g, const double* __restrict__ c, const double* __restrict__ r,
           const double* __restrict__ same, const double* other, double* dst,
-          double* __restrict__ dlt, int n, double tol, int colour)
+          double* __restrict__ dlt, int n, double tol, int colour,
+          const int* __restrict__ nsw, int max_sweeps)
 {
+    if (nsw) {
+        n += *nsw;
+        if (n >= max_sweeps) return;
+    }
     if (n > 0 && dlt[n - 1] < tol) return;
     const int nx = g.nx, ny = g.ny, nxy = nx * ny, h = split_h(nx);
     const int t = blockIdx.x * kOsThreads + threadIdx.x;
@@ -271,6 +283,18 @@ k_gs_half(Geometry g, const double* __restrict__ c, const double* __restrict__ r
         rel = nonneg((acc - same[v]) / acc);
     }
     block_max_to(rel, dlt + n);
+}
+
+// End of one pass of the graph's sweep loop (two sweeps): advance the
+// counter and continue while sweeps remain and the last one had not met
+// the tolerance.
+__global__ void k_sweep_cond(cudaGraphConditionalHandle h, int* nsw, const double* __restrict__ dlt,
+                             int max_sweeps, double tol)
+{
+    const int n = *nsw + 2;
+    *nsw = n;
+    const bool more = n < max_sweeps && !(dlt[n - 1] < tol);
+    cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 __global__ void k_rel_change(long long N, const double* __restrict__ Jn,
@@ -406,8 +430,28 @@ cudaError_t launch_gs_sweep(const Geometry& g, const double* coef, const double*
                             cudaStream_t st)
 {
     dim3 grid((g.ny * split_h(g.nx) + kOsThreads - 1) / kOsThreads, g.nz);
-    k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, J, Jn, dlt, n, tol, 0);
-    k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, Jn, Jn, dlt, n, tol, 1);
+    k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, J, Jn, dlt, n, tol, 0, nullptr, 0);
+    k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, Jn, Jn, dlt, n, tol, 1, nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_pass(const Geometry& g, const double* coef, const double* r, double* b0,
+                              double* b1, double* dlt, int* nsw, int max_sweeps, double tol,
+                              bool gs, cudaGraphConditionalHandle h, cudaStream_t st)
+{
+    // sweep *nsw: b1 -> b0; sweep *nsw + 1: b0 -> b1
+    if (gs) {
+        dim3 grid((g.ny * split_h(g.nx) + kOsThreads - 1) / kOsThreads, g.nz);
+        k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, b1, b1, b0, dlt, 0, tol, 0, nsw, max_sweeps);
+        k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, b1, b0, b0, dlt, 0, tol, 1, nsw, max_sweeps);
+        k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, b0, b0, b1, dlt, 1, tol, 0, nsw, max_sweeps);
+        k_gs_half<<<grid, kOsThreads, 0, st>>>(g, coef, r, b0, b1, b1, dlt, 1, tol, 1, nsw, max_sweeps);
+    } else {
+        dim3 grid((g.nx * g.ny + kOsThreads - 1) / kOsThreads, g.nz);
+        k_jacobi<<<grid, kOsThreads, 0, st>>>(g, coef, r, b1, b0, dlt, 0, tol, nsw, max_sweeps);
+        k_jacobi<<<grid, kOsThreads, 0, st>>>(g, coef, r, b0, b1, dlt, 1, tol, nsw, max_sweeps);
+    }
+    k_sweep_cond<<<1, 1, 0, st>>>(h, nsw, dlt, max_sweeps, tol);
     return cudaGetLastError();
 }
 
@@ -416,7 +460,7 @@ cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r
                           cudaStream_t st)
 {
     dim3 grid((g.nx * g.ny + kOsThreads - 1) / kOsThreads, g.nz);
-    k_jacobi<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, Jn, dlt, n, tol);
+    k_jacobi<<<grid, kOsThreads, 0, st>>>(g, coef, r, J, Jn, dlt, n, tol, nullptr, 0);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,7 @@ _SIGS = {
     "rt_set_source_order": (C.c_int, [VP, C.c_int]),
     "rt_set_precision": (C.c_int, [VP, C.c_int]),
     "rt_set_df_finish": (C.c_int, [VP, C.c_double]),
+    "rt_set_graphs": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_df_finish": (C.c_int, [VP, C.c_double]),
     "rt_checked_build": (C.c_int, []),
     "rt_bounds_selftest": (C.c_int, [VP]),
@@ -358,6 +359,10 @@ def rt_batch_set_precision(b, precision):
 
 def rt_set_df_finish(ctx, delta_switch):
     return _check(ctx, load().rt_set_df_finish(ctx, delta_switch))
+
+
+def rt_set_graphs(ctx, on):
+    return _check(ctx, load().rt_set_graphs(ctx, 1 if on else 0))
 
 
 def rt_batch_set_df_finish(b, delta_switch):
