@@ -54,3 +54,21 @@ def test_solve_graph_equals_host_loop(R, precision, method):
     assert a["converged"] and a["iters"] == b["iters"]
     assert np.array_equal(a["sweeps"], b["sweeps"])
     assert np.array_equal(a["J"], b["J"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_all_options_together_match_oracle(R, oracle_mod, precision):
+    """Short characteristics, red-black Gauss-Seidel, LTE-diffusion inner
+    boundary, Planck outer boundary, Ng, the graph-driven sweeps and (for
+    df64) the double-float arithmetic in one converged solve, against the
+    oracle running the same options."""
+    p = W.random_slab(10, 9, 8, n_theta=6, n_phi=5, seed=77, eps_range=(1e-3, 1.0),
+                      top_bc=W.BC_PLANCK, bottom_bc=W.BC_DIFFUSION, dx=0.8, dz=1.2)
+    ro = oracle_mod.solve(p, tol=1e-9, max_iter=300, tol_inner=0.0, max_sweeps=9, ng_period=4,
+                          os_method=oracle_mod.GAUSS_SEIDEL, fs_method=oracle_mod.SHORT)
+    prec = R.RT_FP64 if precision == "fp64" else R.RT_DF64
+    with R.Solver(p, precision=prec, ng_period=4, fs_method=R.RT_FS_SHORT,
+                  os_method=R.RT_OS_GAUSS_SEIDEL) as s:
+        r = s.solve(tol=1e-9, max_iter=300, tol_inner=0.0, max_sweeps=9)
+    assert r["converged"] and ro["converged"] and r["iters"] == ro["iters"]
+    assert np.allclose(r["J"], ro["J"], rtol=1e-12, atol=0), np.max(np.abs(r["J"] - ro["J"]) / ro["J"])
