@@ -1,0 +1,74 @@
+"""Randomised parity sweep: seeded random small slabs (ragged sizes down to
+3x3x2, anisotropic spacings, every boundary mode, odd and even direction
+counts) through every form and method of the formal solution, J and Lambda*
+against the oracle."""
+
+import numpy as np
+import pytest
+
+from paper_1107_5719_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1107_5719_gb300 import build as B
+    B.build()
+    from paper_1107_5719_gb300 import rt3d
+    rt3d.load()
+    return rt3d
+
+
+def _case(seed):
+    rng = np.random.default_rng(1000 + seed)
+    nx, ny = int(rng.integers(3, 14)), int(rng.integers(3, 14))
+    nz = int(rng.integers(2, 10))
+    nt = int(2 * rng.integers(1, 5))
+    nph = int(rng.integers(1, 7))
+    top = int(rng.integers(0, 2))
+    bottom = int(rng.integers(0, 3))
+    dx, dy, dz = (float(v) for v in 0.5 + rng.random(3))
+    p = W.random_slab(nx, ny, nz, n_theta=nt, n_phi=nph, seed=seed, top_bc=top, bottom_bc=bottom,
+                      dx=dx, dy=dy, dz=dz, chi_decades=2.0)
+    S = 0.3 + rng.random(p.B.shape) * 2.0
+    return p, S
+
+
+def _close_lstar(L, Lo, rtol):
+    scale = np.abs(Lo).reshape(27, -1).max(axis=0)
+    return np.all(np.abs(L - Lo).reshape(27, -1).max(axis=0) <= rtol * scale)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_slab_all_forms(R, oracle_mod, seed):
+    p, S = _case(seed)
+    Jlo, Llo = oracle_mod.formal_solution(p, S)
+    Jso, Lso = oracle_mod.formal_solution(p, S, method=oracle_mod.SHORT)
+    p.src_order = 1
+    Jpo, Lpo = oracle_mod.formal_solution(p, S)
+    p.src_order = 0
+    runs = [
+        (dict(precision=R.RT_FP64), Jlo, Llo, 1e-12),
+        (dict(precision=R.RT_DF64), Jlo, Llo, 1e-12),
+        (dict(precision=R.RT_FP32_SWEEP), Jlo, None, 1e-6),
+        (dict(precision=R.RT_FP64, fs_method=R.RT_FS_SHORT), Jso, Lso, 1e-12),
+        (dict(precision=R.RT_DF64, fs_method=R.RT_FS_SHORT), Jso, Lso, 1e-12),
+    ]
+    for kw, Jo, Lo, rtol in runs:
+        with R.Solver(p, **kw) as s:
+            J, L = s.formal_solution(S)
+        assert np.allclose(J, Jo, rtol=rtol, atol=0), (kw, np.max(np.abs(J - Jo) / Jo))
+        if Lo is not None:
+            assert _close_lstar(L, Lo, rtol), kw
+    p.src_order = 1
+    with R.Solver(p) as s:
+        J, L = s.formal_solution(S)
+    p.src_order = 0
+    # parabolic weights amplify rounding by the neighbouring optical-depth
+    # ratio (up to ~1e2 here)
+    assert np.allclose(J, Jpo, rtol=1e-11, atol=0), np.max(np.abs(J - Jpo) / Jpo)
+    assert _close_lstar(L, Lpo, 1e-11)
