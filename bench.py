@@ -49,9 +49,8 @@ FLOPS_PER_STEP_FP32 = 45
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
 PEAK_FP32_TFLOPS = 80.5
 # DRAM bytes (read + write) per k_fs64 launch on slab65, from one ncu
-# capture of the current kernel: chi and S stay L2-resident, so the march
-# reads 6.4 MB per launch from DRAM and writes none.
-TRAFFIC_FS64_SLAB65 = 6427648
+# capture of the current kernel (None until one is taken).
+TRAFFIC_FS64_SLAB65 = None
 # The double-float march executes 398 thread instructions per step (ncu,
 # slab65); its bound is instruction issue: 152 SMs x 4 schedulers x 32 lanes
 # x 2.07 GHz = 40.3e12 thread instructions/s.
@@ -329,28 +328,30 @@ def run_ours(args):
                 "share_of_step": round(st["fs_ms"] / my_ms, 4)}
 
     # the FP32-sweep form of the same workload on the same GPU
-    tol32 = max(p.tol, TOL_FP32)
-    r32 = timed_solves(R, p, R.RT_FP32_SWEEP, dev, stream, flush, 1, args.fp32_steps,
-                       args.max_iter, ng=args.ng, ng_min=NG_MIN_FP32, tol=tol32)
-    st32 = r32["stats"]
-    ms32 = float(sum(r32["times"]))
-    fs32_ms = st32["fs_ms"] / max(st32["fs_launches"], 1)
-    fp32 = {"value": round(RP.weak_throughput(args.fp32_steps, ms32)[0], 6), "unit": "solves/s",
-            "ms_per_step": round(ms32 / args.fp32_steps, 3),
-            "iters_per_solve": st32["fs_launches"] / args.fp32_steps,
-            "march_steps_per_s": round(st32["steps"] / (ms32 / 1e3), 1),
-            "ms_per_fs_launch": round(fs32_ms, 4),
-            "fs_steps_per_s": round(st32["steps"] / (st32["fs_ms"] / 1e3), 1),
-            "tol": tol32,
-            "max_rel_dev_from_fp64_J": float(np.max(np.abs(r32["J"] - r64["J"]) / r64["J"])),
-            "speedup_vs_fp64": round(my_ms / args.steps / (ms32 / args.fp32_steps), 3)}
-    if st32["fs_ms"] > 0:
-        ach32 = FLOPS_PER_STEP_FP32 * st32["steps"] / (st32["fs_ms"] / 1e3) / 1e12
-        fp32["roofline"] = {"kernel": "k_fs32d (FP32-sweep march)", "bound": "alu",
-                            "achieved": round(ach32, 3), "peak": PEAK_FP32_TFLOPS,
-                            "unit": "TFLOP/s", "frac": round(ach32 / PEAK_FP32_TFLOPS, 4),
-                            "flops_per_step": FLOPS_PER_STEP_FP32,
-                            "note": "ncu: limited by L1 throughput, not the FP32 pipe"}
+    fp32 = None
+    if args.fp32_steps > 0:
+        tol32 = max(p.tol, TOL_FP32)
+        r32 = timed_solves(R, p, R.RT_FP32_SWEEP, dev, stream, flush, 1, args.fp32_steps,
+                           args.max_iter, ng=args.ng, ng_min=NG_MIN_FP32, tol=tol32)
+        st32 = r32["stats"]
+        ms32 = float(sum(r32["times"]))
+        fs32_ms = st32["fs_ms"] / max(st32["fs_launches"], 1)
+        fp32 = {"value": round(RP.weak_throughput(args.fp32_steps, ms32)[0], 6), "unit": "solves/s",
+                "ms_per_step": round(ms32 / args.fp32_steps, 3),
+                "iters_per_solve": st32["fs_launches"] / args.fp32_steps,
+                "march_steps_per_s": round(st32["steps"] / (ms32 / 1e3), 1),
+                "ms_per_fs_launch": round(fs32_ms, 4),
+                "fs_steps_per_s": round(st32["steps"] / (st32["fs_ms"] / 1e3), 1),
+                "tol": tol32,
+                "max_rel_dev_from_fp64_J": float(np.max(np.abs(r32["J"] - r64["J"]) / r64["J"])),
+                "speedup_vs_fp64": round(my_ms / args.steps / (ms32 / args.fp32_steps), 3)}
+        if st32["fs_ms"] > 0:
+            ach32 = FLOPS_PER_STEP_FP32 * st32["steps"] / (st32["fs_ms"] / 1e3) / 1e12
+            fp32["roofline"] = {"kernel": "k_fs32d (FP32-sweep march)", "bound": "alu",
+                                "achieved": round(ach32, 3), "peak": PEAK_FP32_TFLOPS,
+                                "unit": "TFLOP/s", "frac": round(ach32 / PEAK_FP32_TFLOPS, 4),
+                                "flops_per_step": FLOPS_PER_STEP_FP32,
+                                "note": "ncu: limited by L1 throughput, not the FP32 pipe"}
 
     # the double-float form (FP64-accurate march on the FP32 pipes)
     df64 = None

@@ -73,6 +73,7 @@ struct rt_ctx {
     DirInfo* info = nullptr;
     StepGeo* off = nullptr;
     Bw4d* bw = nullptr;
+    Bw4d* bwh = nullptr;
     float4* bw32 = nullptr;
     double *d_mu = nullptr, *d_phi = nullptr, *d_w = nullptr;
     // scalars: [0] smax, [1] inner delta, [2] outer delta
@@ -177,7 +178,8 @@ void free_grid_buffers(rt_ctx* c)
 
 void free_tables(rt_ctx* c)
 {
-    dfree(c->info); dfree(c->off); dfree(c->bw); dfree(c->bw32); dfree(c->poff); dfree(c->bwdf);
+    dfree(c->info); dfree(c->off); dfree(c->bw); dfree(c->bwh); dfree(c->bw32);
+    dfree(c->poff); dfree(c->bwdf);
     dfree(c->dn);
     dfree(c->d_mu); dfree(c->d_phi); dfree(c->d_w);
 }
@@ -429,8 +431,9 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
                         c->scal + 0, cut, G, c->partial, count_steps ? c->d_steps : nullptr,
                         c->stream));
     } else if (c->precision == RT_FP64) {
-        CK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->scal + 0,
-                       cut, G, c->partial, count_steps ? c->d_steps : nullptr, c->stream));
+        CK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->bwh,
+                       c->scal + 0, cut, G, c->partial, count_steps ? c->d_steps : nullptr,
+                       c->stream));
     } else if (c->precision == RT_DF64) {
         CK(launch_fsdf(viewdf(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
     } else {
@@ -1023,7 +1026,8 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
                 BCK(launch_fsdf(viewdf(c), cut_of(c), G, b->d_steps, b->stream));
             else
                 BCK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw,
-                                c->scal + 0, cut_of(c), G, c->partial, b->d_steps, b->stream));
+                                c->bwh, c->scal + 0, cut_of(c), G, c->partial, b->d_steps,
+                                b->stream));
             b->stats.fs_launches += 1;
             b->stats.launches += 1;
         }
@@ -1253,12 +1257,13 @@ int rt_set_quadrature(rt_ctx* c, int ndir, const double* mu, const double* phi, 
     c->g.ndir = ndir;
     const size_t T = (size_t)ndir * c->g.nz;
     CK(dalloc(c->d_mu, ndir)); CK(dalloc(c->d_phi, ndir)); CK(dalloc(c->d_w, ndir));
-    CK(dalloc(c->info, ndir)); CK(dalloc(c->off, T)); CK(dalloc(c->bw, T)); CK(dalloc(c->bw32, T));
+    CK(dalloc(c->info, ndir)); CK(dalloc(c->off, T)); CK(dalloc(c->bw, T));
+    CK(dalloc(c->bwh, T)); CK(dalloc(c->bw32, T));
     CK(cudaMemcpyAsync(c->d_mu, mu, sizeof(double) * ndir, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_phi, phi, sizeof(double) * ndir, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_w, w, sizeof(double) * ndir, cudaMemcpyHostToDevice, c->stream));
     CK(launch_dir_tables(c->g, c->dx, c->dy, c->dz, c->d_mu, c->d_phi, c->d_w, c->info, c->off,
-                         c->bw, c->bw32, c->stream));
+                         c->bw, c->bwh, c->bw32, c->stream));
     c->stats.launches += 1;
     if (c->precision != RT_FP64) {
         CK(dalloc(c->poff, T));

@@ -37,11 +37,12 @@ __global__ void k_dir_tables(Geometry g, double dx, double dy, double dz,
                              const double* __restrict__ mu, const double* __restrict__ phi,
                              const double* __restrict__ w, DirInfo* __restrict__ info,
                              StepGeo* __restrict__ off, Bw4d* __restrict__ bw,
-                             float4* __restrict__ bw32)
+                             Bw4d* __restrict__ bwh, float4* __restrict__ bw32)
 {
     const int d = blockIdx.x;
     const double m_u = mu[d];
     const double amu = fabs(m_u);
+    const double hs = dz / (2.0 * amu);
     const double sint = sqrt(1.0 - m_u * m_u);
     const double ax = (dz / dx) * sint * cos(phi[d]) / amu;
     const double ay = (dz / dy) * sint * sin(phi[d]) / amu;
@@ -56,11 +57,12 @@ __global__ void k_dir_tables(Geometry g, double dx, double dy, double dz,
         off[e] = o;
         const Bw4d b = Bw4d{(1.0 - tx) * (1.0 - ty), tx * (1.0 - ty), (1.0 - tx) * ty, tx * ty};
         bw[e] = b;
+        bwh[e] = Bw4d{hs * b.x, hs * b.y, hs * b.z, hs * b.w};
         bw32[e] = make_float4((float)b.x, (float)b.y, (float)b.z, (float)b.w);
     }
     if (threadIdx.x == 0) {
         DirInfo di;
-        di.hs = dz / (2.0 * amu);
+        di.hs = hs;
         di.hs32 = (float)di.hs;
         di.amu = amu;
         di.amu32 = (float)amu;
@@ -124,8 +126,8 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
        const double* __restrict__ B, const double* __restrict__ G,
        const DirInfo* __restrict__ info,
        const StepGeo* __restrict__ off, const Bw4d* __restrict__ bw,
-       const double* __restrict__ smax_p, double cut, double* __restrict__ partial,
-       unsigned long long* __restrict__ steps)
+       const Bw4d* __restrict__ bwh, const double* __restrict__ smax_p, double cut,
+       double* __restrict__ partial, unsigned long long* __restrict__ steps)
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int t = blockIdx.x * kThreads + threadIdx.x;
@@ -148,7 +150,10 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                 const int M = s > 0 ? k0 : nz - 1 - k0;
                 const StepGeo* od = off + (long long)d * nz;
                 const Bw4d* bd = bw + (long long)d * nz;
-                double I = 0.0, T = 1.0, ca = chi0, sa = S0;
+                const Bw4d* bh = bwh + (long long)d * nz;
+                // ca, cb: chi times the half path length hs, so that a
+                // segment's optical depth is their sum
+                double I = 0.0, T = 1.0, ca = di.hs * chi0, sa = S0;
                 bool early = false;
                 int m = 0;
                 for (; m < M; ++m) {
@@ -156,11 +161,10 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                     const Nodes n = nodes_of(i0, j0, od[m + 1], nx, ny);
                     RT_GUARD(g, pb + nodes_min(n), g.N, kSiteFs64) { early = true; break; }
                     RT_GUARD(g, pb + nodes_max(n), g.N, kSiteFs64) { early = true; break; }
-                    const Bw4d b = bd[m + 1];
-                    const double cb = bilin(chi + pb, n, b);
-                    const double sb = bilin(S + pb, n, b);
+                    const double cb = bilin(chi + pb, n, bh[m + 1]);
+                    const double sb = bilin(S + pb, n, bd[m + 1]);
                     double wc, wu, e;
-                    seg_weights64(di.hs * (ca + cb), tab, wc, wu, e);
+                    seg_weights64(ca + cb, tab, wc, wu, e);
                     I = fma(T, fma(wc, sa, wu * sb), I);
                     T *= e;
                     ca = cb;
@@ -313,21 +317,22 @@ __global__ void k_seg_eval(long long n, int fp32, const double* __restrict__ x,
 
 cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz,
                               const double* mu, const double* phi, const double* w,
-                              DirInfo* info, StepGeo* off, Bw4d* bw, float4* bw32,
+                              DirInfo* info, StepGeo* off, Bw4d* bw, Bw4d* bwh, float4* bw32,
                               cudaStream_t st)
 {
-    k_dir_tables<<<g.ndir, 128, 0, st>>>(g, dx, dy, dz, mu, phi, w, info, off, bw, bw32);
+    k_dir_tables<<<g.ndir, 128, 0, st>>>(g, dx, dy, dz, mu, phi, w, info, off, bw, bwh, bw32);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, const double* B,
                         const double* G, const DirInfo* info, const StepGeo* off,
-                        const Bw4d* bw, const double* smax, double cut, int groups,
-                        double* partial, unsigned long long* steps, cudaStream_t st)
+                        const Bw4d* bw, const Bw4d* bwh, const double* smax, double cut,
+                        int groups, double* partial, unsigned long long* steps, cudaStream_t st)
 {
     const int nxy = g.nx * g.ny;
     dim3 grid((nxy + kThreads - 1) / kThreads, g.nz, groups);
-    k_fs64<<<grid, kThreads, 0, st>>>(g, chi, S, B, G, info, off, bw, smax, cut, partial, steps);
+    k_fs64<<<grid, kThreads, 0, st>>>(g, chi, S, B, G, info, off, bw, bwh, smax, cut, partial,
+                                      steps);
     return cudaGetLastError();
 }
 

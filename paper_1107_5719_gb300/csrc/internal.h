@@ -91,9 +91,12 @@ enum {
 cudaError_t launch_bounds_selftest(const Geometry& g, cudaStream_t st);
 
 // ---- launchers (fs.cu) -----------------------------------------------------
+// Per (direction d, step m) at index d * nz + m: off (lattice offset), bw
+// (bilinear weights), bwh (the weights times hs = dz / (2 |mu|), so that
+// interpolating chi with them gives hs chi) and bw32 (bw in FP32).
 cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz,
                               const double* mu, const double* phi, const double* w,
-                              DirInfo* info, StepGeo* off, Bw4d* bw, float4* bw32,
+                              DirInfo* info, StepGeo* off, Bw4d* bw, Bw4d* bwh, float4* bw32,
                               cudaStream_t st);
 
 // FP64 formal solution: partial[kSlots][N]; `groups` (1..kSlots) is the
@@ -102,8 +105,8 @@ cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz
 // read only when bottom_bc == 2 (may be null otherwise).
 cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, const double* B,
                         const double* G, const DirInfo* info, const StepGeo* off,
-                        const Bw4d* bw, const double* smax, double cut, int groups,
-                        double* partial, unsigned long long* steps, cudaStream_t st);
+                        const Bw4d* bw, const Bw4d* bwh, const double* smax, double cut,
+                        int groups, double* partial, unsigned long long* steps, cudaStream_t st);
 // G[j][i] = (B[nz-1] - B[nz-2]) / (dz (chi[nz-1] + chi[nz-2]) / 2), and its
 // padded FP32 copy g2[2ny][2nx] if g2 != null.
 cudaError_t launch_diffusion_grad(const Geometry& g, double dz, const double* chi,

@@ -45,7 +45,7 @@ cudaError_t scratch_address(int dev, unsigned char** out)
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t smax, mu, phi, w, info, off, bw, bw32, partial, total;
+    size_t smax, mu, phi, w, info, off, bw, bwh, bw32, partial, total;
 };
 
 Layout layout(long long N, int ndir, int nz)
@@ -59,6 +59,7 @@ Layout layout(long long N, int ndir, int nz)
     L.info = o;    o = align256(o + sizeof(DirInfo) * ndir);
     L.off = o;     o = align256(o + sizeof(StepGeo) * (size_t)ndir * nz);
     L.bw = o;      o = align256(o + sizeof(Bw4d) * (size_t)ndir * nz);
+    L.bwh = o;     o = align256(o + sizeof(Bw4d) * (size_t)ndir * nz);
     L.bw32 = o;    o = align256(o + sizeof(float4) * (size_t)ndir * nz);
     L.partial = o; o = align256(o + sizeof(double) * (size_t)kSlots * (size_t)N);
     L.total = o;
@@ -113,6 +114,7 @@ extern "C" int rt_formal_solution_noalloc(int nx, int ny, int nz, double dx, dou
     DirInfo* info = reinterpret_cast<DirInfo*>(base + L.info);
     StepGeo* off = reinterpret_cast<StepGeo*>(base + L.off);
     Bw4d* bw = reinterpret_cast<Bw4d*>(base + L.bw);
+    Bw4d* bwh = reinterpret_cast<Bw4d*>(base + L.bwh);
     float4* bw32 = reinterpret_cast<float4*>(base + L.bw32);
     double* partial = reinterpret_cast<double*>(base + L.partial);
 
@@ -126,11 +128,11 @@ extern "C" int rt_formal_solution_noalloc(int nx, int ny, int nz, double dx, dou
         cudaMemcpyAsync(d_phi, phi, sizeof(double) * ndir, cudaMemcpyHostToDevice, st) ||
         cudaMemcpyAsync(d_w, w, sizeof(double) * ndir, cudaMemcpyHostToDevice, st))
         return RT_ECUDA;
-    if (launch_dir_tables(g, dx, dy, dz, d_mu, d_phi, d_w, info, off, bw, bw32, st)) return RT_ECUDA;
+    if (launch_dir_tables(g, dx, dy, dz, d_mu, d_phi, d_w, info, off, bw, bwh, bw32, st)) return RT_ECUDA;
     // The cutoff bound is a max-reduction: it must start from zero on every call.
     if (cudaMemsetAsync(smax, 0, sizeof(double), st)) return RT_ECUDA;
     if (launch_absmax(N, S, planck ? B : nullptr, smax, nullptr, st)) return RT_ECUDA;
-    if (launch_fs64(g, chi, S, B, nullptr, info, off, bw, smax, 1e-17, G, partial, nullptr, st))
+    if (launch_fs64(g, chi, S, B, nullptr, info, off, bw, bwh, smax, 1e-17, G, partial, nullptr, st))
         return RT_ECUDA;
     if (launch_sum_groups(N, partial, J_fs, st)) return RT_ECUDA;
     return RT_OK;

@@ -21,9 +21,12 @@ namespace {
 // The FP64 pipe of GB300 issues about 2 DFMA per SM per clock, so the FP64
 // weights are written to use few FP64 instructions:
 //
-//  x < 1/4: the phi2 series (Horner in x^2, six terms each: the first
-//    omitted terms, z^6/14! and z^6/15! at z = x^2 <= 1/16, are below 7e-19
-//    and 5e-20); no exp call and no cancellation.
+//  x < 1/4: the phi2 series (Horner in z = x^2, six terms each: the first
+//    omitted terms, z^6/14! and z^6/15! at z <= 1/16, are below 7e-19 and
+//    5e-20); no exp call and no cancellation.  With E as above and
+//    O = x Q, w_cur = xE - zQ and w_up = e (xE + zQ): 17 FP64 operations.
+//  Both branch tests compare the high word of x (x >= 0) as an integer, so
+//    they take no FP64 compare.
 //  x >= 1/4: e from Tang's table-driven method (ACM TOMS 15, 1989):
 //    -x/ln2 = k/256 + r/ln2, k = round(-256 x/ln2), |r| <= ln2/512,
 //    e = 2^{k>>8} * 2^{(k&255)/256} * P(r), P the degree-4 Taylor polynomial
@@ -67,23 +70,28 @@ __device__ __forceinline__ double recip_newton(double x)
     return fma(r, e, r);
 }
 
+constexpr int kHiQuarter = 0x3FD00000;   // high word of 0.25
+constexpr int kHi700 = 0x4085E000;       // high word of 700.0
+
 __device__ __forceinline__ void seg_weights64(double x, const double* __restrict__ tab, double& wc,
                                               double& wu, double& e)
 {
-    if (x < 0.25) {
+    const int hx = __double2hiint(x);
+    if (hx < kHiQuarter) {
         const double z = x * x;
-        // E = sum_j z^j/(2j+2)!,  O' = sum_j z^j/(2j+3)!  (j = 0..5)
+        // E = sum_j z^j/(2j+2)!,  Q = sum_j z^j/(2j+3)!  (j = 0..5)
         double E = fma(fma(fma(fma(1.0 / 479001600.0, z, 1.0 / 3628800.0), z, 1.0 / 40320.0), z,
                            1.0 / 720.0), z, 1.0 / 24.0);
         E = fma(E, z, 0.5);
-        double O = fma(fma(fma(fma(1.0 / 6227020800.0, z, 1.0 / 39916800.0), z, 1.0 / 362880.0), z,
+        double Q = fma(fma(fma(fma(1.0 / 6227020800.0, z, 1.0 / 39916800.0), z, 1.0 / 362880.0), z,
                            1.0 / 5040.0), z, 1.0 / 120.0);
-        O = fma(O, z, 1.0 / 6.0) * x;
-        wc = x * (E - O);
+        Q = fma(Q, z, 1.0 / 6.0);
+        const double xE = x * E;
+        wc = fma(-z, Q, xE);
         e = fma(x, wc, 1.0 - x);
-        wu = (x * e) * (E + O);
+        wu = e * fma(z, Q, xE);
     } else {
-        e = x <= 700.0 ? exp_neg_tang(x, tab) : 0.0;
+        e = hx < kHi700 ? exp_neg_tang(x, tab) : 0.0;
         const double q = (1.0 - e) * recip_newton(x);
         wc = 1.0 - q;
         wu = q - e;
