@@ -415,6 +415,17 @@ int rt_batch_set_os_method(rt_batch *batch, int method);
 int rt_checked_build(void);
 int rt_bounds_selftest(rt_ctx *ctx);
 
+/* Scheduling of the march launches.  Their thread blocks are dispatched
+ * plane by plane, heaviest plane first, so that the light planes fill the
+ * end of a launch (the hardware hands out blocks in index order).  A
+ * plane's work is estimated, whenever the opacity is set, by marching the
+ * plane means of chi up and down to an optical depth of 40 or the boundary
+ * at |mu| = 1, 1/2 and 1/5.  The order changes no result: every voxel and
+ * direction slot is computed by the same thread code whatever the order.
+ * rt_get_plane_order copies it (nz ints, order[r] = plane of rank r) to
+ * host memory; RT_ESTATE before the opacity is set. */
+int rt_get_plane_order(rt_ctx *ctx, int *order);
+
 /* Counters of this context since the last rt_reset_stats: kernel launches,
  * formal-solution march launches and their device time, Jacobi sweeps and
  * their device time, march steps executed.  Device times are measured with

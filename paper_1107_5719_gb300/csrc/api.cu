@@ -56,6 +56,9 @@ struct rt_ctx {
     double *Jfs = nullptr, *Jn = nullptr, *Ja = nullptr, *Jb = nullptr, *r = nullptr;
     double *lstar = nullptr, *coef = nullptr, *rdiag = nullptr, *partial = nullptr;
     int partial_groups = 0;
+    // plane dispatch order of the marches (c->g.zorder points here once set)
+    int* zorder = nullptr;
+    double* zscratch = nullptr;
     // FP32-sweep form: padded {chi, S_hi, S_lo} nodes, padded boundary B pairs,
     // padded step offsets; sum of the quadrature weights
     float4* node4 = nullptr;
@@ -171,6 +174,8 @@ void free_grid_buffers(rt_ctx* c)
     dfree(c->lstar); dfree(c->coef); dfree(c->rdiag); dfree(c->partial);
     dfree(c->node4); dfree(c->b2); dfree(c->gdiff); dfree(c->g2); dfree(c->g2df);
     dfree(c->scpart); dfree(c->scplanes);
+    dfree(c->zorder); dfree(c->zscratch);
+    c->g.zorder = nullptr;
     c->scpart_n = c->scplanes_n = 0;
     free_ng(c);
     c->partial_groups = 0;
@@ -1212,6 +1217,7 @@ int rt_set_grid(rt_ctx* c, int nx, int ny, int nz, double dx, double dy, double 
     CK(dalloc(c->Jb, N)); CK(dalloc(c->r, Ns)); CK(dalloc(c->rdiag, Ns));
     CK(dalloc(c->lstar, 27 * N)); CK(dalloc(c->coef, 27 * Ns));
     CK(dalloc(c->gdiff, (size_t)nx * ny));
+    CK(dalloc(c->zorder, (size_t)nz)); CK(dalloc(c->zscratch, 2 * (size_t)nz));
     if (c->precision != RT_FP64) {
         CK(dalloc(c->node4, 4 * N));
         CK(dalloc(c->b2, (size_t)8 * nx * ny));
@@ -1290,6 +1296,11 @@ static int set_chi(rt_ctx* c, const double* chi, bool device)
 {
     int rc = set_field(c, chi, c ? c->chi : nullptr, device, "chi", true, false);
     if (rc) return rc;
+    // the planes' dispatch order follows the new opacities (stream-ordered
+    // before any march that reads it)
+    CK(launch_plane_order(c->g, c->dz, c->chi, c->zscratch, c->zorder, c->stream));
+    c->g.zorder = c->zorder;
+    c->stats.launches += 2;
     c->have_chi = true;
     c->lstar_valid = c->coef_valid = c->gdiff_valid = false;
     return RT_OK;
@@ -1708,6 +1719,18 @@ int rt_bounds_selftest(rt_ctx* c)
     CK(launch_bounds_selftest(c->g, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return check_bounds(c, RT_OK);
+}
+
+int rt_get_plane_order(rt_ctx* c, int* order)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if ((rc = need(c, c->have_chi, "the opacity"))) return rc;
+    if (!order) return fail(c, RT_EINVAL, "order is NULL");
+    CK(cudaMemcpyAsync(order, c->zorder, sizeof(int) * c->g.nz, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return RT_OK;
 }
 
 static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, int max_sweeps,

@@ -117,10 +117,11 @@ __device__ __forceinline__ void add_steps(unsigned long long* steps, unsigned lo
     if ((threadIdx.x & 31) == 0 && n) atomicAdd(steps, n);
 }
 
-// One thread per voxel of plane blockIdx.y.  Direction d belongs to slot
-// d mod kSlots; each slot is summed in increasing d and written to
-// partial[slot]; block z walks slots zb, zb + gridDim.z, ...  The slot sums
-// are then added in slot order, so J does not depend on gridDim.z.
+// One thread per voxel of plane plane_at(g, blockIdx.z).  Direction d
+// belongs to slot d mod kSlots; each slot is summed in increasing d and
+// written to partial[slot]; block y walks slots zb, zb + gridDim.y, ...
+// The slot sums are then added in slot order, so J depends neither on
+// gridDim.y nor on the plane dispatch order.
 __global__ void __launch_bounds__(kThreads)
 k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
        const double* __restrict__ B, const double* __restrict__ G,
@@ -131,7 +132,7 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int t = blockIdx.x * kThreads + threadIdx.x;
-    const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
+    const int k0 = plane_at(g, blockIdx.z), zb = blockIdx.y, ZB = gridDim.y;
     const bool active = t < nxy;
     __shared__ double tab[kExpTable];
     fill_exp_table(tab);
@@ -197,6 +198,52 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
         }
     }
     if (steps) add_steps(steps, nsteps);
+}
+
+// Mean of chi over each plane (block k: plane k), fixed summation order.
+__global__ void k_plane_mean(Geometry g, const double* __restrict__ chi, double* __restrict__ mean)
+{
+    __shared__ double red[256];
+    const int nxy = g.nx * g.ny;
+    const double* pk = chi + (long long)blockIdx.x * nxy;
+    double s = 0.0;
+    for (int t = threadIdx.x; t < nxy; t += 256) s += pk[t];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mean[blockIdx.x] = red[0] / nxy;
+}
+
+// Estimated march work of every plane (w[k]) and the planes by decreasing
+// work (order[rank] = plane).  One block.
+__global__ void k_plane_rank(int nz, double dz, const double* __restrict__ mean,
+                             double* __restrict__ w, int* __restrict__ order)
+{
+    constexpr double kTauEnd = 40.0;
+    const double amu[3] = {1.0, 0.5, 0.2};
+    for (int k0 = threadIdx.x; k0 < nz; k0 += blockDim.x) {
+        double work = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            const double hs = dz / (2.0 * amu[q]);
+            for (int s = -1; s <= 1; s += 2) {
+                double tau = 0.0;
+                int n = 1;   // per-characteristic overhead, about one step
+                for (int k = k0; k - s >= 0 && k - s < nz && tau <= kTauEnd; k -= s, ++n)
+                    tau += hs * (mean[k] + mean[k - s]);
+                work += n;
+            }
+        }
+        w[k0] = work;
+    }
+    __syncthreads();
+    for (int k0 = threadIdx.x; k0 < nz; k0 += blockDim.x) {
+        int rank = 0;
+        for (int j = 0; j < nz; ++j) rank += (w[j] > w[k0]) || (w[j] == w[k0] && j < k0);
+        order[rank] = k0;
+    }
 }
 
 __global__ void k_sum_groups(long long N, const double* __restrict__ partial,
@@ -324,13 +371,21 @@ cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz
     return cudaGetLastError();
 }
 
+cudaError_t launch_plane_order(const Geometry& g, double dz, const double* chi, double* scratch,
+                               int* order, cudaStream_t st)
+{
+    k_plane_mean<<<g.nz, 256, 0, st>>>(g, chi, scratch);
+    k_plane_rank<<<1, 256, 0, st>>>(g.nz, dz, scratch, scratch + g.nz, order);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, const double* B,
                         const double* G, const DirInfo* info, const StepGeo* off,
                         const Bw4d* bw, const Bw4d* bwh, const double* smax, double cut,
                         int groups, double* partial, unsigned long long* steps, cudaStream_t st)
 {
     const int nxy = g.nx * g.ny;
-    dim3 grid((nxy + kThreads - 1) / kThreads, g.nz, groups);
+    dim3 grid((nxy + kThreads - 1) / kThreads, groups, g.nz);
     k_fs64<<<grid, kThreads, 0, st>>>(g, chi, S, B, G, info, off, bw, bwh, smax, cut, partial,
                                       steps);
     return cudaGetLastError();

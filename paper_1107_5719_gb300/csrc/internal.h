@@ -56,7 +56,17 @@ struct Geometry {
     // Checked builds only: device record {hit, site, index, limit} of the
     // first gathered index found outside its buffer (null: no record).
     unsigned long long* berr;
+    // Dispatch order of the planes in the march launches: the blocks of
+    // rank r (the slowest grid index) work on plane zorder[r]; null means
+    // plane r.  A permutation of 0..nz-1 whenever it is set.
+    const int* zorder;
 };
+
+// Plane worked on by the blocks of dispatch rank r.
+__host__ __device__ __forceinline__ int plane_at(const Geometry& g, int r)
+{
+    return g.zorder ? g.zorder[r] : r;
+}
 
 // Checked builds (compiled with -DRT_CHECKED into librt3d_checked.so): the
 // gathers of the marches and of the operator-splitting stencils test each
@@ -98,6 +108,16 @@ cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz
                               const double* mu, const double* phi, const double* w,
                               DirInfo* info, StepGeo* off, Bw4d* bw, Bw4d* bwh, float4* bw32,
                               cudaStream_t st);
+
+// Plane dispatch order of the march launches, heaviest plane first: the
+// march work of each plane is estimated from the plane means of chi (steps
+// until an optical depth of 40 or the boundary, upward and downward, for
+// |mu| = 1, 1/2, 1/5), and order[r] is the plane of rank r (ties by plane
+// index).  scratch: 2 nz doubles.  Light planes dispatched last fill the end
+// of the launch, where otherwise a partial wave of heavy blocks would run
+// alone.
+cudaError_t launch_plane_order(const Geometry& g, double dz, const double* chi, double* scratch,
+                               int* order, cudaStream_t st);
 
 // FP64 formal solution: partial[kSlots][N]; `groups` (1..kSlots) is the
 // number of z-blocks walking the slots (a tuning knob, no effect on J).

@@ -141,7 +141,7 @@ k_fs64p(Geometry g, const double* __restrict__ chi, const double* __restrict__ S
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int t = blockIdx.x * kThreadsP + threadIdx.x;
-    const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
+    const int k0 = plane_at(g, blockIdx.z), zb = blockIdx.y, ZB = gridDim.y;
     const bool active = t < nxy;
     __shared__ double tab[kExpTable];
     fill_exp_table(tab);
@@ -341,7 +341,7 @@ cudaError_t launch_fs64p(const Geometry& g, const double* chi, const double* S, 
                          int groups, double* partial, unsigned long long* steps, cudaStream_t st)
 {
     const int nxy = g.nx * g.ny;
-    dim3 grid((nxy + kThreadsP - 1) / kThreadsP, g.nz, groups);
+    dim3 grid((nxy + kThreadsP - 1) / kThreadsP, groups, g.nz);
     k_fs64p<<<grid, kThreadsP, 0, st>>>(g, chi, S, B, G, info, off, bw, dn, smax, cut, partial,
                                         steps);
     return cudaGetLastError();

@@ -101,6 +101,7 @@ _SIGS = {
     "rt_batch_set_df_finish": (C.c_int, [VP, C.c_double]),
     "rt_checked_build": (C.c_int, []),
     "rt_bounds_selftest": (C.c_int, [VP]),
+    "rt_get_plane_order": (C.c_int, [VP, VP]),
     "rt_batch_set_precision": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_os_method": (C.c_int, [VP, C.c_int]),
     "rt_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
@@ -351,6 +352,13 @@ def rt_checked_build() -> bool:
 def rt_bounds_selftest(ctx):
     """Raw status: RT_EBOUNDS from the checked build, RT_OK otherwise."""
     return load().rt_bounds_selftest(ctx)
+
+
+def rt_get_plane_order(ctx, nz):
+    """Dispatch order of the planes in the march launches (order[r] = plane)."""
+    out = np.empty(nz, dtype=np.int32)
+    _check(ctx, load().rt_get_plane_order(ctx, out.ctypes.data))
+    return out
 
 
 def rt_batch_set_precision(b, precision):
