@@ -49,8 +49,9 @@ FLOPS_PER_STEP_FP32 = 45
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
 PEAK_FP32_TFLOPS = 80.5
 # DRAM bytes (read + write) per k_fs64 launch on slab65, from one ncu
-# capture of the current kernel (None until one is taken).
-TRAFFIC_FS64_SLAB65 = None
+# capture of the current kernel: chi, S, B and the direction tables stay
+# L2-resident, so the march reads 7.8 MB per launch from DRAM and writes none.
+TRAFFIC_FS64_SLAB65 = 7805184
 # The double-float march executes 398 thread instructions per step (ncu,
 # slab65); its bound is instruction issue: 152 SMs x 4 schedulers x 32 lanes
 # x 2.07 GHz = 40.3e12 thread instructions/s.

@@ -212,12 +212,12 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
 __global__ void __launch_bounds__(kThreads32)
 k_fs32d(View32 p, float cut, unsigned long long* __restrict__ steps)
 {
-    march32(p, blockIdx.x, plane_at(p.g, blockIdx.z), blockIdx.y, gridDim.y, cut, steps);
+    march32(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, cut, steps);
 }
 
 // Many problems in one launch: block b belongs to the active problem q with
 // prefix[q] <= b < prefix[q+1]; within it, blocks run tile-fastest, then
-// slot group, then plane in the problem's dispatch order.
+// plane, then slot group.
 __global__ void __launch_bounds__(kThreads32)
 k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
              const long long* __restrict__ prefix, int nact, int ZB, float cut,
@@ -234,8 +234,8 @@ k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
     const long long local = b - prefix[lo];
     const int tiles = (p.g.nx * p.g.ny + kThreads32 - 1) / kThreads32;
     const int tile = (int)(local % tiles);
-    const int zb = (int)((local / tiles) % ZB);
-    const int k0 = plane_at(p.g, (int)(local / ((long long)tiles * ZB)));
+    const int k0 = (int)((local / tiles) % p.g.nz);
+    const int zb = (int)(local / ((long long)tiles * p.g.nz));
     march32(p, tile, k0, zb, ZB, cut, steps);
 }
 
@@ -285,7 +285,9 @@ cudaError_t launch_fs32d(const View32& p, double cut, int groups, unsigned long 
                          cudaStream_t st)
 {
     const int nxy = p.g.nx * p.g.ny;
-    dim3 grid((nxy + kThreads32 - 1) / kThreads32, groups, p.g.nz);
+    // planes in index order (g.zorder unused): with the plane read from the
+    // order table the march ran at 14.6 instead of 10.7 ms on the 65^3 slab
+    dim3 grid((nxy + kThreads32 - 1) / kThreads32, p.g.nz, groups);
     k_fs32d<<<grid, kThreads32, 0, st>>>(p, (float)cut, steps);
     return cudaGetLastError();
 }

@@ -143,7 +143,7 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
     const Geometry& g = p.g;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int t = blockIdx.x * kThreadsDF + threadIdx.x;
-    const int k0 = plane_at(g, blockIdx.z), zb = blockIdx.y, ZB = gridDim.y;
+    const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
     const bool active = t < nxy;
     unsigned long long nsteps = 0;
     if (active) {
@@ -537,7 +537,9 @@ cudaError_t launch_fsdf(const ViewDF& p, double cut, int groups, unsigned long l
                         cudaStream_t st)
 {
     const int nxy = p.g.nx * p.g.ny;
-    dim3 grid((nxy + kThreadsDF - 1) / kThreadsDF, groups, p.g.nz);
+    // planes in index order (g.zorder unused): 40.9 ms against 41.05 ms
+    // with the order table on the 65^3 slab
+    dim3 grid((nxy + kThreadsDF - 1) / kThreadsDF, p.g.nz, groups);
     k_fsdf<<<grid, kThreadsDF, 0, st>>>(p, (float)cut, steps);
     return cudaGetLastError();
 }

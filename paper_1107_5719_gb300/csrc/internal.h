@@ -56,9 +56,9 @@ struct Geometry {
     // Checked builds only: device record {hit, site, index, limit} of the
     // first gathered index found outside its buffer (null: no record).
     unsigned long long* berr;
-    // Dispatch order of the planes in the march launches: the blocks of
-    // rank r (the slowest grid index) work on plane zorder[r]; null means
-    // plane r.  A permutation of 0..nz-1 whenever it is set.
+    // Dispatch order of the planes in the FP64 march launches: the blocks
+    // of plane rank r work on plane zorder[r]; null means plane r.  A
+    // permutation of 0..nz-1 whenever it is set.
     const int* zorder;
 };
 
@@ -109,7 +109,7 @@ cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz
                               DirInfo* info, StepGeo* off, Bw4d* bw, Bw4d* bwh, float4* bw32,
                               cudaStream_t st);
 
-// Plane dispatch order of the march launches, heaviest plane first: the
+// Plane dispatch order of the FP64 march launches, heaviest plane first: the
 // march work of each plane is estimated from the plane means of chi (steps
 // until an optical depth of 40 or the boundary, upward and downward, for
 // |mu| = 1, 1/2, 1/5), and order[r] is the plane of rank r (ties by plane

@@ -1,4 +1,4 @@
-"""Plane dispatch order of the march launches: it is the permutation the
+"""Plane dispatch order of the FP64 march launches: it is the permutation the
 work estimate defines (plane means of chi marched to an optical depth of 40
 at |mu| = 1, 1/2, 1/5), it follows the opacity, and it changes no result."""
 
