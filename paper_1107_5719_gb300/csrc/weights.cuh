@@ -25,14 +25,14 @@ namespace {
 //    omitted terms, z^6/14! and z^6/15! at z <= 1/16, are below 7e-19 and
 //    5e-20); no exp call and no cancellation.  With E as above and
 //    O = x Q, w_cur = xE - zQ and w_up = e (xE + zQ): 17 FP64 operations.
-//  Both branch tests compare the high word of x (x >= 0) as an integer, so
-//    they take no FP64 compare.
 //  x >= 1/4: e from Tang's table-driven method (ACM TOMS 15, 1989):
 //    -x/ln2 = k/256 + r/ln2, k = round(-256 x/ln2), |r| <= ln2/512,
 //    e = 2^{k>>8} * 2^{(k&255)/256} * P(r), P the degree-4 Taylor polynomial
 //    of e^r (relative error < 4e-17), the 256 powers 2^{j/256} in shared
 //    memory; then (1-e)/x from a reciprocal seed and two Newton steps.
 //    Above x = 700 e is taken as 0 (it would scale I by < 1e-304).
+//  Both branch tests compare the high word of x (x >= 0) as an integer, so
+//    they take no FP64 compare.
 
 constexpr int kExpTable = 256;
 
