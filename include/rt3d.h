@@ -114,8 +114,10 @@ const char *rt_last_error(const rt_ctx *ctx);
 int rt_set_stream(rt_ctx *ctx, void *stream);
 
 /* Grid of nx x ny x nz voxels with spacings dx, dy, dz (> 0).  nx, ny >= 3
- * (a smaller periodic grid would alias the 27-point neighbourhood), nz >= 2.
- * Invalidates every field set before. */
+ * (a smaller periodic grid would alias the 27-point neighbourhood),
+ * 2 <= nz <= 65535 (the march launches give the planes a grid dimension of
+ * at most 65535 blocks), nx * ny <= 2^30.  Invalidates every field set
+ * before. */
 int rt_set_grid(rt_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz);
 
 /* Incoming intensity at the top (entered by mu > 0) and bottom (mu < 0):
@@ -318,7 +320,7 @@ int rt_segment_weights(int precision, long long n, const double *x, double *w_cu
  * library owns.  Every GPU that loads the library holds that array until
  * the process exits.
  *
- * Arguments: grid (nx, ny >= 3, nz >= 2, spacings > 0), boundary modes,
+ * Arguments: grid (nx, ny >= 3, 2 <= nz <= 65535, spacings > 0), boundary modes,
  * ndir and HOST arrays mu, phi, w of the quadrature (same rules as
  * rt_set_quadrature); DEVICE pointers chi[N] (> 0), S[N], B[N] (only read
  * where a boundary mode is RT_BC_PLANCK; may be NULL otherwise) and the
@@ -327,7 +329,7 @@ int rt_segment_weights(int precision, long long n, const double *x, double *w_cu
  * thread's current device and is enqueued on `stream`; the call returns
  * without waiting for it (only the small quadrature copy from host memory
  * is synchronous).  Returns RT_ESCRATCH, before touching the GPU, when
- * 64*N + 56*ndir*nz + 72*ndir bytes (plus up to 2 KiB of alignment) exceed
+ * 64*N + 88*ndir*nz + 72*ndir bytes (plus up to 2 KiB of alignment) exceed
  * the scratch; RT_EINVAL for invalid arguments (device data is not
  * inspected); RT_ECUDA if a CUDA call fails.
  *

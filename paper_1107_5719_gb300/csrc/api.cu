@@ -1191,8 +1191,9 @@ int rt_set_grid(rt_ctx* c, int nx, int ny, int nz, double dx, double dy, double 
 {
     int rc = enter(c);
     if (rc) return rc;
-    if (nx < 3 || ny < 3 || nz < 2)
-        return fail(c, RT_EINVAL, "grid %dx%dx%d: need nx, ny >= 3 and nz >= 2", nx, ny, nz);
+    if (nx < 3 || ny < 3 || nz < 2 || nz > 65535)
+        return fail(c, RT_EINVAL, "grid %dx%dx%d: need nx, ny >= 3 and 2 <= nz <= 65535", nx, ny,
+                    nz);
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) ||
         !std::isfinite(dz))
         return fail(c, RT_EINVAL, "spacings must be finite and > 0");

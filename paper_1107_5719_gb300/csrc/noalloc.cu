@@ -75,7 +75,7 @@ extern "C" int rt_formal_solution_noalloc(int nx, int ny, int nz, double dx, dou
                                           double* J_fs, void* stream)
 {
     // Host-side checks first: nothing below touches the GPU if they fail.
-    if (nx < 3 || ny < 3 || nz < 2 || ndir < 1) return RT_EINVAL;
+    if (nx < 3 || ny < 3 || nz < 2 || nz > 65535 || ndir < 1) return RT_EINVAL;
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) ||
         !std::isfinite(dz))
         return RT_EINVAL;

@@ -79,3 +79,16 @@ def test_no_gpu_fails_loudly(lib):
 def test_version_string(lib):
     from paper_1107_5719_gb300 import rt3d as R
     assert "rt3d" in R.rt_version()
+
+
+def test_noalloc_rejects_bad_grids_before_touching_the_gpu(lib):
+    """The allocation-free call checks its grid on the host first: these
+    return RT_EINVAL without a CUDA call (the device pointers are never
+    dereferenced), so they run without a GPU."""
+    from paper_1107_5719_gb300 import rt3d as R, workloads as W
+    mu, phi, w = W.quadrature(2, 2)
+    fake = 1 << 20   # a device address that is never used
+    for shape in [(2, 5, 5), (5, 5, 1), (5, 5, 65536)]:
+        rc = R.rt_formal_solution_noalloc(*shape, 1.0, 1.0, 1.0, R.RT_BC_ZERO, R.RT_BC_PLANCK,
+                                          mu, phi, w, fake, fake, fake, fake)
+        assert rc == R.RT_EINVAL, shape

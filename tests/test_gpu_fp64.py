@@ -259,9 +259,10 @@ def test_invalid_inputs_rejected(R, bad):
     ctx = R.rt_create(0, R.RT_FP64)
     try:
         if bad == "grid":
-            with pytest.raises(R.RtError) as e:
-                R.rt_set_grid(ctx, 2, 5, 5)
-            assert e.value.code == R.RT_EINVAL
+            for shape in [(2, 5, 5), (5, 5, 1), (5, 5, 65536)]:
+                with pytest.raises(R.RtError) as e:
+                    R.rt_set_grid(ctx, *shape)
+                assert e.value.code == R.RT_EINVAL
             return
         R.rt_set_grid(ctx, p.nx, p.ny, p.nz)
         chi, eps, mu, w = p.chi.copy(), p.eps.copy(), p.mu.copy(), p.w.copy()
