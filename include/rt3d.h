@@ -248,10 +248,15 @@ int rt_set_graphs(rt_ctx *ctx, int on);
  * returns (converged or not) the context is back in the FP32 sweep with its
  * Ng threshold.  The FP32 sweep's iterate stops improving near delta 1e-8
  * and its Ng must stop near 1e-6; at small eps the remaining iterations
- * converge slowly, which the double-float stage with Ng avoids.  0 (default)
- * = off.  The batch version applies it per problem: problems still in the
- * FP32 sweep share the fused launch, those in their finishing stage run one
- * launch each. */
+ * converge slowly, which the double-float stage with Ng avoids: where the
+ * error of a solve stopped at delta is ~ delta / (1 - rho) for a contraction
+ * rho close to 1 (about 70 delta at eps = 1e-6), a 1e-6 accuracy target
+ * needs tol ~ 1e-8, below the FP32 sweep's floor.  Default for
+ * RT_FP32_SWEEP contexts (and batches): on, delta_switch = 1e-6;
+ * delta_switch = 0 turns it off (the FP32 sweep alone, tol >= 5e-8).  The
+ * batch version applies it per problem: problems still in the FP32 sweep
+ * share the fused launch, those in their finishing stage run one launch
+ * each. */
 int rt_set_df_finish(rt_ctx *ctx, double delta_switch);
 
 /* Source interpolation on each segment of a characteristic (the paper
@@ -398,6 +403,15 @@ int rt_batch_get_J(rt_batch *batch, int p, double *J);
 int rt_batch_get_J_dev(rt_batch *batch, int p, double *J);
 /* As rt_set_direction_groups, for the fused launch (0 = auto). */
 int rt_batch_set_direction_groups(rt_batch *batch, int groups);
+/* on != 0 (the default): every outer iteration runs the operator-splitting
+ * solves of all active problems (Sect. 2.3) as ONE CUDA graph, one
+ * independent branch per problem (right-hand side, a device-side loop of
+ * sweeps to tol_inner or max_sweeps, the pick of the last sweep's iterate),
+ * so the host launches once and waits once per iteration (plus once when Ng
+ * extrapolates); the graph is rebuilt when the set of active problems
+ * changes.  on == 0: the sweeps are enqueued from the host in growing chunks
+ * with one wait per chunk.  Results are identical. */
+int rt_batch_set_graphs(rt_batch *batch, int on);
 /* As rt_set_ng, for every problem of the batch. */
 int rt_batch_set_ng(rt_batch *batch, int period, double min_delta);
 /* As rt_set_os_method, for every problem of the batch. */
@@ -445,6 +459,8 @@ typedef struct {
     double jacobi_ms;                   /* their summed device time (profiling on) */
     unsigned long long steps;           /* march steps executed */
     unsigned long long lstar_launches;  /* Lambda* builds */
+    unsigned long long iterations;      /* outer iterations of rt_solve / rt_batch_solve */
+    unsigned long long host_syncs;      /* host waits for the stream inside those solves */
 } rt_stats;
 
 int rt_set_profiling(rt_ctx *ctx, int on);

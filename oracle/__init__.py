@@ -8,6 +8,8 @@ baseline leg of the benchmark may import it; the GPU library never does.
 Sections of Hauschildt & Baron (2011) that each function follows:
   formal_solution     Sect. 2.2 (formal solution, J and Lambda*; long or
                       short characteristics)
+  mean_intensity_at,  Sect. 2.2 (J, Lambda* at sampled voxels only)
+  lstar_at
   intensity           Sect. 2.2 (intensity along one characteristic)
   os_step             Sect. 2.3 (operator splitting, Jordan iterations or
                       red-black Gauss-Seidel)
@@ -68,6 +70,8 @@ def _configure(lib):
     lib.orc_formal_solution.argtypes = [G, P, P, P, C.c_int, P, P, P, P, P, C.c_int]
     lib.orc_mean_intensity_at.argtypes = [G, P, P, P, C.c_int, P, P, P, C.c_long,
                                           C.POINTER(C.c_long), P, C.c_int]
+    lib.orc_lstar_at.argtypes = [G, P, C.c_int, P, P, P, C.c_long, C.POINTER(C.c_long), P,
+                                 C.c_int]
     lib.orc_os_step.argtypes = [G, P, P, P, P, P, C.c_double, C.c_int,
                                 C.POINTER(C.c_int)]
     lib.orc_solve.argtypes = [G, P, P, P, C.c_int, P, P, P, C.c_double, C.c_int,
@@ -166,6 +170,25 @@ def mean_intensity_at(p, S, voxels, nthreads: int = 0):
                                    out.ctypes.data_as(C.POINTER(C.c_double)), nthreads)
     if rc:
         raise ValueError(f"oracle mean_intensity_at rejected its input ({rc})")
+    return out
+
+
+def lstar_at(p, voxels, nthreads: int = 0):
+    """Lambda* rows [len(voxels)][27] at the given flat voxel indices only
+    (the same contributions as formal_solution's Lambda*)."""
+    lib = _load()
+    g = _grid(p)
+    chi, pc = _d(p.chi)
+    mu, pm = _d(p.mu)
+    phi, pp = _d(p.phi)
+    w, pw = _d(p.w)
+    vox = np.ascontiguousarray(voxels, dtype=np.int64)
+    out = np.empty((vox.shape[0], 27))
+    rc = lib.orc_lstar_at(C.byref(g), pc, len(mu), pm, pp, pw, vox.shape[0],
+                          vox.ctypes.data_as(C.POINTER(C.c_long)),
+                          out.ctypes.data_as(C.POINTER(C.c_double)), nthreads)
+    if rc:
+        raise ValueError(f"oracle lstar_at rejected its input ({rc})")
     return out
 
 

@@ -673,6 +673,37 @@ int orc_mean_intensity_at(const orc_grid *g, const double *chi, const double *S,
     return ORC_OK;
 }
 
+/* Lambda* rows [27] of a sample of voxels only (full-size spot checks):
+ * the same per-characteristic contributions (lstar_one) as
+ * orc_formal_solution, for the listed flat voxel indices; lstar_out is
+ * [nsample][27], rows of indices outside the grid are NaN. */
+int orc_lstar_at(const orc_grid *g, const double *chi, int ndir, const double *mu,
+                 const double *phi, const double *w, long nsample, const long *voxels,
+                 double *lstar_out, int nthreads)
+{
+    if (check_grid(g) || check_dirs(ndir, mu)) return ORC_EINVAL;
+    long N = (long)g->nx * g->ny * g->nz;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long q = 0; q < nsample; ++q) {
+        long v = voxels[q];
+        double *row = lstar_out + q * 27;
+        if (v < 0 || v >= N) {
+            for (int o = 0; o < 27; ++o) row[o] = NAN;
+            continue;
+        }
+        long i0 = v % g->nx, j0 = (v / g->nx) % g->ny, k0 = v / ((long)g->nx * g->ny);
+        for (int o = 0; o < 27; ++o) row[o] = 0.0;
+        for (int d = 0; d < ndir; ++d)
+            lstar_one(g, chi, mu[d], phi[d], w[d], i0, j0, k0, row);
+    }
+    return ORC_OK;
+}
+
 /* Index of the neighbour of voxel v at offset o, or -1 outside the grid. */
 static long neighbour_index(const orc_grid *g, long v, int o)
 {

@@ -59,8 +59,13 @@ struct rt_ctx {
     // plane dispatch order of the marches (c->g.zorder points here once set)
     int* zorder = nullptr;
     double* zscratch = nullptr;
-    // FP32-sweep form: padded {chi, S_hi, S_lo} nodes, padded boundary B pairs,
-    // padded step offsets; sum of the quadrature weights
+    // FP32-sweep form: padded pair records {chi, S_hi} x 2 and their S_lo,
+    // step offsets in those planes (poff32); double-float march: padded
+    // {chi_hi, chi_lo, S_hi, S_lo} nodes and their step offsets (poff); both:
+    // padded boundary B pairs; sum of the quadrature weights
+    float4* pair = nullptr;
+    float2* plo = nullptr;
+    int* poff32 = nullptr;
     float4* node4 = nullptr;
     float2* b2 = nullptr;
     // LTE-diffusion inner boundary: dB/dtau of the bottom nodes (FP64, padded FP32)
@@ -172,7 +177,8 @@ void free_grid_buffers(rt_ctx* c)
     dfree(c->chi); dfree(c->eps); dfree(c->B); dfree(c->J); dfree(c->S);
     dfree(c->Jfs); dfree(c->Jn); dfree(c->Ja); dfree(c->Jb); dfree(c->r);
     dfree(c->lstar); dfree(c->coef); dfree(c->rdiag); dfree(c->partial);
-    dfree(c->node4); dfree(c->b2); dfree(c->gdiff); dfree(c->g2); dfree(c->g2df);
+    dfree(c->node4); dfree(c->pair); dfree(c->plo);
+    dfree(c->b2); dfree(c->gdiff); dfree(c->g2); dfree(c->g2df);
     dfree(c->scpart); dfree(c->scplanes);
     dfree(c->zorder); dfree(c->zscratch);
     c->g.zorder = nullptr;
@@ -184,7 +190,7 @@ void free_grid_buffers(rt_ctx* c)
 void free_tables(rt_ctx* c)
 {
     dfree(c->info); dfree(c->off); dfree(c->bw); dfree(c->bwh); dfree(c->bw32);
-    dfree(c->poff); dfree(c->bwdf);
+    dfree(c->poff); dfree(c->poff32); dfree(c->bwdf);
     dfree(c->dn);
     dfree(c->d_mu); dfree(c->d_phi); dfree(c->d_w);
 }
@@ -209,6 +215,10 @@ int enter(rt_ctx* c)
     if (e != cudaSuccess) return fail(c, RT_ECUDA, "cudaSetDevice(%d): %s", c->device, cudaGetErrorString(e));
     return RT_OK;
 }
+
+// Default delta below which an RT_FP32_SWEEP solve continues in double-float
+// (rt_set_df_finish): where the FP32 sweep's Ng extrapolation has to stop.
+constexpr double kDefaultDfSwitch = 1e-6;
 
 double default_cut(int precision)
 {
@@ -259,6 +269,28 @@ int ensure_partial(rt_ctx* c)
     return RT_OK;
 }
 
+// Buffers the march of `precision` needs beyond the ones every form has:
+// the FP32 pair planes, or the double-float nodes, gradient and weights
+// (allocated once, also when a live context switches form).
+int form_buffers(rt_ctx* c, int precision)
+{
+    if (c->have_grid && precision == RT_FP32_SWEEP && !c->pair) {
+        CK(dalloc(c->pair, (size_t)pair_records(c->g)));
+        CK(dalloc(c->plo, (size_t)pair_records(c->g)));
+    }
+    if (c->have_grid && precision == RT_DF64) {
+        if (!c->node4) CK(dalloc(c->node4, (size_t)(4 * c->g.N)));
+        if (!c->g2df) CK(dalloc(c->g2df, (size_t)4 * c->g.nx * c->g.ny));
+    }
+    if (c->have_quad && precision == RT_DF64 && !c->bwdf) {
+        const long long T = (long long)c->g.ndir * c->g.nz;
+        CK(dalloc(c->bwdf, (size_t)(2 * T)));
+        CK(launch_bw_df(T, c->bw, c->bwdf, c->stream));
+        c->stats.launches += 1;
+    }
+    return RT_OK;
+}
+
 int check_field(rt_ctx* c, const double* h, const char* what, bool positive, bool eps_range)
 {
     for (long long v = 0; v < c->g.N; ++v) {
@@ -306,12 +338,13 @@ View32 view32(rt_ctx* c)
 {
     View32 v;
     v.g = c->g;
-    v.node = c->node4;
+    v.pair = c->pair;
+    v.lo = c->plo;
     v.b2 = c->b2;
     v.g2 = c->g2;
     v.info = c->info;
     v.off = c->off;
-    v.poff = c->poff;
+    v.poff = c->poff32;
     v.bw = c->bw32;
     v.smax = c->scal + 0;
     v.partial = c->partial;
@@ -472,7 +505,7 @@ int prepare_source(rt_ctx* c, const double* S_in, bool device)
     }
     c->stats.launches += 1;
     if (c->precision == RT_FP32_SWEEP) {
-        CK(launch_pack32(c->g, c->chi, c->S, c->node4, c->stream));
+        CK(launch_pack_pairs(c->g, c->chi, c->S, c->pair, c->plo, c->stream));
         c->stats.launches += 1;
     } else if (c->precision == RT_DF64) {
         CK(launch_packdf(c->g, c->chi, c->S, c->node4, c->stream));
@@ -648,6 +681,7 @@ int run_os_graph(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew,
     CK(cudaMemcpyAsync(c->h_dlt, c->dlt, sizeof(double) * max_sweeps, cudaMemcpyDeviceToHost,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    c->stats.host_syncs += 1;
     harvest(c);
     int sweeps = max_sweeps;
     for (int n = 0; n < max_sweeps; ++n)
@@ -701,6 +735,7 @@ int run_os(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, doubl
         CK(cudaMemcpyAsync(c->h_dlt + n0, c->dlt + n0, sizeof(double) * (n1 - n0),
                            cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        c->stats.host_syncs += 1;
         harvest(c);
         for (int n = n0; n < n1; ++n)
             if (c->h_dlt[n] < tol_inner) {
@@ -806,16 +841,8 @@ int switch_precision(rt_ctx* c, int precision)
     if (!ok) return fail(c, RT_EINVAL, "precision switches only between RT_FP32_SWEEP and RT_DF64");
     if (precision == RT_FP32_SWEEP && c->fs_method == RT_FS_SHORT)
         return fail(c, RT_EINVAL, "short characteristics have no FP32-sweep form");
-    if (precision == RT_DF64) {
-        // buffers the double-float march needs beyond the FP32 sweep's
-        if (c->have_grid && !c->g2df) CK(dalloc(c->g2df, (size_t)4 * c->g.nx * c->g.ny));
-        if (c->have_quad && !c->bwdf) {
-            const long long T = (long long)c->g.ndir * c->g.nz;
-            CK(dalloc(c->bwdf, (size_t)(2 * T)));
-            CK(launch_bw_df(T, c->bw, c->bwdf, c->stream));
-            c->stats.launches += 1;
-        }
-    }
+    int rc = form_buffers(c, precision);
+    if (rc) return rc;
     c->precision = precision;
     c->gdiff_valid = false;    // the gradient's packed copy differs between the forms
     c->lstar_valid = c->coef_valid = false;   // Lambda* is rebuilt by the new form's kernel
@@ -859,6 +886,7 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
         if ((rc = ng_push(c, it + 1, &ng_pending))) return rc;
         if (ng_pending) {
             CK(cudaStreamSynchronize(c->stream));
+            c->stats.host_syncs += 1;
             if ((rc = ng_finish(c))) return rc;
         }
         CK(cudaMemsetAsync(c->scal + 2, 0, sizeof(double), c->stream));
@@ -867,6 +895,8 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
         CK(cudaMemcpyAsync(c->h_scal + 2, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost,
                            c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        c->stats.host_syncs += 1;
+        c->stats.iterations += 1;
         harvest(c);
         total_steps += *c->h_steps;
         delta = c->h_scal[2];
@@ -929,6 +959,21 @@ struct rt_batch {
     int groups_req = 0;
     bool profiling = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool jac_pending = false;
+    // The operator-splitting step of all active problems as one CUDA graph:
+    // per problem an independent branch (right-hand side, a device-side
+    // WHILE loop of sweeps, the pick of the last sweep's buffer).  Keyed by
+    // the active set and the buffers it touches; two cached instances,
+    // because J and J_new alternate between two buffers.
+    struct OsGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<const void*> key;
+    } osg[2];
+    int osg_next = 0;
+    bool use_graphs = true;
+    int* d_sweeps = nullptr;        // sweeps of each problem's last OS step
+    int* h_sweeps = nullptr;        // pinned
     rt_stats stats{};
     std::string err;
 };
@@ -978,6 +1023,116 @@ void bharvest(rt_batch* b)
     float ms = 0.f;
     if (b->profiling && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess)
         b->stats.fs_ms += ms;
+    if (b->jac_pending && cudaEventElapsedTime(&ms, b->ev[2], b->ev[3]) == cudaSuccess)
+        b->stats.jacobi_ms += ms;
+    b->jac_pending = false;
+}
+
+void free_batch_graphs(rt_batch* b)
+{
+    for (auto& e : b->osg) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (e.graph) cudaGraphDestroy(e.graph);
+        e = rt_batch::OsGraph{};
+    }
+}
+
+std::vector<const void*> batch_graph_key(const rt_batch* b, const std::vector<int>& act,
+                                         double tol, int max_sweeps)
+{
+    std::vector<const void*> k;
+    k.push_back(reinterpret_cast<const void*>((intptr_t)max_sweeps));
+    long long tb;
+    std::memcpy(&tb, &tol, sizeof tb);
+    k.push_back(reinterpret_cast<const void*>((intptr_t)tb));
+    for (int p : act) {
+        const rt_ctx* c = b->ctx[p];
+        k.push_back(reinterpret_cast<const void*>((intptr_t)p));
+        k.push_back(reinterpret_cast<const void*>((intptr_t)c->os_method));
+        for (const void* q : {(const void*)c->J, (const void*)c->Jn, (const void*)c->Jfs,
+                              (const void*)c->coef, (const void*)c->rdiag, (const void*)c->r,
+                              (const void*)c->Ja, (const void*)c->Jb, (const void*)c->dlt,
+                              (const void*)c->d_nsw})
+            k.push_back(q);
+    }
+    return k;
+}
+
+// Capture the per-problem branches of the batch operator-splitting graph.
+// Every capture that begins is ended, also after an error.
+cudaError_t build_batch_os_graph(rt_batch* b, const std::vector<int>& act, double tol,
+                                 int max_sweeps, cudaGraph_t* out)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t err = cudaGraphCreate(&g, 0);
+    if (err != cudaSuccess) return err;
+    const cudaStream_t st = b->stream;
+    for (int p : act) {
+        rt_ctx* c = b->ctx[p];
+        const bool gs = c->os_method == RT_OS_GAUSS_SEIDEL;
+        cudaGraphConditionalHandle h;
+        err = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+        if (err != cudaSuccess) break;
+        // prologue, a branch of its own (no dependencies)
+        err = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+        if (err != cudaSuccess) break;
+        std::vector<cudaGraphNode_t> deps;
+        {
+            cudaError_t e1 = launch_os_rhs(c->g, c->coef, c->rdiag, c->Jfs, c->J, c->r, gs, st);
+            cudaError_t e2 = cudaMemsetAsync(c->dlt, 0, sizeof(double) * (max_sweeps + 2), st);
+            cudaError_t e3 = cudaMemcpyAsync(c->Jb, c->J, sizeof(double) * c->g.N,
+                                             cudaMemcpyDeviceToDevice, st);
+            cudaError_t e4 = cudaMemsetAsync(c->d_nsw, 0, sizeof(int), st);
+            cudaStreamCaptureStatus cs;
+            const cudaGraphNode_t* dp = nullptr;
+            size_t nd = 0;
+            cudaError_t e5 = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &dp, nullptr, &nd);
+            if (e5 == cudaSuccess) deps.assign(dp, dp + nd);
+            cudaGraph_t o = nullptr;
+            cudaError_t e6 = cudaStreamEndCapture(st, &o);
+            for (cudaError_t x : {e1, e2, e3, e4, e5, e6})
+                if (err == cudaSuccess && x != cudaSuccess) err = x;
+        }
+        if (err != cudaSuccess) break;
+        // the sweep loop
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        err = cudaGraphAddNode(&cn, g, deps.data(), nullptr, deps.size(), &cp);
+        if (err != cudaSuccess) break;
+        err = cudaStreamBeginCaptureToGraph(st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+        if (err != cudaSuccess) break;
+        {
+            cudaError_t e1 = launch_sweep_pass(c->g, c->coef, c->r, c->Ja, c->Jb, c->dlt, c->d_nsw,
+                                               max_sweeps, tol, gs, h, st);
+            cudaGraph_t o = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(st, &o);
+            err = e1 != cudaSuccess ? e1 : e2;
+        }
+        if (err != cudaSuccess) break;
+        // epilogue: the last sweep's iterate into J_new, after the loop
+        err = cudaStreamBeginCaptureToGraph(st, g, &cn, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+        if (err != cudaSuccess) break;
+        {
+            cudaError_t e1 = launch_os_select(c->g.N, c->dlt, max_sweeps, tol, c->Ja, c->Jb, c->Jn,
+                                              b->d_sweeps + p, st);
+            cudaGraph_t o = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(st, &o);
+            err = e1 != cudaSuccess ? e1 : e2;
+        }
+        if (err != cudaSuccess) break;
+    }
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return err;
+    }
+    *out = g;
+    return cudaSuccess;
 }
 
 // Formal solutions of the active problems: FP32 sweep in one fused launch,
@@ -1045,9 +1200,69 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
     return RT_OK;
 }
 
-// Operator-splitting solves of the active problems; sweeps are enqueued in
-// chunks for every problem still iterating and checked with one host sync
-// per chunk (a sweep after a converged one is a device-side no-op).
+// Operator-splitting solves of the active problems as one graph launch (no
+// host synchronisation); the sweep counts reach b->d_sweeps.
+int batch_os_graph(rt_batch* b, const std::vector<int>& act, double tol_inner, int max_sweeps)
+{
+    int rc;
+    for (int p : act) {
+        rt_ctx* c = b->ctx[p];
+        if ((rc = bpass(b, p, ensure_coef(c)))) return rc;
+        if ((rc = bpass(b, p, ensure_dlt(c, max_sweeps + 2)))) return rc;
+        if (!c->d_nsw) BCK(cudaMalloc((void**)&c->d_nsw, sizeof(int)));
+    }
+    std::vector<const void*> key = batch_graph_key(b, act, tol_inner, max_sweeps);
+    rt_batch::OsGraph* e = nullptr;
+    for (auto& x : b->osg)
+        if (x.exec && x.key == key) e = &x;
+    if (!e) {
+        e = &b->osg[b->osg_next];
+        b->osg_next ^= 1;
+        if (e->exec) cudaGraphExecDestroy(e->exec);
+        if (e->graph) cudaGraphDestroy(e->graph);
+        *e = rt_batch::OsGraph{};
+        cudaGraph_t g = nullptr;
+        cudaError_t err = build_batch_os_graph(b, act, tol_inner, max_sweeps, &g);
+        cudaGraphExec_t exec = nullptr;
+        if (err == cudaSuccess) {
+            err = cudaGraphInstantiate(&exec, g, 0);
+            if (err != cudaSuccess) cudaGraphDestroy(g);
+        }
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, RT_ECUDA, "building the batch operator-splitting graph: %s",
+                         cudaGetErrorString(err));
+        }
+        e->graph = g;
+        e->exec = exec;
+        e->key.swap(key);
+        b->stats.launches += 0;
+    }
+    if (b->profiling) BCK(cudaEventRecord(b->ev[2], b->stream));
+    BCK(cudaGraphLaunch(e->exec, b->stream));
+    if (b->profiling) {
+        BCK(cudaEventRecord(b->ev[3], b->stream));
+        b->jac_pending = true;
+    }
+    return RT_OK;
+}
+
+// Launch counts of the graph-driven operator splitting of `act`, from the
+// sweep counts the graph wrote (read after the iteration's synchronisation).
+void batch_os_graph_counts(rt_batch* b, const std::vector<int>& act)
+{
+    for (int p : act) {
+        const int per = b->ctx[p]->os_method == RT_OS_GAUSS_SEIDEL ? 2 : 1;
+        const int passes = (b->h_sweeps[p] + 1) / 2;
+        b->stats.launches += 2 + passes * (2 * per + 1);
+        b->stats.jacobi_launches += passes * 2 * per;
+    }
+}
+
+// Operator-splitting solves of the active problems without graphs; sweeps
+// are enqueued in chunks for every problem still iterating and checked with
+// one host sync per chunk (a sweep after a converged one is a device-side
+// no-op).
 int batch_os(rt_batch* b, const std::vector<int>& act, double tol_inner, int max_sweeps)
 {
     int rc;
@@ -1086,6 +1301,7 @@ int batch_os(rt_batch* b, const std::vector<int>& act, double tol_inner, int max
             b->stats.jacobi_launches += per * (n1 - n0);
         }
         BCK(cudaStreamSynchronize(b->stream));
+        b->stats.host_syncs += 1;
         std::vector<int> still;
         for (int p : inner) {
             rt_ctx* c = b->ctx[p];
@@ -1139,6 +1355,8 @@ int rt_create(rt_ctx** out, int device, int precision)
     }
     *c->h_steps = 0;
     c->stream = c->own_stream;
+    // the FP32 sweep finishes in double-float by default (rt_set_df_finish)
+    c->df_switch = precision == RT_FP32_SWEEP ? kDefaultDfSwitch : 0.0;
     c->g.top_bc = RT_BC_ZERO;
     c->g.bottom_bc = RT_BC_PLANCK;
 #ifdef RT_CHECKED
@@ -1199,8 +1417,10 @@ int rt_set_grid(rt_ctx* c, int nx, int ny, int nz, double dx, double dy, double 
         return fail(c, RT_EINVAL, "spacings must be finite and > 0");
     if ((long long)nx * ny > (1LL << 30) || (long long)nx * ny * nz > (1LL << 40))
         return fail(c, RT_EINVAL, "grid too large");
-    if (c->precision != RT_FP64 && 4LL * nx * ny * nz >= (1LL << 31))
-        return fail(c, RT_EINVAL, "grid too large for the FP32-sweep form (4*nx*ny*nz >= 2^31)");
+    if (c->precision != RT_FP64 && (2LL * ny + 1) * 2LL * nx * nz >= (1LL << 31))
+        return fail(c, RT_EINVAL,
+                    "grid too large for the FP32-sweep and double-float forms "
+                    "((2ny+1)*2nx*nz >= 2^31)");
     CK(cudaStreamSynchronize(c->stream));
     free_grid_buffers(c);
     free_tables(c);
@@ -1220,13 +1440,11 @@ int rt_set_grid(rt_ctx* c, int nx, int ny, int nz, double dx, double dy, double 
     CK(dalloc(c->gdiff, (size_t)nx * ny));
     CK(dalloc(c->zorder, (size_t)nz)); CK(dalloc(c->zscratch, 2 * (size_t)nz));
     if (c->precision != RT_FP64) {
-        CK(dalloc(c->node4, 4 * N));
         CK(dalloc(c->b2, (size_t)8 * nx * ny));
         CK(dalloc(c->g2, (size_t)4 * nx * ny));
     }
-    if (c->precision == RT_DF64) CK(dalloc(c->g2df, (size_t)4 * nx * ny));
     c->have_grid = true;
-    return RT_OK;
+    return form_buffers(c, c->precision);
 }
 
 int rt_set_boundary(rt_ctx* c, int top_mode, int bottom_mode)
@@ -1274,21 +1492,22 @@ int rt_set_quadrature(rt_ctx* c, int ndir, const double* mu, const double* phi, 
     c->stats.launches += 1;
     if (c->precision != RT_FP64) {
         CK(dalloc(c->poff, T));
-        CK(launch_pad_offsets(c->g, c->info, c->off, c->poff, c->stream));
-        c->stats.launches += 1;
+        CK(dalloc(c->poff32, T));
+        CK(launch_pad_offsets(c->g, c->info, c->off, 2LL * c->g.ny, c->poff, c->stream));
+        CK(launch_pad_offsets(c->g, c->info, c->off, 2LL * c->g.ny + 1, c->poff32, c->stream));
+        c->stats.launches += 2;
     } else {
         CK(dalloc(c->dn, (size_t)ndir));
         CK(launch_down_tables(c->g, c->dx, c->dy, c->dz, c->d_mu, c->d_phi, c->dn, c->stream));
         c->stats.launches += 1;
     }
-    if (c->precision == RT_DF64) {
-        CK(dalloc(c->bwdf, 2 * T));
-        CK(launch_bw_df((long long)T, c->bw, c->bwdf, c->stream));
-        c->stats.launches += 1;
-    }
     c->wsum = sw;
-    CK(cudaStreamSynchronize(c->stream));
     c->have_quad = true;
+    if ((rc = form_buffers(c, c->precision))) {
+        c->have_quad = false;
+        return rc;
+    }
+    CK(cudaStreamSynchronize(c->stream));
     c->lstar_valid = c->coef_valid = false;
     return RT_OK;
 }
@@ -1608,6 +1827,9 @@ int rt_batch_create(rt_batch** out, int device, int precision, int nprob, const 
     BCK(cudaMallocHost((void**)&b->h_prefix, sizeof(long long) * (nprob + 1)));
     BCK(cudaMallocHost((void**)&b->h_delta, sizeof(double) * nprob));
     BCK(cudaMallocHost((void**)&b->h_steps, sizeof(unsigned long long)));
+    BCK(cudaMalloc((void**)&b->d_sweeps, sizeof(int) * nprob));
+    BCK(cudaMemset(b->d_sweeps, 0, sizeof(int) * nprob));
+    BCK(cudaMallocHost((void**)&b->h_sweeps, sizeof(int) * nprob));
     *out = b;
     return RT_OK;
 }
@@ -1617,7 +1839,10 @@ int rt_batch_destroy(rt_batch* b)
     if (!b) return RT_OK;
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
+    free_batch_graphs(b);
     for (rt_ctx* c : b->ctx) rt_destroy(c);
+    if (b->d_sweeps) cudaFree(b->d_sweeps);
+    if (b->h_sweeps) cudaFreeHost(b->h_sweeps);
     if (b->d_views) cudaFree(b->d_views);
     if (b->d_ids) cudaFree(b->d_ids);
     if (b->d_prefix) cudaFree(b->d_prefix);
@@ -1643,6 +1868,7 @@ int rt_batch_set_stream(rt_batch* b, void* stream)
     BCK(cudaSetDevice(b->device));
     BCK(cudaStreamSynchronize(b->stream));
     b->stream = stream ? (cudaStream_t)stream : b->own_stream;
+    free_batch_graphs(b);
     for (size_t p = 0; p < b->ctx.size(); ++p) {
         int rc = rt_set_stream(b->ctx[p], b->stream);
         if (rc) return bpass(b, (int)p, rc);
@@ -1752,7 +1978,11 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
             if (!b->converged[p] && b->iters[p] < max_iter) act.push_back(p);
         if (act.empty()) break;
         if ((rc = batch_fs(b, act))) return rc;
-        if ((rc = batch_os(b, act, tol_inner, max_sweeps))) return rc;
+        if (b->use_graphs)
+            rc = batch_os_graph(b, act, tol_inner, max_sweeps);
+        else
+            rc = batch_os(b, act, tol_inner, max_sweeps);
+        if (rc) return rc;
         std::vector<int> ng_now;
         for (int p : act) {
             bool pend = false;
@@ -1761,6 +1991,7 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
         }
         if (!ng_now.empty()) {
             BCK(cudaStreamSynchronize(b->stream));
+            b->stats.host_syncs += 1;
             for (int p : ng_now)
                 if ((rc = bpass(b, p, ng_finish(b->ctx[p])))) return rc;
         }
@@ -1772,7 +2003,13 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
         }
         BCK(cudaMemcpyAsync(b->h_delta, b->d_delta, sizeof(double) * P, cudaMemcpyDeviceToHost,
                             b->stream));
+        if (b->use_graphs)
+            BCK(cudaMemcpyAsync(b->h_sweeps, b->d_sweeps, sizeof(int) * P, cudaMemcpyDeviceToHost,
+                                b->stream));
         BCK(cudaStreamSynchronize(b->stream));
+        b->stats.host_syncs += 1;
+        b->stats.iterations += 1;
+        if (b->use_graphs) batch_os_graph_counts(b, act);
         bharvest(b);
         b->stats.steps += *b->h_steps;
         for (int p : act) {
@@ -1828,6 +2065,17 @@ int rt_batch_get_J_dev(rt_batch* b, int p, double* J)
     BCK(cudaSetDevice(b->device));
     rt_ctx* c = b->ctx[p];
     BCK(cudaMemcpyAsync(J, c->J, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, b->stream));
+    return RT_OK;
+}
+
+int rt_batch_set_graphs(rt_batch* b, int on)
+{
+    if (!b) return RT_EINVAL;
+    b->err.clear();
+    BCK(cudaSetDevice(b->device));
+    BCK(cudaStreamSynchronize(b->stream));
+    free_batch_graphs(b);
+    b->use_graphs = on != 0;
     return RT_OK;
 }
 

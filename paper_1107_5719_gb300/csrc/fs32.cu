@@ -19,12 +19,18 @@
 // instead of S.  J = sum_d w_d S_0 + sum_d w_d (I_d - S_0) is accumulated in
 // FP64.  Lambda*, the operator splitting and the convergence test are FP64.
 //
-// Layout: chi and the S pair are interleaved per node as float4
-// {chi, S_hi, S_lo, 0} in planes padded to 2ny x 2nx by periodic copies, so
-// that the four bilinear nodes of every upstream point are
-// base(voxel) + off(direction, step) + {0, 1, 2nx, 2nx + 1}: one integer add
-// per step and no wrap arithmetic.  B of the two boundary planes is kept as
-// padded float2 {B_hi, B_lo}.
+// Layout.  chi and the S pair of two x-neighbouring nodes share one record:
+// pair[k][y][x] = {chi(x), S_hi(x), chi(x+1), S_hi(x+1)} (float4) and
+// lo[k][y][x] = {S_lo(x), S_lo(x+1)} (float2), in planes padded by periodic
+// copies to 2ny+1 rows of 2nx records.  The upstream nodes of every
+// voxel at every step are then plain offsets from the voxel's own record
+// (one integer add per step, no wrap arithmetic), and one thread marches
+// the two voxels (i, j) and (i, j+1): their bilinear stencils share the
+// middle row, so a step reads three records and three lo pairs (72 bytes,
+// exactly the twelve values each voxel needs, with the middle row read
+// once for both) where one voxel per thread with one record per node read
+// four 16-byte records per voxel.  B of the two boundary planes is kept as
+// padded float2 {B_hi, B_lo} (planes 2ny x 2nx).
 #include "internal.h"
 #include "weights.cuh"
 
@@ -33,36 +39,50 @@ namespace rt3d {
 namespace {
 
 constexpr int kThreads32 = 128;
+// 80 registers (six blocks of 128 threads per SM) and the step loop
+// unrolled twice: measured on the 65^3 slab with 32x32 directions, 9.43 ms
+// per formal solution against 9.94 ms (no unrolling), 9.88 ms (96
+// registers) and 10.1-11.1 ms for variants that load the next step's
+// records before computing the current one (more registers, fewer warps).
+constexpr int kMinBlocks32 = 6;
 
+// poff[d][m] = offset of the upstream node (x0, y0) of step m from the
+// voxel's own node in planes of `rows` padded rows of 2nx entries.
 __global__ void k_pad_offsets(Geometry g, const DirInfo* __restrict__ info,
-                              const StepGeo* __restrict__ off, int* __restrict__ poff)
+                              const StepGeo* __restrict__ off, long long rows,
+                              int* __restrict__ poff)
 {
     const int d = blockIdx.x;
     const int s = info[d].sgn;
-    const long long W = 2LL * g.nx, H = 2LL * g.ny;
+    const long long W = 2LL * g.nx;
     for (int m = threadIdx.x; m < g.nz; m += blockDim.x) {
         const StepGeo o = off[(long long)d * g.nz + m];
-        poff[(long long)d * g.nz + m] = (int)((-(long long)m * s * H + o.oy) * W + o.ox);
+        poff[(long long)d * g.nz + m] = (int)((-(long long)m * s * rows + o.oy) * W + o.ox);
     }
 }
 
-__global__ void k_pack32(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
-                         float4* __restrict__ node)
+// One thread per padded record (k, y, x): the nodes (x mod nx, y mod ny) and
+// (x+1 mod nx, y mod ny) of plane k.
+__global__ void k_pack_pairs(Geometry g, const double* __restrict__ chi,
+                             const double* __restrict__ S, float4* __restrict__ pair,
+                             float2* __restrict__ lo)
 {
     const int nx = g.nx, ny = g.ny;
-    const long long W = 2LL * nx, P = 4LL * nx * ny;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.N;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(v % nx), j = (int)((v / nx) % ny);
-        const long long k = v / ((long long)nx * ny);
-        const double s = S[v];
-        const float hi = (float)s;
-        const float4 q = make_float4((float)chi[v], hi, (float)(s - (double)hi), 0.f);
-        float4* p = node + k * P + (long long)j * W + i;
-        p[0] = q;
-        p[nx] = q;
-        p[(long long)ny * W] = q;
-        p[(long long)ny * W + nx] = q;
+    const long long W = 2LL * nx, R = 2LL * ny + 1, P = R * W;
+    const long long n = P * g.nz;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+         r += (long long)gridDim.x * blockDim.x) {
+        const long long k = r / P, rem = r - k * P;
+        const int y = (int)(rem / W), x = (int)(rem - (long long)y * W);
+        int j = y, i0 = x, i1 = x + 1;
+        while (j >= ny) j -= ny;
+        while (i0 >= nx) i0 -= nx;
+        while (i1 >= nx) i1 -= nx;
+        const long long row = (k * ny + j) * (long long)nx;
+        const double s0 = S[row + i0], s1 = S[row + i1];
+        const float h0 = (float)s0, h1 = (float)s1;
+        pair[r] = make_float4((float)chi[row + i0], h0, (float)chi[row + i1], h1);
+        lo[r] = make_float2((float)(s0 - (double)h0), (float)(s1 - (double)h1));
     }
 }
 
@@ -90,9 +110,81 @@ __device__ __forceinline__ void add_steps32(unsigned long long* steps, unsigned 
     if ((threadIdx.x & 31) == 0 && n) atomicAdd(steps, n);
 }
 
-// One thread per voxel of plane k0, tile `tile` (kThreads32 voxels); block z
-// index zb of ZB walks the direction slots zb, zb + ZB, ... (d mod kSlots);
-// partial[slot][v] = sum_{d in slot} w_d (I_d - S_0).
+// Per-voxel state of one characteristic of the FP32 march.
+struct Ray32 {
+    float s0h, s0l, tcut;   // S_0 as an FP32 pair; transmission cutoff
+    float I, Ilo;           // I - S_0 as an unevaluated pair
+    float tau, T, ca, da;   // optical depth, transmission, hs chi and S - S_0 at p_m
+};
+
+// One step of a voxel's characteristic, from p_m to p_m+1: the upstream
+// point's four nodes are u0 = {chi, S_hi} of (x0, y0) and (x1, y0), u1 the
+// same of (x0, y1), (x1, y1); l0, l1 their S_lo; b the bilinear weights.
+__device__ __forceinline__ void step32(Ray32& r, float hs, float4 b, float4 u0, float4 u1,
+                                       float2 l0, float2 l1)
+{
+    constexpr float kLog2e = 1.4426950408889634f;
+    const float cb = b.x * u0.x + b.y * u0.z + b.z * u1.x + b.w * u1.z;
+    // S(p) - S_0: hi differences are exact for nearby values
+    const float dh = b.x * (u0.y - r.s0h) + b.y * (u0.w - r.s0h) + b.z * (u1.y - r.s0h) +
+                     b.w * (u1.w - r.s0h);
+    const float dl = b.x * l0.x + b.y * l0.y + b.z * l1.x + b.w * l1.y;
+    const float db = dh + (dl - r.s0l);
+    const float x = hs * (r.ca + cb);
+    float wc, wu, e;
+    seg_weights32(x, wc, wu, e);
+    // I - S_0 += T (w_cur D_m + w_up D_m+1), TwoSum
+    const float inc = r.T * fmaf(wc, r.da, wu * db);
+    const float sI = r.I + inc, bb = sI - r.I;
+    r.Ilo += (r.I - (sI - bb)) + (inc - bb);
+    r.I = sI;
+    r.tau += x;
+    r.T = ex2_approx(-r.tau * kLog2e);
+    r.ca = cb;
+    r.da = db;
+}
+
+// Boundary term T_M (I_bc - S_0) of a characteristic that reached the
+// boundary plane, added with its rounding error.  j0: the voxel's row.
+__device__ __forceinline__ void boundary32(Ray32& r, const View32& p, const DirInfo& di,
+                                           int d, int M, int i0, int j0)
+{
+    const Geometry& g = p.g;
+    const int s = di.sgn;
+    const int bc = s > 0 ? g.top_bc : g.bottom_bc;
+    float inc, inc_lo;
+    if (bc) {
+        const long long W = 2LL * g.nx, P = 4LL * g.nx * g.ny;
+        const StepGeo o = p.off[(long long)d * g.nz + M];
+        const float4 b = p.bw[(long long)d * g.nz + M];
+        long long ip = (j0 + o.oy) * W + (i0 + o.ox);
+        RT_GUARD(g, ip, P - W - 1, kSiteFs32) ip = 0;   // record, read a safe node
+        const float2* pb = p.b2 + (s > 0 ? 0LL : P) + ip;
+        const float2 c00 = pb[0], c10 = pb[1], c01 = pb[W], c11 = pb[W + 1];
+        const float h = b.x * (c00.x - r.s0h) + b.y * (c10.x - r.s0h) + b.z * (c01.x - r.s0h) +
+                        b.w * (c11.x - r.s0h);
+        const float l = b.x * c00.y + b.y * c10.y + b.z * c01.y + b.w * c11.y;
+        float ibc = h + (l - r.s0l);
+        if (bc == 2) {   // + |mu| dB/dtau (LTE diffusion)
+            const float* pg = p.g2 + ip;
+            ibc = fmaf(__ldg(&p.info[d].amu32),
+                       b.x * pg[0] + b.y * pg[1] + b.z * pg[W] + b.w * pg[W + 1], ibc);
+        }
+        inc = r.T * ibc;
+        inc_lo = fmaf(r.T, ibc, -inc);
+    } else {
+        inc = -r.T * r.s0h;
+        inc_lo = fmaf(-r.T, r.s0h, -inc) - r.T * r.s0l;
+    }
+    const float sI = r.I + inc, bb = sI - r.I;
+    r.Ilo += (r.I - (sI - bb)) + (inc - bb) + inc_lo;
+    r.I = sI;
+}
+
+// One thread per pair of voxels (i0, j0) and (i0, j0 + 1) of plane k0,
+// j0 even (the second one absent when j0 = ny - 1), tile `tile`
+// (kThreads32 pairs); block z index zb of ZB walks the direction slots zb,
+// zb + ZB, ... (d mod kSlots); partial[slot][v] = sum_{d in slot} w_d (I_d - S_0).
 //
 // Two details keep the FP32 rounding from reaching J at small eps:
 //  - I - S_0 is accumulated as an unevaluated pair (Knuth's TwoSum), so the
@@ -104,121 +196,99 @@ __device__ __forceinline__ void add_steps32(unsigned long long* steps, unsigned 
 // Measured on a 9x9x129 slab (32x8 directions): converged J within 2.5e-8
 // of the FP64 solution at eps = 1e-6 (1.4e-6 with a plain FP32 sum and
 // product).
+//
+// The two characteristics of a thread are marched together until both are
+// cut off (or reach the boundary, where both take their boundary term); a
+// voxel whose own cutoff came first keeps adding its (negligible) terms.
+// The step count is that of each voxel's own cutoff.
 __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int zb, int ZB,
                                         float cut, unsigned long long* __restrict__ steps)
 {
-    constexpr float kLog2e = 1.4426950408889634f;
     const Geometry& g = p.g;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const int nyp = (ny + 1) >> 1;
     const int t = tile * kThreads32 + threadIdx.x;
-    const bool active = t < nxy;
+    const bool active = t < nx * nyp;
     unsigned long long nsteps = 0;
     if (active) {
-        const int j0 = t / nx, i0 = t - j0 * nx;
-        const long long v = (long long)k0 * nxy + t;
-        const long long W = 2LL * nx, P = 4LL * nxy;
+        const int jp = t / nx, i0 = t - jp * nx, j0 = 2 * jp;
+        const bool two = j0 + 1 < ny;
+        const long long va = (long long)k0 * nxy + (long long)j0 * nx + i0;
+        const long long W = 2LL * nx, P = (2LL * ny + 1) * W;
         const long long base = k0 * P + j0 * W + i0;
-        const float4 me = p.node[base];
-        const float chi0 = me.x, s0h = me.y, s0l = me.z;
-        const float s0 = s0h + s0l;
+        const float4* pa = p.pair + base;
+        const float2* pl = p.lo + base;
+        const float4 ma = pa[0], mb = pa[W];
+        const float2 la = pl[0], lb = pl[W];
         // The rest of a characteristic changes I - S_0 by at most
         // T * max|S - S_0| <= T * 2 smax: stop once that is below cut * S_0.
+        // An absent second voxel counts as cut off from the start.
         const float smax = (float)*p.smax;
-        const float tcut = smax > 0.f ? cut * s0 / (2.0f * smax) : 0.f;
-        const float4* nb = p.node + base;
+        const float ka = smax > 0.f ? cut / (2.0f * smax) : 0.f;
+        const float tca = ka * (ma.y + la.x);
+        const float tcb = two ? ka * (mb.y + lb.x) : 2.0f;
         for (int slot = zb; slot < kSlots; slot += ZB) {
-            double Jp = 0.0;
+            double Ja = 0.0, Jb = 0.0;
             for (int d = slot; d < g.ndir; d += kSlots) {
                 const DirInfo di = p.info[d];
                 const int s = di.sgn;
                 const int M = s > 0 ? k0 : nz - 1 - k0;
                 const int* od = p.poff + (long long)d * nz;
                 const float4* bd = p.bw + (long long)d * nz;
-                float I = 0.f, Ilo = 0.f, T = 1.f, tau = 0.f, ca = chi0, da = 0.f;
-                bool early = false;
+                Ray32 a{ma.y, la.x, tca, 0.f, 0.f, 0.f, 1.f, ma.x, 0.f};
+                Ray32 b{mb.y, lb.x, tcb, 0.f, 0.f, 0.f, 1.f, mb.x, 0.f};
+                bool alive_a = true, alive_b = true, early = false;
+                int na = 0, nb = 0;
                 int m = 0;
+#pragma unroll 2
                 for (; m < M; ++m) {
-                    RT_GUARD(g, base + od[m + 1], 4 * g.N, kSiteFs32) { early = true; break; }
-                    RT_GUARD(g, base + od[m + 1] + W + 1, 4 * g.N, kSiteFs32) { early = true; break; }
-                    const float4* q = nb + od[m + 1];
-                    const float4 b = bd[m + 1];
-                    const float4 q00 = __ldg(q), q10 = __ldg(q + 1);
-                    const float4 q01 = __ldg(q + W), q11 = __ldg(q + W + 1);
-                    const float cb = b.x * q00.x + b.y * q10.x + b.z * q01.x + b.w * q11.x;
-                    // S(p) - S_0: hi differences are exact for nearby values
-                    const float dh = b.x * (q00.y - s0h) + b.y * (q10.y - s0h) +
-                                     b.z * (q01.y - s0h) + b.w * (q11.y - s0h);
-                    const float dl = b.x * q00.z + b.y * q10.z + b.z * q01.z + b.w * q11.z;
-                    const float db = dh + (dl - s0l);
-                    const float x = di.hs32 * (ca + cb);
-                    float wc, wu, e;
-                    seg_weights32(x, wc, wu, e);
-                    // I - S_0 += T (w_cur D_m + w_up D_m+1), TwoSum
-                    const float inc = T * fmaf(wc, da, wu * db);
-                    const float sI = I + inc, bb = sI - I;
-                    Ilo += (I - (sI - bb)) + (inc - bb);
-                    I = sI;
-                    tau += x;
-                    T = ex2_approx(-tau * kLog2e);
-                    ca = cb;
-                    da = db;
-                    if (T <= tcut) {
+                    const int o = od[m + 1];
+                    RT_GUARD(g, base + o, P * nz, kSiteFs32) { early = true; break; }
+                    RT_GUARD(g, base + o + 2 * W, P * nz, kSiteFs32) { early = true; break; }
+                    const float4 bw = bd[m + 1];
+                    const float4* q = pa + o;
+                    const float2* ql = pl + o;
+                    const float4 u0 = __ldg(q), u1 = __ldg(q + W), u2 = __ldg(q + 2 * W);
+                    const float2 l0 = __ldg(ql), l1 = __ldg(ql + W), l2 = __ldg(ql + 2 * W);
+                    step32(a, di.hs32, bw, u0, u1, l0, l1);
+                    step32(b, di.hs32, bw, u1, u2, l1, l2);
+                    na += alive_a;
+                    nb += alive_b;
+                    alive_a = alive_a && a.T > a.tcut;
+                    alive_b = alive_b && b.T > b.tcut;
+                    if (!alive_a && !alive_b) {
                         early = true;
                         ++m;
                         break;
                     }
                 }
                 if (!early) {
-                    // boundary term T_M (I_bc - S_0), added with its rounding error
-                    float inc, inc_lo;
-                    const int bc = s > 0 ? g.top_bc : g.bottom_bc;
-                    if (bc) {
-                        const StepGeo o = p.off[(long long)d * nz + M];
-                        const float4 b = bd[M];
-                        long long ip = (j0 + o.oy) * W + (i0 + o.ox);
-                        RT_GUARD(g, ip, P - W - 1, kSiteFs32) ip = 0;   // record, read a safe node
-                        const float2* pb = p.b2 + (s > 0 ? 0LL : P) + ip;
-                        const float2 c00 = pb[0], c10 = pb[1], c01 = pb[W], c11 = pb[W + 1];
-                        const float h = b.x * (c00.x - s0h) + b.y * (c10.x - s0h) +
-                                        b.z * (c01.x - s0h) + b.w * (c11.x - s0h);
-                        const float l = b.x * c00.y + b.y * c10.y + b.z * c01.y + b.w * c11.y;
-                        float ibc = h + (l - s0l);
-                        if (bc == 2) {   // + |mu| dB/dtau (LTE diffusion)
-                            // |mu| read here, not kept live through the march
-                            // loop (that cost the loop 13%)
-                            const float* pg = p.g2 + ip;
-                            ibc = fmaf(__ldg(&p.info[d].amu32),
-                                       b.x * pg[0] + b.y * pg[1] + b.z * pg[W] + b.w * pg[W + 1], ibc);
-                        }
-                        inc = T * ibc;
-                        inc_lo = fmaf(T, ibc, -inc);
-                    } else {
-                        inc = -T * s0h;
-                        inc_lo = fmaf(-T, s0h, -inc) - T * s0l;
-                    }
-                    const float sI = I + inc, bb = sI - I;
-                    Ilo += (I - (sI - bb)) + (inc - bb) + inc_lo;
-                    I = sI;
+                    boundary32(a, p, di, d, M, i0, j0);
+                    if (two) boundary32(b, p, di, d, M, i0, j0 + 1);
                 }
-                nsteps += (unsigned long long)m;
-                Jp = fma(di.w, (double)I + (double)Ilo, Jp);
+                nsteps += (unsigned long long)na + (two ? (unsigned long long)nb : 0ull);
+                Ja = fma(di.w, (double)a.I + (double)a.Ilo, Ja);
+                Jb = fma(di.w, (double)b.I + (double)b.Ilo, Jb);
             }
-            p.partial[(long long)slot * g.N + v] = Jp;
+            p.partial[(long long)slot * g.N + va] = Ja;
+            if (two) p.partial[(long long)slot * g.N + va + nx] = Jb;
         }
     }
     if (steps) add_steps32(steps, nsteps);
 }
 
-__global__ void __launch_bounds__(kThreads32)
+__global__ void __launch_bounds__(kThreads32, kMinBlocks32)
 k_fs32d(View32 p, float cut, unsigned long long* __restrict__ steps)
 {
     march32(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, cut, steps);
 }
 
+int tiles32(const Geometry& g) { return (g.nx * ((g.ny + 1) / 2) + kThreads32 - 1) / kThreads32; }
+
 // Many problems in one launch: block b belongs to the active problem q with
 // prefix[q] <= b < prefix[q+1]; within it, blocks run tile-fastest, then
 // plane, then slot group.
-__global__ void __launch_bounds__(kThreads32)
+__global__ void __launch_bounds__(kThreads32, kMinBlocks32)
 k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
              const long long* __restrict__ prefix, int nact, int ZB, float cut,
              unsigned long long* __restrict__ steps)
@@ -232,7 +302,7 @@ k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
     if (b >= prefix[nact]) return;
     const View32& p = views[ids[lo]];
     const long long local = b - prefix[lo];
-    const int tiles = (p.g.nx * p.g.ny + kThreads32 - 1) / kThreads32;
+    const int tiles = (p.g.nx * ((p.g.ny + 1) >> 1) + kThreads32 - 1) / kThreads32;
     const int tile = (int)(local % tiles);
     const int k0 = (int)((local / tiles) % p.g.nz);
     const int zb = (int)(local / ((long long)tiles * p.g.nz));
@@ -261,17 +331,19 @@ unsigned grid1d(long long n, int threads)
 
 }  // namespace
 
+long long pair_records(const Geometry& g) { return (2LL * g.ny + 1) * 2LL * g.nx * g.nz; }
+
 cudaError_t launch_pad_offsets(const Geometry& g, const DirInfo* info, const StepGeo* off,
-                               int* poff, cudaStream_t st)
+                               long long rows, int* poff, cudaStream_t st)
 {
-    k_pad_offsets<<<g.ndir, 128, 0, st>>>(g, info, off, poff);
+    k_pad_offsets<<<g.ndir, 128, 0, st>>>(g, info, off, rows, poff);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack32(const Geometry& g, const double* chi, const double* S, float4* node,
-                          cudaStream_t st)
+cudaError_t launch_pack_pairs(const Geometry& g, const double* chi, const double* S, float4* pair,
+                              float2* lo, cudaStream_t st)
 {
-    k_pack32<<<grid1d(g.N, 256), 256, 0, st>>>(g, chi, S, node);
+    k_pack_pairs<<<grid1d(pair_records(g), 256), 256, 0, st>>>(g, chi, S, pair, lo);
     return cudaGetLastError();
 }
 
@@ -284,17 +356,16 @@ cudaError_t launch_pack_b2(const Geometry& g, const double* B, float2* b2, cudaS
 cudaError_t launch_fs32d(const View32& p, double cut, int groups, unsigned long long* steps,
                          cudaStream_t st)
 {
-    const int nxy = p.g.nx * p.g.ny;
     // planes in index order (g.zorder unused): with the plane read from the
     // order table the march ran at 14.6 instead of 10.7 ms on the 65^3 slab
-    dim3 grid((nxy + kThreads32 - 1) / kThreads32, p.g.nz, groups);
+    dim3 grid(tiles32(p.g), p.g.nz, groups);
     k_fs32d<<<grid, kThreads32, 0, st>>>(p, (float)cut, steps);
     return cudaGetLastError();
 }
 
 long long fs32_blocks(const Geometry& g, int groups)
 {
-    return (long long)((g.nx * g.ny + kThreads32 - 1) / kThreads32) * g.nz * groups;
+    return (long long)tiles32(g) * g.nz * groups;
 }
 
 cudaError_t launch_fs32_batch(const View32* views, const int* ids, const long long* prefix,

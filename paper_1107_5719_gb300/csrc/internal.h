@@ -161,24 +161,30 @@ cudaError_t launch_lstar_sc64(const Geometry& g, const double* chi, const DirInf
                               const StepGeo* off, const Bw4d* bw, double* lstar, cudaStream_t st);
 
 // ---- FP32-sweep form (fs32.cu) ---------------------------------------------
-// poff[d][m]: offset of the upstream node (x0, y0) of step m in the padded
-// [nz][2ny][2nx] layout, relative to the voxel's own padded index.
+// poff[d][m]: offset of the upstream node (x0, y0) of step m from the
+// voxel's own entry in planes of `rows` padded rows of 2nx entries
+// ([nz][rows][2nx]; rows = 2ny for the double-float nodes, 2ny + 1 for the
+// FP32 pair records).
 cudaError_t launch_pad_offsets(const Geometry& g, const DirInfo* info, const StepGeo* off,
-                               int* poff, cudaStream_t st);
-// node[k][y][x] = {chi, S_hi, S_lo, 0} with periodic copies (planes 2ny x 2nx).
-cudaError_t launch_pack32(const Geometry& g, const double* chi, const double* S, float4* node,
-                          cudaStream_t st);
+                               long long rows, int* poff, cudaStream_t st);
+// Entries of the padded FP32 pair planes: nz * (2ny + 1) * 2nx.
+long long pair_records(const Geometry& g);
+// pair[k][y][x] = {chi, S_hi} of the nodes (x mod nx, y mod ny) and
+// (x+1 mod nx, y mod ny); lo[k][y][x] = their S_lo (planes (2ny+1) x 2nx).
+cudaError_t launch_pack_pairs(const Geometry& g, const double* chi, const double* S, float4* pair,
+                              float2* lo, cudaStream_t st);
 // b2[plane][y][x] = {B_hi, B_lo} of the top (0) and bottom (1) planes, padded.
 cudaError_t launch_pack_b2(const Geometry& g, const double* B, float2* b2, cudaStream_t st);
 // Everything the FP32 march of one problem reads and writes.
 struct View32 {
     Geometry g;
-    const float4* node;     // padded {chi, S_hi, S_lo, 0}
+    const float4* pair;     // padded pair records {chi, S_hi, chi', S_hi'}
+    const float2* lo;       // padded {S_lo, S_lo'}
     const float2* b2;       // padded boundary {B_hi, B_lo}
     const float* g2;        // padded dB/dtau of the bottom nodes (diffusion boundary)
     const DirInfo* info;
     const StepGeo* off;
-    const int* poff;
+    const int* poff;        // offsets in the pair planes (rows = 2ny + 1)
     const float4* bw;       // FP32 bilinear weights per (direction, step)
     const double* smax;     // source bound of the cutoff
     double* partial;        // [kSlots][N]
@@ -272,6 +278,13 @@ cudaError_t launch_gs_sweep(const Geometry& g, const double* coef, const double*
 cudaError_t launch_sweep_pass(const Geometry& g, const double* coef, const double* r, double* b0,
                               double* b1, double* dlt, int* nsw, int max_sweeps, double tol,
                               bool gs, cudaGraphConditionalHandle h, cudaStream_t st);
+// After a device-side sweep loop from the buffers Ja (even sweeps) and Jb
+// (odd sweeps): Jn = the iterate of the last sweep that ran (the first n
+// with dlt[n] < tol, else max_sweeps - 1) and *sweeps_out = n + 1 (may be
+// null).  The host loop picks the same buffer from the same deltas.
+cudaError_t launch_os_select(long long N, const double* dlt, int max_sweeps, double tol,
+                             const double* Ja, const double* Jb, double* Jn, int* sweeps_out,
+                             cudaStream_t st);
 // Sweep n: Jn[v] = r[v] + sum_{o != 13} c[o][v] J[nb(v,o)];  dlt[n] = max |Jn - J| / |Jn|;
 // no-op when n > 0 and dlt[n-1] < tol.
 cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r,

@@ -297,6 +297,33 @@ __global__ void k_sweep_cond(cudaGraphConditionalHandle h, int* nsw, const doubl
     cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// End of a device-side sweep loop: the solve stopped at the first sweep n
+// whose dlt[n] < tol (all sweeps when none did), and that sweep wrote Ja
+// (n even) or Jb (n odd): copy it to Jn and record the sweep count.  Every
+// block finds the count itself (the deltas are a few hundred doubles).
+__global__ void k_os_select(long long N, const double* __restrict__ dlt, int max_sweeps,
+                            double tol, const double* __restrict__ Ja,
+                            const double* __restrict__ Jb, double* __restrict__ Jn,
+                            int* __restrict__ sweeps_out)
+{
+    __shared__ int s_sweeps;
+    if (threadIdx.x == 0) {
+        int s = max_sweeps;
+        for (int n = 0; n < max_sweeps; ++n)
+            if (dlt[n] < tol) {
+                s = n + 1;
+                break;
+            }
+        s_sweeps = s;
+        if (blockIdx.x == 0 && sweeps_out) *sweeps_out = s;
+    }
+    __syncthreads();
+    const double* src = ((s_sweeps - 1) & 1) ? Jb : Ja;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x)
+        Jn[v] = src[v];
+}
+
 __global__ void k_rel_change(long long N, const double* __restrict__ Jn,
                              const double* __restrict__ Jo, double* __restrict__ delta)
 {
@@ -452,6 +479,16 @@ cudaError_t launch_sweep_pass(const Geometry& g, const double* coef, const doubl
         k_jacobi<<<grid, kOsThreads, 0, st>>>(g, coef, r, b0, b1, dlt, 1, tol, nsw, max_sweeps);
     }
     k_sweep_cond<<<1, 1, 0, st>>>(h, nsw, dlt, max_sweeps, tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_os_select(long long N, const double* dlt, int max_sweeps, double tol,
+                             const double* Ja, const double* Jb, double* Jn, int* sweeps_out,
+                             cudaStream_t st)
+{
+    long long blocks = (N + 255) / 256;
+    if (blocks > 152LL * 8) blocks = 152LL * 8;
+    k_os_select<<<(unsigned)blocks, 256, 0, st>>>(N, dlt, max_sweeps, tol, Ja, Jb, Jn, sweeps_out);
     return cudaGetLastError();
 }
 

@@ -121,7 +121,10 @@ __device__ __forceinline__ int cut_need(double smax, double cut)
 
 // ---- FP32 -----------------------------------------------------------------
 //
-//  x < 2: the phi2 series in FP32 (seven terms each, truncation < 2e-9);
+//  x < 2: phi2(+-x) = E(z) +- x Q(z) with E, Q degree-4 polynomials in
+//  z = x^2 fitted on z in [0, 4] for the least maximum relative error
+//  (fit_weights32.py: 1.9e-8 for E, 3.0e-8 for Q with the coefficients
+//  rounded to FP32, against 2e-9 truncation for seven Taylor terms each);
 //  x >= 2: closed form (1-e loses nothing there).  e from the MUFU ex2.
 __device__ __forceinline__ float ex2_approx(float y)
 {
@@ -143,14 +146,12 @@ __device__ __forceinline__ void seg_weights32(float x, float& wc, float& wu, flo
     e = ex2_approx(-x * kLog2e);
     if (x < 2.0f) {
         const float z = x * x;
-        float E = fmaf(fmaf(fmaf(fmaf(fmaf(1.0f / 87178291200.0f, z, 1.0f / 479001600.0f), z,
-                                     1.0f / 3628800.0f), z, 1.0f / 40320.0f), z, 1.0f / 720.0f),
-                       z, 1.0f / 24.0f);
+        float E = fmaf(fmaf(fmaf(2.968770900e-07f, z, 2.472764936e-05f), z, 1.388992299e-03f), z,
+                       4.166661575e-02f);
         E = fmaf(E, z, 0.5f);
-        float O = fmaf(fmaf(fmaf(fmaf(fmaf(1.0f / 1307674368000.0f, z, 1.0f / 6227020800.0f), z,
-                                     1.0f / 39916800.0f), z, 1.0f / 362880.0f), z, 1.0f / 5040.0f),
-                       z, 1.0f / 120.0f);
-        O = fmaf(O, z, 1.0f / 6.0f) * x;
+        float O = fmaf(fmaf(fmaf(2.669341548e-08f, z, 2.749998430e-06f), z, 1.984207920e-04f), z,
+                       8.333329111e-03f);
+        O = fmaf(O, z, 1.666666716e-01f) * x;
         wc = x * (E - O);
         wu = (x * e) * (E + O);
     } else {

@@ -52,7 +52,8 @@ class rt_stats(C.Structure):
     _fields_ = [("launches", C.c_ulonglong), ("fs_launches", C.c_ulonglong),
                 ("fs_ms", C.c_double), ("jacobi_launches", C.c_ulonglong),
                 ("jacobi_ms", C.c_double), ("steps", C.c_ulonglong),
-                ("lstar_launches", C.c_ulonglong)]
+                ("lstar_launches", C.c_ulonglong), ("iterations", C.c_ulonglong),
+                ("host_syncs", C.c_ulonglong)]
 
 
 class rt_problem(C.Structure):
@@ -117,6 +118,7 @@ _SIGS = {
     "rt_batch_get_J": (C.c_int, [VP, C.c_int, VP]),
     "rt_batch_get_J_dev": (C.c_int, [VP, C.c_int, VP]),
     "rt_batch_set_direction_groups": (C.c_int, [VP, C.c_int]),
+    "rt_batch_set_graphs": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_profiling": (C.c_int, [VP, C.c_int]),
     "rt_batch_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
     "rt_batch_reset_stats": (C.c_int, [VP]),
@@ -487,6 +489,10 @@ def rt_batch_get_J_dev(b, p, J):
 
 def rt_batch_set_direction_groups(b, groups):
     return _bcheck(b, load().rt_batch_set_direction_groups(b, groups))
+
+
+def rt_batch_set_graphs(b, on=True):
+    return _bcheck(b, load().rt_batch_set_graphs(b, 1 if on else 0))
 
 
 def rt_batch_set_profiling(b, on=True):

@@ -109,3 +109,33 @@ def test_batch_wavelengths_of_one_slab(R):
             assert np.array_equal(J, ri["J"])
     finally:
         R.rt_batch_destroy(b)
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_batch_graph_equals_host_loop(R, method):
+    """The operator-splitting step of all active problems as one CUDA graph
+    (per-problem branches with device-side sweep loops) gives the iterates
+    of the host-driven sweep chunks bit for bit, Jacobi and red-black
+    Gauss-Seidel, with one host wait per iteration (two when Ng
+    extrapolates) instead of one per chunk of sweeps."""
+    probs = _uneven()
+    out = {}
+    for graphs in (True, False):
+        b = R.rt_batch_create(probs, precision=1)
+        try:
+            R.rt_batch_set_graphs(b, graphs)
+            R.rt_batch_set_os_method(b, method)
+            R.rt_batch_set_ng(b, 4, 1e-6)
+            r = R.rt_batch_solve(b, len(probs), tol=TOL[1], max_iter=500)
+            assert r["converged"]
+            Js = [R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx)) for i, p in enumerate(probs)]
+            out[graphs] = (r, Js, R.rt_batch_get_stats(b))
+        finally:
+            R.rt_batch_destroy(b)
+    (rg, Jg, sg), (rh, Jh, sh) = out[True], out[False]
+    assert np.array_equal(rg["iters"], rh["iters"])
+    for a, c in zip(Jg, Jh):
+        assert np.array_equal(a, c)
+    assert sg["iterations"] == sh["iterations"] == max(rg["iters"])
+    assert sg["host_syncs"] <= 2 * sg["iterations"]
+    assert sh["host_syncs"] > sg["host_syncs"]

@@ -30,6 +30,7 @@ def test_fp32_then_double_float_reaches_1e6(R):
         r64 = s.solve(tol=1e-11, max_iter=5000)
     assert r64["converged"]
     with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+        R.rt_set_df_finish(s.ctx, 0.0)          # the FP32 sweep alone, switched by hand
         r32 = s.solve(tol=5e-8, max_iter=5000)
         assert r32["converged"]
         err32 = np.max(np.abs(r32["J"] - r64["J"]) / r64["J"])
@@ -74,6 +75,7 @@ def test_batch_fp32_then_double_float_equals_single(R):
     b = R.rt_batch_create(probs, precision=R.RT_FP32_SWEEP)
     try:
         R.rt_batch_set_ng(b, 4, 1e-6)
+        R.rt_batch_set_df_finish(b, 0.0)        # stages switched by hand
         r1 = R.rt_batch_solve(b, len(probs), tol=5e-8, max_iter=3000)
         assert r1["converged"]
         R.rt_batch_set_precision(b, R.RT_DF64)
@@ -85,6 +87,7 @@ def test_batch_fp32_then_double_float_equals_single(R):
         R.rt_batch_destroy(b)
     for i, q in enumerate(probs):
         with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+            R.rt_set_df_finish(s.ctx, 0.0)
             a = s.solve(tol=5e-8, max_iter=3000)
             R.rt_set_precision(s.ctx, R.RT_DF64)
             R.rt_set_ng(s.ctx, 4, 0.0)
@@ -94,21 +97,22 @@ def test_batch_fp32_then_double_float_equals_single(R):
 
 
 def test_automatic_double_float_finish(R):
-    """rt_set_df_finish: the FP32-sweep solve switches itself to double-float
-    once delta < 1e-6 and reaches a tolerance below the FP32 noise floor, in
-    fewer iterations than the FP32 sweep needs for 5e-8; afterwards the
-    context is an FP32-sweep context again."""
+    """rt_set_df_finish (on by default for FP32-sweep contexts): the
+    FP32-sweep solve switches itself to double-float once delta < 1e-6 and
+    reaches a tolerance below the FP32 noise floor, in fewer iterations than
+    the FP32 sweep alone needs for 5e-8; afterwards the context is an
+    FP32-sweep context again."""
     p = W.slab_precision(n=9, nzz=129, n_theta=32, n_phi=8)
     with R.Solver(p, precision=R.RT_FP64, ng_period=4) as s:
         r64 = s.solve(tol=1e-11, max_iter=5000)
     with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+        R.rt_set_df_finish(s.ctx, 0.0)
         r32 = s.solve(tol=5e-8, max_iter=5000)
     S = p.B * 1.1
     with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
         Jref, _ = s.formal_solution(S)
     with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
-        R.rt_set_df_finish(s.ctx, 1e-6)
-        r = s.solve(tol=1e-8, max_iter=5000)
+        r = s.solve(tol=1e-8, max_iter=5000)        # the context's default finish
         J, _ = s.formal_solution(S)                 # back in the FP32 sweep
     assert r["converged"]
     err = np.max(np.abs(r["J"] - r64["J"]) / r64["J"])

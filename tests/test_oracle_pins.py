@@ -323,6 +323,24 @@ def _neighbour(p, v, o):
     return (kk * p.ny + (j + oy) % p.ny) * p.nx + (i + ox) % p.nx
 
 
+@pytest.mark.parametrize("shape,seed", [((5, 5, 5), 11), ((3, 4, 5), 12)])
+def test_lstar_at_equals_brute_force_lambda(oracle_mod, shape, seed):
+    """Lambda* rows at a sample of voxels (the full-size spot-check call)
+    equal the nearest-neighbour elements of the brute-force Lambda, for
+    voxels listed in random order and with repeats (Sect. 2.2)."""
+    nx, ny, nz = shape
+    p = W.random_slab(nx, ny, nz, n_theta=4, n_phi=5, seed=seed)
+    Lam = _brute_lambda(oracle_mod, p)
+    rng = np.random.default_rng(seed)
+    vox = np.concatenate([rng.permutation(p.nvox), rng.integers(0, p.nvox, 7)])
+    rows = oracle_mod.lstar_at(p, vox)
+    for q, v in enumerate(vox):
+        for o in range(27):
+            j = _neighbour(p, v, o)
+            ref = 0.0 if j < 0 else Lam[v, j]
+            assert abs(rows[q, o] - ref) <= 1e-14 * max(abs(ref), 1e-3), (v, o)
+
+
 @pytest.mark.parametrize("shape,seed", [((5, 5, 5), 11), ((3, 4, 5), 12), ((4, 3, 2), 13)])
 def test_lstar_equals_brute_force_lambda(oracle_mod, shape, seed):
     """Lambda* entries equal the matching elements of the full Lambda
@@ -758,6 +776,8 @@ _MUTANTS = {
     "lstar_xy_swapped": ("return ((int)dzv + 1) * 9 + (oy + 1) * 3 + (ox + 1);",
                          "return ((int)dzv + 1) * 9 + (ox + 1) * 3 + (oy + 1);"),
     "lstar_drops_upstream_term": ("if (m >= 1) c += T[m - 1] * wu[m - 1];", "(void)0;"),
+    "lstar_at_rows_reversed": ("double *row = lstar_out + q * 27;",
+                               "double *row = lstar_out + (nsample - 1 - q) * 27;"),
     "os_forgets_destruction": ("r -= lstar[(long)o * N + v] * (1.0 - eps[j]) * J_old[j];",
                                "r -= lstar[(long)o * N + v] * J_old[j];"),
     "os_diag_uses_neighbour_eps": ("return acc / (1.0 - lstar[13L * N + v] * (1.0 - eps[v]));",
@@ -799,6 +819,7 @@ def _pin_battery(mod):
         ("geometry", lambda: test_single_direction_unit_source_geometry(mod, +1, 0.0, (1, 0))),
         ("half_node", lambda: test_half_node_shift_splits_bilinearly(mod)),
         ("lstar", lambda: test_lstar_equals_brute_force_lambda(mod, (3, 4, 5), 12)),
+        ("lstar_at", lambda: test_lstar_at_equals_brute_force_lambda(mod, (3, 4, 5), 12)),
         ("short", lambda: test_short_characteristics_equal_long_on_lattice_directions(mod, (0, 1))),
         ("parabolic", lambda: test_parabolic_weights_match_high_precision(mod, 0.2, 0.05)),
         ("parabolic_exact", lambda: test_parabolic_source_exact_for_quadratic_source(mod)),
