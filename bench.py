@@ -58,6 +58,36 @@ TRAFFIC_FS64_SLAB65 = 7805184
 INSTR_PER_STEP_DF64 = 398
 PEAK_ISSUE_TINST = 40.3
 
+# HBM bandwidth of the GB300s: the driver's measured copy
+# (MEASURED_PEAKS.json, hbm_gbs), read at run time when the file is there.
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6796.5
+
+
+MEASURED_HBM_GBS = _measured_hbm()
+
+# Outer iterations and Jacobi sweeps of one converged ORACLE solve (Ng every
+# 4 iterations, tol 1e-8), from full oracle solves run once on the GPU machine's
+# 16 Arm cores: the counts the sampled CPU timings are scaled by.
+# 16 Arm cores (Neoverse-V2) of the GPU machine: slab65 converged in 633.4 s
+# (18 iterations, 485 sweeps), slab17 in 0.82 s (17 iterations, 416 sweeps).
+ORACLE_COUNTS = {
+    "slab65": {"iters": 18, "sweeps": 485, "full_solve_s": 633.4, "cores": 16},
+    "slab17": {"iters": 17, "sweeps": 416, "full_solve_s": 0.82, "cores": 16},
+}
+# DRAM bytes (read + write) of one k_jacobi launch on the 129^3 grid, from
+# one ncu capture of the current kernel: 478.6 MB read + 16.2 MB written,
+# the algorithmic 232 B per voxel.
+TRAFFIC_JACOBI_129 = 494826240
+# DRAM bytes (read + write) of one k_fs32d launch on slab65, from one ncu
+# capture of the current kernel: 27.80 MB read (the padded pair planes,
+# the tables) + 0.06 MB written; then everything is served from L2.
+TRAFFIC_FS32_SLAB65 = 27860480
+
 # The FP32-sweep iterate stops changing below a relative delta of ~1e-8
 # (rounding), so its outer tolerance is at least 5e-8, and Ng extrapolation
 # is skipped once delta < 1e-6 (it would amplify that rounding).
@@ -230,6 +260,37 @@ def timed_solves(R, p, precision, dev, stream, flush, warmup, steps, max_iter, c
         R.rt_destroy(ctx)
 
 
+def march_rate(R, p, precision, dev, stream, launches=5):
+    """Device time and executed steps per launch of the march alone: formal
+    solutions of the workload's source S = eps B + (1 - eps) B, timed with
+    the library's CUDA events."""
+    import torch
+    S = torch.from_numpy(p.eps * p.B + (1 - p.eps) * p.B).to(dev)
+    J = torch.empty_like(S)
+    ctx = R.rt_create(dev.index, precision)
+    try:
+        R.rt_set_stream(ctx, stream)
+        R.rt_set_grid(ctx, p.nx, p.ny, p.nz, p.dx, p.dy, p.dz)
+        R.rt_set_boundary(ctx, p.top_bc, p.bottom_bc)
+        R.rt_set_quadrature(ctx, p.mu, p.phi, p.w)
+        R.rt_set_opacity(ctx, p.chi)
+        R.rt_set_epsilon(ctx, p.eps)
+        R.rt_set_planck(ctx, p.B)
+        R.rt_formal_solution_dev(ctx, S, J, None)
+        stream.synchronize()
+        R.rt_reset_stats(ctx)
+        R.rt_set_profiling(ctx, True)
+        for _ in range(launches):
+            R.rt_formal_solution_dev(ctx, S, J, None)
+        st = R.rt_get_stats(ctx)
+    finally:
+        R.rt_destroy(ctx)
+    ms = st["fs_ms"] / max(st["fs_launches"], 1)
+    steps = st["steps"] / max(st["fs_launches"], 1)
+    return {"ms_per_launch": round(ms, 4), "steps_per_launch": round(steps),
+            "fs_steps_per_s": round(steps / (ms / 1e3), 1)}
+
+
 def replicas_barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
@@ -293,10 +354,33 @@ def init_ranks():
     return ws, rank, local, dev, R
 
 
+def run_only(args, dev, R):
+    """One companion measurement alone (for profiling and diagnostics): its
+    JSON object, not a bench line."""
+    import torch
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.zeros(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    name = args.only
+    if name == "os_sweep":
+        out = os_sweep_roofline(R, dev, args.os_sweeps)
+    elif name == "precision":
+        out = precision_check(R, dev, args.precision_n)
+    elif name == "batched":
+        out = batched_vs_fp64(R, dev, stream, flush, args.batch_lambdas, args.fp64_subset,
+                              args.batch_tol, args.ng, args.max_iter)
+    elif name == "config5":
+        out = config5_iteration(R, dev, stream, args.ng)
+    else:
+        raise SystemExit(f"unknown companion {name}")
+    print(json.dumps({"only": name, name: out}), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_1107_5719_gb300 import replicas as RP
     ws, rank, local, dev, R = init_ranks()
+    if args.only:
+        return run_only(args, dev, R)
     if args.workload.startswith("batch"):
         return run_batch(args, ws, rank, dev, R)
     p = make_problem(args.workload)
@@ -314,6 +398,12 @@ def run_ours(args):
     vd_per_s = RP.sum_over_ranks(st["fs_launches"] * pairs) / (total_ms / 1e3)
     steps_per_s = RP.sum_over_ranks(st["steps"]) / (total_ms / 1e3)
 
+    # measured arithmetic peaks (FMA chains), reported beside the unit-count peaks
+    try:
+        probe = R.rt_probe_peaks(dev.index)
+    except R.RtError:
+        probe = {"fp64_tflops": None, "fp32_tflops": None}
+
     # dominant kernel: the FP64 formal-solution march
     fs_ms = st["fs_ms"] / max(st["fs_launches"], 1)
     steps_per_launch = st["steps"] / max(st["fs_launches"], 1)
@@ -322,37 +412,52 @@ def run_ours(args):
                 "achieved": round(achieved, 4), "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(achieved / PEAK_FP64_TFLOPS, 4),
                 "traffic": TRAFFIC_FS64_SLAB65 if args.workload == "slab65" else None,
-                "peak_source": "recipe FP64 figure (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "peak_source": "unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz",
+                "peak_measured": round(probe["fp64_tflops"], 4) if probe["fp64_tflops"] else None,
+                "frac_of_measured": round(achieved / probe["fp64_tflops"], 4)
+                if probe["fp64_tflops"] else None,
+                "peak_measured_source": "rt_probe_peaks: register-resident DFMA chains on every "
+                                        "SM, CUDA events",
                 "flops_per_step": FLOPS_PER_STEP_FP64,
                 "steps_per_launch": round(steps_per_launch),
                 "ms_per_launch": round(fs_ms, 4),
                 "share_of_step": round(st["fs_ms"] / my_ms, 4)}
 
-    # the FP32-sweep form of the same workload on the same GPU
+    # the FP32-sweep form of the same workload on the same GPU: converged
+    # solves of the form as created (double-float finish from delta < 1e-6),
+    # at the headline's tolerance; the march's own rate from FP32-only
+    # formal solutions (the finishing stage runs the double-float march)
     fp32 = None
     if args.fp32_steps > 0:
-        tol32 = max(p.tol, TOL_FP32)
         r32 = timed_solves(R, p, R.RT_FP32_SWEEP, dev, stream, flush, 1, args.fp32_steps,
-                           args.max_iter, ng=args.ng, ng_min=NG_MIN_FP32, tol=tol32)
+                           args.max_iter, ng=args.ng, ng_min=NG_MIN_FP32, tol=p.tol)
         st32 = r32["stats"]
         ms32 = float(sum(r32["times"]))
-        fs32_ms = st32["fs_ms"] / max(st32["fs_launches"], 1)
+        m32 = march_rate(R, p, R.RT_FP32_SWEEP, dev, stream)
         fp32 = {"value": round(RP.weak_throughput(args.fp32_steps, ms32)[0], 6), "unit": "solves/s",
+                "form": "FP32 sweep + double-float finish from delta < 1e-6 (the default)",
                 "ms_per_step": round(ms32 / args.fp32_steps, 3),
-                "iters_per_solve": st32["fs_launches"] / args.fp32_steps,
-                "march_steps_per_s": round(st32["steps"] / (ms32 / 1e3), 1),
-                "ms_per_fs_launch": round(fs32_ms, 4),
-                "fs_steps_per_s": round(st32["steps"] / (st32["fs_ms"] / 1e3), 1),
-                "tol": tol32,
+                "iters_per_solve": st32["iterations"] / args.fp32_steps,
+                "march_launches_per_solve": st32["fs_launches"] / args.fp32_steps,
+                "tol": p.tol,
                 "max_rel_dev_from_fp64_J": float(np.max(np.abs(r32["J"] - r64["J"]) / r64["J"])),
-                "speedup_vs_fp64": round(my_ms / args.steps / (ms32 / args.fp32_steps), 3)}
-        if st32["fs_ms"] > 0:
-            ach32 = FLOPS_PER_STEP_FP32 * st32["steps"] / (st32["fs_ms"] / 1e3) / 1e12
-            fp32["roofline"] = {"kernel": "k_fs32d (FP32-sweep march)", "bound": "alu",
-                                "achieved": round(ach32, 3), "peak": PEAK_FP32_TFLOPS,
-                                "unit": "TFLOP/s", "frac": round(ach32 / PEAK_FP32_TFLOPS, 4),
-                                "flops_per_step": FLOPS_PER_STEP_FP32,
-                                "note": "ncu: limited by L1 throughput, not the FP32 pipe"}
+                "speedup_vs_fp64": round(my_ms / args.steps / (ms32 / args.fp32_steps), 3),
+                "march": m32}
+        ach32 = FLOPS_PER_STEP_FP32 * m32["steps_per_launch"] / (m32["ms_per_launch"] / 1e3) / 1e12
+        fp32["roofline"] = {"kernel": "k_fs32d (FP32-sweep march)", "bound": "alu",
+                            "achieved": round(ach32, 3), "peak": PEAK_FP32_TFLOPS,
+                            "unit": "TFLOP/s", "frac": round(ach32 / PEAK_FP32_TFLOPS, 4),
+                            "flops_per_step": FLOPS_PER_STEP_FP32,
+                            "peak_source": "unit counts and clock: 152 SMs x 128 lanes x 2 "
+                                           "flops x 2.07 GHz",
+                            "peak_measured": round(probe["fp32_tflops"], 3)
+                            if probe["fp32_tflops"] else None,
+                            "frac_of_measured": round(ach32 / probe["fp32_tflops"], 4)
+                            if probe["fp32_tflops"] else None,
+                            "traffic": TRAFFIC_FS32_SLAB65,
+                            "note": "ncu: bound by instruction issue (77% of issue slots; "
+                                    "86 thread instructions per step, 48 of them FP32 "
+                                    "arithmetic), L1 55%"}
 
     # the double-float form (FP64-accurate march on the FP32 pipes)
     df64 = None
@@ -424,86 +529,18 @@ def run_ours(args):
                 "median_rel_diff_from_linear_J": float(np.median(np.abs(rpa["J"] - r64["J"]) / r64["J"])),
                 "note": "different discretisation (second-order source)"}
 
-    # precision form at eps = 1e-6 (strong scattering) on a 9x9x129 column
-    # with 32x8 directions: FP32 sweep to its tolerance, then double-float
-    # iterations with Ng from that J, each against the FP64 fixed point
-    precision = None
-    if args.precision_check:
-        import time as _t
-        from paper_1107_5719_gb300 import workloads as W
-        pc = W.slab_precision(n=9, nzz=129, n_theta=32, n_phi=8)
-
-        def _solve(prec, tol, ngmin=0.0, then=None):
-            ctx = R.rt_create(dev.index, prec)
-            try:
-                R.rt_set_grid(ctx, pc.nx, pc.ny, pc.nz, pc.dx, pc.dy, pc.dz)
-                R.rt_set_boundary(ctx, pc.top_bc, pc.bottom_bc)
-                R.rt_set_quadrature(ctx, pc.mu, pc.phi, pc.w)
-                R.rt_set_opacity(ctx, pc.chi)
-                R.rt_set_epsilon(ctx, pc.eps)
-                R.rt_set_planck(ctx, pc.B)
-                R.rt_set_ng(ctx, 4, ngmin)
-                t0 = _t.time()
-                r = R.rt_solve(ctx, (pc.nz, pc.ny, pc.nx), tol=tol, max_iter=5000)
-                out = [(r, _t.time() - t0)]
-                if then is not None:
-                    R.rt_set_precision(ctx, then[0])
-                    R.rt_set_ng(ctx, 4, 0.0)
-                    t0 = _t.time()
-                    out.append((R.rt_solve(ctx, (pc.nz, pc.ny, pc.nx), tol=then[1], max_iter=500),
-                                _t.time() - t0))
-                return out
-            finally:
-                R.rt_destroy(ctx)
-
-        (c64, t64), = _solve(R.RT_FP64, 1e-11)
-        (c32, t32), (cfin, tfin) = _solve(R.RT_FP32_SWEEP, TOL_FP32, NG_MIN_FP32,
-                                          then=(R.RT_DF64, 1e-8))
-        err = lambda r: float(np.max(np.abs(r["J"] - c64["J"]) / c64["J"]))
-        precision = {"workload": "9x9x129 column, strong-scattering chi law, eps = 1e-6, "
-                                 "32x8 directions",
-                     "fp64": {"iters": c64["iters"], "s": round(t64, 2), "tol": 1e-11},
-                     "fp32_sweep": {"iters": c32["iters"], "s": round(t32, 2), "tol": TOL_FP32,
-                                    "max_rel_err_vs_fp64": err(c32)},
-                     "fp32_then_df64": {"iters": cfin["iters"], "s": round(tfin, 2), "tol": 1e-8,
-                                        "max_rel_err_vs_fp64": err(cfin)},
-                     "target": 1e-6}
-
-    # FP32-batched form on the same GPU: a batch of wavelength points (each
-    # its own chi scale and eps) in one fused launch per outer iteration
+    budget = Budget(args.budget_s)
+    precision = precision_check(R, dev, args.precision_n) if args.precision_n > 0 else None
+    os_sweep = os_sweep_roofline(R, dev, args.os_sweeps) if args.os_sweeps > 0 else None
     batched = None
-    if args.batch_lambdas > 0:
-        from paper_1107_5719_gb300 import workloads as W
-        probs = W.batch_65(n_lambda=args.batch_lambdas)
-        bt = R.rt_batch_create(probs, device=dev.index, precision=R.RT_FP32_SWEEP)
-        try:
-            R.rt_batch_set_ng(bt, args.ng, NG_MIN_FP32)
-            R.rt_batch_set_stream(bt, stream)
-            R.rt_batch_solve(bt, len(probs), tol=TOL_FP32, max_iter=2)     # warm-up
-            R.rt_batch_reset(bt, rebuild_lstar=True)
-            R.rt_batch_reset_stats(bt)
-            R.rt_batch_set_profiling(bt, True)
-            with torch.cuda.stream(stream):
-                flush_l2(flush)
-            stream.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rb = R.rt_batch_solve(bt, len(probs), tol=TOL_FP32, max_iter=args.max_iter)
-            e1.record(stream)
-            e1.synchronize()
-            msb = e0.elapsed_time(e1)
-            stb = R.rt_batch_get_stats(bt)
-        finally:
-            R.rt_batch_destroy(bt)
-        vb = RP.weak_throughput(len(probs), msb)[0]
-        batched = {"value": round(vb, 6), "unit": "wavelength-solves/s",
-                   "workload": f"{len(probs)} wavelengths x 65^3, chi x 10^(-2+4U), "
-                               f"eps 10^(-5+5U), 32x32 directions, tol {TOL_FP32:g}",
-                   "converged": bool(rb["converged"]), "s": round(msb / 1e3, 2),
-                   "iters_mean": float(np.mean(rb["iters"])), "iters_max": int(np.max(rb["iters"])),
-                   "fused_fs_ms_per_launch": round(stb["fs_ms"] / max(stb["fs_launches"], 1), 3),
-                   "vs_fp64_plain": round(vb / solves_per_s, 3)}
+    if args.batch_lambdas > 0 and budget.left() > 0:
+        batched = batched_vs_fp64(R, dev, stream, flush, args.batch_lambdas, args.fp64_subset,
+                                  args.batch_tol, args.ng, args.max_iter)
+    config5 = None
+    if args.config5 and budget.left() > 0:
+        config5 = config5_iteration(R, dev, stream, args.ng)
+    elif args.config5:
+        config5 = {"skipped": f"time budget of {args.budget_s:.0f} s used up"}
 
     e2e = None
     if args.e2e_steps > 0:
@@ -533,17 +570,275 @@ def run_ours(args):
         "parabolic_source": para,
         "precision_eps1e-6": precision,
         "fp32_batched": batched,
+        "os_sweep": os_sweep,
+        "config5_iteration": config5,
+        "measured_peaks": probe,
         "gpu_launches": int(st["launches"]),
         "clocks": r64["clocks"],
         "e2e": e2e,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(p, fs_per_solve, st["jacobi_launches"] / args.steps,
-                                            args.cpu_seconds)
+        counts = ORACLE_COUNTS.get(args.workload, ORACLE_COUNTS["slab65"])
+        line["cpu_baseline"] = cpu_baseline(p, counts["iters"], counts["sweeps"], args.cpu_seconds)
+        line["cpu_baseline"]["extrapolated"] = True
     if ws > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+class Budget:
+    """Wall-clock budget of the companion measurements (seconds since the
+    bench started); the last ones are skipped, and say so, when it is used
+    up."""
+
+    T0 = time.time()
+
+    def __init__(self, seconds):
+        self.seconds = seconds
+
+    def left(self):
+        return self.seconds - (time.time() - Budget.T0)
+
+
+def _ctx_for(R, dev, p, precision):
+    ctx = R.rt_create(dev.index, precision)
+    R.rt_set_grid(ctx, p.nx, p.ny, p.nz, p.dx, p.dy, p.dz)
+    R.rt_set_boundary(ctx, p.top_bc, p.bottom_bc)
+    R.rt_set_quadrature(ctx, p.mu, p.phi, p.w)
+    R.rt_set_opacity(ctx, p.chi)
+    R.rt_set_epsilon(ctx, p.eps)
+    R.rt_set_planck(ctx, p.B)
+    return ctx
+
+
+def precision_check(R, dev, n=33):
+    """Precision form at eps = 1e-6 (strong scattering): n x n x 129 slab
+    with the 64 x 64 directions of the 129^3 configuration.  The FP32-sweep
+    context as created (double-float finish from delta < 1e-6, Ng every 4)
+    is solved to tol 1e-8; the reference continues the same iteration in
+    double-float (FP64-accurate march) to delta < 1e-9, i.e. to the FP64
+    fixed point within ~70 x 1e-9 at this eps."""
+    from paper_1107_5719_gb300 import workloads as W
+    pc = W.slab_precision(n=n, nzz=129, n_theta=64, n_phi=64)
+    shape = (pc.nz, pc.ny, pc.nx)
+    ctx = _ctx_for(R, dev, pc, R.RT_FP32_SWEEP)
+    try:
+        R.rt_set_ng(ctx, 4, NG_MIN_FP32)
+        t0 = time.time()
+        r = R.rt_solve(ctx, shape, tol=1e-8, max_iter=5000)
+        t32 = time.time() - t0
+        d = np.asarray(r["deltas"])
+        n32 = int(np.argmax(d < 1e-6)) + 1 if np.any(d < 1e-6) else int(r["iters"])
+        R.rt_set_precision(ctx, R.RT_DF64)
+        R.rt_set_ng(ctx, 4, 0.0)
+        t0 = time.time()
+        rr = R.rt_solve(ctx, shape, tol=1e-9, max_iter=3000)
+        tref = time.time() - t0
+    finally:
+        R.rt_destroy(ctx)
+    err = np.abs(r["J"] - rr["J"]) / rr["J"]
+    return {"workload": f"{n}x{n}x129 slab, strong-scattering chi law (tau 1e-4..1e4), eps = 1e-6, "
+                        "B = 1, 64x64 directions",
+            "fp32_default": {"form": "FP32 sweep, double-float finish from delta < 1e-6, Ng every 4",
+                             "tol": 1e-8, "converged": bool(r["converged"]), "iters": int(r["iters"]),
+                             "fp32_iters": n32, "double_float_iters": int(r["iters"]) - n32,
+                             "s": round(t32, 2), "max_rel_err": float(err.max()),
+                             "median_rel_err": float(np.median(err))},
+            "reference": {"form": "same iteration continued in double-float to delta < 1e-9",
+                          "iters": int(rr["iters"]), "converged": bool(rr["converged"]),
+                          "s": round(tref, 2)},
+            "target": 1e-6}
+
+
+def os_sweep_roofline(R, dev, sweeps=200):
+    """Operator-splitting Jacobi sweep (k_jacobi) alone: 232 algorithmic
+    bytes per voxel and sweep (26 coefficients, r and J read, J written;
+    J's stencil neighbours come from cache), timed over `sweeps` sweeps with
+    CUDA events (host-driven sweeps, no graph), on the 65^3 slab (its 64 MB
+    per sweep stays in the 129 MB L2) and on 129^3 (498 MB per sweep, from
+    HBM).  Directions do not enter the sweep: 2x2 directions build Lambda*."""
+    import torch
+    from paper_1107_5719_gb300 import workloads as W
+    out = {}
+    for name, n in (("slab65", 65), ("slab129", 129)):
+        p = W.slab_65(n=n, n_theta=2, n_phi=2)
+        ctx = _ctx_for(R, dev, p, R.RT_FP64)
+        try:
+            R.rt_set_graphs(ctx, 0)
+            Bt = torch.from_numpy(p.B).to(dev)
+            Jfs, Jn = torch.empty_like(Bt), torch.empty_like(Bt)
+            R.rt_formal_solution_dev(ctx, Bt, Jfs, None)
+            R.rt_os_step_dev(ctx, Jfs, Bt, Jn, 0.0, 20)
+            torch.cuda.synchronize()
+            R.rt_reset_stats(ctx)
+            R.rt_set_profiling(ctx, True)
+            R.rt_os_step_dev(ctx, Jfs, Bt, Jn, 0.0, sweeps)
+            st = R.rt_get_stats(ctx)
+        finally:
+            R.rt_destroy(ctx)
+        ms = st["jacobi_ms"] / max(st["jacobi_launches"], 1)
+        gbs = 232.0 * p.nvox / (ms / 1e3) / 1e9
+        out[name] = {"voxels": p.nvox, "bytes_per_sweep": 232 * p.nvox, "ms_per_sweep": round(ms, 5),
+                     "achieved_GBps": round(gbs, 1),
+                     "frac_of_hbm": round(gbs / MEASURED_HBM_GBS, 4)}
+    tfl = 2 * 26 * out["slab129"]["voxels"] / (out["slab129"]["ms_per_sweep"] / 1e3) / 1e12
+    out["roofline"] = {"kernel": "k_jacobi (operator-splitting sweep, FP64), 129^3",
+                       "bound": "alu", "achieved": round(tfl, 4), "peak": PEAK_FP64_TFLOPS,
+                       "unit": "TFLOP/s", "frac": round(tfl / PEAK_FP64_TFLOPS, 4),
+                       "flops_per_voxel": 52, "traffic": TRAFFIC_JACOBI_129,
+                       "hbm_GBps": out["slab129"]["achieved_GBps"],
+                       "hbm_frac": out["slab129"]["frac_of_hbm"],
+                       "peak_source": "unit counts and clock (FP64); HBM: measured copy "
+                                      "bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                       "note": "ncu: FP64 pipe 91% busy (26 stencil FMAs and the FP64 "
+                               "division of the convergence test, ~41 FP64 instructions per "
+                               "voxel), DRAM traffic = the algorithmic 232 B per voxel, so "
+                               "the FP64 pipe, not HBM, bounds the sweep on this GPU; slab65's "
+                               "sweep is L2-resident"}
+    return out
+
+
+def batched_vs_fp64(R, dev, stream, flush, nl, nsub, tol, ng, max_iter):
+    """FP32-batched form against FP64 plain on the same GPU.  The batch: all
+    nl wavelengths of the 512-point configuration (65^3, 32x32 directions,
+    chi x 10^(-2+4U), eps 10^(-5+5U) per wavelength), FP32 sweep with the
+    default double-float finish, tol 1e-8, one fused march launch per outer
+    iteration and the OS step of all active wavelengths as one CUDA graph.
+    FP64 plain: nsub wavelengths spread evenly over the batch (every
+    nl/nsub-th), one rt_solve each at the same tolerance; the ratio is the
+    batch's wavelength-solves/s over FP64 plain's on that subset, and each
+    subset wavelength's batch J is compared with its FP64 J."""
+    import torch
+    from paper_1107_5719_gb300 import workloads as W
+    probs = W.batch_65(n_lambda=nl)
+    t0 = time.time()
+    bt = R.rt_batch_create(probs, device=dev.index, precision=R.RT_FP32_SWEEP)
+    t_create = time.time() - t0
+    sub = list(range(0, nl, max(1, nl // nsub)))[:nsub]
+    try:
+        R.rt_batch_set_ng(bt, ng, NG_MIN_FP32)
+        R.rt_batch_set_stream(bt, stream)
+        R.rt_batch_solve(bt, len(probs), tol=tol, max_iter=1)              # warm-up
+        R.rt_batch_reset(bt, rebuild_lstar=True)
+        R.rt_batch_reset_stats(bt)
+        R.rt_batch_set_profiling(bt, True)
+        with torch.cuda.stream(stream):
+            flush_l2(flush)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(smi_id(dev)) as clk:
+            e0.record(stream)
+            rb = R.rt_batch_solve(bt, len(probs), tol=tol, max_iter=max_iter)
+            e1.record(stream)
+            e1.synchronize()
+        msb = e0.elapsed_time(e1)
+        stb = R.rt_batch_get_stats(bt)
+        Jb = {i: R.rt_batch_get_J(bt, i, (probs[i].nz, probs[i].ny, probs[i].nx)) for i in sub}
+    finally:
+        R.rt_batch_destroy(bt)
+    vb = len(probs) / (msb / 1e3)
+    # FP64 plain on the subset
+    per, ms64 = [], 0.0
+    for i in sub:
+        p = probs[i]
+        ctx = _ctx_for(R, dev, p, R.RT_FP64)
+        try:
+            if ng:
+                R.rt_set_ng(ctx, ng)
+            R.rt_set_stream(ctx, stream)
+            e0.record(stream)
+            r = R.rt_solve(ctx, (p.nz, p.ny, p.nx), tol=tol, max_iter=max_iter)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+        finally:
+            R.rt_destroy(ctx)
+        ms64 += ms
+        per.append({"lambda": i, "chi_scale_eps": p.name.split(": ")[1],
+                    "fp64_iters": int(r["iters"]), "fp64_s": round(ms / 1e3, 2),
+                    "batch_iters": int(rb["iters"][i]),
+                    "max_rel_err_vs_fp64": float(np.max(np.abs(Jb[i] - r["J"]) / r["J"]))})
+    v64 = len(sub) / (ms64 / 1e3)
+    march_steps = stb["steps"]
+    ach = FLOPS_PER_STEP_FP32 * march_steps / (stb["fs_ms"] / 1e3) / 1e12 if stb["fs_ms"] else None
+    return {"value": round(vb, 6), "unit": "wavelength-solves/s",
+            "workload": f"{nl} wavelengths x 65^3, chi x 10^(-2+4U), eps 10^(-5+5U), 32x32 directions",
+            "form": "FP32 sweep + double-float finish from delta < 1e-6, FP64 J/Lambda*/OS",
+            "tol": tol, "converged": bool(rb["converged"]), "s": round(msb / 1e3, 2),
+            "create_s": round(t_create, 1),
+            "iters_mean": float(np.mean(rb["iters"])), "iters_max": int(np.max(rb["iters"])),
+            "outer_iterations": int(stb["iterations"]),
+            "host_syncs_per_iteration": round(stb["host_syncs"] / max(stb["iterations"], 1), 3),
+            "fused_march_s": round(stb["fs_ms"] / 1e3, 2),
+            "os_graph_s": round(stb["jacobi_ms"] / 1e3, 2),
+            "march_steps_per_s": round(march_steps / (stb["fs_ms"] / 1e3), 1) if stb["fs_ms"] else None,
+            "march_roofline": {"bound": "alu", "achieved": round(ach, 3) if ach else None,
+                               "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                               "frac": round(ach / PEAK_FP32_TFLOPS, 4) if ach else None,
+                               "note": "all march launches of the solve (fused FP32 and the "
+                                       "double-float finish), 45 FP32 flops per executed step"},
+            "clocks": clk.summary(),
+            "fp64_plain_subset": {"lambdas": sub, "value": round(v64, 6), "unit": "wavelength-solves/s",
+                                  "s": round(ms64 / 1e3, 2), "per_lambda": per},
+            "vs_fp64_plain_same_wavelengths": round(vb / v64, 3),
+            "max_rel_err_vs_fp64": max(q["max_rel_err_vs_fp64"] for q in per),
+            "target": 1e-6}
+
+
+def config5_iteration(R, dev, stream, ng):
+    """The uneven batch at its configured 64x64 directions (8 x 257^2x129,
+    24 x 129^3, 32 x 65^3; strong-scattering chi law x 10^(-2+4U), eps
+    10^(-5+5U)): ONE outer iteration of the FP32-batched solve from J = B
+    (the fused march over all 64 problems, Lambda* of every problem, the OS
+    graph, the convergence tests), timed with CUDA events.  A converged
+    solve is extrapolated from it with the iteration counts measured on the
+    same batch at 16x8 directions and says so."""
+    import torch
+    from paper_1107_5719_gb300 import workloads as W
+    t0 = time.time()
+    probs = W.batch_uneven()
+    bt = R.rt_batch_create(probs, device=dev.index, precision=R.RT_FP32_SWEEP)
+    t_create = time.time() - t0
+    try:
+        R.rt_batch_set_ng(bt, ng, NG_MIN_FP32)
+        R.rt_batch_set_stream(bt, stream)
+        R.rt_batch_reset_stats(bt)
+        R.rt_batch_set_profiling(bt, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        R.rt_batch_solve(bt, len(probs), tol=1e-8, max_iter=1)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = R.rt_batch_get_stats(bt)
+    finally:
+        R.rt_batch_destroy(bt)
+    ach = FLOPS_PER_STEP_FP32 * st["steps"] / (st["fs_ms"] / 1e3) / 1e12
+    # iterations per class measured at 16x8 directions (FP32 sweep, double-float
+    # finish from delta < 1e-6, tol 1e-8): mean 293 / 134 / 35
+    iters = {257: 293, 129: 134, 65: 35}
+    w = [p.nvox * p.nz for p in probs]
+    it_w = sum(wi * iters[p.nx] for wi, p in zip(w, probs)) / sum(w)
+    march_ms = st["fs_ms"]
+    return {"workload": "8 x 257x257x129 + 24 x 129^3 + 32 x 65^3, 64x64 directions, "
+                        "chi x 10^(-2+4U), eps 10^(-5+5U)",
+            "voxels": int(sum(p.nvox for p in probs)), "create_s": round(t_create, 1),
+            "first_iteration_ms": round(ms, 1), "fused_march_ms": round(march_ms, 1),
+            "os_graph_ms": round(st["jacobi_ms"], 1),
+            "lambda_star_and_rest_ms": round(ms - march_ms - st["jacobi_ms"], 1),
+            "march_steps": int(st["steps"]),
+            "march_steps_per_s": round(st["steps"] / (march_ms / 1e3), 1),
+            "march_roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": PEAK_FP32_TFLOPS,
+                               "unit": "TFLOP/s", "frac": round(ach / PEAK_FP32_TFLOPS, 4)},
+            "converged_s_extrapolated": round(march_ms / 1e3 * it_w, 0),
+            "extrapolation": "fused march time x the march-work-weighted mean of the iteration "
+                             "counts measured at 16x8 directions (293 / 134 / 35 for the three "
+                             "sizes); EXTRAPOLATED, not run"}
+
 
 
 def run_batch(args, ws, rank, dev, R):
@@ -653,28 +948,55 @@ def cpu_baseline(p, iters, sweeps, seconds, seed=0):
                       f"scaled to {iters:.0f} formal solutions and {sweeps:.0f} sweeps per solve"}
 
 
+def oracle_full_solve(p, ng):
+    """One full converged oracle solve (Ng every `ng` iterations) on this
+    host's cores: seconds, iterations, Jacobi sweeps."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.solve(p, tol=p.tol, max_iter=1000, ng_period=ng, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"s": round(dt, 2), "solves_per_s": 1.0 / dt, "iters": int(r["iters"]),
+            "sweeps": int(np.sum(r["sweeps"])), "converged": bool(r["converged"]), "cores": cores}
+
+
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
+    """Reference arm: the FP64 CPU oracle, as it stands, on this host's cores.
+
+    Every step is one bounded sample of the bench workload (J at sampled
+    voxels with all directions, plus one full-grid Jacobi sweep), timed;
+    the line's value extrapolates the sampled costs to one converged solve
+    with the oracle's own iteration and sweep counts (ORACLE_COUNTS, from
+    full oracle solves on the GPU machine's cores) and says so
+    ("extrapolated": true); ms_per_step is the sample's own wall time.  A
+    full converged oracle solve of the 17^3 slab is run and timed too."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     p = make_problem(args.workload, args.lambdas)
-    iters = args.ref_iters
-    sweeps = args.ref_sweeps
-    vals = []
+    counts = ORACLE_COUNTS.get(args.workload, ORACLE_COUNTS["slab65"])
+    vals, walls = [], []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(p, iters, sweeps, args.cpu_seconds / 2, seed=i)
+        t0 = time.perf_counter()
+        cb = cpu_baseline(p, counts["iters"], counts["sweeps"], args.cpu_seconds / 2, seed=i)
         if i >= args.warmup:
             vals.append(cb["value"])
+            walls.append(time.perf_counter() - t0)
     v = float(np.mean(vals))
+    full17 = oracle_full_solve(make_problem("slab17"), args.ng)
     line = {"impl": "reference", "metric": "converged J solves/s", "value": v, "unit": "solves/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": round(1e3 * float(np.mean(walls)), 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "extrapolated": True,
             "config": {"workload": args.workload + ": " + WORKLOADS[args.workload]["desc"],
                        "nx": p.nx, "ny": p.ny, "nz": p.nz, "ndir": p.ndir, "tol": p.tol},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cb["cores"],
-                             "kind": "oracle", "sample": cb["sample"]},
+                             "kind": "oracle", "sample": cb["sample"] + " (each step one such "
+                             "sample; value extrapolated from the samples)"},
+            "oracle_counts": counts,
+            "full_solve_slab17": full17,
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -693,21 +1015,32 @@ def main():
     ap.add_argument("--df64-steps", type=int, default=2)
     ap.add_argument("--sc-steps", type=int, default=2)
     ap.add_argument("--para-steps", type=int, default=1)
-    ap.add_argument("--batch-lambdas", type=int, default=16,
+    ap.add_argument("--batch-lambdas", type=int, default=512,
                     help="wavelengths of the FP32-batched companion (0 = skip)")
-    ap.add_argument("--no-precision-check", dest="precision_check", action="store_false",
-                    help="skip the eps = 1e-6 precision comparison")
+    ap.add_argument("--fp64-subset", type=int, default=8,
+                    help="wavelengths of the batch solved in FP64 plain for the same-wavelength "
+                         "ratio and the per-wavelength error")
+    ap.add_argument("--batch-tol", type=float, default=1e-8,
+                    help="outer tolerance of the batched companion and its FP64 subset")
+    ap.add_argument("--precision-n", type=int, default=33,
+                    help="horizontal size of the eps = 1e-6 precision check (n x n x 129, "
+                         "64x64 directions; 0 = skip)")
+    ap.add_argument("--no-precision-check", dest="precision_n", action="store_const", const=0,
+                    help="skip the eps = 1e-6 precision check")
+    ap.add_argument("--os-sweeps", type=int, default=200,
+                    help="sweeps timed for the operator-splitting roofline (0 = skip)")
+    ap.add_argument("--config5", type=int, default=1,
+                    help="time one outer iteration of the uneven batch at 64x64 directions (0 = skip)")
+    ap.add_argument("--only", choices=["os_sweep", "precision", "batched", "config5"],
+                    help="run one companion measurement alone and print its JSON object "
+                         "(profiling and diagnostics; not a bench line)")
+    ap.add_argument("--budget-s", type=float, default=1500.0,
+                    help="wall-clock seconds after which the remaining companions are skipped")
     ap.add_argument("--ng", type=int, default=4,
                     help="Ng acceleration period of the outer iteration (0 = off)")
     ap.add_argument("--lambdas", type=int, default=512, help="wavelengths of the batch workload")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-iters", type=float, default=18.0,
-                    help="outer iterations per solve assumed by the reference arm (the GPU "
-                         "solve of slab65 with Ng period 4 takes 18)")
-    ap.add_argument("--ref-sweeps", type=float, default=764.0,
-                    help="Jacobi sweeps per solve assumed by the reference arm (764 in the "
-                         "GPU solve of slab65 with Ng period 4)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -293,6 +293,10 @@ int rt_set_os_method(rt_ctx *ctx, int method);
  * is bit-reproducible and independent of this knob.  `groups` (1..8) sets
  * how many thread blocks share the slots of one voxel tile; 0 = auto. */
 int rt_set_direction_groups(rt_ctx *ctx, int groups);
+/* Tuning: threads per block of the FP32-sweep march, 64, 128 or 256 (0 =
+ * default, 128).  Each size keeps 768 resident threads per SM (the same
+ * registers per thread); J does not depend on it.  RT_EINVAL otherwise. */
+int rt_set_block_threads(rt_ctx *ctx, int threads);
 
 /* Tuning: relative transmission cutoff.  The march along a characteristic
  * stops once T * max(|S|, |I_bc|) <= cut * |I| (the rest can change I by
@@ -308,6 +312,15 @@ int rt_set_cutoff(rt_ctx *ctx, double cut);
  * on `stream`. */
 int rt_segment_weights(int precision, long long n, const double *x, double *w_cur,
                        double *w_up, double *e, void *stream);
+
+/* Measured arithmetic peaks of `device` (diagnostics; the paper has no
+ * counterpart): dense FP64 and FP32 fused multiply-add throughput in
+ * TFLOP/s (an FMA counts 2 flops), from register-resident FMA chains that
+ * fill every SM, timed with CUDA events at the clocks the GPU runs at.
+ * These are the denominators of the formal-solution marches' rooflines,
+ * which are bound by arithmetic, not memory.  Allocates and frees a small
+ * device buffer; synchronises the device. */
+int rt_probe_peaks(int device, double *fp64_tflops, double *fp32_tflops);
 
 /* Allocation-free formal solution.
  *
@@ -334,9 +347,12 @@ int rt_segment_weights(int precision, long long n, const double *x, double *w_cu
  * thread's current device and is enqueued on `stream`; the call returns
  * without waiting for it (only the small quadrature copy from host memory
  * is synchronous).  Returns RT_ESCRATCH, before touching the GPU, when
- * 64*N + 88*ndir*nz + 72*ndir bytes (plus up to 2 KiB of alignment) exceed
- * the scratch; RT_EINVAL for invalid arguments (device data is not
- * inspected); RT_ECUDA if a CUDA call fails.
+ * 64*N + 88*ndir*nz + 88*ndir + 8 bytes (plus up to 2.5 KiB of alignment
+ * padding) exceed the scratch: per voxel the eight direction-slot partial
+ * sums of J, per (direction, plane) the lattice offset and three tables of
+ * bilinear weights, per direction mu, phi, w and the direction record; the
+ * 65^3 slab with 1024 directions takes 23.5 MB.  RT_EINVAL for invalid
+ * arguments (device data is not inspected); RT_ECUDA if a CUDA call fails.
  *
  * The first call on a device looks up the device address of the scratch
  * array (once per device, with that device current); make that first call
@@ -403,6 +419,8 @@ int rt_batch_get_J(rt_batch *batch, int p, double *J);
 int rt_batch_get_J_dev(rt_batch *batch, int p, double *J);
 /* As rt_set_direction_groups, for the fused launch (0 = auto). */
 int rt_batch_set_direction_groups(rt_batch *batch, int groups);
+/* As rt_set_block_threads, for the fused FP32 launch. */
+int rt_batch_set_block_threads(rt_batch *batch, int threads);
 /* on != 0 (the default): every outer iteration runs the operator-splitting
  * solves of all active problems (Sect. 2.3) as ONE CUDA graph, one
  * independent branch per problem (right-hand side, a device-side loop of

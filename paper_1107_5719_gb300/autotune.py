@@ -1,15 +1,21 @@
 """Launch-shape autotuner for the formal-solution march.
 
-The march's work per voxel is split into 8 fixed direction slots; the one
-free launch parameter is how many thread blocks share the slots of a voxel
-tile ("direction groups", 1, 2, 4 or 8).  More groups give more, shorter
-blocks (better balance of the depth-dependent characteristic lengths and
-of the transmission cutoff), fewer groups give fewer blocks that re-read
-less.  J does not depend on the choice (fixed summation order), so the
-tuner only times it: each candidate runs a few formal solutions with CUDA
-events on the launching stream (the library's profiling counters), and the
-fastest mean wins.  Results are cached in a JSON file keyed by grid shape,
-direction count, precision and SM count.
+The march's work per voxel is split into 8 fixed direction slots.  Free
+launch parameters: how many thread blocks share the slots of a voxel tile
+("direction groups", 1, 2, 4 or 8) and, for the FP32-sweep march, the
+threads per block (64, 128 or 256: the tile width, at the same 768 resident
+threads per SM).  More groups give more, shorter blocks (better balance of
+the depth-dependent characteristic lengths and of the transmission cutoff),
+fewer groups give fewer blocks that re-read less; narrower blocks give a
+finer last wave.  J does not depend on either choice (fixed summation
+order), so the tuner only times them: each candidate runs a few formal
+solutions (or batch iterations) with CUDA events on the launching stream
+(the library's profiling counters), and the fastest mean wins.  Results are
+cached in a JSON file keyed by grid shape, direction count, precision and
+SM count (and the batch size for batches).  Every direction sums into its
+slot whatever its sign, so each thread already marches both members of a
+mirror pair mu, -mu (k0 and nz-1-k0 steps): the per-thread work is balanced
+across planes without a separate pairing knob.
 """
 
 from __future__ import annotations
@@ -19,6 +25,8 @@ import os
 from typing import Callable, Dict, Iterable, Optional, Tuple
 
 CANDIDATES = (1, 2, 4, 8)
+# (groups, threads per block) of the FP32-sweep march
+CANDIDATES_FP32 = tuple((g, t) for t in (64, 128, 256) for g in (1, 2, 4, 8))
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rt3d_autotune.json")
 
 
@@ -45,34 +53,53 @@ def save_cache(path: str, data: Dict[str, dict]) -> None:
     os.replace(tmp, path)
 
 
-def pick(timings: Dict[int, float]) -> int:
-    """Fastest candidate; ties go to fewer groups (fewer blocks)."""
+def pick(timings: Dict) -> object:
+    """Fastest candidate; ties go to the smaller one (fewer groups, then
+    fewer threads per block)."""
     return min(timings, key=lambda g: (timings[g], g))
 
 
-def tune(key: str, time_candidate: Callable[[int], float],
-         candidates: Iterable[int] = CANDIDATES, cache_path: Optional[str] = DEFAULT_CACHE,
-         refresh: bool = False) -> Tuple[int, Dict[int, float]]:
-    """Return (best groups, {groups: ms}) for `key`, from the cache unless
-    `refresh`; `time_candidate(g)` returns the mean ms of the march with g
-    groups."""
+def _enc(c):
+    """Cache form of a candidate: an int, or "groups x threads"."""
+    return "x".join(str(v) for v in c) if isinstance(c, tuple) else int(c)
+
+
+def _dec(s):
+    s = str(s)
+    return tuple(int(v) for v in s.split("x")) if "x" in s else int(s)
+
+
+def tune(key: str, time_candidate: Callable, candidates: Iterable = CANDIDATES,
+         cache_path: Optional[str] = DEFAULT_CACHE, refresh: bool = False) -> Tuple[object, Dict]:
+    """Return (best candidate, {candidate: ms}) for `key`, from the cache
+    unless `refresh`; `time_candidate(c)` returns the mean ms of the march
+    with candidate c (a group count, or a (groups, threads) pair)."""
     cache = load_cache(cache_path) if cache_path else {}
     if not refresh and key in cache and "groups" in cache[key]:
-        return int(cache[key]["groups"]), {int(k): v for k, v in cache[key].get("ms", {}).items()}
-    timings = {int(g): float(time_candidate(int(g))) for g in candidates}
+        return _dec(cache[key]["groups"]), {_dec(k): v for k, v in cache[key].get("ms", {}).items()}
+    cands = [tuple(c) if isinstance(c, (tuple, list)) else int(c) for c in candidates]
+    timings = {c: float(time_candidate(c)) for c in cands}
     best = pick(timings)
     if cache_path:
-        cache[key] = {"groups": best, "ms": {str(k): v for k, v in timings.items()}}
+        cache[key] = {"groups": _enc(best), "ms": {str(_enc(k)): v for k, v in timings.items()}}
         save_cache(cache_path, cache)
     return best, timings
 
 
-def time_solver_fs(R, ctx, J_dev: int, groups: int, repeats: int = 2) -> float:
+def _apply(R, ctx, cand):
+    if isinstance(cand, tuple):
+        R.rt_set_direction_groups(ctx, cand[0])
+        R.rt_set_block_threads(ctx, cand[1])
+    else:
+        R.rt_set_direction_groups(ctx, cand)
+
+
+def time_solver_fs(R, ctx, J_dev: int, cand, repeats: int = 2) -> float:
     """Mean device time (ms) of the march kernel over `repeats` formal
-    solutions of context `ctx` with `groups` direction groups (J_dev: a
-    device buffer for the results)."""
+    solutions of context `ctx` with launch shape `cand` (J_dev: a device
+    buffer for the results)."""
     lib = R.load()
-    R.rt_set_direction_groups(ctx, groups)
+    _apply(R, ctx, cand)
     R.rt_set_profiling(ctx, True)
     R.rt_reset_stats(ctx)
     for _ in range(repeats):
@@ -85,16 +112,53 @@ def time_solver_fs(R, ctx, J_dev: int, groups: int, repeats: int = 2) -> float:
 
 
 def autotune_solver(solver, cache_path: Optional[str] = DEFAULT_CACHE, refresh: bool = False,
-                    repeats: int = 2) -> int:
-    """Tune and apply the direction groups of a ``rt3d.Solver``."""
+                    repeats: int = 2):
+    """Tune and apply the launch shape of a ``rt3d.Solver`` (direction
+    groups; for the FP32 sweep also threads per block)."""
     import torch
     from . import rt3d as R
     p = solver.p
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     key = cache_key(p.nx, p.ny, p.nz, p.ndir, solver.precision, sms)
+    cands = CANDIDATES_FP32 if solver.precision == R.RT_FP32_SWEEP else CANDIDATES
     buf = torch.empty((p.nz, p.ny, p.nx), dtype=torch.float64, device="cuda")
     R.load().rt_formal_solution_dev(solver.ctx, None, buf.data_ptr(), None)  # warm-up
-    best, _ = tune(key, lambda g: time_solver_fs(R, solver.ctx, buf.data_ptr(), g, repeats),
-                   CANDIDATES, cache_path, refresh)
-    R.rt_set_direction_groups(solver.ctx, best)
+    best, _ = tune(key, lambda c: time_solver_fs(R, solver.ctx, buf.data_ptr(), c, repeats),
+                   cands, cache_path, refresh)
+    _apply(R, solver.ctx, best)
+    return best
+
+
+def time_batch_fs(R, b, nprob: int, cand, iters: int = 1) -> float:
+    """Mean device time (ms) of the fused FP32 march of a batch over `iters`
+    outer iterations from J = B with launch shape `cand` = (groups, threads);
+    the batch is reset afterwards (Lambda* kept)."""
+    R.rt_batch_set_direction_groups(b, cand[0])
+    R.rt_batch_set_block_threads(b, cand[1])
+    R.rt_batch_reset(b)
+    R.rt_batch_reset_stats(b)
+    R.rt_batch_set_profiling(b, True)
+    R.rt_batch_solve(b, nprob, tol=0.0, max_iter=iters)
+    st = R.rt_batch_get_stats(b)
+    R.rt_batch_set_profiling(b, False)
+    R.rt_batch_reset(b)
+    return st["fs_ms"] / max(st["fs_launches"], 1)
+
+
+def autotune_batch(b, problems, cache_path: Optional[str] = DEFAULT_CACHE, refresh: bool = False,
+                   iters: int = 1):
+    """Tune and apply the fused launch shape, (groups, threads per block), of
+    an FP32-sweep batch, keyed by the largest grid, direction count, batch
+    size and SM count."""
+    import torch
+    from . import rt3d as R
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    big = max(problems, key=lambda p: p.nvox)
+    key = cache_key(big.nx, big.ny, big.nz, big.ndir, R.RT_FP32_SWEEP, sms) + f":b{len(problems)}"
+    R.rt_batch_solve(b, len(problems), tol=0.0, max_iter=1)          # warm-up, builds Lambda*
+    best, _ = tune(key, lambda c: time_batch_fs(R, b, len(problems), c, iters),
+                   CANDIDATES_FP32, cache_path, refresh)
+    R.rt_batch_set_direction_groups(b, best[0])
+    R.rt_batch_set_block_threads(b, best[1])
+    R.rt_batch_reset(b)
     return best

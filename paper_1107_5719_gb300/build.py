@@ -24,7 +24,8 @@ BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "librt3d_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["fs.cu", "fs32.cu", "fsdf.cu", "sc.cu", "para.cu", "os.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["fs.cu", "fs32.cu", "fsdf.cu", "sc.cu", "para.cu", "os.cu", "api.cu", "noalloc.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -49,6 +49,7 @@ struct rt_ctx {
     double *scpart = nullptr, *scplanes = nullptr;   // short characteristics
     size_t scpart_n = 0, scplanes_n = 0;
     int groups_req = 0;
+    int threads32 = 0;       // threads per block of the FP32 march (0: 128)
     double cut = -1.0;
 
     // device state, FP64
@@ -402,12 +403,22 @@ int fs_finish(rt_ctx* c, double* Jout)
         CK(launch_sum_groups_src(c->g.N, c->partial, c->S, c->wsum, Jout, c->stream));
     c->stats.launches += 1;
     if (!c->lstar_valid) {
-        if (c->src_order == RT_SRC_PARABOLIC)
+        if (c->src_order == RT_SRC_PARABOLIC) {
             CK(launch_lstar64p(c->g, c->chi, c->info, c->off, c->bw, c->dn, c->lstar, c->stream));
-        else if (c->precision == RT_DF64)
-            CK(launch_lstar_df(viewdf(c), false, c->lstar, c->stream));
-        else
+        } else if (c->precision == RT_FP64) {
             CK(launch_lstar64(c->g, c->chi, c->info, c->off, c->bw, c->lstar, c->stream));
+        } else {
+            // FP32 sweep and double-float march: Lambda* in double-float
+            // (FP64-accurate; 5.7 against 25 ms for the FP64 kernel on the
+            // 65^3 slab with 1024 directions), from the double-float nodes
+            if (c->precision == RT_FP32_SWEEP) {
+                int rc = form_buffers(c, RT_DF64);
+                if (rc) return rc;
+                CK(launch_packdf(c->g, c->chi, c->S, c->node4, c->stream));
+                c->stats.launches += 1;
+            }
+            CK(launch_lstar_df(viewdf(c), false, c->lstar, c->stream));
+        }
         c->lstar_valid = true;
         c->coef_valid = false;
         c->stats.launches += 1;
@@ -475,7 +486,8 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
     } else if (c->precision == RT_DF64) {
         CK(launch_fsdf(viewdf(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
     } else {
-        CK(launch_fs32d(view32(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
+        CK(launch_fs32d(view32(c), cut, G, c->threads32, count_steps ? c->d_steps : nullptr,
+                        c->stream));
     }
     if (c->profiling) {
         CK(cudaEventRecord(c->ev[1], c->stream));
@@ -957,6 +969,7 @@ struct rt_batch {
     unsigned long long* d_steps = nullptr;
     unsigned long long* h_steps = nullptr;
     int groups_req = 0;
+    int threads32 = 0;              // threads per block of the fused FP32 launch (0: 128)
     bool profiling = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool jac_pending = false;
@@ -1012,7 +1025,7 @@ int batch_groups(const rt_batch* b, const std::vector<int>& act)
 {
     if (b->groups_req > 0) return b->groups_req < kSlots ? b->groups_req : kSlots;
     long long blocks = 0;
-    for (int p : act) blocks += fs32_blocks(b->ctx[p]->g, 1);
+    for (int p : act) blocks += fs32_blocks(b->ctx[p]->g, 1, b->threads32);
     int G = 1;
     while (G < kSlots && blocks * G < 64LL * (b->num_sms > 0 ? b->num_sms : 152)) G *= 2;
     return G;
@@ -1158,7 +1171,7 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
             if (b->ctx[p]->precision != RT_FP32_SWEEP) continue;
             b->h_ids[q] = p;
             b->h_prefix[q] = total;
-            total += fs32_blocks(b->ctx[p]->g, G);
+            total += fs32_blocks(b->ctx[p]->g, G, b->threads32);
             ++q;
         }
         b->h_prefix[q] = total;
@@ -1167,7 +1180,7 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
                                 b->stream));
             BCK(cudaMemcpyAsync(b->d_prefix, b->h_prefix, sizeof(long long) * (q + 1),
                                 cudaMemcpyHostToDevice, b->stream));
-            BCK(launch_fs32_batch(b->d_views, b->d_ids, b->d_prefix, q, total, G,
+            BCK(launch_fs32_batch(b->d_views, b->d_ids, b->d_prefix, q, total, G, b->threads32,
                                   cut_of(b->ctx[0]), b->d_steps, b->stream));
             b->stats.fs_launches += 1;
             b->stats.launches += 1;
@@ -1629,6 +1642,16 @@ int rt_set_direction_groups(rt_ctx* c, int groups)
     return RT_OK;
 }
 
+int rt_set_block_threads(rt_ctx* c, int threads)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if (threads != 0 && threads != 64 && threads != 128 && threads != 256)
+        return fail(c, RT_EINVAL, "threads per block must be 0 (default), 64, 128 or 256");
+    c->threads32 = threads;
+    return RT_OK;
+}
+
 int rt_set_cutoff(rt_ctx* c, double cut)
 {
     if (!c) return RT_EINVAL;
@@ -2065,6 +2088,15 @@ int rt_batch_get_J_dev(rt_batch* b, int p, double* J)
     BCK(cudaSetDevice(b->device));
     rt_ctx* c = b->ctx[p];
     BCK(cudaMemcpyAsync(J, c->J, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, b->stream));
+    return RT_OK;
+}
+
+int rt_batch_set_block_threads(rt_batch* b, int threads)
+{
+    if (!b) return RT_EINVAL;
+    if (threads != 0 && threads != 64 && threads != 128 && threads != 256)
+        return bfail(b, RT_EINVAL, "threads per block must be 0 (default), 64, 128 or 256");
+    b->threads32 = threads;
     return RT_OK;
 }
 

@@ -38,13 +38,16 @@ namespace rt3d {
 
 namespace {
 
-constexpr int kThreads32 = 128;
+constexpr int kThreads32 = 128;     // default threads per block
 // 80 registers (six blocks of 128 threads per SM) and the step loop
 // unrolled twice: measured on the 65^3 slab with 32x32 directions, 9.43 ms
 // per formal solution against 9.94 ms (no unrolling), 9.88 ms (96
 // registers) and 10.1-11.1 ms for variants that load the next step's
 // records before computing the current one (more registers, fewer warps).
 constexpr int kMinBlocks32 = 6;
+// Threads per block are a launch knob (64, 128 or 256, rt_set_block_threads);
+// every size keeps 768 resident threads per SM, i.e. the same 80 registers.
+constexpr int kResident32 = kThreads32 * kMinBlocks32;
 
 // poff[d][m] = offset of the upstream node (x0, y0) of step m from the
 // voxel's own node in planes of `rows` padded rows of 2nx entries.
@@ -128,8 +131,12 @@ __device__ __forceinline__ void step32(Ray32& r, float hs, float4 b, float4 u0, 
     // S(p) - S_0: hi differences are exact for nearby values
     const float dh = b.x * (u0.y - r.s0h) + b.y * (u0.w - r.s0h) + b.z * (u1.y - r.s0h) +
                      b.w * (u1.w - r.s0h);
+#ifdef RT_FS32_NOLO
+    const float db = dh;
+#else
     const float dl = b.x * l0.x + b.y * l0.y + b.z * l1.x + b.w * l1.y;
     const float db = dh + (dl - r.s0l);
+#endif
     const float x = hs * (r.ca + cb);
     float wc, wu, e;
     seg_weights32(x, wc, wu, e);
@@ -201,13 +208,14 @@ __device__ __forceinline__ void boundary32(Ray32& r, const View32& p, const DirI
 // cut off (or reach the boundary, where both take their boundary term); a
 // voxel whose own cutoff came first keeps adding its (negligible) terms.
 // The step count is that of each voxel's own cutoff.
+template <int TB>
 __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int zb, int ZB,
                                         float cut, unsigned long long* __restrict__ steps)
 {
     const Geometry& g = p.g;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int nyp = (ny + 1) >> 1;
-    const int t = tile * kThreads32 + threadIdx.x;
+    const int t = tile * TB + threadIdx.x;
     const bool active = t < nx * nyp;
     unsigned long long nsteps = 0;
     if (active) {
@@ -277,18 +285,20 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
     if (steps) add_steps32(steps, nsteps);
 }
 
-__global__ void __launch_bounds__(kThreads32, kMinBlocks32)
+template <int TB>
+__global__ void __launch_bounds__(TB, kResident32 / TB)
 k_fs32d(View32 p, float cut, unsigned long long* __restrict__ steps)
 {
-    march32(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, cut, steps);
+    march32<TB>(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, cut, steps);
 }
 
-int tiles32(const Geometry& g) { return (g.nx * ((g.ny + 1) / 2) + kThreads32 - 1) / kThreads32; }
+int tiles32(const Geometry& g, int tb) { return (g.nx * ((g.ny + 1) / 2) + tb - 1) / tb; }
 
 // Many problems in one launch: block b belongs to the active problem q with
 // prefix[q] <= b < prefix[q+1]; within it, blocks run tile-fastest, then
 // plane, then slot group.
-__global__ void __launch_bounds__(kThreads32, kMinBlocks32)
+template <int TB>
+__global__ void __launch_bounds__(TB, kResident32 / TB)
 k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
              const long long* __restrict__ prefix, int nact, int ZB, float cut,
              unsigned long long* __restrict__ steps)
@@ -302,11 +312,11 @@ k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
     if (b >= prefix[nact]) return;
     const View32& p = views[ids[lo]];
     const long long local = b - prefix[lo];
-    const int tiles = (p.g.nx * ((p.g.ny + 1) >> 1) + kThreads32 - 1) / kThreads32;
+    const int tiles = (p.g.nx * ((p.g.ny + 1) >> 1) + TB - 1) / TB;
     const int tile = (int)(local % tiles);
     const int k0 = (int)((local / tiles) % p.g.nz);
     const int zb = (int)(local / ((long long)tiles * p.g.nz));
-    march32(p, tile, k0, zb, ZB, cut, steps);
+    march32<TB>(p, tile, k0, zb, ZB, cut, steps);
 }
 
 // J[v] = wsum * S[v] + sum_slot partial[slot][v]  (slot order fixed)
@@ -353,23 +363,31 @@ cudaError_t launch_pack_b2(const Geometry& g, const double* B, float2* b2, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_fs32d(const View32& p, double cut, int groups, unsigned long long* steps,
-                         cudaStream_t st)
+int block_threads32(int threads) { return threads == 64 || threads == 256 ? threads : kThreads32; }
+
+cudaError_t launch_fs32d(const View32& p, double cut, int groups, int threads,
+                         unsigned long long* steps, cudaStream_t st)
 {
     // planes in index order (g.zorder unused): with the plane read from the
     // order table the march ran at 14.6 instead of 10.7 ms on the 65^3 slab
-    dim3 grid(tiles32(p.g), p.g.nz, groups);
-    k_fs32d<<<grid, kThreads32, 0, st>>>(p, (float)cut, steps);
+    const int tb = block_threads32(threads);
+    dim3 grid(tiles32(p.g, tb), p.g.nz, groups);
+    if (tb == 64)
+        k_fs32d<64><<<grid, 64, 0, st>>>(p, (float)cut, steps);
+    else if (tb == 256)
+        k_fs32d<256><<<grid, 256, 0, st>>>(p, (float)cut, steps);
+    else
+        k_fs32d<kThreads32><<<grid, kThreads32, 0, st>>>(p, (float)cut, steps);
     return cudaGetLastError();
 }
 
-long long fs32_blocks(const Geometry& g, int groups)
+long long fs32_blocks(const Geometry& g, int groups, int threads)
 {
-    return (long long)tiles32(g) * g.nz * groups;
+    return (long long)tiles32(g, block_threads32(threads)) * g.nz * groups;
 }
 
 cudaError_t launch_fs32_batch(const View32* views, const int* ids, const long long* prefix,
-                              int nact, long long total_blocks, int groups, double cut,
+                              int nact, long long total_blocks, int groups, int threads, double cut,
                               unsigned long long* steps, cudaStream_t st)
 {
     if (nact <= 0 || total_blocks <= 0) return cudaSuccess;
@@ -378,7 +396,15 @@ cudaError_t launch_fs32_batch(const View32* views, const int* ids, const long lo
         grid.x = 1u << 30;
         grid.y = (unsigned)((total_blocks + grid.x - 1) / grid.x);
     }
-    k_fs32_batch<<<grid, kThreads32, 0, st>>>(views, ids, prefix, nact, groups, (float)cut, steps);
+    const int tb = block_threads32(threads);
+    const float c = (float)cut;
+    if (tb == 64)
+        k_fs32_batch<64><<<grid, 64, 0, st>>>(views, ids, prefix, nact, groups, c, steps);
+    else if (tb == 256)
+        k_fs32_batch<256><<<grid, 256, 0, st>>>(views, ids, prefix, nact, groups, c, steps);
+    else
+        k_fs32_batch<kThreads32><<<grid, kThreads32, 0, st>>>(views, ids, prefix, nact, groups, c,
+                                                              steps);
     return cudaGetLastError();
 }
 

@@ -190,14 +190,16 @@ struct View32 {
     double* partial;        // [kSlots][N]
 };
 // FP32 march of I - S_0: partial[kSlots][N] of sum_d w_d (I_d - S_0).
-cudaError_t launch_fs32d(const View32& p, double cut, int groups, unsigned long long* steps,
-                         cudaStream_t st);
+// threads: threads per block, 64, 128 or 256 (anything else: 128); J does
+// not depend on it.
+cudaError_t launch_fs32d(const View32& p, double cut, int groups, int threads,
+                         unsigned long long* steps, cudaStream_t st);
 // Blocks one problem takes in a batched launch with `groups` slot groups.
-long long fs32_blocks(const Geometry& g, int groups);
+long long fs32_blocks(const Geometry& g, int groups, int threads);
 // One launch over the active problems ids[0..nact) of views (device arrays);
 // prefix[q] = first block of active problem q, prefix[nact] = total_blocks.
 cudaError_t launch_fs32_batch(const View32* views, const int* ids, const long long* prefix,
-                              int nact, long long total_blocks, int groups, double cut,
+                              int nact, long long total_blocks, int groups, int threads, double cut,
                               unsigned long long* steps, cudaStream_t st);
 // ---- double-float march (fsdf.cu) -------------------------------------------
 struct ViewDF {

@@ -44,6 +44,13 @@ cudaError_t scratch_address(int dev, unsigned char** out)
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The scratch size stated in include/rt3d.h (64*N + 88*ndir*nz + 88*ndir + 8
+// bytes plus alignment) counts these record sizes.
+static_assert(sizeof(DirInfo) == 64, "direction record size changed: update the stated scratch size");
+static_assert(sizeof(StepGeo) + 2 * sizeof(Bw4d) + sizeof(float4) == 88,
+              "per-(direction, plane) tables changed: update the stated scratch size");
+static_assert(kSlots * sizeof(double) == 64, "partial sums per voxel changed: update the stated scratch size");
+
 struct Layout {
     size_t smax, mu, phi, w, info, off, bw, bwh, bw32, partial, total;
 };

@@ -119,6 +119,9 @@ _SIGS = {
     "rt_batch_get_J_dev": (C.c_int, [VP, C.c_int, VP]),
     "rt_batch_set_direction_groups": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_graphs": (C.c_int, [VP, C.c_int]),
+    "rt_set_block_threads": (C.c_int, [VP, C.c_int]),
+    "rt_batch_set_block_threads": (C.c_int, [VP, C.c_int]),
+    "rt_probe_peaks": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "rt_batch_set_profiling": (C.c_int, [VP, C.c_int]),
     "rt_batch_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
     "rt_batch_reset_stats": (C.c_int, [VP]),
@@ -489,6 +492,23 @@ def rt_batch_get_J_dev(b, p, J):
 
 def rt_batch_set_direction_groups(b, groups):
     return _bcheck(b, load().rt_batch_set_direction_groups(b, groups))
+
+
+def rt_probe_peaks(device: int = 0) -> dict:
+    """Measured FP64 and FP32 FMA throughput of the device (TFLOP/s)."""
+    a, b = C.c_double(), C.c_double()
+    rc = load().rt_probe_peaks(device, C.byref(a), C.byref(b))
+    if rc:
+        raise RtError(rc, "rt_probe_peaks failed")
+    return {"fp64_tflops": a.value, "fp32_tflops": b.value}
+
+
+def rt_set_block_threads(ctx, threads):
+    return _check(ctx, load().rt_set_block_threads(ctx, threads))
+
+
+def rt_batch_set_block_threads(b, threads):
+    return _bcheck(b, load().rt_batch_set_block_threads(b, threads))
 
 
 def rt_batch_set_graphs(b, on=True):

@@ -139,3 +139,24 @@ def test_batch_graph_equals_host_loop(R, method):
     assert sg["iterations"] == sh["iterations"] == max(rg["iters"])
     assert sg["host_syncs"] <= 2 * sg["iterations"]
     assert sh["host_syncs"] > sg["host_syncs"]
+
+
+def test_batch_launch_shape_does_not_change_results(R):
+    """Threads per block and direction groups of the fused FP32 launch are
+    tuning knobs only: bit-identical iterates."""
+    probs = _uneven()[:3]
+    out = []
+    for groups, threads in ((0, 0), (2, 64), (8, 256)):
+        b = R.rt_batch_create(probs, precision=1)
+        try:
+            R.rt_batch_set_direction_groups(b, groups)
+            R.rt_batch_set_block_threads(b, threads)
+            r = R.rt_batch_solve(b, len(probs), tol=TOL[1], max_iter=500)
+            out.append((r["iters"], [R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx))
+                                     for i, p in enumerate(probs)]))
+        finally:
+            R.rt_batch_destroy(b)
+    for it, Js in out[1:]:
+        assert np.array_equal(it, out[0][0])
+        for a, c in zip(Js, out[0][1]):
+            assert np.array_equal(a, c)
