@@ -435,7 +435,7 @@ def run_ours(args):
         ms32 = float(sum(r32["times"]))
         m32 = march_rate(R, p, R.RT_FP32_SWEEP, dev, stream)
         fp32 = {"value": round(RP.weak_throughput(args.fp32_steps, ms32)[0], 6), "unit": "solves/s",
-                "form": "FP32 sweep + double-float finish from delta < 1e-6 (the default)",
+                "form": "FP32 sweep + finishing stage from delta < 1e-6 (the default)",
                 "ms_per_step": round(ms32 / args.fp32_steps, 3),
                 "iters_per_solve": st32["iterations"] / args.fp32_steps,
                 "march_launches_per_solve": st32["fs_launches"] / args.fp32_steps,
@@ -640,7 +640,7 @@ def precision_check(R, dev, n=33):
     err = np.abs(r["J"] - rr["J"]) / rr["J"]
     return {"workload": f"{n}x{n}x129 slab, strong-scattering chi law (tau 1e-4..1e4), eps = 1e-6, "
                         "B = 1, 64x64 directions",
-            "fp32_default": {"form": "FP32 sweep, double-float finish from delta < 1e-6, Ng every 4",
+            "fp32_default": {"form": "FP32 sweep, finishing stage from delta < 1e-6, Ng every 4",
                              "tol": 1e-8, "converged": bool(r["converged"]), "iters": int(r["iters"]),
                              "fp32_iters": n32, "double_float_iters": int(r["iters"]) - n32,
                              "s": round(t32, 2), "max_rel_err": float(err.max()),
@@ -765,7 +765,8 @@ def batched_vs_fp64(R, dev, stream, flush, nl, nsub, tol, ng, max_iter):
     ach = FLOPS_PER_STEP_FP32 * march_steps / (stb["fs_ms"] / 1e3) / 1e12 if stb["fs_ms"] else None
     return {"value": round(vb, 6), "unit": "wavelength-solves/s",
             "workload": f"{nl} wavelengths x 65^3, chi x 10^(-2+4U), eps 10^(-5+5U), 32x32 directions",
-            "form": "FP32 sweep + double-float finish from delta < 1e-6, FP64 J/Lambda*/OS",
+            "form": "FP32 sweep, finishing stage from delta < 1e-6 (one double-float formal "
+                    "solution, then FP32 marches of the source change), FP64 J/Lambda*/OS",
             "tol": tol, "converged": bool(rb["converged"]), "s": round(msb / 1e3, 2),
             "create_s": round(t_create, 1),
             "iters_mean": float(np.mean(rb["iters"])), "iters_max": int(np.max(rb["iters"])),

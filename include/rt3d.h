@@ -241,22 +241,28 @@ int rt_set_precision(rt_ctx *ctx, int precision);
  * on = 0 selects the host-driven loop. */
 int rt_set_graphs(rt_ctx *ctx, int on);
 
-/* Automatic double-float finishing stage for RT_FP32_SWEEP contexts:
- * within rt_solve, once an iteration's delta falls below delta_switch (and
- * not yet below tol), the iteration continues in double-float with Ng
- * applied regardless of its delta threshold, down to tol; when the solve
- * returns (converged or not) the context is back in the FP32 sweep with its
- * Ng threshold.  The FP32 sweep's iterate stops improving near delta 1e-8
- * and its Ng must stop near 1e-6; at small eps the remaining iterations
- * converge slowly, which the double-float stage with Ng avoids: where the
- * error of a solve stopped at delta is ~ delta / (1 - rho) for a contraction
- * rho close to 1 (about 70 delta at eps = 1e-6), a 1e-6 accuracy target
- * needs tol ~ 1e-8, below the FP32 sweep's floor.  Default for
- * RT_FP32_SWEEP contexts (and batches): on, delta_switch = 1e-6;
- * delta_switch = 0 turns it off (the FP32 sweep alone, tol >= 5e-8).  The
- * batch version applies it per problem: problems still in the FP32 sweep
- * share the fused launch, those in their finishing stage run one launch
- * each. */
+/* Automatic finishing stage for RT_FP32_SWEEP contexts: within rt_solve,
+ * once an iteration's delta falls below delta_switch (and not yet below
+ * tol), the next formal solution is a double-float (FP64-accurate) one,
+ * J_ref = J_FS(S_ref) of the current source S_ref, and every later one is
+ * J_FS(S) = J_ref + J_FS(S - S_ref) with the second term marched in FP32
+ * with zero boundary intensities (the formal solution is linear in S and
+ * in the boundary intensities): its FP32 rounding scales with |S - S_ref|,
+ * ~1e-6 of S, so these formal solutions are accurate to ~1e-12 of J at
+ * the FP32 march's cost (less: its transmission cutoff is relative to
+ * |S - S_ref| against min |S_ref|).  Ng is applied every period from the
+ * switch on, its history restarted.  When the solve returns (converged or
+ * not) the context is back in the plain FP32 sweep with its Ng threshold.
+ * The FP32 sweep's iterate stops improving near delta 1e-8 and its Ng must
+ * stop near 1e-6; at small eps the remaining iterations converge slowly,
+ * which the finishing stage with Ng avoids: where the error of a solve
+ * stopped at delta is ~ delta / (1 - rho) for a contraction rho close to 1
+ * (about 70 delta at eps = 1e-6), a 1e-6 accuracy target needs tol ~ 1e-8,
+ * below the FP32 sweep's floor.  Default for RT_FP32_SWEEP contexts (and
+ * batches): on, delta_switch = 1e-6; delta_switch = 0 turns it off (the
+ * FP32 sweep alone, tol >= 5e-8).  The batch version applies it per
+ * problem: the reference formal solution runs one double-float launch per
+ * problem, the later ones share the fused FP32 launch. */
 int rt_set_df_finish(rt_ctx *ctx, double delta_switch);
 
 /* Source interpolation on each segment of a characteristic (the paper

@@ -27,7 +27,14 @@ struct rt_ctx {
     bool have_grid = false, have_quad = false, have_chi = false, have_eps = false, have_B = false;
     bool lstar_valid = false, coef_valid = false, b2_valid = false;
     int os_method = RT_OS_JACOBI;
-    double df_switch = 0.0;   // FP32 sweep: continue in double-float once delta < this
+    double df_switch = 0.0;   // FP32 sweep: finishing stage once delta < this
+    // Finishing stage of an FP32-sweep solve: 0 off; 1 the next formal
+    // solution is the double-float reference J_ref = J_FS(S_ref) of the
+    // current source; 2 formal solutions march the source change
+    // dS = S - S_ref in FP32 and add it: J_FS(S) = J_ref + J_FS(dS) with zero
+    // boundary intensities (the formal solution is linear in S).
+    int fin = 0;
+    double *S_ref = nullptr, *J_ref = nullptr, *dS = nullptr;
     // operator-splitting step as a CUDA graph with the sweep loop in a WHILE
     // node (two cached instances: J_old alternates between two buffers)
     struct OsGraph {
@@ -179,6 +186,7 @@ void free_grid_buffers(rt_ctx* c)
     dfree(c->Jfs); dfree(c->Jn); dfree(c->Ja); dfree(c->Jb); dfree(c->r);
     dfree(c->lstar); dfree(c->coef); dfree(c->rdiag); dfree(c->partial);
     dfree(c->node4); dfree(c->pair); dfree(c->plo);
+    dfree(c->S_ref); dfree(c->J_ref); dfree(c->dS);
     dfree(c->b2); dfree(c->gdiff); dfree(c->g2); dfree(c->g2df);
     dfree(c->scpart); dfree(c->scplanes);
     dfree(c->zorder); dfree(c->zscratch);
@@ -348,7 +356,19 @@ View32 view32(rt_ctx* c)
     v.poff = c->poff32;
     v.bw = c->bw32;
     v.smax = c->scal + 0;
+    v.sfloor = nullptr;
     v.partial = c->partial;
+    return v;
+}
+
+// The FP32 march of the finishing stage: source dS (packed in the pair
+// planes), zero boundary intensities, cutoff relative to min |S_ref|.
+View32 view32_fin(rt_ctx* c)
+{
+    View32 v = view32(c);
+    v.g.top_bc = RT_BC_ZERO;
+    v.g.bottom_bc = RT_BC_ZERO;
+    v.sfloor = c->scal + 3;
     return v;
 }
 
@@ -399,6 +419,8 @@ int fs_finish(rt_ctx* c, double* Jout)
 {
     if (c->precision == RT_FP64)
         CK(launch_sum_groups(c->g.N, c->partial, Jout, c->stream));
+    else if (c->precision == RT_FP32_SWEEP && c->fin == 2)
+        CK(launch_sum_groups_ref(c->g.N, c->partial, c->dS, c->wsum, c->J_ref, Jout, c->stream));
     else
         CK(launch_sum_groups_src(c->g.N, c->partial, c->S, c->wsum, Jout, c->stream));
     c->stats.launches += 1;
@@ -424,6 +446,38 @@ int fs_finish(rt_ctx* c, double* Jout)
         c->stats.launches += 1;
         c->stats.lstar_launches += 1;
     }
+    return RT_OK;
+}
+
+// The finishing stage's reference (c->fin == 1): a double-float formal
+// solution of the current source S into c->partial (same sum convention as
+// the FP32 march); fin_record() then keeps S and J as the reference.
+int fin_reference_march(rt_ctx* c, int G, unsigned long long* steps, cudaStream_t st)
+{
+    int rc = form_buffers(c, RT_DF64);
+    if (rc) return rc;
+    if (!c->S_ref) {
+        CK(dalloc(c->S_ref, (size_t)c->g.N));
+        CK(dalloc(c->J_ref, (size_t)c->g.N));
+        CK(dalloc(c->dS, (size_t)c->g.N));
+    }
+    if (c->g.bottom_bc == RT_BC_DIFFUSION) {
+        CK(launch_grad_df(c->g, c->gdiff, c->g2df, st));
+        c->stats.launches += 1;
+    }
+    CK(launch_packdf(c->g, c->chi, c->S, c->node4, st));
+    CK(launch_fsdf(viewdf(c), c->cut >= 0 ? c->cut : default_cut(RT_DF64), G, steps, st));
+    c->stats.launches += 2;
+    return RT_OK;
+}
+
+int fin_record(rt_ctx* c, const double* Jfs, cudaStream_t st)
+{
+    CK(cudaMemcpyAsync(c->S_ref, c->S, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->J_ref, Jfs, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, st));
+    CK(launch_absmin(c->g.N, c->S, c->scal + 3, st));
+    c->stats.launches += 1;
+    c->fin = 2;
     return RT_OK;
 }
 
@@ -485,9 +539,12 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
                        c->stream));
     } else if (c->precision == RT_DF64) {
         CK(launch_fsdf(viewdf(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
+    } else if (c->fin == 1) {
+        if ((rc = fin_reference_march(c, G, count_steps ? c->d_steps : nullptr, c->stream)))
+            return rc;
     } else {
-        CK(launch_fs32d(view32(c), cut, G, c->threads32, count_steps ? c->d_steps : nullptr,
-                        c->stream));
+        CK(launch_fs32d(c->fin == 2 ? view32_fin(c) : view32(c), cut, G, c->threads32,
+                        count_steps ? c->d_steps : nullptr, c->stream));
     }
     if (c->profiling) {
         CK(cudaEventRecord(c->ev[1], c->stream));
@@ -496,6 +553,8 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
     c->stats.fs_launches += 1;
     c->stats.launches += 1;
     if ((rc = fs_finish(c, Jout))) return rc;
+    if (c->precision == RT_FP32_SWEEP && c->fin == 1 && (rc = fin_record(c, Jout, c->stream)))
+        return rc;
     if (count_steps) {
         CK(cudaMemcpyAsync(c->h_steps, c->d_steps, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, c->stream));
@@ -516,7 +575,16 @@ int prepare_source(rt_ctx* c, const double* S_in, bool device)
                          c->scal + 0, c->stream));
     }
     c->stats.launches += 1;
-    if (c->precision == RT_FP32_SWEEP) {
+    if (c->precision == RT_FP32_SWEEP && c->fin == 2) {
+        // finishing stage: march dS = S - S_ref, cutoff bound max |dS|
+        CK(launch_delta_source(c->g.N, c->S, c->S_ref, c->dS, c->stream));
+        CK(cudaMemsetAsync(c->scal + 0, 0, sizeof(double), c->stream));
+        CK(launch_absmax(c->g.N, c->dS, nullptr, c->scal + 0, nullptr, c->stream));
+        CK(launch_pack_pairs(c->g, c->chi, c->dS, c->pair, c->plo, c->stream));
+        c->stats.launches += 3;
+    } else if (c->precision == RT_FP32_SWEEP && c->fin == 1) {
+        // the reference formal solution packs its own double-float nodes
+    } else if (c->precision == RT_FP32_SWEEP) {
         CK(launch_pack_pairs(c->g, c->chi, c->S, c->pair, c->plo, c->stream));
         c->stats.launches += 1;
     } else if (c->precision == RT_DF64) {
@@ -870,21 +938,20 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
     if ((rc = need_all(c))) return rc;
     if (max_iter < 1 || max_sweeps < 1 || !(tol >= 0) || !(tol_inner >= 0))
         return fail(c, RT_EINVAL, "bad iteration controls");
-    // double-float finishing stage: the context returns to its form and Ng
-    // threshold when the solve ends, whichever way it ends
+    // finishing stage: the context leaves it, and gets its Ng threshold
+    // back, when the solve ends, whichever way it ends
     struct FinishGuard {
         rt_ctx* c;
-        int precision;
         double ng_min;
         bool on;
         ~FinishGuard()
         {
             if (on) {
-                switch_precision(c, precision);
+                c->fin = 0;
                 c->ng_min_delta = ng_min;
             }
         }
-    } guard{c, c->precision, c->ng_min_delta, false};
+    } guard{c, c->ng_min_delta, false};
     int it = 0;
     double delta = 0.0;
     bool converged = false;
@@ -924,8 +991,9 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
             break;
         }
         if (!guard.on && c->df_switch > 0 && c->precision == RT_FP32_SWEEP && delta < c->df_switch) {
-            if ((rc = switch_precision(c, RT_DF64))) return rc;
-            c->ng_min_delta = 0.0;
+            c->fin = 1;               // next formal solution: the double-float reference
+            c->ng_min_delta = 0.0;    // Ng on every period from here
+            c->ng_count = 1;          // its history restarts with FP64-accurate iterates
             guard.on = true;
         }
     }
@@ -960,6 +1028,8 @@ struct rt_batch {
     std::vector<double> delta;      // last outer delta
     std::vector<char> converged;
     View32* d_views = nullptr;      // device copies of the per-problem FP32 views
+    View32* h_views = nullptr;      // pinned host copies (uploaded when a view changes)
+    std::vector<char> view_fin;     // problems whose device view is the finishing-stage one
     int* d_ids = nullptr;
     long long* d_prefix = nullptr;
     int* h_ids = nullptr;           // pinned
@@ -1162,16 +1232,25 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
     BCK(cudaMemsetAsync(b->d_steps, 0, sizeof(unsigned long long), b->stream));
     if (b->profiling) BCK(cudaEventRecord(b->ev[0], b->stream));
     if (b->precision == RT_FP32_SWEEP) {
-        // one fused launch over the problems still in the FP32 sweep (act is
-        // in launch order); those in their double-float finishing stage run
-        // one launch each
+        // one fused launch over the problems in the FP32 sweep, including
+        // those marching their source change in the finishing stage (act is
+        // in launch order); a finishing-stage reference and problems switched
+        // to the double-float march by hand run one launch each
         long long total = 0;
         int q = 0;
         for (int p : act) {
-            if (b->ctx[p]->precision != RT_FP32_SWEEP) continue;
+            rt_ctx* c = b->ctx[p];
+            if (c->precision != RT_FP32_SWEEP || c->fin == 1) continue;
+            const char want = c->fin == 2;
+            if (b->view_fin[p] != want) {     // this problem's view changed form
+                b->h_views[p] = want ? view32_fin(c) : view32(c);
+                BCK(cudaMemcpyAsync(b->d_views + p, b->h_views + p, sizeof(View32),
+                                    cudaMemcpyHostToDevice, b->stream));
+                b->view_fin[p] = want;
+            }
             b->h_ids[q] = p;
             b->h_prefix[q] = total;
-            total += fs32_blocks(b->ctx[p]->g, G, b->threads32);
+            total += fs32_blocks(c->g, G, b->threads32);
             ++q;
         }
         b->h_prefix[q] = total;
@@ -1187,8 +1266,13 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
         }
         for (int p : act) {
             rt_ctx* c = b->ctx[p];
-            if (c->precision != RT_DF64) continue;
-            BCK(launch_fsdf(viewdf(c), cut_of(c), G, b->d_steps, b->stream));
+            if (c->precision == RT_DF64) {
+                BCK(launch_fsdf(viewdf(c), cut_of(c), G, b->d_steps, b->stream));
+            } else if (c->fin == 1) {
+                if ((rc = bpass(b, p, fin_reference_march(c, G, b->d_steps, b->stream)))) return rc;
+            } else {
+                continue;
+            }
             b->stats.fs_launches += 1;
             b->stats.launches += 1;
         }
@@ -1206,8 +1290,13 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
         }
     }
     if (b->profiling) BCK(cudaEventRecord(b->ev[1], b->stream));
-    for (int p : act)
-        if ((rc = bpass(b, p, fs_finish(b->ctx[p], b->ctx[p]->Jfs)))) return rc;
+    for (int p : act) {
+        rt_ctx* c = b->ctx[p];
+        if ((rc = bpass(b, p, fs_finish(c, c->Jfs)))) return rc;
+        if (c->precision == RT_FP32_SWEEP && c->fin == 1 &&
+            (rc = bpass(b, p, fin_record(c, c->Jfs, b->stream))))
+            return rc;
+    }
     BCK(cudaMemcpyAsync(b->h_steps, b->d_steps, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                         b->stream));
     return RT_OK;
@@ -1838,10 +1927,11 @@ int rt_batch_create(rt_batch** out, int device, int precision, int nprob, const 
     b->iters.assign(nprob, 0);
     b->delta.assign(nprob, 0.0);
     b->converged.assign(nprob, 0);
-    std::vector<View32> views(nprob);
-    for (int p = 0; p < nprob; ++p) views[p] = view32(b->ctx[p]);
+    BCK(cudaMallocHost((void**)&b->h_views, sizeof(View32) * nprob));
+    for (int p = 0; p < nprob; ++p) b->h_views[p] = view32(b->ctx[p]);
+    b->view_fin.assign(nprob, 0);
     BCK(cudaMalloc((void**)&b->d_views, sizeof(View32) * nprob));
-    BCK(cudaMemcpy(b->d_views, views.data(), sizeof(View32) * nprob, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_views, b->h_views, sizeof(View32) * nprob, cudaMemcpyHostToDevice));
     BCK(cudaMalloc((void**)&b->d_ids, sizeof(int) * nprob));
     BCK(cudaMalloc((void**)&b->d_prefix, sizeof(long long) * (nprob + 1)));
     BCK(cudaMalloc((void**)&b->d_delta, sizeof(double) * nprob));
@@ -1867,6 +1957,7 @@ int rt_batch_destroy(rt_batch* b)
     if (b->d_sweeps) cudaFree(b->d_sweeps);
     if (b->h_sweeps) cudaFreeHost(b->h_sweeps);
     if (b->d_views) cudaFree(b->d_views);
+    if (b->h_views) cudaFreeHost(b->h_views);
     if (b->d_ids) cudaFree(b->d_ids);
     if (b->d_prefix) cudaFree(b->d_prefix);
     if (b->d_delta) cudaFree(b->d_delta);
@@ -1993,8 +2084,23 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
         return bfail(b, RT_EINVAL, "bad iteration controls");
     const int P = (int)b->ctx.size();
     int rc;
-    std::vector<char> switched(P, 0);   // problems in their double-float finishing stage
-    std::vector<double> ng_min0(P, 0.0);
+    // problems in their finishing stage leave it (and get their Ng threshold
+    // back) when the solve ends, whichever way it ends
+    struct FinishGuard {
+        rt_batch* b;
+        std::vector<char> switched;
+        std::vector<double> ng_min0;
+        ~FinishGuard()
+        {
+            for (size_t p = 0; p < switched.size(); ++p)
+                if (switched[p]) {
+                    b->ctx[p]->fin = 0;
+                    b->ctx[p]->ng_min_delta = ng_min0[p];
+                }
+        }
+    } guard{b, std::vector<char>(P, 0), std::vector<double>(P, 0.0)};
+    std::vector<char>& switched = guard.switched;
+    std::vector<double>& ng_min0 = guard.ng_min0;
     for (int it = 0; it < max_iter; ++it) {
         std::vector<int> act;
         for (int p : b->order)
@@ -2044,21 +2150,17 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
             if (tol > 0 && b->h_delta[p] < tol) {
                 b->converged[p] = 1;
             } else if (c->df_switch > 0 && c->precision == RT_FP32_SWEEP &&
-                       b->precision == RT_FP32_SWEEP && b->h_delta[p] < c->df_switch) {
-                // double-float finishing stage for this problem
-                if ((rc = bpass(b, p, switch_precision(c, RT_DF64)))) return rc;
+                       b->precision == RT_FP32_SWEEP && c->fin == 0 &&
+                       b->h_delta[p] < c->df_switch) {
+                // finishing stage for this problem (see solve())
+                c->fin = 1;
                 switched[p] = 1;
                 ng_min0[p] = c->ng_min_delta;
                 c->ng_min_delta = 0.0;
+                c->ng_count = 1;
             }
         }
     }
-    for (int p = 0; p < P; ++p)
-        if (switched[p]) {
-            rt_ctx* c = b->ctx[p];
-            switch_precision(c, RT_FP32_SWEEP);
-            c->ng_min_delta = ng_min0[p];
-        }
     int nconv = 0;
     for (int p = 0; p < P; ++p) {
         if (iters) iters[p] = b->iters[p];

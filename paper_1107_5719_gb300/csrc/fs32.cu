@@ -230,11 +230,20 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
         const float2 la = pl[0], lb = pl[W];
         // The rest of a characteristic changes I - S_0 by at most
         // T * max|S - S_0| <= T * 2 smax: stop once that is below cut * S_0.
-        // An absent second voxel counts as cut off from the start.
+        // A march of a source change (p.sfloor set) stops once that is
+        // below cut * sfloor, a lower bound of the source it changes.  An
+        // absent second voxel counts as cut off from the start.
         const float smax = (float)*p.smax;
-        const float ka = smax > 0.f ? cut / (2.0f * smax) : 0.f;
-        const float tca = ka * (ma.y + la.x);
-        const float tcb = two ? ka * (mb.y + lb.x) : 2.0f;
+        float tca, tcb;
+        if (p.sfloor) {
+            const float t = smax > 0.f ? cut * (float)*p.sfloor / (2.0f * smax) : 2.0f;
+            tca = t;
+            tcb = two ? t : 2.0f;
+        } else {
+            const float ka = smax > 0.f ? cut / (2.0f * smax) : 0.f;
+            tca = ka * (ma.y + la.x);
+            tcb = two ? ka * (mb.y + lb.x) : 2.0f;
+        }
         for (int slot = zb; slot < kSlots; slot += ZB) {
             double Ja = 0.0, Jb = 0.0;
             for (int d = slot; d < g.ndir; d += kSlots) {
@@ -317,6 +326,43 @@ k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
     const int k0 = (int)((local / tiles) % p.g.nz);
     const int zb = (int)(local / ((long long)tiles * p.g.nz));
     march32<TB>(p, tile, k0, zb, ZB, cut, steps);
+}
+
+// dS = S - Sref (the source change the finishing stage marches)
+__global__ void k_delta_source(long long N, const double* __restrict__ S,
+                               const double* __restrict__ Sref, double* __restrict__ dS)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x)
+        dS[v] = S[v] - Sref[v];
+}
+
+// *out = min_v |x[v]| (one block, fixed reduction order)
+__global__ void k_absmin(long long N, const double* __restrict__ x, double* __restrict__ out)
+{
+    __shared__ double sm[256];
+    double m = __longlong_as_double(0x7FF0000000000000LL);   // +inf
+    for (long long v = threadIdx.x; v < N; v += blockDim.x) m = fmin(m, fabs(x[v]));
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] = fmin(sm[threadIdx.x], sm[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sm[0];
+}
+
+// J[v] = Jref[v] + wsum * dS[v] + sum_slot partial[slot][v]  (slot order fixed)
+__global__ void k_sum_groups_ref(long long N, const double* __restrict__ partial,
+                                 const double* __restrict__ dS, double wsum,
+                                 const double* __restrict__ Jref, double* __restrict__ J)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N;
+         v += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < kSlots; ++q) s += partial[q * N + v];
+        J[v] = Jref[v] + fma(wsum, dS[v], s);
+    }
 }
 
 // J[v] = wsum * S[v] + sum_slot partial[slot][v]  (slot order fixed)
@@ -405,6 +451,26 @@ cudaError_t launch_fs32_batch(const View32* views, const int* ids, const long lo
     else
         k_fs32_batch<kThreads32><<<grid, kThreads32, 0, st>>>(views, ids, prefix, nact, groups, c,
                                                               steps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_delta_source(long long N, const double* S, const double* Sref, double* dS,
+                                cudaStream_t st)
+{
+    k_delta_source<<<grid1d(N, 256), 256, 0, st>>>(N, S, Sref, dS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmin(long long N, const double* x, double* out, cudaStream_t st)
+{
+    k_absmin<<<1, 256, 0, st>>>(N, x, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_groups_ref(long long N, const double* partial, const double* dS,
+                                  double wsum, const double* Jref, double* J, cudaStream_t st)
+{
+    k_sum_groups_ref<<<grid1d(N, 256), 256, 0, st>>>(N, partial, dS, wsum, Jref, J);
     return cudaGetLastError();
 }
 

@@ -187,6 +187,10 @@ struct View32 {
     const int* poff;        // offsets in the pair planes (rows = 2ny + 1)
     const float4* bw;       // FP32 bilinear weights per (direction, step)
     const double* smax;     // source bound of the cutoff
+    // Null: the march's source is S itself and the cutoff is relative to
+    // each voxel's S.  Otherwise the source is a change dS of a source whose
+    // magnitude is at least *sfloor, and the cutoff is relative to that.
+    const double* sfloor;
     double* partial;        // [kSlots][N]
 };
 // FP32 march of I - S_0: partial[kSlots][N] of sum_d w_d (I_d - S_0).
@@ -229,6 +233,14 @@ cudaError_t launch_bw_df(long long n, const Bw4d* bw, float4* out, cudaStream_t 
 cudaError_t launch_grad_df(const Geometry& g, const double* G, float2* out, cudaStream_t st);
 cudaError_t launch_fsdf(const ViewDF& p, double cut, int groups, unsigned long long* steps,
                         cudaStream_t st);
+
+// Finishing stage of the FP32 sweep (formal solution of a source change):
+// dS = S - Sref; *out = min |x|; J = Jref + wsum dS + sum_slot partial.
+cudaError_t launch_delta_source(long long N, const double* S, const double* Sref, double* dS,
+                                cudaStream_t st);
+cudaError_t launch_absmin(long long N, const double* x, double* out, cudaStream_t st);
+cudaError_t launch_sum_groups_ref(long long N, const double* partial, const double* dS,
+                                  double wsum, const double* Jref, double* J, cudaStream_t st);
 
 // J[v] = wsum S[v] + sum_slot partial[slot][v].
 cudaError_t launch_sum_groups_src(long long N, const double* partial, const double* S,

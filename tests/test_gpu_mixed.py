@@ -139,3 +139,21 @@ def test_batch_automatic_finish_equals_single(R):
             r = s.solve(tol=1e-8, max_iter=3000)
         assert r["iters"] == rb["iters"][i]
         assert np.array_equal(r["J"], Jb[i])
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4])
+def test_finishing_stage_is_fp64_accurate(R, eps):
+    """After the switch the FP32-sweep context's formal solutions are
+    J_ref + J_FS(S - S_ref), the reference in double-float and the change in
+    FP32: accurate enough to iterate to delta < 1e-10, two orders below the
+    FP32 sweep's own floor, and to land on the double-float fixed point."""
+    p = W.random_slab(13, 11, 17, n_theta=8, n_phi=6, seed=33, eps_range=(eps, eps),
+                      chi_decades=4.0)
+    with R.Solver(p, precision=R.RT_DF64, ng_period=4) as s:
+        rdf = s.solve(tol=1e-11, max_iter=3000)
+    assert rdf["converged"]
+    with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+        r = s.solve(tol=1e-10, max_iter=3000)
+    assert r["converged"]
+    err = np.max(np.abs(r["J"] - rdf["J"]) / rdf["J"])
+    assert err < 1e-8, err
