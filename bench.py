@@ -424,9 +424,9 @@ def run_ours(args):
                 "share_of_step": round(st["fs_ms"] / my_ms, 4)}
 
     # the FP32-sweep form of the same workload on the same GPU: converged
-    # solves of the form as created (double-float finish from delta < 1e-6),
+    # solves of the form as created (finishing stage from delta < 1e-6),
     # at the headline's tolerance; the march's own rate from FP32-only
-    # formal solutions (the finishing stage runs the double-float march)
+    # formal solutions (the finishing stage marches a source change)
     fp32 = None
     if args.fp32_steps > 0:
         r32 = timed_solves(R, p, R.RT_FP32_SWEEP, dev, stream, flush, 1, args.fp32_steps,
@@ -615,7 +615,7 @@ def _ctx_for(R, dev, p, precision):
 def precision_check(R, dev, n=33):
     """Precision form at eps = 1e-6 (strong scattering): n x n x 129 slab
     with the 64 x 64 directions of the 129^3 configuration.  The FP32-sweep
-    context as created (double-float finish from delta < 1e-6, Ng every 4)
+    context as created (finishing stage from delta < 1e-6, Ng every 4)
     is solved to tol 1e-8; the reference continues the same iteration in
     double-float (FP64-accurate march) to delta < 1e-9, i.e. to the FP64
     fixed point within ~70 x 1e-9 at this eps."""
@@ -703,7 +703,7 @@ def batched_vs_fp64(R, dev, stream, flush, nl, nsub, tol, ng, max_iter):
     """FP32-batched form against FP64 plain on the same GPU.  The batch: all
     nl wavelengths of the 512-point configuration (65^3, 32x32 directions,
     chi x 10^(-2+4U), eps 10^(-5+5U) per wavelength), FP32 sweep with the
-    default double-float finish, tol 1e-8, one fused march launch per outer
+    default finishing stage, tol 1e-8, one fused march launch per outer
     iteration and the OS step of all active wavelengths as one CUDA graph.
     FP64 plain: nsub wavelengths spread evenly over the batch (every
     nl/nsub-th), one rt_solve each at the same tolerance; the ratio is the
@@ -779,7 +779,7 @@ def batched_vs_fp64(R, dev, stream, flush, nl, nsub, tol, ng, max_iter):
                                "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                                "frac": round(ach / PEAK_FP32_TFLOPS, 4) if ach else None,
                                "note": "all march launches of the solve (fused FP32 and the "
-                                       "double-float finish), 45 FP32 flops per executed step"},
+                                       "finishing stage), 45 FP32 flops per executed step"},
             "clocks": clk.summary(),
             "fp64_plain_subset": {"lambdas": sub, "value": round(v64, 6), "unit": "wavelength-solves/s",
                                   "s": round(ms64 / 1e3, 2), "per_lambda": per},
