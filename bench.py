@@ -642,7 +642,7 @@ def precision_check(R, dev, n=33):
                         "B = 1, 64x64 directions",
             "fp32_default": {"form": "FP32 sweep, finishing stage from delta < 1e-6, Ng every 4",
                              "tol": 1e-8, "converged": bool(r["converged"]), "iters": int(r["iters"]),
-                             "fp32_iters": n32, "double_float_iters": int(r["iters"]) - n32,
+                             "fp32_iters": n32, "finishing_iters": int(r["iters"]) - n32,
                              "s": round(t32, 2), "max_rel_err": float(err.max()),
                              "median_rel_err": float(np.median(err))},
             "reference": {"form": "same iteration continued in double-float to delta < 1e-9",

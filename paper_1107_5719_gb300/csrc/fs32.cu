@@ -48,6 +48,9 @@ constexpr int kMinBlocks32 = 6;
 // Threads per block are a launch knob (64, 128 or 256, rt_set_block_threads);
 // every size keeps 768 resident threads per SM, i.e. the same 80 registers.
 constexpr int kResident32 = kThreads32 * kMinBlocks32;
+#ifndef RT_FS32_TNEXT
+#define RT_FS32_TNEXT 0
+#endif
 
 // poff[d][m] = offset of the upstream node (x0, y0) of step m from the
 // voxel's own node in planes of `rows` padded rows of 2nx entries.
@@ -131,13 +134,32 @@ __device__ __forceinline__ void step32(Ray32& r, float hs, float4 b, float4 u0, 
     // S(p) - S_0: hi differences are exact for nearby values
     const float dh = b.x * (u0.y - r.s0h) + b.y * (u0.w - r.s0h) + b.z * (u1.y - r.s0h) +
                      b.w * (u1.w - r.s0h);
-#ifdef RT_FS32_NOLO
-    const float db = dh;
-#else
     const float dl = b.x * l0.x + b.y * l0.y + b.z * l1.x + b.w * l1.y;
     const float db = dh + (dl - r.s0l);
-#endif
     const float x = hs * (r.ca + cb);
+#if RT_FS32_TNEXT
+    // T_m w_up = T_m e x phi2(x) = T_{m+1} x phi2(x): below x = 2 the
+    // upstream weight takes the next transmission instead of e
+    r.tau += x;
+    const float Tn = ex2_approx(-r.tau * kLog2e);
+    float wcT, wuT;
+    if (x < 2.0f) {
+        float E, O;
+        phi2_parts32(x, E, O);
+        wcT = r.T * (x * (E - O));
+        wuT = Tn * (x * (E + O));
+    } else {
+        const float e = ex2_approx(-x * kLog2e);
+        const float q = (1.0f - e) * rcp_approx(x);
+        wcT = r.T * (1.0f - q);
+        wuT = r.T * (q - e);
+    }
+    const float inc = fmaf(wcT, r.da, wuT * db);
+    const float sI = r.I + inc, bb = sI - r.I;
+    r.Ilo += (r.I - (sI - bb)) + (inc - bb);
+    r.I = sI;
+    r.T = Tn;
+#else
     float wc, wu, e;
     seg_weights32(x, wc, wu, e);
     // I - S_0 += T (w_cur D_m + w_up D_m+1), TwoSum
@@ -147,6 +169,7 @@ __device__ __forceinline__ void step32(Ray32& r, float hs, float4 b, float4 u0, 
     r.I = sI;
     r.tau += x;
     r.T = ex2_approx(-r.tau * kLog2e);
+#endif
     r.ca = cb;
     r.da = db;
 }

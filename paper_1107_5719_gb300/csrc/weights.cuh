@@ -140,18 +140,25 @@ __device__ __forceinline__ float rcp_approx(float y)
     return r;
 }
 
+// E = phi2 even part, O = odd part at x < 2 (phi2(+-x) = E +- O)
+__device__ __forceinline__ void phi2_parts32(float x, float& E, float& O)
+{
+    const float z = x * x;
+    E = fmaf(fmaf(fmaf(2.968770900e-07f, z, 2.472764936e-05f), z, 1.388992299e-03f), z,
+             4.166661575e-02f);
+    E = fmaf(E, z, 0.5f);
+    O = fmaf(fmaf(fmaf(2.669341548e-08f, z, 2.749998430e-06f), z, 1.984207920e-04f), z,
+             8.333329111e-03f);
+    O = fmaf(O, z, 1.666666716e-01f) * x;
+}
+
 __device__ __forceinline__ void seg_weights32(float x, float& wc, float& wu, float& e)
 {
     constexpr float kLog2e = 1.4426950408889634f;
     e = ex2_approx(-x * kLog2e);
     if (x < 2.0f) {
-        const float z = x * x;
-        float E = fmaf(fmaf(fmaf(2.968770900e-07f, z, 2.472764936e-05f), z, 1.388992299e-03f), z,
-                       4.166661575e-02f);
-        E = fmaf(E, z, 0.5f);
-        float O = fmaf(fmaf(fmaf(2.669341548e-08f, z, 2.749998430e-06f), z, 1.984207920e-04f), z,
-                       8.333329111e-03f);
-        O = fmaf(O, z, 1.666666716e-01f) * x;
+        float E, O;
+        phi2_parts32(x, E, O);
         wc = x * (E - O);
         wu = (x * e) * (E + O);
     } else {

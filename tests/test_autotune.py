@@ -1,6 +1,8 @@
 """Host logic of the launch-shape autotuner (no GPU): candidate choice,
 tie-breaking, JSON cache round trip and reuse."""
 
+import pytest
+
 from paper_1107_5719_gb300 import autotune as A
 
 
@@ -56,3 +58,36 @@ def test_pairs_of_groups_and_threads_round_trip_through_the_cache(tmp_path):
 def test_fp32_candidates_cover_every_block_size_and_group_count():
     assert {t for _, t in A.CANDIDATES_FP32} == {64, 128, 256}
     assert {g for g, _ in A.CANDIDATES_FP32} == set(A.CANDIDATES)
+
+
+@pytest.mark.gpu
+def test_autotune_solver_and_batch_on_gpu(tmp_path):
+    """The tuner times every candidate on the GPU, caches the winner and
+    applies it; J is unchanged by the tuned launch shape."""
+    import numpy as np
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1107_5719_gb300 import build as B
+    B.build()
+    from paper_1107_5719_gb300 import rt3d as R, workloads as W
+    R.load()
+    path = str(tmp_path / "tune.json")
+    p = W.random_slab(21, 17, 9, n_theta=6, n_phi=4, seed=3)
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        J0, _ = s.formal_solution(want_lstar=False)
+        best = A.autotune_solver(s, cache_path=path, repeats=1)
+        J1, _ = s.formal_solution(want_lstar=False)
+    assert best in A.CANDIDATES_FP32
+    assert np.array_equal(J0, J1)
+    assert len(A.load_cache(path)) == 1
+    probs = W.batch_65(n_lambda=3, n=9, n_theta=4, n_phi=4)
+    b = R.rt_batch_create(probs, precision=R.RT_FP32_SWEEP)
+    try:
+        bb = A.autotune_batch(b, probs, cache_path=path)
+        assert bb in A.CANDIDATES_FP32
+        r = R.rt_batch_solve(b, len(probs), tol=1e-6, max_iter=500)
+        assert r["converged"]
+    finally:
+        R.rt_batch_destroy(b)
+    assert len(A.load_cache(path)) == 2
