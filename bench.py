@@ -80,9 +80,9 @@ ORACLE_COUNTS = {
     "slab17": {"iters": 17, "sweeps": 416, "full_solve_s": 0.82, "cores": 16},
 }
 # DRAM bytes (read + write) of one k_jacobi launch on the 129^3 grid, from
-# one ncu capture of the current kernel: 478.6 MB read + 16.2 MB written,
+# one ncu capture of the current kernel: 478.5 MB read + 16.4 MB written,
 # the algorithmic 232 B per voxel.
-TRAFFIC_JACOBI_129 = 494826240
+TRAFFIC_JACOBI_129 = 494896128
 # DRAM bytes (read + write) of one k_fs32d launch on slab65, from one ncu
 # capture of the current kernel: 27.80 MB read (the padded pair planes,
 # the tables) + 0.06 MB written; then everything is served from L2.
@@ -691,11 +691,11 @@ def os_sweep_roofline(R, dev, sweeps=200):
                        "hbm_frac": out["slab129"]["frac_of_hbm"],
                        "peak_source": "unit counts and clock (FP64); HBM: measured copy "
                                       "bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                       "note": "ncu: FP64 pipe 91% busy (26 stencil FMAs and the FP64 "
-                               "division of the convergence test, ~41 FP64 instructions per "
-                               "voxel), DRAM traffic = the algorithmic 232 B per voxel, so "
-                               "the FP64 pipe, not HBM, bounds the sweep on this GPU; slab65's "
-                               "sweep is L2-resident"}
+                       "note": "ncu: FP64 pipe 90% busy (26 stencil FMAs and the "
+                               "convergence test, ~36 FP64 instructions per voxel), DRAM "
+                               "traffic = the algorithmic 232 B per voxel, so the FP64 pipe, "
+                               "not HBM, bounds the sweep on this GPU; slab65's sweep is "
+                               "L2-resident"}
     return out
 
 

@@ -314,8 +314,10 @@ int rt_set_cutoff(rt_ctx *ctx, double cut);
  * march uses for n optical depths x[n] (device pointers): w_cur (weight of
  * the downstream node), w_up (upstream node) and e = exp(-x) of the linear-
  * in-tau source integral over one segment, in the arithmetic of `precision`
- * (RT_FP64 or RT_FP32_SWEEP; FP32 results are widened to double).  Enqueued
- * on `stream`. */
+ * (RT_FP64 or RT_FP32_SWEEP; FP32 results are widened to double).  Below
+ * x = 2 the FP32 march itself forms T w_up from the next transmission
+ * (T e = T_next) with the same polynomials instead of multiplying by e.
+ * Enqueued on `stream`. */
 int rt_segment_weights(int precision, long long n, const double *x, double *w_cur,
                        double *w_up, double *e, void *stream);
 
@@ -360,9 +362,10 @@ int rt_probe_peaks(int device, double *fp64_tflops, double *fp32_tflops);
  * 65^3 slab with 1024 directions takes 23.5 MB.  RT_EINVAL for invalid
  * arguments (device data is not inspected); RT_ECUDA if a CUDA call fails.
  *
- * The first call on a device looks up the device address of the scratch
- * array (once per device, with that device current); make that first call
- * before any stream capture.  All calls share the one array and it keeps
+ * Every call copies mu, phi and w from the caller's host arrays into the
+ * scratch with cudaMemcpyAsync on `stream`.  The first call on a device
+ * looks up the device address of the scratch array (once per device, with
+ * that device current); make that first call before any stream capture.  All calls share the one array and it keeps
  * the last call's contents, so calls whose GPU work may overlap (several
  * streams, several host threads) race with each other: serialise them. */
 #define RT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

@@ -48,9 +48,7 @@ constexpr int kMinBlocks32 = 6;
 // Threads per block are a launch knob (64, 128 or 256, rt_set_block_threads);
 // every size keeps 768 resident threads per SM, i.e. the same 80 registers.
 constexpr int kResident32 = kThreads32 * kMinBlocks32;
-#ifndef RT_FS32_TNEXT
-#define RT_FS32_TNEXT 0
-#endif
+
 
 // poff[d][m] = offset of the upstream node (x0, y0) of step m from the
 // voxel's own node in planes of `rows` padded rows of 2nx entries.
@@ -137,9 +135,12 @@ __device__ __forceinline__ void step32(Ray32& r, float hs, float4 b, float4 u0, 
     const float dl = b.x * l0.x + b.y * l0.y + b.z * l1.x + b.w * l1.y;
     const float db = dh + (dl - r.s0l);
     const float x = hs * (r.ca + cb);
-#if RT_FS32_TNEXT
+    // I - S_0 += T_m w_cur D_m + T_m w_up D_m+1 (TwoSum), with
     // T_m w_up = T_m e x phi2(x) = T_{m+1} x phi2(x): below x = 2 the
-    // upstream weight takes the next transmission instead of e
+    // upstream weight takes the next transmission (from the optical depth)
+    // instead of e, which saves its exponential (measured on the 65^3 slab:
+    // 9.49 against 9.73 ms; converged J at eps = 1e-6 within 2.1e-8 of FP64
+    // against 3.3e-8)
     r.tau += x;
     const float Tn = ex2_approx(-r.tau * kLog2e);
     float wcT, wuT;
@@ -159,17 +160,6 @@ __device__ __forceinline__ void step32(Ray32& r, float hs, float4 b, float4 u0, 
     r.Ilo += (r.I - (sI - bb)) + (inc - bb);
     r.I = sI;
     r.T = Tn;
-#else
-    float wc, wu, e;
-    seg_weights32(x, wc, wu, e);
-    // I - S_0 += T (w_cur D_m + w_up D_m+1), TwoSum
-    const float inc = r.T * fmaf(wc, r.da, wu * db);
-    const float sI = r.I + inc, bb = sI - r.I;
-    r.Ilo += (r.I - (sI - bb)) + (inc - bb);
-    r.I = sI;
-    r.tau += x;
-    r.T = ex2_approx(-r.tau * kLog2e);
-#endif
     r.ca = cb;
     r.da = db;
 }
