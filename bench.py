@@ -84,9 +84,9 @@ ORACLE_COUNTS = {
 # the algorithmic 232 B per voxel.
 TRAFFIC_JACOBI_129 = 494896128
 # DRAM bytes (read + write) of one k_fs32d launch on slab65, from one ncu
-# capture of the current kernel: 27.80 MB read (the padded pair planes,
-# the tables) + 0.06 MB written; then everything is served from L2.
-TRAFFIC_FS32_SLAB65 = 27860480
+# capture of the current kernel: 27.77 MB read (the padded pair planes,
+# the tables) + 0.01 MB written; then everything is served from L2.
+TRAFFIC_FS32_SLAB65 = 27782144
 
 # The FP32-sweep iterate stops changing below a relative delta of ~1e-8
 # (rounding), so its outer tolerance is at least 5e-8, and Ng extrapolation
@@ -455,9 +455,9 @@ def run_ours(args):
                             "frac_of_measured": round(ach32 / probe["fp32_tflops"], 4)
                             if probe["fp32_tflops"] else None,
                             "traffic": TRAFFIC_FS32_SLAB65,
-                            "note": "ncu: bound by instruction issue (77% of issue slots; "
-                                    "86 thread instructions per step, 48 of them FP32 "
-                                    "arithmetic), L1 55%"}
+                            "note": "ncu: bound by instruction issue (72% of issue slots; "
+                                    "79 thread instructions per step, 46 of them FP32 "
+                                    "arithmetic), L1 57%"}
 
     # the double-float form (FP64-accurate march on the FP32 pipes)
     df64 = None
