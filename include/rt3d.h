@@ -197,7 +197,10 @@ int rt_last_step_count(rt_ctx *ctx, unsigned long long *steps);
  * iteration's delta is below min_delta (>= 0): once the iterates differ only
  * by rounding noise (about 5e-8 relative for the FP32 sweep) the
  * extrapolation would amplify that noise.  delta is measured against the
- * extrapolated iterate.  period 0 (default) = off; otherwise >= 4. */
+ * extrapolated iterate.  The weighted sums and the 2x2 system are reduced
+ * and solved on the GPU (the system in FP64 with products and differences
+ * rounded as written; a singular system leaves x0 unchanged), so Ng adds
+ * no host synchronisation.  period 0 (default) = off; otherwise >= 4. */
 int rt_set_ng(rt_ctx *ctx, int period, double min_delta);
 
 /* Formal-solution method.  RT_FS_LONG (default): the long characteristic
@@ -233,12 +236,13 @@ int rt_set_fs_method(rt_ctx *ctx, int method);
  * Allocates the double-float tables on the first switch to RT_DF64. */
 int rt_set_precision(rt_ctx *ctx, int precision);
 
-/* Operator-splitting steps as CUDA graphs (default on): the right-hand side
- * and the sweep loop of one step form one graph whose WHILE node runs the
- * sweeps and their convergence test on the device, so the host launches it
- * and synchronises once per step instead of once per chunk of sweeps.
- * Results are identical either way (same kernels, same sweep count).
- * on = 0 selects the host-driven loop. */
+/* Operator-splitting steps as CUDA graphs (default on): the right-hand side,
+ * the sweep loop and the pick of the last sweep's iterate form one graph
+ * whose WHILE node runs the sweeps and their convergence test on the
+ * device, so the host launches it without waiting; an outer iteration of
+ * rt_solve waits for the GPU once (for delta and the sweep count) instead
+ * of once per chunk of sweeps.  Results are identical either way (same
+ * kernels, same sweep count).  on = 0 selects the host-driven loop. */
 int rt_set_graphs(rt_ctx *ctx, int on);
 
 /* Automatic finishing stage for RT_FP32_SWEEP contexts: within rt_solve,
@@ -434,8 +438,8 @@ int rt_batch_set_block_threads(rt_batch *batch, int threads);
  * solves of all active problems (Sect. 2.3) as ONE CUDA graph, one
  * independent branch per problem (right-hand side, a device-side loop of
  * sweeps to tol_inner or max_sweeps, the pick of the last sweep's iterate),
- * so the host launches once and waits once per iteration (plus once when Ng
- * extrapolates); the graph is rebuilt when the set of active problems
+ * so the host launches once and waits once per iteration (Ng runs on the
+ * device too); the graph is rebuilt when the set of active problems
  * changes.  on == 0: the sweeps are enqueued from the host in growing chunks
  * with one wait per chunk.  Results are identical. */
 int rt_batch_set_graphs(rt_batch *batch, int on);

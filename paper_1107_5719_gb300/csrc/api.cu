@@ -42,12 +42,15 @@ struct rt_ctx {
         cudaGraphExec_t exec = nullptr;
         const double* jold = nullptr;
         const double* jfs = nullptr;
+        const double* jnew = nullptr;
         const double* dlt = nullptr;
         int max_sweeps = 0, method = -1;
         double tol = -1.0;
     } osg[2];
     int osg_next = 0;
     int* d_nsw = nullptr;     // the graph's sweep counter
+    int* d_sw = nullptr;      // sweeps of the graph's last OS step (device), and a pinned copy
+    int* h_sw = nullptr;
     bool use_graphs = true;
     unsigned long long* berr = nullptr;   // checked builds: out-of-bounds record
     int fs_method = RT_FS_LONG;
@@ -111,7 +114,6 @@ struct rt_ctx {
     double* ng_old[3] = {nullptr, nullptr, nullptr};  // J_{n-1}, J_{n-2}, J_{n-3}
     double* ng_part = nullptr;
     double* ng_out = nullptr;           // device [5]
-    double* h_ng = nullptr;             // pinned [5]
     int ng_applied = 0;
 
     // profiling
@@ -166,8 +168,6 @@ void free_ng(rt_ctx* c)
     for (auto& p : c->ng_old) dfree(p);
     dfree(c->ng_part);
     dfree(c->ng_out);
-    if (c->h_ng) cudaFreeHost(c->h_ng);
-    c->h_ng = nullptr;
 }
 
 void free_os_graphs(rt_ctx* c)
@@ -666,7 +666,7 @@ int ensure_dlt(rt_ctx* c, int max_sweeps)
 // of synchronising after every chunk of sweeps.  Results are those of the
 // host loop: same kernels, same no-op rule after convergence.
 int build_os_graph(rt_ctx* c, rt_ctx::OsGraph& e, const double* Jfs, const double* Jold,
-                   double tol, int max_sweeps)
+                   double* Jnew, double tol, int max_sweeps)
 {
     const bool gs = c->os_method == RT_OS_GAUSS_SEIDEL;
     cudaGraph_t g = nullptr;
@@ -715,6 +715,19 @@ int build_os_graph(rt_ctx* c, rt_ctx::OsGraph& e, const double* Jfs, const doubl
             err = e1 != cudaSuccess ? e1 : e2;
         }
     }
+    if (err == cudaSuccess) {
+        // epilogue after the loop: the last sweep's iterate into J_new and
+        // the sweep count, on the device
+        err = cudaStreamBeginCaptureToGraph(c->stream, g, &cn, nullptr, 1,
+                                            cudaStreamCaptureModeThreadLocal);
+        if (err == cudaSuccess) {
+            cudaError_t e1 = launch_os_select(c->g.N, c->dlt, max_sweeps, tol, c->Ja, c->Jb, Jnew,
+                                              c->d_sw, c->stream);
+            cudaGraph_t out = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(c->stream, &out);
+            err = e1 != cudaSuccess ? e1 : e2;
+        }
+    }
     cudaGraphExec_t exec = nullptr;
     if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, g, 0);
     if (err != cudaSuccess) {
@@ -726,6 +739,7 @@ int build_os_graph(rt_ctx* c, rt_ctx::OsGraph& e, const double* Jfs, const doubl
     e.exec = exec;
     e.jold = Jold;
     e.jfs = Jfs;
+    e.jnew = Jnew;
     e.dlt = c->dlt;
     e.max_sweeps = max_sweeps;
     e.method = c->os_method;
@@ -733,15 +747,23 @@ int build_os_graph(rt_ctx* c, rt_ctx::OsGraph& e, const double* Jfs, const doubl
     return RT_OK;
 }
 
+// The operator-splitting step as one graph launch, without waiting for it:
+// J_new and the sweep count (c->d_sw) are written on the device.  The
+// caller copies d_sw to h_sw before its next synchronisation and then calls
+// os_graph_done().
 int run_os_graph(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, double tol_inner,
-                 int max_sweeps, int* sweeps_out)
+                 int max_sweeps)
 {
     int rc;
     if ((rc = ensure_dlt(c, max_sweeps + 2))) return rc;
     if (!c->d_nsw) CK(cudaMalloc((void**)&c->d_nsw, sizeof(int)));
+    if (!c->d_sw) {
+        CK(cudaMalloc((void**)&c->d_sw, sizeof(int)));
+        CK(cudaMallocHost((void**)&c->h_sw, sizeof(int)));
+    }
     rt_ctx::OsGraph* e = nullptr;
     for (auto& x : c->osg)
-        if (x.exec && x.jold == Jold && x.jfs == Jfs && x.dlt == c->dlt &&
+        if (x.exec && x.jold == Jold && x.jfs == Jfs && x.jnew == Jnew && x.dlt == c->dlt &&
             x.max_sweeps == max_sweeps && x.tol == tol_inner && x.method == c->os_method)
             e = &x;
     if (!e) {
@@ -750,7 +772,7 @@ int run_os_graph(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew,
         if (e->exec) cudaGraphExecDestroy(e->exec);
         if (e->graph) cudaGraphDestroy(e->graph);
         *e = rt_ctx::OsGraph{};
-        if ((rc = build_os_graph(c, *e, Jfs, Jold, tol_inner, max_sweeps))) return rc;
+        if ((rc = build_os_graph(c, *e, Jfs, Jold, Jnew, tol_inner, max_sweeps))) return rc;
     }
     if (c->profiling) CK(cudaEventRecord(c->ev[2], c->stream));
     CK(cudaGraphLaunch(e->exec, c->stream));
@@ -758,26 +780,20 @@ int run_os_graph(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew,
         CK(cudaEventRecord(c->ev[3], c->stream));
         c->jac_pending = true;
     }
-    CK(cudaMemcpyAsync(c->h_dlt, c->dlt, sizeof(double) * max_sweeps, cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    c->stats.host_syncs += 1;
-    harvest(c);
-    int sweeps = max_sweeps;
-    for (int n = 0; n < max_sweeps; ++n)
-        if (c->h_dlt[n] < tol_inner) {
-            sweeps = n + 1;
-            break;
-        }
-    // sweep n wrote Ja for even n, Jb for odd n
-    CK(cudaMemcpyAsync(Jnew, (sweeps - 1) & 1 ? c->Jb : c->Ja, sizeof(double) * c->g.N,
-                       cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->h_sw, c->d_sw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    return RT_OK;
+}
+
+// After the synchronisation that follows run_os_graph: the sweep count and
+// the launch counters of that step.
+int os_graph_done(rt_ctx* c)
+{
+    const int sweeps = *c->h_sw;
     const int per = c->os_method == RT_OS_GAUSS_SEIDEL ? 2 : 1;
     const int passes = (sweeps + 1) / 2;
-    c->stats.launches += 1 + passes * (2 * per + 1);
+    c->stats.launches += 2 + passes * (2 * per + 1);
     c->stats.jacobi_launches += passes * 2 * per;
-    if (sweeps_out) *sweeps_out = sweeps;
-    return RT_OK;
+    return sweeps;
 }
 
 int run_os(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, double tol_inner,
@@ -785,7 +801,11 @@ int run_os(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, doubl
 {
     int rc = ensure_coef(c);
     if (rc) return rc;
-    if (c->use_graphs) return run_os_graph(c, Jfs, Jold, Jnew, tol_inner, max_sweeps, sweeps_out);
+    if (c->use_graphs) {
+        // sweep count after the caller's synchronisation (os_graph_done)
+        if (sweeps_out) *sweeps_out = -1;
+        return run_os_graph(c, Jfs, Jold, Jnew, tol_inner, max_sweeps);
+    }
     if ((rc = ensure_dlt(c, max_sweeps))) return rc;
     const bool gs = c->os_method == RT_OS_GAUSS_SEIDEL;
     CK(launch_os_rhs(c->g, c->coef, c->rdiag, Jfs, Jold, c->r, gs, c->stream));
@@ -850,10 +870,14 @@ int os_step(rt_ctx* c, const double* Jfs, const double* Jold, double* Jnew, doub
         dold = c->Jn;
     }
     double* dnew = device ? Jnew : c->S;  // S is free as scratch here
-    if ((rc = run_os(c, dfs, dold, dnew, tol_inner, max_sweeps, sweeps))) return rc;
+    int ns = 0;
+    if ((rc = run_os(c, dfs, dold, dnew, tol_inner, max_sweeps, &ns))) return rc;
     if (!device)
         CK(cudaMemcpyAsync(Jnew, dnew, sizeof(double) * c->g.N, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    harvest(c);
+    if (ns < 0) ns = os_graph_done(c);
+    if (sweeps) *sweeps = ns;
     return RT_OK;
 }
 
@@ -863,17 +887,16 @@ int ensure_ng(rt_ctx* c)
     for (auto& p : c->ng_old) CK(dalloc(p, (size_t)c->g.N));
     CK(dalloc(c->ng_part, (size_t)ng_partial_size()));
     CK(dalloc(c->ng_out, 5));
-    CK(cudaMallocHost((void**)&c->h_ng, 5 * sizeof(double)));
     return RT_OK;
 }
 
 // Ng bookkeeping after iteration `it` (1-based) produced J_new in c->Jn from
 // the previous iterate c->J: remember c->J, and when four iterates are held
-// and it is a multiple of the period, enqueue the weighted sums.  Returns
-// in *pending whether ng_finish must run after the next synchronisation.
-int ng_push(rt_ctx* c, int it, bool* pending)
+// and it is a multiple of the period, enqueue the weighted sums and the
+// extrapolation of J_new, whose 2x2 system is solved on the device (no
+// host synchronisation; the iterate is left unchanged if it is singular).
+int ng_push(rt_ctx* c, int it)
 {
-    *pending = false;
     if (!c->ng_period) return RT_OK;
     int rc = ensure_ng(c);
     if (rc) return rc;
@@ -888,27 +911,11 @@ int ng_push(rt_ctx* c, int it, bool* pending)
         (it == 1 || c->ng_last_delta >= c->ng_min_delta)) {
         CK(launch_ng_dots(c->g.N, c->Jn, c->ng_old[0], c->ng_old[1], c->ng_old[2], c->ng_part,
                           c->ng_out, c->stream));
-        CK(cudaMemcpyAsync(c->h_ng, c->ng_out, 5 * sizeof(double), cudaMemcpyDeviceToHost,
-                           c->stream));
-        c->stats.launches += 2;
-        *pending = true;
+        CK(launch_ng_apply(c->g.N, c->ng_out, c->ng_old[0], c->ng_old[1], c->Jn, c->stream));
+        c->stats.launches += 3;
+        c->ng_applied += 1;
+        c->ng_count = 1;
     }
-    return RT_OK;
-}
-
-// After the sums are on the host: solve the 2x2 least-squares system and
-// replace J_new by the extrapolation (left unchanged if it is singular).
-int ng_finish(rt_ctx* c)
-{
-    const double* s = c->h_ng;  // a11 a12 a22 b1 b2
-    const double det = s[0] * s[2] - s[1] * s[1];
-    c->ng_count = 1;
-    if (!(std::fabs(det) > 1e-300) || det != det) return RT_OK;
-    const double a = (s[3] * s[2] - s[4] * s[1]) / det;
-    const double b = (s[4] * s[0] - s[3] * s[1]) / det;
-    CK(launch_ng_combine(c->g.N, c->Jn, c->ng_old[0], c->ng_old[1], a, b, c->Jn, c->stream));
-    c->stats.launches += 1;
-    c->ng_applied += 1;
     return RT_OK;
 }
 
@@ -961,13 +968,7 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
         if ((rc = run_fs(c, c->Jfs, true))) return rc;
         int ns = 0;
         if ((rc = run_os(c, c->Jfs, c->J, c->Jn, tol_inner, max_sweeps, &ns))) return rc;
-        bool ng_pending = false;
-        if ((rc = ng_push(c, it + 1, &ng_pending))) return rc;
-        if (ng_pending) {
-            CK(cudaStreamSynchronize(c->stream));
-            c->stats.host_syncs += 1;
-            if ((rc = ng_finish(c))) return rc;
-        }
+        if ((rc = ng_push(c, it + 1))) return rc;
         CK(cudaMemsetAsync(c->scal + 2, 0, sizeof(double), c->stream));
         CK(launch_rel_change(c->g.N, c->Jn, c->J, c->scal + 2, c->stream));
         c->stats.launches += 1;
@@ -977,6 +978,7 @@ int solve(rt_ctx* c, double tol, int max_iter, double tol_inner, int max_sweeps,
         c->stats.host_syncs += 1;
         c->stats.iterations += 1;
         harvest(c);
+        if (ns < 0) ns = os_graph_done(c);
         total_steps += *c->h_steps;
         delta = c->h_scal[2];
         c->ng_last_delta = delta;
@@ -1485,6 +1487,10 @@ int rt_destroy(rt_ctx* c)
     dfree(c->berr);
     if (c->d_nsw) cudaFree(c->d_nsw);
     c->d_nsw = nullptr;
+    if (c->d_sw) cudaFree(c->d_sw);
+    c->d_sw = nullptr;
+    if (c->h_sw) cudaFreeHost(c->h_sw);
+    c->h_sw = nullptr;
     if (c->h_scal) cudaFreeHost(c->h_scal);
     if (c->h_steps) cudaFreeHost(c->h_steps);
     if (c->h_dlt) cudaFreeHost(c->h_dlt);
@@ -2112,18 +2118,8 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
         else
             rc = batch_os(b, act, tol_inner, max_sweeps);
         if (rc) return rc;
-        std::vector<int> ng_now;
-        for (int p : act) {
-            bool pend = false;
-            if ((rc = bpass(b, p, ng_push(b->ctx[p], b->iters[p] + 1, &pend)))) return rc;
-            if (pend) ng_now.push_back(p);
-        }
-        if (!ng_now.empty()) {
-            BCK(cudaStreamSynchronize(b->stream));
-            b->stats.host_syncs += 1;
-            for (int p : ng_now)
-                if ((rc = bpass(b, p, ng_finish(b->ctx[p])))) return rc;
-        }
+        for (int p : act)
+            if ((rc = bpass(b, p, ng_push(b->ctx[p], b->iters[p] + 1)))) return rc;
         BCK(cudaMemsetAsync(b->d_delta, 0, sizeof(double) * P, b->stream));
         for (int p : act) {
             rt_ctx* c = b->ctx[p];

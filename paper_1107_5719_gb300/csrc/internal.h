@@ -309,9 +309,11 @@ cudaError_t launch_jacobi(const Geometry& g, const double* coef, const double* r
 int ng_partial_size();
 cudaError_t launch_ng_dots(long long N, const double* x0, const double* x1, const double* x2,
                            const double* x3, double* part, double* out5, cudaStream_t st);
-// out = (1 - a - b) x0 + a x1 + b x2 (out may alias x0).
-cudaError_t launch_ng_combine(long long N, const double* x0, const double* x1, const double* x2,
-                              double a, double b, double* out, cudaStream_t st);
+// x0 = (1 - a - b) x0 + a x1 + b x2 with (a, b) the solution of the 2x2
+// system of the five sums s5 (device), computed on the device; no change
+// when the system is singular.
+cudaError_t launch_ng_apply(long long N, const double* s5, const double* x1, const double* x2,
+                            double* x0, cudaStream_t st);
 // *delta = max |Jn - Jo| / |Jn|
 cudaError_t launch_rel_change(long long N, const double* Jn, const double* Jo, double* delta,
                               cudaStream_t st);

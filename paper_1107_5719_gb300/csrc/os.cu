@@ -407,13 +407,23 @@ k_ng_sum(const double* __restrict__ part, double* __restrict__ out)
     if (threadIdx.x < 5) out[threadIdx.x] = sm[threadIdx.x][0];
 }
 
-__global__ void k_ng_combine(long long N, const double* __restrict__ x0,
-                             const double* __restrict__ x1, const double* __restrict__ x2,
-                             double a, double b, double* __restrict__ out)
+// The Ng extrapolation with its 2x2 least-squares system solved on the
+// device from the five sums s5 = {a11, a12, a22, b1, b2} (every thread
+// solves it; products and differences rounded separately, as written):
+// x0 <- (1 - a - b) x0 + a x1 + b x2, left unchanged when the system is
+// singular (|det| <= 1e-300) or not finite.
+__global__ void k_ng_apply(long long N, const double* __restrict__ s5,
+                           const double* __restrict__ x1, const double* __restrict__ x2,
+                           double* __restrict__ x0)
 {
+    const double s0 = s5[0], s1 = s5[1], s2 = s5[2], s3 = s5[3], s4 = s5[4];
+    const double det = __dsub_rn(__dmul_rn(s0, s2), __dmul_rn(s1, s1));
+    if (!(fabs(det) > 1e-300) || det != det) return;
+    const double a = __ddiv_rn(__dsub_rn(__dmul_rn(s3, s2), __dmul_rn(s4, s1)), det);
+    const double b = __ddiv_rn(__dsub_rn(__dmul_rn(s4, s0), __dmul_rn(s3, s1)), det);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x)
-        out[i] = (1.0 - a - b) * x0[i] + a * x1[i] + b * x2[i];
+        x0[i] = (1.0 - a - b) * x0[i] + a * x1[i] + b * x2[i];
 }
 
 unsigned grid_1d(long long N, int threads)
@@ -531,10 +541,10 @@ cudaError_t launch_ng_dots(long long N, const double* x0, const double* x1, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_ng_combine(long long N, const double* x0, const double* x1, const double* x2,
-                              double a, double b, double* out, cudaStream_t st)
+cudaError_t launch_ng_apply(long long N, const double* s5, const double* x1, const double* x2,
+                            double* x0, cudaStream_t st)
 {
-    k_ng_combine<<<grid_1d(N, 256), 256, 0, st>>>(N, x0, x1, x2, a, b, out);
+    k_ng_apply<<<grid_1d(N, 256), 256, 0, st>>>(N, s5, x1, x2, x0);
     return cudaGetLastError();
 }
 

@@ -116,8 +116,8 @@ def test_batch_graph_equals_host_loop(R, method):
     """The operator-splitting step of all active problems as one CUDA graph
     (per-problem branches with device-side sweep loops) gives the iterates
     of the host-driven sweep chunks bit for bit, Jacobi and red-black
-    Gauss-Seidel, with one host wait per iteration (two when Ng
-    extrapolates) instead of one per chunk of sweeps."""
+    Gauss-Seidel, with one host wait per iteration (Ng on the device too)
+    instead of one per chunk of sweeps."""
     probs = _uneven()
     out = {}
     for graphs in (True, False):
@@ -137,7 +137,7 @@ def test_batch_graph_equals_host_loop(R, method):
     for a, c in zip(Jg, Jh):
         assert np.array_equal(a, c)
     assert sg["iterations"] == sh["iterations"] == max(rg["iters"])
-    assert sg["host_syncs"] <= 2 * sg["iterations"]
+    assert sg["host_syncs"] == sg["iterations"]        # one wait per outer iteration
     assert sh["host_syncs"] > sg["host_syncs"]
 
 

@@ -45,15 +45,20 @@ def test_solve_graph_equals_host_loop(R, precision, method):
     p = W.random_slab(11, 10, 9, n_theta=6, n_phi=6, seed=51, eps_range=(1e-3, 1.0))
     prec = R.RT_FP64 if precision == "fp64" else R.RT_FP32_SWEEP
     tol = 1e-9 if precision == "fp64" else 5e-8
-    res = {}
+    res, stats = {}, {}
     for graphs in (True, False):
         with R.Solver(p, precision=prec, ng_period=4, ng_min_delta=1e-6, os_method=method) as s:
             R.rt_set_graphs(s.ctx, graphs)
+            R.rt_reset_stats(s.ctx)
             res[graphs] = s.solve(tol=tol, max_iter=300, tol_inner=1e-11, max_sweeps=200)
+            stats[graphs] = R.rt_get_stats(s.ctx)
     a, b = res[True], res[False]
     assert a["converged"] and a["iters"] == b["iters"]
     assert np.array_equal(a["sweeps"], b["sweeps"])
     assert np.array_equal(a["J"], b["J"])
+    # with graphs, one host wait per outer iteration (Ng runs on the device)
+    assert stats[True]["host_syncs"] == stats[True]["iterations"] == a["iters"]
+    assert stats[False]["host_syncs"] > stats[True]["host_syncs"]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
