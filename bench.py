@@ -41,11 +41,22 @@ FLOPS_PER_STEP_FP64 = 49
 # Peak FP64 of GB300 from the profiling recipe's figure (1.25 TFLOP/s,
 # i.e. 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz).
 PEAK_FP64_TFLOPS = 1.25
-# FP32 arithmetic of one step of the FP32-sweep march (closed-form branch,
-# FMA = 2): chi interpolation 7, source differences S(p) - S_0 20, optical
-# depth 2, weights 4 (plus 2 MUFU: ex2, rcp), the I - S_0 update 4 and its
-# TwoSum 6, optical-depth sum 1, transmission 1 (plus 1 MUFU ex2).
-FLOPS_PER_STEP_FP32 = 45
+# FP32 arithmetic of one step of the FP32-sweep march (FMA = 2), common to
+# both branches of the segment weights: chi interpolation 7, source
+# differences S(p) - S_0 20, optical depth 2 and its running sum 1, the
+# transmission's argument 1 (plus 1 MUFU ex2), the I - S_0 update 3 and its
+# TwoSum 7: 41.  Closed form (x >= 2): e^-x argument, 1 - e, (1 - e)/x,
+# 1 - q, q - e and the two transmission products, 7 (plus MUFU ex2, rcp):
+# 48 per step.  Series (x < 2): z = x^2, two degree-4 Horner chains (16),
+# the odd part's factor x, E -+ O, two factors x and two transmission
+# products, 24 (no MUFU): 65 per step.  The branch mix is counted by the
+# library's branch-counting march (rt_fs32_branch_counts).
+FLOPS_COMMON_FP32 = 41
+FLOPS_CLOSED_FP32 = 48
+FLOPS_SERIES_FP32 = 65
+FLOPS_PER_STEP_FP32 = FLOPS_CLOSED_FP32     # lower bound: every step on the closed form
+# Thread instructions per step of k_fs32d (ncu, 65^3 slab, 32 x 32 directions)
+INSTR_PER_STEP_FP32 = 79.1
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
 PEAK_FP32_TFLOPS = 80.5
 # DRAM bytes (read + write) per k_fs64 launch on slab65, from one ncu
@@ -278,6 +289,11 @@ def march_rate(R, p, precision, dev, stream, launches=5):
         R.rt_set_planck(ctx, p.B)
         R.rt_formal_solution_dev(ctx, S, J, None)
         stream.synchronize()
+        branches = {}
+        if precision == R.RT_FP32_SWEEP:
+            # outside the timed launches: the branch-counting copy of the march
+            n, ser = R.rt_fs32_branch_counts(ctx, S.cpu().numpy())
+            branches = {"branch_count_steps": n, "series_steps": ser}
         R.rt_reset_stats(ctx)
         R.rt_set_profiling(ctx, True)
         for _ in range(launches):
@@ -288,7 +304,7 @@ def march_rate(R, p, precision, dev, stream, launches=5):
     ms = st["fs_ms"] / max(st["fs_launches"], 1)
     steps = st["steps"] / max(st["fs_launches"], 1)
     return {"ms_per_launch": round(ms, 4), "steps_per_launch": round(steps),
-            "fs_steps_per_s": round(steps / (ms / 1e3), 1)}
+            "fs_steps_per_s": round(steps / (ms / 1e3), 1), **branches}
 
 
 def replicas_barrier():
@@ -370,9 +386,52 @@ def run_only(args, dev, R):
                               args.batch_tol, args.ng, args.max_iter)
     elif name == "config5":
         out = config5_iteration(R, dev, stream, args.ng)
+    elif name == "march32":
+        m32 = march_rate(R, make_problem(args.workload), R.RT_FP32_SWEEP, dev, stream)
+        out = {"march": m32, "roofline": fp32_roofline(m32, R.rt_probe_peaks(dev.index))}
     else:
         raise SystemExit(f"unknown companion {name}")
     print(json.dumps({"only": name, name: out}), flush=True)
+
+
+def fp32_roofline(m32, probe):
+    """Roofline of the FP32 march from march_rate's figures: algorithmic
+    flops weighted by the counted branch mix, the closed-form-only lower
+    bound beside it, and the instruction-issue rate that bounds it."""
+    ms, n = m32["ms_per_launch"], m32["steps_per_launch"]
+    ser = m32.get("series_steps")
+    if ser is None:
+        flops = FLOPS_PER_STEP_FP32 * n
+    else:
+        # the counting march ran the same source: its step count is this one's
+        frac_ser = ser / max(m32["branch_count_steps"], 1)
+        flops = n * (FLOPS_SERIES_FP32 * frac_ser + FLOPS_CLOSED_FP32 * (1 - frac_ser))
+    ach32 = flops / (ms / 1e3) / 1e12
+    low = FLOPS_PER_STEP_FP32 * n / (ms / 1e3) / 1e12
+    issue = INSTR_PER_STEP_FP32 * n / (ms / 1e3) / 1e12
+    return {"kernel": "k_fs32d (FP32-sweep march)", "bound": "alu",
+            "achieved": round(ach32, 3), "peak": PEAK_FP32_TFLOPS,
+            "unit": "TFLOP/s", "frac": round(ach32 / PEAK_FP32_TFLOPS, 4),
+            "flops_per_step": round(flops / max(n, 1), 2),
+            "flops_per_step_branches": {"series": FLOPS_SERIES_FP32,
+                                        "closed": FLOPS_CLOSED_FP32},
+            "series_fraction": round(frac_ser, 4) if ser is not None else None,
+            "achieved_closed_form_only": round(low, 3),
+            "frac_closed_form_only": round(low / PEAK_FP32_TFLOPS, 4),
+            "issue": {"instr_per_step": INSTR_PER_STEP_FP32,
+                      "achieved_tinst_s": round(issue, 2),
+                      "peak_tinst_s": PEAK_ISSUE_TINST,
+                      "frac": round(issue / PEAK_ISSUE_TINST, 4)},
+            "peak_source": "unit counts and clock: 152 SMs x 128 lanes x 2 "
+                           "flops x 2.07 GHz",
+            "peak_measured": round(probe["fp32_tflops"], 3)
+            if probe["fp32_tflops"] else None,
+            "frac_of_measured": round(ach32 / probe["fp32_tflops"], 4)
+            if probe["fp32_tflops"] else None,
+            "traffic": TRAFFIC_FS32_SLAB65,
+            "note": "ncu: bound by instruction issue (72% of issue slots; "
+                    "79 thread instructions per step, 46 of them FP32 "
+                    "arithmetic), L1 57%"}
 
 
 def run_ours(args):
@@ -443,21 +502,7 @@ def run_ours(args):
                 "max_rel_dev_from_fp64_J": float(np.max(np.abs(r32["J"] - r64["J"]) / r64["J"])),
                 "speedup_vs_fp64": round(my_ms / args.steps / (ms32 / args.fp32_steps), 3),
                 "march": m32}
-        ach32 = FLOPS_PER_STEP_FP32 * m32["steps_per_launch"] / (m32["ms_per_launch"] / 1e3) / 1e12
-        fp32["roofline"] = {"kernel": "k_fs32d (FP32-sweep march)", "bound": "alu",
-                            "achieved": round(ach32, 3), "peak": PEAK_FP32_TFLOPS,
-                            "unit": "TFLOP/s", "frac": round(ach32 / PEAK_FP32_TFLOPS, 4),
-                            "flops_per_step": FLOPS_PER_STEP_FP32,
-                            "peak_source": "unit counts and clock: 152 SMs x 128 lanes x 2 "
-                                           "flops x 2.07 GHz",
-                            "peak_measured": round(probe["fp32_tflops"], 3)
-                            if probe["fp32_tflops"] else None,
-                            "frac_of_measured": round(ach32 / probe["fp32_tflops"], 4)
-                            if probe["fp32_tflops"] else None,
-                            "traffic": TRAFFIC_FS32_SLAB65,
-                            "note": "ncu: bound by instruction issue (72% of issue slots; "
-                                    "79 thread instructions per step, 46 of them FP32 "
-                                    "arithmetic), L1 57%"}
+        fp32["roofline"] = fp32_roofline(m32, probe)
 
     # the double-float form (FP64-accurate march on the FP32 pipes)
     df64 = None
@@ -779,7 +824,9 @@ def batched_vs_fp64(R, dev, stream, flush, nl, nsub, tol, ng, max_iter):
                                "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                                "frac": round(ach / PEAK_FP32_TFLOPS, 4) if ach else None,
                                "note": "all march launches of the solve (fused FP32 and the "
-                                       "finishing stage), 45 FP32 flops per executed step"},
+                                       "finishing stage), 48 FP32 flops per executed step: "
+                                       "the closed-form count, a lower bound (series steps "
+                                       "do 65)"},
             "clocks": clk.summary(),
             "fp64_plain_subset": {"lambdas": sub, "value": round(v64, 6), "unit": "wavelength-solves/s",
                                   "s": round(ms64 / 1e3, 2), "per_lambda": per},
@@ -834,7 +881,9 @@ def config5_iteration(R, dev, stream, ng):
             "march_steps": int(st["steps"]),
             "march_steps_per_s": round(st["steps"] / (march_ms / 1e3), 1),
             "march_roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": PEAK_FP32_TFLOPS,
-                               "unit": "TFLOP/s", "frac": round(ach / PEAK_FP32_TFLOPS, 4)},
+                               "unit": "TFLOP/s", "frac": round(ach / PEAK_FP32_TFLOPS, 4),
+                               "note": "48 FP32 flops per executed step: the closed-form "
+                                       "count, a lower bound (series steps do 65)"},
             "converged_s_extrapolated": round(march_ms / 1e3 * it_w, 0),
             "extrapolation": "fused march time x the march-work-weighted mean of the iteration "
                              "counts measured at 16x8 directions (293 / 134 / 35 for the three "
@@ -1032,7 +1081,7 @@ def main():
                     help="sweeps timed for the operator-splitting roofline (0 = skip)")
     ap.add_argument("--config5", type=int, default=1,
                     help="time one outer iteration of the uneven batch at 64x64 directions (0 = skip)")
-    ap.add_argument("--only", choices=["os_sweep", "precision", "batched", "config5"],
+    ap.add_argument("--only", choices=["os_sweep", "precision", "batched", "config5", "march32"],
                     help="run one companion measurement alone and print its JSON object "
                          "(profiling and diagnostics; not a bench line)")
     ap.add_argument("--budget-s", type=float, default=1500.0,

@@ -187,6 +187,18 @@ int rt_set_J(rt_ctx *ctx, const double *J);
  * the transmission cutoff are not counted). */
 int rt_last_step_count(rt_ctx *ctx, unsigned long long *steps);
 
+/* Diagnostics for the FP32-sweep long-characteristics march: march the
+ * source S (host array [N], or NULL for S = eps B + (1 - eps) J from the
+ * current iterate) once through a branch-counting copy of the march kernel
+ * and return the steps executed (*steps, as rt_last_step_count) and how
+ * many of them evaluated the linear-source segment weights (Sect. 2.2)
+ * through the series branch, optical depth x < 2 (*series; the rest took
+ * the closed form).
+ * J is not returned and the iterate is unchanged.  RT_EINVAL for another
+ * precision or method, or NULL outputs. */
+int rt_fs32_branch_counts(rt_ctx *ctx, const double *S, unsigned long long *steps,
+                          unsigned long long *series);
+
 /* Ng acceleration of the outer iteration (the paper keeps it, with the
  * set-up, in host code, Sect. 2): after every `period`-th iteration, once
  * the four latest iterates x0 (newest) .. x3 are held, x0 is replaced by

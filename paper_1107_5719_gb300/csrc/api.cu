@@ -1722,6 +1722,42 @@ int rt_set_J(rt_ctx* c, const double* J)
     return RT_OK;
 }
 
+// Diagnostics: one FP32 march of the source S (host, or NULL for
+// eps B + (1 - eps) J) through the branch-counting kernel instantiation.
+static int fs32_branch_counts(rt_ctx* c, const double* S, unsigned long long* steps,
+                              unsigned long long* series)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if ((rc = need_all(c))) return rc;
+    if (!steps || !series) return fail(c, RT_EINVAL, "steps or series is NULL");
+    if (c->precision != RT_FP32_SWEEP || c->fs_method != RT_FS_LONG)
+        return fail(c, RT_EINVAL, "branch counts need the FP32-sweep long-characteristics march");
+    if ((rc = prepare_source(c, S, false))) return rc;
+    if ((rc = fs_prepare(c))) return rc;
+    unsigned long long* d = nullptr;
+    CK(cudaMalloc((void**)&d, 2 * sizeof(unsigned long long)));
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess)
+        e = launch_fs32d(view32(c), cut_of(c), auto_groups(c), c->threads32, d, c->stream, d + 1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(c, RT_ECUDA, "CUDA error %s", cudaGetErrorString(e));
+    c->stats.launches += 1;
+    *steps = h[0];
+    *series = h[1];
+    return RT_OK;
+}
+
+int rt_fs32_branch_counts(rt_ctx* c, const double* S, unsigned long long* steps,
+                          unsigned long long* series)
+{
+    return check_bounds(c, fs32_branch_counts(c, S, steps, series));
+}
+
 int rt_last_step_count(rt_ctx* c, unsigned long long* steps)
 {
     if (!c || !steps) return RT_EINVAL;

@@ -124,7 +124,8 @@ struct Ray32 {
 // One step of a voxel's characteristic, from p_m to p_m+1: the upstream
 // point's four nodes are u0 = {chi, S_hi} of (x0, y0) and (x1, y0), u1 the
 // same of (x0, y1), (x1, y1); l0, l1 their S_lo; b the bilinear weights.
-__device__ __forceinline__ void step32(Ray32& r, float hs, float4 b, float4 u0, float4 u1,
+// Returns whether the segment took the series branch (x < 2).
+__device__ __forceinline__ bool step32(Ray32& r, float hs, float4 b, float4 u0, float4 u1,
                                        float2 l0, float2 l1)
 {
     constexpr float kLog2e = 1.4426950408889634f;
@@ -162,6 +163,7 @@ __device__ __forceinline__ void step32(Ray32& r, float hs, float4 b, float4 u0, 
     r.T = Tn;
     r.ca = cb;
     r.da = db;
+    return x < 2.0f;
 }
 
 // Boundary term T_M (I_bc - S_0) of a characteristic that reached the
@@ -221,16 +223,19 @@ __device__ __forceinline__ void boundary32(Ray32& r, const View32& p, const DirI
 // cut off (or reach the boundary, where both take their boundary term); a
 // voxel whose own cutoff came first keeps adding its (negligible) terms.
 // The step count is that of each voxel's own cutoff.
-template <int TB>
+// COUNT (diagnostics only): also count the steps that took the series
+// branch of the segment weights into *series.
+template <int TB, bool COUNT>
 __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int zb, int ZB,
-                                        float cut, unsigned long long* __restrict__ steps)
+                                        float cut, unsigned long long* __restrict__ steps,
+                                        unsigned long long* __restrict__ series)
 {
     const Geometry& g = p.g;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int nyp = (ny + 1) >> 1;
     const int t = tile * TB + threadIdx.x;
     const bool active = t < nx * nyp;
-    unsigned long long nsteps = 0;
+    unsigned long long nsteps = 0, nseries = 0;
     if (active) {
         const int jp = t / nx, i0 = t - jp * nx, j0 = 2 * jp;
         const bool two = j0 + 1 < ny;
@@ -268,7 +273,7 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                 Ray32 a{ma.y, la.x, tca, 0.f, 0.f, 0.f, 1.f, ma.x, 0.f};
                 Ray32 b{mb.y, lb.x, tcb, 0.f, 0.f, 0.f, 1.f, mb.x, 0.f};
                 bool alive_a = true, alive_b = true, early = false;
-                int na = 0, nb = 0;
+                int na = 0, nb = 0, sa = 0, sb = 0;
                 int m = 0;
 #pragma unroll 2
                 for (; m < M; ++m) {
@@ -280,8 +285,12 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                     const float2* ql = pl + o;
                     const float4 u0 = __ldg(q), u1 = __ldg(q + W), u2 = __ldg(q + 2 * W);
                     const float2 l0 = __ldg(ql), l1 = __ldg(ql + W), l2 = __ldg(ql + 2 * W);
-                    step32(a, di.hs32, bw, u0, u1, l0, l1);
-                    step32(b, di.hs32, bw, u1, u2, l1, l2);
+                    const bool ba = step32(a, di.hs32, bw, u0, u1, l0, l1);
+                    const bool bb = step32(b, di.hs32, bw, u1, u2, l1, l2);
+                    if (COUNT) {
+                        sa += alive_a && ba;
+                        sb += alive_b && bb;
+                    }
                     na += alive_a;
                     nb += alive_b;
                     alive_a = alive_a && a.T > a.tcut;
@@ -297,6 +306,7 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                     if (two) boundary32(b, p, di, d, M, i0, j0 + 1);
                 }
                 nsteps += (unsigned long long)na + (two ? (unsigned long long)nb : 0ull);
+                if (COUNT) nseries += (unsigned long long)sa + (two ? (unsigned long long)sb : 0ull);
                 Ja = fma(di.w, (double)a.I + (double)a.Ilo, Ja);
                 Jb = fma(di.w, (double)b.I + (double)b.Ilo, Jb);
             }
@@ -305,13 +315,15 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
         }
     }
     if (steps) add_steps32(steps, nsteps);
+    if (COUNT && series) add_steps32(series, nseries);
 }
 
-template <int TB>
+template <int TB, bool COUNT>
 __global__ void __launch_bounds__(TB, kResident32 / TB)
-k_fs32d(View32 p, float cut, unsigned long long* __restrict__ steps)
+k_fs32d(View32 p, float cut, unsigned long long* __restrict__ steps,
+        unsigned long long* __restrict__ series)
 {
-    march32<TB>(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, cut, steps);
+    march32<TB, COUNT>(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, cut, steps, series);
 }
 
 int tiles32(const Geometry& g, int tb) { return (g.nx * ((g.ny + 1) / 2) + tb - 1) / tb; }
@@ -338,7 +350,7 @@ k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
     const int tile = (int)(local % tiles);
     const int k0 = (int)((local / tiles) % p.g.nz);
     const int zb = (int)(local / ((long long)tiles * p.g.nz));
-    march32<TB>(p, tile, k0, zb, ZB, cut, steps);
+    march32<TB, false>(p, tile, k0, zb, ZB, cut, steps, nullptr);
 }
 
 // dS = S - Sref (the source change the finishing stage marches)
@@ -425,18 +437,22 @@ cudaError_t launch_pack_b2(const Geometry& g, const double* B, float2* b2, cudaS
 int block_threads32(int threads) { return threads == 64 || threads == 256 ? threads : kThreads32; }
 
 cudaError_t launch_fs32d(const View32& p, double cut, int groups, int threads,
-                         unsigned long long* steps, cudaStream_t st)
+                         unsigned long long* steps, cudaStream_t st, unsigned long long* series)
 {
     // planes in index order (g.zorder unused): with the plane read from the
     // order table the march ran at 14.6 instead of 10.7 ms on the 65^3 slab
     const int tb = block_threads32(threads);
     dim3 grid(tiles32(p.g, tb), p.g.nz, groups);
-    if (tb == 64)
-        k_fs32d<64><<<grid, 64, 0, st>>>(p, (float)cut, steps);
+    const float c = (float)cut;
+    if (series)   // diagnostics: the branch-counting instantiation, 128 threads
+        k_fs32d<kThreads32, true><<<dim3(tiles32(p.g, kThreads32), p.g.nz, groups), kThreads32, 0,
+                                     st>>>(p, c, steps, series);
+    else if (tb == 64)
+        k_fs32d<64, false><<<grid, 64, 0, st>>>(p, c, steps, nullptr);
     else if (tb == 256)
-        k_fs32d<256><<<grid, 256, 0, st>>>(p, (float)cut, steps);
+        k_fs32d<256, false><<<grid, 256, 0, st>>>(p, c, steps, nullptr);
     else
-        k_fs32d<kThreads32><<<grid, kThreads32, 0, st>>>(p, (float)cut, steps);
+        k_fs32d<kThreads32, false><<<grid, kThreads32, 0, st>>>(p, c, steps, nullptr);
     return cudaGetLastError();
 }
 

@@ -195,9 +195,12 @@ struct View32 {
 };
 // FP32 march of I - S_0: partial[kSlots][N] of sum_d w_d (I_d - S_0).
 // threads: threads per block, 64, 128 or 256 (anything else: 128); J does
-// not depend on it.
+// not depend on it.  series != null (diagnostics): a kernel instantiation
+// that also counts the steps whose segment took the series branch of the
+// weights (x < 2) into *series (same J).
 cudaError_t launch_fs32d(const View32& p, double cut, int groups, int threads,
-                         unsigned long long* steps, cudaStream_t st);
+                         unsigned long long* steps, cudaStream_t st,
+                         unsigned long long* series = nullptr);
 // Blocks one problem takes in a batched launch with `groups` slot groups.
 long long fs32_blocks(const Geometry& g, int groups, int threads);
 // One launch over the active problems ids[0..nact) of views (device arrays);

@@ -88,6 +88,8 @@ _SIGS = {
     "rt_get_J": (C.c_int, [VP, VP]),
     "rt_set_J": (C.c_int, [VP, VP]),
     "rt_last_step_count": (C.c_int, [VP, C.POINTER(C.c_ulonglong)]),
+    "rt_fs32_branch_counts": (C.c_int, [VP, VP, C.POINTER(C.c_ulonglong),
+                                        C.POINTER(C.c_ulonglong)]),
     "rt_set_direction_groups": (C.c_int, [VP, C.c_int]),
     "rt_set_cutoff": (C.c_int, [VP, C.c_double]),
     "rt_set_profiling": (C.c_int, [VP, C.c_int]),
@@ -316,6 +318,17 @@ def rt_last_step_count(ctx) -> int:
     n = C.c_ulonglong()
     _check(ctx, load().rt_last_step_count(ctx, C.byref(n)))
     return n.value
+
+
+def rt_fs32_branch_counts(ctx, S=None):
+    """(steps, series steps) of one counting FP32 march of S (None: from
+    the current iterate)."""
+    p = None
+    if S is not None:
+        S, p = _host(S)
+    n, s = C.c_ulonglong(), C.c_ulonglong()
+    _check(ctx, load().rt_fs32_branch_counts(ctx, p, C.byref(n), C.byref(s)))
+    return n.value, s.value
 
 
 def rt_set_direction_groups(ctx, groups):

@@ -133,3 +133,40 @@ def test_fs32_slab65_sampled(R, oracle_mod):
     Jo = oracle_mod.mean_intensity_at(p, S, vox)
     assert np.allclose(J.ravel()[vox], Jo, rtol=FS_RTOL, atol=0)
 
+
+
+def test_branch_counts_split_steps_by_segment_optical_depth(R):
+    """The diagnostic branch count of the FP32 march: with a uniform opacity
+    every segment of direction mu has optical depth chi dz / |mu|, so the
+    series branch (x < 2) is taken on every step of the directions with
+    chi dz < 2 |mu| and on no step of the others; the step count of each
+    direction does not depend on the others (no cutoff)."""
+    nx, ny, nz = 9, 8, 7
+    base = W.random_slab(nx, ny, nz, seed=41)
+    chi = np.full_like(base.chi, 0.5)
+    S = base.B * 1.1
+    thin = ([0.9, -0.5, 0.35, -0.9], [0.3, 1.7, 2.9, 4.4])   # x = 0.56, 1.0, 1.43, 0.56
+    thick = ([0.1, -0.2, 0.15], [0.8, 2.2, 5.1])             # x = 5.0, 2.5, 3.3
+
+    def counts(mu, phi):
+        mu, phi = np.array(mu), np.array(phi)
+        p = W.Problem(nx, ny, nz, chi, base.eps, base.B, mu, phi, np.full(len(mu), 1 / len(mu)))
+        with R.Solver(p, precision=R.RT_FP32_SWEEP, cutoff=0.0) as s:
+            n, ser = R.rt_fs32_branch_counts(s.ctx, S)
+            s.formal_solution(S, want_lstar=False)
+            assert n == R.rt_last_step_count(s.ctx)
+        return n, ser
+
+    n_thin, s_thin = counts(*thin)
+    n_thick, s_thick = counts(*thick)
+    assert n_thin > 0 and s_thin == n_thin
+    assert n_thick > 0 and s_thick == 0
+    n_mix, s_mix = counts(thin[0] + thick[0], thin[1] + thick[1])
+    assert (n_mix, s_mix) == (n_thin + n_thick, n_thin)
+
+
+def test_branch_counts_reject_other_precisions(R):
+    p = W.random_slab(5, 4, 3, seed=2)
+    with R.Solver(p) as s:
+        with pytest.raises(R.RtError):
+            R.rt_fs32_branch_counts(s.ctx)
