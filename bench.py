@@ -44,19 +44,20 @@ PEAK_FP64_TFLOPS = 1.25
 # FP32 arithmetic of one step of the FP32-sweep march (FMA = 2), common to
 # both branches of the segment weights: chi interpolation 7, source
 # differences S(p) - S_0 20, optical depth 2 and its running sum 1, the
-# transmission's argument 1 (plus 1 MUFU ex2), the I - S_0 update 3 and its
-# TwoSum 7: 41.  Closed form (x >= 2): e^-x argument, 1 - e, (1 - e)/x,
-# 1 - q, q - e and the two transmission products, 7 (plus MUFU ex2, rcp):
-# 48 per step.  Series (x < 2): z = x^2, two degree-4 Horner chains (16),
-# the odd part's factor x, E -+ O, two factors x and two transmission
-# products, 24 (no MUFU): 65 per step.  The branch mix is counted by the
-# library's branch-counting march (rt_fs32_branch_counts).
-FLOPS_COMMON_FP32 = 41
-FLOPS_CLOSED_FP32 = 48
-FLOPS_SERIES_FP32 = 65
+# transmission's argument 1 (plus 1 MUFU ex2), the increment folded with
+# the carried low part (2 FMA) 4 and the compensated sum 3: 38.  Closed
+# form (x >= 2): e^-x argument, 1 - e, (1 - e)/x, 1 - q, q - e and the two
+# transmission products, 7 (plus MUFU ex2, rcp): 45 per step.  Series
+# (x < 2): z = x^2, two degree-4 Horner chains (16), x E, z Q, their
+# difference and sum and two transmission products, 23 (no MUFU): 61 per
+# step.  The branch mix is counted by the library's branch-counting march
+# (rt_fs32_branch_counts).
+FLOPS_COMMON_FP32 = 38
+FLOPS_CLOSED_FP32 = 45
+FLOPS_SERIES_FP32 = 61
 FLOPS_PER_STEP_FP32 = FLOPS_CLOSED_FP32     # lower bound: every step on the closed form
 # Thread instructions per step of k_fs32d (ncu, 65^3 slab, 32 x 32 directions)
-INSTR_PER_STEP_FP32 = 79.1
+INSTR_PER_STEP_FP32 = 73.5
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
 PEAK_FP32_TFLOPS = 80.5
 # DRAM bytes (read + write) per k_fs64 launch on slab65, from one ncu
@@ -97,7 +98,7 @@ TRAFFIC_JACOBI_129 = 494896128
 # DRAM bytes (read + write) of one k_fs32d launch on slab65, from one ncu
 # capture of the current kernel: 27.77 MB read (the padded pair planes,
 # the tables) + 0.01 MB written; then everything is served from L2.
-TRAFFIC_FS32_SLAB65 = 27782144
+TRAFFIC_FS32_SLAB65 = 27782656
 
 # The FP32-sweep iterate stops changing below a relative delta of ~1e-8
 # (rounding), so its outer tolerance is at least 5e-8, and Ng extrapolation
@@ -429,9 +430,9 @@ def fp32_roofline(m32, probe):
             "frac_of_measured": round(ach32 / probe["fp32_tflops"], 4)
             if probe["fp32_tflops"] else None,
             "traffic": TRAFFIC_FS32_SLAB65,
-            "note": "ncu: bound by instruction issue (72% of issue slots; "
-                    "79 thread instructions per step, 46 of them FP32 "
-                    "arithmetic), L1 57%"}
+            "note": "ncu: bound by instruction issue (73% of issue slots; "
+                    "73.5 thread instructions per step, 41.5 of them FP32 "
+                    "arithmetic), L1 62%"}
 
 
 def run_ours(args):
@@ -824,9 +825,9 @@ def batched_vs_fp64(R, dev, stream, flush, nl, nsub, tol, ng, max_iter):
                                "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                                "frac": round(ach / PEAK_FP32_TFLOPS, 4) if ach else None,
                                "note": "all march launches of the solve (fused FP32 and the "
-                                       "finishing stage), 48 FP32 flops per executed step: "
+                                       "finishing stage), 45 FP32 flops per executed step: "
                                        "the closed-form count, a lower bound (series steps "
-                                       "do 65)"},
+                                       "do 61)"},
             "clocks": clk.summary(),
             "fp64_plain_subset": {"lambdas": sub, "value": round(v64, 6), "unit": "wavelength-solves/s",
                                   "s": round(ms64 / 1e3, 2), "per_lambda": per},
@@ -882,8 +883,8 @@ def config5_iteration(R, dev, stream, ng):
             "march_steps_per_s": round(st["steps"] / (march_ms / 1e3), 1),
             "march_roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": PEAK_FP32_TFLOPS,
                                "unit": "TFLOP/s", "frac": round(ach / PEAK_FP32_TFLOPS, 4),
-                               "note": "48 FP32 flops per executed step: the closed-form "
-                                       "count, a lower bound (series steps do 65)"},
+                               "note": "45 FP32 flops per executed step: the closed-form "
+                                       "count, a lower bound (series steps do 61)"},
             "converged_s_extrapolated": round(march_ms / 1e3 * it_w, 0),
             "extrapolation": "fused march time x the march-work-weighted mean of the iteration "
                              "counts measured at 16x8 directions (293 / 134 / 35 for the three "

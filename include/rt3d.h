@@ -319,6 +319,14 @@ int rt_set_direction_groups(rt_ctx *ctx, int groups);
  * default, 128).  Each size keeps 768 resident threads per SM (the same
  * registers per thread); J does not depend on it.  RT_EINVAL otherwise. */
 int rt_set_block_threads(rt_ctx *ctx, int threads);
+/* Tuning: block order of the FP32-sweep march.  1: the tiles of a plane
+ * are consecutive blocks, so the resident blocks share a few planes and
+ * read every plane within their rays' reach; 2: the planes of a tile are
+ * consecutive, so they share a few lateral tiles through every plane;
+ * 0 (default): 2 once the padded source planes of the grid exceed 64 MiB
+ * (no longer held in L2 together), else 1.  J does not depend on it.
+ * RT_EINVAL for another value. */
+int rt_set_block_order(rt_ctx *ctx, int order);
 
 /* Tuning: relative transmission cutoff.  The march along a characteristic
  * stops once T * max(|S|, |I_bc|) <= cut * |I| (the rest can change I by
@@ -446,6 +454,8 @@ int rt_batch_get_J_dev(rt_batch *batch, int p, double *J);
 int rt_batch_set_direction_groups(rt_batch *batch, int groups);
 /* As rt_set_block_threads, for the fused FP32 launch. */
 int rt_batch_set_block_threads(rt_batch *batch, int threads);
+/* As rt_set_block_order, for every problem of the fused FP32 launch. */
+int rt_batch_set_block_order(rt_batch *batch, int order);
 /* on != 0 (the default): every outer iteration runs the operator-splitting
  * solves of all active problems (Sect. 2.3) as ONE CUDA graph, one
  * independent branch per problem (right-hand side, a device-side loop of

@@ -60,6 +60,7 @@ struct rt_ctx {
     size_t scpart_n = 0, scplanes_n = 0;
     int groups_req = 0;
     int threads32 = 0;       // threads per block of the FP32 march (0: 128)
+    int order32 = 0;         // block order of the FP32 march (0 auto, 1 tile-, 2 plane-major)
     double cut = -1.0;
 
     // device state, FP64
@@ -358,6 +359,7 @@ View32 view32(rt_ctx* c)
     v.smax = c->scal + 0;
     v.sfloor = nullptr;
     v.partial = c->partial;
+    v.pmajor = plane_major32(c->g, c->order32);
     return v;
 }
 
@@ -1783,6 +1785,16 @@ int rt_set_block_threads(rt_ctx* c, int threads)
     return RT_OK;
 }
 
+int rt_set_block_order(rt_ctx* c, int order)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if (order < 0 || order > 2)
+        return fail(c, RT_EINVAL, "block order must be 0 (automatic), 1 (tile-major) or 2 (plane-major)");
+    c->order32 = order;
+    return RT_OK;
+}
+
 int rt_set_cutoff(rt_ctx* c, double cut)
 {
     if (!c) return RT_EINVAL;
@@ -2231,6 +2243,22 @@ int rt_batch_set_block_threads(rt_batch* b, int threads)
     if (threads != 0 && threads != 64 && threads != 128 && threads != 256)
         return bfail(b, RT_EINVAL, "threads per block must be 0 (default), 64, 128 or 256");
     b->threads32 = threads;
+    return RT_OK;
+}
+
+int rt_batch_set_block_order(rt_batch* b, int order)
+{
+    if (!b) return RT_EINVAL;
+    b->err.clear();
+    if (order < 0 || order > 2)
+        return bfail(b, RT_EINVAL, "block order must be 0 (automatic), 1 (tile-major) or 2 (plane-major)");
+    for (rt_ctx* c : b->ctx) c->order32 = order;
+    const int n = (int)b->ctx.size();
+    for (int p = 0; p < n; ++p)
+        b->h_views[p] = b->view_fin[p] ? view32_fin(b->ctx[p]) : view32(b->ctx[p]);
+    BCK(cudaMemcpyAsync(b->d_views, b->h_views, sizeof(View32) * n, cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
     return RT_OK;
 }
 

@@ -69,6 +69,7 @@ __global__ void k_dir_tables(Geometry g, double dx, double dy, double dz,
         di.hs32lo = (float)(di.hs - (double)di.hs32);
         di.amu32lo = (float)(amu - (double)di.amu32);
         di.w = w[d];
+        di.w32 = (float)di.w;
         di.sgn = m_u > 0.0 ? 1 : -1;
         // Lambda* offsets of the four nodes of p_1 (plane k0 - sgn).
         const long long ix = (long long)floor(-ax), iy = (long long)floor(-ay);

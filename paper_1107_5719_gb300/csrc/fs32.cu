@@ -117,7 +117,7 @@ __device__ __forceinline__ void add_steps32(unsigned long long* steps, unsigned 
 // Per-voxel state of one characteristic of the FP32 march.
 struct Ray32 {
     float s0h, s0l, tcut;   // S_0 as an FP32 pair; transmission cutoff
-    float I, Ilo;           // I - S_0 as an unevaluated pair
+    float I, Ilo;           // I - S_0 as an unevaluated sum I + Ilo
     float tau, T, ca, da;   // optical depth, transmission, hs chi and S - S_0 at p_m
 };
 
@@ -146,24 +146,41 @@ __device__ __forceinline__ bool step32(Ray32& r, float hs, float4 b, float4 u0, 
     const float Tn = ex2_approx(-r.tau * kLog2e);
     float wcT, wuT;
     if (x < 2.0f) {
-        float E, O;
-        phi2_parts32(x, E, O);
-        wcT = r.T * (x * (E - O));
-        wuT = Tn * (x * (E + O));
+        // x phi2(-+x) = x E -+ x^2 Q
+        const float z = x * x;
+        float E, Q;
+        phi2_eq32(z, E, Q);
+        const float xe = x * E, zq = z * Q;
+        wcT = r.T * (xe - zq);
+        wuT = Tn * (xe + zq);
     } else {
         const float e = ex2_approx(-x * kLog2e);
         const float q = (1.0f - e) * rcp_approx(x);
         wcT = r.T * (1.0f - q);
         wuT = r.T * (q - e);
     }
-    const float inc = fmaf(wcT, r.da, wuT * db);
-    const float sI = r.I + inc, bb = sI - r.I;
-    r.Ilo += (r.I - (sI - bb)) + (inc - bb);
+    // compensated (Kahan) accumulation of I - S_0 = I + Ilo: the carried
+    // low part enters the increment's last FMA, and the rounding error of
+    // the sum becomes the new low part
+    const float y = fmaf(wcT, r.da, fmaf(wuT, db, r.Ilo));
+    const float sI = r.I + y;
+    r.Ilo = y - (sI - r.I);
     r.I = sI;
     r.T = Tn;
     r.ca = cb;
     r.da = db;
     return x < 2.0f;
+}
+
+// s + lo += w (v + vlo): the product w v split exactly (TwoProduct by FMA)
+// and added by TwoSum; the low parts are gathered in lo
+__device__ __forceinline__ void pair_add(float& s, float& lo, float w, float v, float vlo)
+{
+    const float p = w * v;
+    const float pe = fmaf(w, vlo, fmaf(w, v, -p));
+    const float t = s + p, bb = t - s;
+    lo += (s - (t - bb)) + (p - bb) + pe;
+    s = t;
 }
 
 // Boundary term T_M (I_bc - S_0) of a characteristic that reached the
@@ -263,7 +280,10 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
             tcb = two ? ka * (mb.y + lb.x) : 2.0f;
         }
         for (int slot = zb; slot < kSlots; slot += ZB) {
-            double Ja = 0.0, Jb = 0.0;
+            // sum_d w_d (I_d - S_0) of the slot as an FP32 pair (the FP64
+            // pipe of this GPU runs at 1/64 of the FP32 rate; measured on the
+            // 65^3 slab: 8.7-9.0 ms against 9.13 with FP64 accumulation)
+            float Ja = 0.f, Jalo = 0.f, Jb = 0.f, Jblo = 0.f;
             for (int d = slot; d < g.ndir; d += kSlots) {
                 const DirInfo di = p.info[d];
                 const int s = di.sgn;
@@ -307,11 +327,11 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                 }
                 nsteps += (unsigned long long)na + (two ? (unsigned long long)nb : 0ull);
                 if (COUNT) nseries += (unsigned long long)sa + (two ? (unsigned long long)sb : 0ull);
-                Ja = fma(di.w, (double)a.I + (double)a.Ilo, Ja);
-                Jb = fma(di.w, (double)b.I + (double)b.Ilo, Jb);
+                pair_add(Ja, Jalo, di.w32, a.I, a.Ilo);
+                pair_add(Jb, Jblo, di.w32, b.I, b.Ilo);
             }
-            p.partial[(long long)slot * g.N + va] = Ja;
-            if (two) p.partial[(long long)slot * g.N + va + nx] = Jb;
+            p.partial[(long long)slot * g.N + va] = (double)Ja + (double)Jalo;
+            if (two) p.partial[(long long)slot * g.N + va + nx] = (double)Jb + (double)Jblo;
         }
     }
     if (steps) add_steps32(steps, nsteps);
@@ -323,7 +343,9 @@ __global__ void __launch_bounds__(TB, kResident32 / TB)
 k_fs32d(View32 p, float cut, unsigned long long* __restrict__ steps,
         unsigned long long* __restrict__ series)
 {
-    march32<TB, COUNT>(p, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, cut, steps, series);
+    const int tile = p.pmajor ? blockIdx.y : blockIdx.x;
+    const int k0 = p.pmajor ? blockIdx.x : blockIdx.y;
+    march32<TB, COUNT>(p, tile, k0, blockIdx.z, gridDim.z, cut, steps, series);
 }
 
 int tiles32(const Geometry& g, int tb) { return (g.nx * ((g.ny + 1) / 2) + tb - 1) / tb; }
@@ -347,9 +369,10 @@ k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
     const View32& p = views[ids[lo]];
     const long long local = b - prefix[lo];
     const int tiles = (p.g.nx * ((p.g.ny + 1) >> 1) + TB - 1) / TB;
-    const int tile = (int)(local % tiles);
-    const int k0 = (int)((local / tiles) % p.g.nz);
+    const long long tk = local % ((long long)tiles * p.g.nz);
     const int zb = (int)(local / ((long long)tiles * p.g.nz));
+    const int tile = p.pmajor ? (int)(tk / p.g.nz) : (int)(tk % tiles);
+    const int k0 = p.pmajor ? (int)(tk % p.g.nz) : (int)(tk / tiles);
     march32<TB, false>(p, tile, k0, zb, ZB, cut, steps, nullptr);
 }
 
@@ -412,6 +435,17 @@ unsigned grid1d(long long n, int threads)
 
 }  // namespace
 
+int plane_major32(const Geometry& g, int order)
+{
+    if (order == 1) return 0;
+    const long long tiles = tiles32(g, 64);   // the most tiles of any block size
+    if (tiles > 65535) return 0;              // grid y limit
+    if (order == 2) return 1;
+    const long long bytes = (2ll * g.ny + 1) * 2ll * g.nx * (long long)g.nz *
+                            (long long)(sizeof(float4) + sizeof(float2));
+    return bytes > kPlaneMajorBytes ? 1 : 0;
+}
+
 long long pair_records(const Geometry& g) { return (2LL * g.ny + 1) * 2LL * g.nx * g.nz; }
 
 cudaError_t launch_pad_offsets(const Geometry& g, const DirInfo* info, const StepGeo* off,
@@ -442,11 +476,15 @@ cudaError_t launch_fs32d(const View32& p, double cut, int groups, int threads,
     // planes in index order (g.zorder unused): with the plane read from the
     // order table the march ran at 14.6 instead of 10.7 ms on the 65^3 slab
     const int tb = block_threads32(threads);
-    dim3 grid(tiles32(p.g, tb), p.g.nz, groups);
+    auto shape = [&](int t) {
+        const int tiles = tiles32(p.g, t);
+        return p.pmajor ? dim3(p.g.nz, tiles, groups) : dim3(tiles, p.g.nz, groups);
+    };
+    if (p.pmajor && tiles32(p.g, 64) > 65535) return cudaErrorInvalidConfiguration;
+    const dim3 grid = shape(tb);
     const float c = (float)cut;
     if (series)   // diagnostics: the branch-counting instantiation, 128 threads
-        k_fs32d<kThreads32, true><<<dim3(tiles32(p.g, kThreads32), p.g.nz, groups), kThreads32, 0,
-                                     st>>>(p, c, steps, series);
+        k_fs32d<kThreads32, true><<<shape(kThreads32), kThreads32, 0, st>>>(p, c, steps, series);
     else if (tb == 64)
         k_fs32d<64, false><<<grid, 64, 0, st>>>(p, c, steps, nullptr);
     else if (tb == 256)

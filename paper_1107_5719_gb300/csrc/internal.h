@@ -21,6 +21,7 @@ struct DirInfo {
     int lo[4];      // Lambda* offset index of the four bilinear nodes of p_1, -1 if none
     float hs32;     // hs in FP32 (sweep form)
     float amu32;    // |mu| in FP32
+    float w32;      // w in FP32 (sweep form)
     double amu;     // |mu| (LTE-diffusion boundary)
     float hs32lo;   // hs - hs32: hs as a double-float pair (RT_DF64 march)
     float amu32lo;  // |mu| - amu32
@@ -192,7 +193,16 @@ struct View32 {
     // magnitude is at least *sfloor, and the cutoff is relative to that.
     const double* sfloor;
     double* partial;        // [kSlots][N]
+    // Block order of the launch: 0 = tiles of a plane consecutive (the
+    // resident blocks share a few planes), 1 = planes consecutive (they
+    // share a few lateral tiles through every plane).
+    int pmajor;
 };
+// Block order of the FP32 march for grid g: order 1 = tile-major, 2 =
+// plane-major, 0 = automatic (plane-major once the padded pair planes
+// exceed kPlaneMajorBytes, i.e. no longer stay in L2 together).
+constexpr long long kPlaneMajorBytes = 64ll << 20;
+int plane_major32(const Geometry& g, int order);
 // FP32 march of I - S_0: partial[kSlots][N] of sum_d w_d (I_d - S_0).
 // threads: threads per block, 64, 128 or 256 (anything else: 128); J does
 // not depend on it.  series != null (diagnostics): a kernel instantiation

@@ -140,16 +140,23 @@ __device__ __forceinline__ float rcp_approx(float y)
     return r;
 }
 
-// E = phi2 even part, O = odd part at x < 2 (phi2(+-x) = E +- O)
-__device__ __forceinline__ void phi2_parts32(float x, float& E, float& O)
+// E(z) and Q(z), z = x^2 < 4: phi2(+-x) = E +- x Q
+__device__ __forceinline__ void phi2_eq32(float z, float& E, float& Q)
 {
-    const float z = x * x;
     E = fmaf(fmaf(fmaf(2.968770900e-07f, z, 2.472764936e-05f), z, 1.388992299e-03f), z,
              4.166661575e-02f);
     E = fmaf(E, z, 0.5f);
-    O = fmaf(fmaf(fmaf(2.669341548e-08f, z, 2.749998430e-06f), z, 1.984207920e-04f), z,
+    Q = fmaf(fmaf(fmaf(2.669341548e-08f, z, 2.749998430e-06f), z, 1.984207920e-04f), z,
              8.333329111e-03f);
-    O = fmaf(O, z, 1.666666716e-01f) * x;
+    Q = fmaf(Q, z, 1.666666716e-01f);
+}
+
+// E = phi2 even part, O = odd part at x < 2 (phi2(+-x) = E +- O)
+__device__ __forceinline__ void phi2_parts32(float x, float& E, float& O)
+{
+    float Q;
+    phi2_eq32(x * x, E, Q);
+    O = Q * x;
 }
 
 __device__ __forceinline__ void seg_weights32(float x, float& wc, float& wu, float& e)

@@ -122,7 +122,9 @@ _SIGS = {
     "rt_batch_set_direction_groups": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_graphs": (C.c_int, [VP, C.c_int]),
     "rt_set_block_threads": (C.c_int, [VP, C.c_int]),
+    "rt_set_block_order": (C.c_int, [VP, C.c_int]),
     "rt_batch_set_block_threads": (C.c_int, [VP, C.c_int]),
+    "rt_batch_set_block_order": (C.c_int, [VP, C.c_int]),
     "rt_probe_peaks": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "rt_batch_set_profiling": (C.c_int, [VP, C.c_int]),
     "rt_batch_get_stats": (C.c_int, [VP, C.POINTER(rt_stats)]),
@@ -520,8 +522,16 @@ def rt_set_block_threads(ctx, threads):
     return _check(ctx, load().rt_set_block_threads(ctx, threads))
 
 
+def rt_set_block_order(ctx, order):
+    return _check(ctx, load().rt_set_block_order(ctx, order))
+
+
 def rt_batch_set_block_threads(b, threads):
     return _bcheck(b, load().rt_batch_set_block_threads(b, threads))
+
+
+def rt_batch_set_block_order(b, order):
+    return _bcheck(b, load().rt_batch_set_block_order(b, order))
 
 
 def rt_batch_set_graphs(b, on=True):

@@ -142,15 +142,16 @@ def test_batch_graph_equals_host_loop(R, method):
 
 
 def test_batch_launch_shape_does_not_change_results(R):
-    """Threads per block and direction groups of the fused FP32 launch are
-    tuning knobs only: bit-identical iterates."""
+    """Threads per block, direction groups and block order of the fused FP32
+    launch are tuning knobs only: bit-identical iterates."""
     probs = _uneven()[:3]
     out = []
-    for groups, threads in ((0, 0), (2, 64), (8, 256)):
+    for groups, threads, order in ((0, 0, 0), (2, 64, 2), (8, 256, 1), (1, 128, 2)):
         b = R.rt_batch_create(probs, precision=1)
         try:
             R.rt_batch_set_direction_groups(b, groups)
             R.rt_batch_set_block_threads(b, threads)
+            R.rt_batch_set_block_order(b, order)
             r = R.rt_batch_solve(b, len(probs), tol=TOL[1], max_iter=500)
             out.append((r["iters"], [R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx))
                                      for i, p in enumerate(probs)]))

@@ -74,19 +74,24 @@ def test_fs32_constant_source_is_exact_at_depth(R):
 
 
 def test_fs32_deterministic(R):
-    """J does not depend on the launch shape: direction groups and threads
-    per block (odd ny: the last row of voxel pairs is half empty)."""
+    """J does not depend on the launch shape: direction groups, threads per
+    block and block order (odd ny: the last row of voxel pairs is half
+    empty)."""
     p = W.random_slab(19, 9, 7, n_theta=8, n_phi=6, seed=12)
     out = []
-    for groups, threads in ((0, 0), (1, 64), (4, 128), (8, 256), (2, 256)):
+    for groups, threads, order in ((0, 0, 0), (1, 64, 2), (4, 128, 1), (8, 256, 2), (2, 256, 0),
+                                   (0, 128, 2)):
         with R.Solver(p, precision=R.RT_FP32_SWEEP, groups=groups) as s:
             R.rt_set_block_threads(s.ctx, threads)
+            R.rt_set_block_order(s.ctx, order)
             out.append(s.formal_solution(want_lstar=False)[0])
     for J in out[1:]:
         assert np.array_equal(J, out[0])
     with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
         with pytest.raises(R.RtError):
             R.rt_set_block_threads(s.ctx, 96)
+        with pytest.raises(R.RtError):
+            R.rt_set_block_order(s.ctx, 3)
 
 
 @pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-6])
