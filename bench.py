@@ -57,7 +57,7 @@ FLOPS_CLOSED_FP32 = 45
 FLOPS_SERIES_FP32 = 61
 FLOPS_PER_STEP_FP32 = FLOPS_CLOSED_FP32     # lower bound: every step on the closed form
 # Thread instructions per step of k_fs32d (ncu, 65^3 slab, 32 x 32 directions)
-INSTR_PER_STEP_FP32 = 73.5
+INSTR_PER_STEP_FP32 = 74.2
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
 PEAK_FP32_TFLOPS = 80.5
 # DRAM bytes (read + write) per k_fs64 launch on slab65, from one ncu
@@ -98,7 +98,7 @@ TRAFFIC_JACOBI_129 = 494896128
 # DRAM bytes (read + write) of one k_fs32d launch on slab65, from one ncu
 # capture of the current kernel: 27.77 MB read (the padded pair planes,
 # the tables) + 0.01 MB written; then everything is served from L2.
-TRAFFIC_FS32_SLAB65 = 27782656
+TRAFFIC_FS32_SLAB65 = 27855872
 
 # The FP32-sweep iterate stops changing below a relative delta of ~1e-8
 # (rounding), so its outer tolerance is at least 5e-8, and Ng extrapolation
@@ -430,9 +430,9 @@ def fp32_roofline(m32, probe):
             "frac_of_measured": round(ach32 / probe["fp32_tflops"], 4)
             if probe["fp32_tflops"] else None,
             "traffic": TRAFFIC_FS32_SLAB65,
-            "note": "ncu: bound by instruction issue (73% of issue slots; "
-                    "73.5 thread instructions per step, 41.5 of them FP32 "
-                    "arithmetic), L1 62%"}
+            "note": "ncu: bound by instruction issue (76.5% of issue slots; "
+                    "74.2 thread instructions per step, 41.5 of them FP32 "
+                    "arithmetic), L1 66%"}
 
 
 def run_ours(args):

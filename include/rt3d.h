@@ -316,8 +316,10 @@ int rt_set_os_method(rt_ctx *ctx, int method);
  * how many thread blocks share the slots of one voxel tile; 0 = auto. */
 int rt_set_direction_groups(rt_ctx *ctx, int groups);
 /* Tuning: threads per block of the FP32-sweep march, 64, 128 or 256 (0 =
- * default, 128).  Each size keeps 768 resident threads per SM (the same
- * registers per thread); J does not depend on it.  RT_EINVAL otherwise. */
+ * default, 128).  64 and 128 keep 896 resident threads per SM (72
+ * registers per thread), 256 keeps 768 (80 registers); the fused batch
+ * launch keeps 768 at every size.  J does not depend on it.  RT_EINVAL
+ * otherwise. */
 int rt_set_block_threads(rt_ctx *ctx, int threads);
 /* Tuning: block order of the FP32-sweep march.  1: the tiles of a plane
  * are consecutive blocks, so the resident blocks share a few planes and

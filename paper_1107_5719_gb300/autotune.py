@@ -3,8 +3,8 @@
 The march's work per voxel is split into 8 fixed direction slots.  Free
 launch parameters: how many thread blocks share the slots of a voxel tile
 ("direction groups", 1, 2, 4 or 8) and, for the FP32-sweep march, the
-threads per block (64, 128 or 256: the tile width, at the same 768 resident
-threads per SM).  More groups give more, shorter blocks (better balance of
+threads per block (64, 128 or 256: the tile width, at about the same
+resident threads per SM) and the block order (tile- or plane-major).  More groups give more, shorter blocks (better balance of
 the depth-dependent characteristic lengths and of the transmission cutoff),
 fewer groups give fewer blocks that re-read less; narrower blocks give a
 finer last wave.  J does not depend on either choice (fixed summation
@@ -25,8 +25,9 @@ import os
 from typing import Callable, Dict, Iterable, Optional, Tuple
 
 CANDIDATES = (1, 2, 4, 8)
-# (groups, threads per block) of the FP32-sweep march
-CANDIDATES_FP32 = tuple((g, t) for t in (64, 128, 256) for g in (1, 2, 4, 8))
+# (groups, threads per block, block order) of the FP32-sweep march; block
+# order 1 = the tiles of a plane consecutive, 2 = the planes of a tile
+CANDIDATES_FP32 = tuple((g, t, o) for o in (1, 2) for t in (64, 128, 256) for g in (1, 2, 4, 8))
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rt3d_autotune.json")
 
 
@@ -55,12 +56,12 @@ def save_cache(path: str, data: Dict[str, dict]) -> None:
 
 def pick(timings: Dict) -> object:
     """Fastest candidate; ties go to the smaller one (fewer groups, then
-    fewer threads per block)."""
+    fewer threads per block, then the lower block order)."""
     return min(timings, key=lambda g: (timings[g], g))
 
 
 def _enc(c):
-    """Cache form of a candidate: an int, or "groups x threads"."""
+    """Cache form of a candidate: an int, or "groups x threads x order"."""
     return "x".join(str(v) for v in c) if isinstance(c, tuple) else int(c)
 
 
@@ -73,7 +74,7 @@ def tune(key: str, time_candidate: Callable, candidates: Iterable = CANDIDATES,
          cache_path: Optional[str] = DEFAULT_CACHE, refresh: bool = False) -> Tuple[object, Dict]:
     """Return (best candidate, {candidate: ms}) for `key`, from the cache
     unless `refresh`; `time_candidate(c)` returns the mean ms of the march
-    with candidate c (a group count, or a (groups, threads) pair)."""
+    with candidate c (a group count, or a (groups, threads, order) tuple)."""
     cache = load_cache(cache_path) if cache_path else {}
     if not refresh and key in cache and "groups" in cache[key]:
         return _dec(cache[key]["groups"]), {_dec(k): v for k, v in cache[key].get("ms", {}).items()}
@@ -90,8 +91,17 @@ def _apply(R, ctx, cand):
     if isinstance(cand, tuple):
         R.rt_set_direction_groups(ctx, cand[0])
         R.rt_set_block_threads(ctx, cand[1])
+        if len(cand) > 2:
+            R.rt_set_block_order(ctx, cand[2])
     else:
         R.rt_set_direction_groups(ctx, cand)
+
+
+def _apply_batch(R, b, cand):
+    R.rt_batch_set_direction_groups(b, cand[0])
+    R.rt_batch_set_block_threads(b, cand[1])
+    if len(cand) > 2:
+        R.rt_batch_set_block_order(b, cand[2])
 
 
 def time_solver_fs(R, ctx, J_dev: int, cand, repeats: int = 2) -> float:
@@ -114,7 +124,7 @@ def time_solver_fs(R, ctx, J_dev: int, cand, repeats: int = 2) -> float:
 def autotune_solver(solver, cache_path: Optional[str] = DEFAULT_CACHE, refresh: bool = False,
                     repeats: int = 2):
     """Tune and apply the launch shape of a ``rt3d.Solver`` (direction
-    groups; for the FP32 sweep also threads per block)."""
+    groups; for the FP32 sweep also threads per block and block order)."""
     import torch
     from . import rt3d as R
     p = solver.p
@@ -131,10 +141,10 @@ def autotune_solver(solver, cache_path: Optional[str] = DEFAULT_CACHE, refresh: 
 
 def time_batch_fs(R, b, nprob: int, cand, iters: int = 1) -> float:
     """Mean device time (ms) of the fused FP32 march of a batch over `iters`
-    outer iterations from J = B with launch shape `cand` = (groups, threads);
+    outer iterations from J = B with launch shape `cand` = (groups, threads,
+    block order);
     the batch is reset afterwards (Lambda* kept)."""
-    R.rt_batch_set_direction_groups(b, cand[0])
-    R.rt_batch_set_block_threads(b, cand[1])
+    _apply_batch(R, b, cand)
     R.rt_batch_reset(b)
     R.rt_batch_reset_stats(b)
     R.rt_batch_set_profiling(b, True)
@@ -147,7 +157,8 @@ def time_batch_fs(R, b, nprob: int, cand, iters: int = 1) -> float:
 
 def autotune_batch(b, problems, cache_path: Optional[str] = DEFAULT_CACHE, refresh: bool = False,
                    iters: int = 1):
-    """Tune and apply the fused launch shape, (groups, threads per block), of
+    """Tune and apply the fused launch shape, (groups, threads per block,
+    block order), of
     an FP32-sweep batch, keyed by the largest grid, direction count, batch
     size and SM count."""
     import torch
@@ -158,7 +169,6 @@ def autotune_batch(b, problems, cache_path: Optional[str] = DEFAULT_CACHE, refre
     R.rt_batch_solve(b, len(problems), tol=0.0, max_iter=1)          # warm-up, builds Lambda*
     best, _ = tune(key, lambda c: time_batch_fs(R, b, len(problems), c, iters),
                    CANDIDATES_FP32, cache_path, refresh)
-    R.rt_batch_set_direction_groups(b, best[0])
-    R.rt_batch_set_block_threads(b, best[1])
+    _apply_batch(R, b, best)
     R.rt_batch_reset(b)
     return best

@@ -39,15 +39,27 @@ namespace rt3d {
 namespace {
 
 constexpr int kThreads32 = 128;     // default threads per block
-// 80 registers (six blocks of 128 threads per SM) and the step loop
-// unrolled twice: measured on the 65^3 slab with 32x32 directions, 9.43 ms
-// per formal solution against 9.94 ms (no unrolling), 9.88 ms (96
-// registers) and 10.1-11.1 ms for variants that load the next step's
-// records before computing the current one (more registers, fewer warps).
-constexpr int kMinBlocks32 = 6;
+// 72 registers (seven blocks of 128 threads per SM) and the step loop
+// unrolled twice: measured on the 65^3 slab with 32x32 directions, 8.40 ms
+// per formal solution against 8.70 ms at 80 registers (six blocks) and
+// 8.89 ms at 64 (eight blocks, spilling in the loop); with the earlier
+// step, 9.43 ms against 9.94 ms without unrolling, 9.88 ms at 96 registers
+// and 10.1-11.1 ms for variants that load the next step's records before
+// computing the current one (more registers, fewer warps).
+#ifndef RT_FS32_MINB
+#define RT_FS32_MINB 7
+#endif
+#ifndef RT_FS32B_MINB
+#define RT_FS32B_MINB 6
+#endif
+constexpr int kMinBlocks32 = RT_FS32_MINB;
 // Threads per block are a launch knob (64, 128 or 256, rt_set_block_threads);
-// every size keeps 768 resident threads per SM, i.e. the same 80 registers.
+// 64 and 128 keep the same resident threads per SM and registers, 256
+// rounds down to three blocks (768 threads, 80 registers).
 constexpr int kResident32 = kThreads32 * kMinBlocks32;
+// The fused batch launch keeps six blocks (80 registers): at seven it
+// spills in the loop, 171 against 157 ms per launch of 16 x 65^3 problems.
+constexpr int kResidentB32 = kThreads32 * RT_FS32B_MINB;
 
 
 // poff[d][m] = offset of the upstream node (x0, y0) of step m from the
@@ -354,20 +366,29 @@ int tiles32(const Geometry& g, int tb) { return (g.nx * ((g.ny + 1) / 2) + tb - 
 // prefix[q] <= b < prefix[q+1]; within it, blocks run tile-fastest, then
 // plane, then slot group.
 template <int TB>
-__global__ void __launch_bounds__(TB, kResident32 / TB)
+__global__ void __launch_bounds__(TB, kResidentB32 / TB)
 k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
              const long long* __restrict__ prefix, int nact, int ZB, float cut,
              unsigned long long* __restrict__ steps)
 {
-    const long long b = blockIdx.x + (long long)blockIdx.y * gridDim.x;
-    int lo = 0, hi = nact;  // prefix[lo] <= b < prefix[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= b) lo = mid; else hi = mid;
+    // the block's problem view, staged once in shared memory by one
+    // thread (measured: 157.1 against 158.0 ms per launch of 16 x 65^3
+    // problems read from global memory by every thread)
+    __shared__ View32 p;
+    __shared__ long long s_local;
+    if (threadIdx.x == 0) {
+        const long long b = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+        int lo = 0, hi = nact;  // prefix[lo] <= b < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= b) lo = mid; else hi = mid;
+        }
+        s_local = b < prefix[nact] ? b - prefix[lo] : -1;
+        if (s_local >= 0) p = views[ids[lo]];
     }
-    if (b >= prefix[nact]) return;
-    const View32& p = views[ids[lo]];
-    const long long local = b - prefix[lo];
+    __syncthreads();
+    const long long local = s_local;
+    if (local < 0) return;
     const int tiles = (p.g.nx * ((p.g.ny + 1) >> 1) + TB - 1) / TB;
     const long long tk = local % ((long long)tiles * p.g.nz);
     const int zb = (int)(local / ((long long)tiles * p.g.nz));

@@ -45,19 +45,22 @@ def test_key_distinguishes_shape_precision_and_device():
     assert len(keys) == 4
 
 
-def test_pairs_of_groups_and_threads_round_trip_through_the_cache(tmp_path):
+def test_fp32_launch_shapes_round_trip_through_the_cache(tmp_path):
     path = str(tmp_path / "tune.json")
-    ms = {(g, t): 10.0 - g * 0.5 + (t == 128) * 0.1 for (g, t) in A.CANDIDATES_FP32}
+    ms = {(g, t, o): 10.0 - g * 0.5 + (t == 128) * 0.1 - (o == 2) * 0.05
+          for (g, t, o) in A.CANDIDATES_FP32}
     best, _ = A.tune("k32", lambda c: ms[c], A.CANDIDATES_FP32, cache_path=path)
-    assert best == (8, 64)
+    assert best == (8, 64, 2)
     calls = []
     best2, t2 = A.tune("k32", lambda c: calls.append(c) or 0.0, A.CANDIDATES_FP32, cache_path=path)
-    assert best2 == (8, 64) and not calls and set(t2) == set(A.CANDIDATES_FP32)
+    assert best2 == (8, 64, 2) and not calls and set(t2) == set(A.CANDIDATES_FP32)
 
 
-def test_fp32_candidates_cover_every_block_size_and_group_count():
-    assert {t for _, t in A.CANDIDATES_FP32} == {64, 128, 256}
-    assert {g for g, _ in A.CANDIDATES_FP32} == set(A.CANDIDATES)
+def test_fp32_candidates_cover_every_block_size_group_count_and_order():
+    assert {t for _, t, _ in A.CANDIDATES_FP32} == {64, 128, 256}
+    assert {g for g, _, _ in A.CANDIDATES_FP32} == set(A.CANDIDATES)
+    assert {o for _, _, o in A.CANDIDATES_FP32} == {1, 2}
+    assert len(set(A.CANDIDATES_FP32)) == 24
 
 
 @pytest.mark.gpu
