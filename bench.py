@@ -38,6 +38,10 @@ sys.path.insert(0, ROOT)
 # division (8: Newton from a reciprocal seed, 4 FMA), w_cur and w_up (2),
 # the intensity update (5) and the transmission update (1).
 FLOPS_PER_STEP_FP64 = 49
+# Replay of the recorded FP64 march, per step: the bilinear interpolation
+# of S (one multiply and three FMA, 7 flops) and I += c S (one FMA, 2): five
+# FP64 instructions; 8 coefficient bytes streamed from memory.
+FLOPS_PER_STEP_FP64_REPLAY = 9
 # Peak FP64 of GB300 from the profiling recipe's figure (1.25 TFLOP/s,
 # i.e. 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz).
 PEAK_FP64_TFLOPS = 1.25
@@ -64,6 +68,9 @@ PEAK_FP32_TFLOPS = 80.5
 # capture of the current kernel: chi, S, B and the direction tables stay
 # L2-resident, so the march reads 7.8 MB per launch from DRAM and writes none.
 TRAFFIC_FS64_SLAB65 = 7805184
+# DRAM bytes per k_fs64rep launch on slab65: 8.35 bytes per replayed step
+# (ncu on the 33^3 slab, whose recording fits a capture) x 3.576e9 steps
+TRAFFIC_FS64REP_SLAB65 = 29843233564
 # The double-float march executes 398 thread instructions per step (ncu,
 # slab65); its bound is instruction issue: 152 SMs x 4 schedulers x 32 lanes
 # x 2.07 GHz = 40.3e12 thread instructions/s.
@@ -113,6 +120,9 @@ WORKLOADS = {
     "slab17": dict(desc="17^3 slab, chi = 10^(-4+8k/16)(1+0.2(U-1/2)), eps = 1e-2, B = 1, "
                         "16x16 directions, tol 1e-8",
                    make="slab_small"),
+    "slab33": dict(desc="33^3 slab, the 65^3 slab's laws on half the grid, 16x16 directions "
+                        "(a small case for profiles)", make="slab_65",
+                   kw=dict(n=33, n_theta=16, n_phi=16)),
     "batch": dict(desc="wavelength batch (see --lambdas)", make=None),
 }
 
@@ -129,7 +139,8 @@ def make_problem(name, lambdas=512):
     if name == "batch":
         # one wavelength of the batch stands for the per-wavelength cost
         return W.batch_65(n_lambda=lambdas)[0]
-    return getattr(W, WORKLOADS[name]["make"])()
+    spec = WORKLOADS[name]
+    return getattr(W, spec["make"])(**spec.get("kw", {}))
 
 
 class ClockSampler:
@@ -308,6 +319,50 @@ def march_rate(R, p, precision, dev, stream, launches=5):
             "fs_steps_per_s": round(steps / (ms / 1e3), 1), **branches}
 
 
+def record_rate(R, p, dev, stream, reps=2):
+    """The recorded FP64 march on problem p: device time of a recording
+    formal solution (the march that records, then the replay that gives J)
+    and of replays alone, with their steps; new opacities before each
+    recording.  Source S = eps B + (1 - eps) B."""
+    import torch
+    S = torch.from_numpy(p.eps * p.B + (1 - p.eps) * p.B).to(dev)
+    chi = torch.from_numpy(p.chi).to(dev)
+    J = torch.empty_like(S)
+    ctx = R.rt_create(dev.index, R.RT_FP64)
+    try:
+        R.rt_set_stream(ctx, stream)
+        R.rt_set_grid(ctx, p.nx, p.ny, p.nz, p.dx, p.dy, p.dz)
+        R.rt_set_boundary(ctx, p.top_bc, p.bottom_bc)
+        R.rt_set_quadrature(ctx, p.mu, p.phi, p.w)
+        R.rt_set_opacity_dev(ctx, chi)
+        R.rt_set_epsilon(ctx, p.eps)
+        R.rt_set_planck(ctx, p.B)
+        R.rt_formal_solution_dev(ctx, S, J, None)
+        stream.synchronize()
+        nbytes, valid = R.rt_fs_record_info(ctx)
+        out = {"recorded": bool(valid), "bytes": nbytes}
+        if not valid:
+            return out
+        R.rt_set_profiling(ctx, True)
+        R.rt_reset_stats(ctx)
+        for _ in range(reps):
+            R.rt_formal_solution_dev(ctx, S, J, None)
+        rep = R.rt_get_stats(ctx)
+        R.rt_reset_stats(ctx)
+        for _ in range(reps):
+            R.rt_set_opacity_dev(ctx, chi)        # the next formal solution records
+            R.rt_formal_solution_dev(ctx, S, J, None)
+        both = R.rt_get_stats(ctx)
+    finally:
+        R.rt_destroy(ctx)
+    rep_ms = rep["fs_ms"] / reps
+    rep_steps = rep["steps"] / reps
+    out.update(replay_ms=rep_ms, replay_steps=rep_steps,
+               record_ms=both["fs_ms"] / reps - rep_ms,
+               record_steps=both["steps"] / reps - rep_steps)
+    return out
+
+
 def replicas_barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
@@ -464,24 +519,50 @@ def run_ours(args):
     except R.RtError:
         probe = {"fp64_tflops": None, "fp32_tflops": None}
 
-    # dominant kernel: the FP64 formal-solution march
-    fs_ms = st["fs_ms"] / max(st["fs_launches"], 1)
-    steps_per_launch = st["steps"] / max(st["fs_launches"], 1)
-    achieved = FLOPS_PER_STEP_FP64 * steps_per_launch / (fs_ms / 1e3) / 1e12
-    roofline = {"kernel": "k_fs64 (formal-solution march, FP64)", "bound": "alu",
-                "achieved": round(achieved, 4), "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(achieved / PEAK_FP64_TFLOPS, 4),
-                "traffic": TRAFFIC_FS64_SLAB65 if args.workload == "slab65" else None,
-                "peak_source": "unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz",
-                "peak_measured": round(probe["fp64_tflops"], 4) if probe["fp64_tflops"] else None,
-                "frac_of_measured": round(achieved / probe["fp64_tflops"], 4)
-                if probe["fp64_tflops"] else None,
-                "peak_measured_source": "rt_probe_peaks: register-resident DFMA chains on every "
-                                        "SM, CUDA events",
-                "flops_per_step": FLOPS_PER_STEP_FP64,
-                "steps_per_launch": round(steps_per_launch),
-                "ms_per_launch": round(fs_ms, 4),
-                "share_of_step": round(st["fs_ms"] / my_ms, 4)}
+    # dominant kernel: the replay of the recorded FP64 march (every formal
+    # solution of a solve evaluates J from the recording; the first one
+    # also records it), timed alone; the recording march beside it
+    rec = record_rate(R, p, dev, stream)
+    iters = st["iterations"] / args.steps
+    if rec["recorded"]:
+        rep_ms, rep_steps = rec["replay_ms"], rec["replay_steps"]
+        achieved = FLOPS_PER_STEP_FP64_REPLAY * rep_steps / (rep_ms / 1e3) / 1e12
+        roofline = {"kernel": "k_fs64rep (replay of the recorded FP64 march)", "bound": "alu",
+                    "achieved": round(achieved, 4), "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": round(achieved / PEAK_FP64_TFLOPS, 4),
+                    "traffic": TRAFFIC_FS64REP_SLAB65 if args.workload == "slab65" else None,
+                    "flops_per_step": FLOPS_PER_STEP_FP64_REPLAY,
+                    "fp64_instructions_per_step": 5,
+                    "coefficient_bytes_per_step": 8,
+                    "hbm_gbs_coefficients": round(8 * rep_steps / (rep_ms / 1e3) / 1e9, 1),
+                    "steps_per_launch": round(rep_steps),
+                    "ms_per_launch": round(rep_ms, 4),
+                    "share_of_step": round(rep_ms * iters / (my_ms / args.steps), 4),
+                    "record": {"kernel": "k_fs64<true> (the march, recording)",
+                               "ms": round(rec["record_ms"], 3),
+                               "steps": round(rec["record_steps"]),
+                               "achieved_tflops": round(FLOPS_PER_STEP_FP64 * rec["record_steps"]
+                                                        / (rec["record_ms"] / 1e3) / 1e12, 4),
+                               "flops_per_step": FLOPS_PER_STEP_FP64,
+                               "bytes_held": rec["bytes"]}}
+    else:
+        fs_ms = st["fs_ms"] / max(st["fs_launches"], 1)
+        steps_per_launch = st["steps"] / max(st["fs_launches"], 1)
+        achieved = FLOPS_PER_STEP_FP64 * steps_per_launch / (fs_ms / 1e3) / 1e12
+        roofline = {"kernel": "k_fs64 (formal-solution march, FP64)", "bound": "alu",
+                    "achieved": round(achieved, 4), "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": round(achieved / PEAK_FP64_TFLOPS, 4), "traffic": None,
+                    "flops_per_step": FLOPS_PER_STEP_FP64,
+                    "steps_per_launch": round(steps_per_launch),
+                    "ms_per_launch": round(fs_ms, 4),
+                    "share_of_step": round(st["fs_ms"] / my_ms, 4)}
+    roofline.update({
+        "peak_source": "unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz",
+        "peak_measured": round(probe["fp64_tflops"], 4) if probe["fp64_tflops"] else None,
+        "frac_of_measured": round(achieved / probe["fp64_tflops"], 4)
+        if probe["fp64_tflops"] else None,
+        "peak_measured_source": "rt_probe_peaks: register-resident DFMA chains on every "
+                                "SM, CUDA events"})
 
     # the FP32-sweep form of the same workload on the same GPU: converged
     # solves of the form as created (finishing stage from delta < 1e-6),

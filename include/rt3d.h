@@ -187,6 +187,29 @@ int rt_set_J(rt_ctx *ctx, const double *J);
  * the transmission cutoff are not counted). */
 int rt_last_step_count(rt_ctx *ctx, unsigned long long *steps);
 
+/* Recorded formal solution (RT_FP64, long characteristics, linear source).
+ * The march is linear in the source S once the opacities, directions and
+ * boundary values are fixed (Sect. 2.2: I is a sum of weighted S values
+ * along the characteristic plus the transmitted boundary intensity).  The
+ * first formal solution after any of them changes runs the march as usual
+ * and also stores, per (voxel, direction, step), the coefficient of S at
+ * that step's upstream point (the products of transmissions and segment
+ * weights), cut at 1e-2 times the cutoff; every formal solution then
+ * evaluates J from those coefficients and its S (five FP64 operations per
+ * step instead of the weights' exponential and division), so J does not
+ * depend on which formal solution recorded.  Memory:
+ * 8 ndir nx ny nz (nz-1)/2 bytes of coefficients plus 4 ndir nz
+ * ceil(nx ny/32) + 128 N bytes (65^3 x 1024 directions: 72 GB).
+ * max_bytes: -1 (default) records when that fits in 60% of the device and
+ * leaves 2 GiB free, 0 never records, > 0 records when it fits in
+ * max_bytes; otherwise every formal solution marches.  J agrees with the
+ * march to rounding (the terms are summed in another order).  Other
+ * precisions and methods ignore the setting.  RT_EINVAL for max_bytes < -1. */
+int rt_set_fs_record(rt_ctx *ctx, long long max_bytes);
+/* Bytes held for the recorded march (0 if none) and whether a recording
+ * valid for the current opacities, directions and boundary is held. */
+int rt_fs_record_info(rt_ctx *ctx, long long *bytes, int *valid);
+
 /* Diagnostics for the FP32-sweep long-characteristics march: march the
  * source S (host array [N], or NULL for S = eps B + (1 - eps) J from the
  * current iterate) once through a branch-counting copy of the march kernel

@@ -62,6 +62,14 @@ struct rt_ctx {
     int threads32 = 0;       // threads per block of the FP32 march (0: 128)
     int order32 = 0;         // block order of the FP32 march (0 auto, 1 tile-, 2 plane-major)
     double cut = -1.0;
+    // recorded FP64 march (FsRec): the first formal solution after the
+    // opacities, directions or boundary change records it, later ones
+    // replay it.  rec_mode: -1 automatic, 0 off, > 0 a byte limit.
+    long long rec_mode = -1;
+    FsRec rec{};
+    char* rec_mem = nullptr;
+    long long rec_cap = 0;
+    bool rec_valid = false;
 
     // device state, FP64
     double *chi = nullptr, *eps = nullptr, *B = nullptr, *J = nullptr, *S = nullptr;
@@ -180,6 +188,15 @@ void free_os_graphs(rt_ctx* c)
     }
 }
 
+void free_rec(rt_ctx* c)
+{
+    if (c->rec_mem) cudaFree(c->rec_mem);
+    c->rec_mem = nullptr;
+    c->rec = FsRec{};
+    c->rec_cap = 0;
+    c->rec_valid = false;
+}
+
 void free_grid_buffers(rt_ctx* c)
 {
     free_os_graphs(c);
@@ -195,6 +212,7 @@ void free_grid_buffers(rt_ctx* c)
     c->scpart_n = c->scplanes_n = 0;
     free_ng(c);
     c->partial_groups = 0;
+    free_rec(c);
 }
 
 void free_tables(rt_ctx* c)
@@ -249,6 +267,53 @@ int auto_groups(const rt_ctx* c)
     int G = 1;
     while (G < kSlots && blocks * G < target) G *= 2;
     return G;
+}
+
+// The recorded FP64 march: whether this context records and replays it
+// (FP64, long characteristics, linear source, a byte budget that admits
+// it), with its buffers sized for the grid and directions.  When it does
+// not fit, the march runs as it is every time.
+int ensure_rec(rt_ctx* c, bool& use)
+{
+    use = false;
+    if (c->rec_mode == 0 || c->precision != RT_FP64 || c->fs_method != RT_FS_LONG ||
+        c->src_order != RT_SRC_LINEAR || c->g.nz < 2)
+        return RT_OK;
+    const long long nxy = (long long)c->g.nx * c->g.ny;
+    const long long nwp = (nxy + 31) / 32;
+    auto up = [](long long b) { return (b + 255) / 256 * 256; };
+    const long long b_coef = up((long long)c->g.ndir * nxy * ((long long)c->g.nz * (c->g.nz - 1) / 2) *
+                                (long long)sizeof(double));
+    const long long b_lmax = up((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int));
+    const long long b_slot = up((long long)kSlots * c->g.N * (long long)sizeof(double));
+    const long long need = b_coef + b_lmax + 2 * b_slot;
+    if (need > c->rec_cap) {
+        long long limit = c->rec_mode;
+        if (limit < 0) {
+            size_t fr = 0, tot = 0;
+            CK(cudaMemGetInfo(&fr, &tot));
+            // at most 60% of the device, leaving 2 GiB free
+            limit = (long long)(0.6 * (double)tot);
+            const long long avail = (long long)fr + c->rec_cap - (2LL << 30);
+            if (avail < limit) limit = avail;
+        }
+        if (need > limit) return RT_OK;
+        CK(cudaStreamSynchronize(c->stream));
+        free_rec(c);
+        if (cudaMalloc((void**)&c->rec_mem, (size_t)need) != cudaSuccess) {
+            cudaGetLastError();
+            c->rec_mem = nullptr;
+            return RT_OK;
+        }
+        c->rec_cap = need;
+    }
+    c->rec.coef = reinterpret_cast<double*>(c->rec_mem);
+    c->rec.lmax = reinterpret_cast<int*>(c->rec_mem + b_coef);
+    c->rec.c0 = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax);
+    c->rec.bc = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax + b_slot);
+    c->rec.nwp = (int)nwp;
+    use = true;
+    return RT_OK;
 }
 
 // Buffers of the short-characteristics march (sized by grid and directions).
@@ -536,9 +601,25 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
                         c->scal + 0, cut, G, c->partial, count_steps ? c->d_steps : nullptr,
                         c->stream));
     } else if (c->precision == RT_FP64) {
-        CK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->bwh,
-                       c->scal + 0, cut, G, c->partial, count_steps ? c->d_steps : nullptr,
-                       c->stream));
+        bool use = false;
+        if ((rc = ensure_rec(c, use))) return rc;
+        if (use && !c->rec_valid) {
+            // record; J then comes from the replay like every later one, so
+            // that it does not depend on which formal solution recorded
+            CK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->bwh,
+                           c->scal + 0, cut, G, c->partial, count_steps ? c->d_steps : nullptr,
+                           c->stream, &c->rec));
+            c->rec_valid = true;
+            c->stats.launches += 1;
+        }
+        if (use) {
+            CK(launch_fs64rep(c->g, c->S, c->info, c->off, c->bw, c->rec, G, c->partial,
+                              count_steps ? c->d_steps : nullptr, c->stream));
+        } else {
+            CK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->bwh,
+                           c->scal + 0, cut, G, c->partial, count_steps ? c->d_steps : nullptr,
+                           c->stream));
+        }
     } else if (c->precision == RT_DF64) {
         CK(launch_fsdf(viewdf(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
     } else if (c->fin == 1) {
@@ -933,6 +1014,7 @@ int switch_precision(rt_ctx* c, int precision)
     int rc = form_buffers(c, precision);
     if (rc) return rc;
     c->precision = precision;
+    c->rec_valid = false;
     c->gdiff_valid = false;    // the gradient's packed copy differs between the forms
     c->lstar_valid = c->coef_valid = false;   // Lambda* is rebuilt by the new form's kernel
     c->ng_count = 1;           // restart the Ng history with iterates of the new form
@@ -1535,7 +1617,7 @@ int rt_set_grid(rt_ctx* c, int nx, int ny, int nz, double dx, double dy, double 
     free_grid_buffers(c);
     free_tables(c);
     c->have_grid = c->have_quad = c->have_chi = c->have_eps = c->have_B = false;
-    c->lstar_valid = c->coef_valid = c->b2_valid = false;
+    c->lstar_valid = c->coef_valid = c->b2_valid = c->rec_valid = false;
     c->g.nx = nx; c->g.ny = ny; c->g.nz = nz;
     c->g.N = (long long)nx * ny * nz;
     c->g.ndir = 0;
@@ -1566,7 +1648,7 @@ int rt_set_boundary(rt_ctx* c, int top_mode, int bottom_mode)
         return fail(c, RT_EINVAL, "boundary modes: top ZERO or PLANCK, bottom ZERO, PLANCK or DIFFUSION");
     c->g.top_bc = top_mode;
     c->g.bottom_bc = bottom_mode;
-    c->gdiff_valid = false;
+    c->gdiff_valid = c->rec_valid = false;
     return RT_OK;
 }
 
@@ -1618,7 +1700,7 @@ int rt_set_quadrature(rt_ctx* c, int ndir, const double* mu, const double* phi, 
         return rc;
     }
     CK(cudaStreamSynchronize(c->stream));
-    c->lstar_valid = c->coef_valid = false;
+    c->lstar_valid = c->coef_valid = c->rec_valid = false;
     return RT_OK;
 }
 
@@ -1632,7 +1714,7 @@ static int set_chi(rt_ctx* c, const double* chi, bool device)
     c->g.zorder = c->zorder;
     c->stats.launches += 2;
     c->have_chi = true;
-    c->lstar_valid = c->coef_valid = c->gdiff_valid = false;
+    c->lstar_valid = c->coef_valid = c->gdiff_valid = c->rec_valid = false;
     return RT_OK;
 }
 
@@ -1653,7 +1735,7 @@ static int set_B(rt_ctx* c, const double* B, bool device)
     c->ng_count = 1;
     c->ng_last_delta = 0.0;
     c->have_B = true;
-    c->b2_valid = c->gdiff_valid = false;
+    c->b2_valid = c->gdiff_valid = c->rec_valid = false;
     return RT_OK;
 }
 
@@ -1800,6 +1882,27 @@ int rt_set_cutoff(rt_ctx* c, double cut)
     if (!c) return RT_EINVAL;
     if (!(cut >= 0) || !(cut < 1)) return fail(c, RT_EINVAL, "cutoff must lie in [0, 1)");
     c->cut = cut;
+    c->rec_valid = false;
+    return RT_OK;
+}
+
+int rt_set_fs_record(rt_ctx* c, long long max_bytes)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if (max_bytes < -1) return fail(c, RT_EINVAL, "max_bytes must be -1 (automatic), 0 (off) or a byte limit");
+    CK(cudaStreamSynchronize(c->stream));
+    c->rec_mode = max_bytes;
+    if (max_bytes >= 0 && c->rec_cap > max_bytes) free_rec(c);
+    c->rec_valid = false;
+    return RT_OK;
+}
+
+int rt_fs_record_info(rt_ctx* c, long long* bytes, int* valid)
+{
+    if (!c || !bytes || !valid) return RT_EINVAL;
+    *bytes = c->rec_cap;
+    *valid = c->rec_valid ? 1 : 0;
     return RT_OK;
 }
 
@@ -1837,7 +1940,7 @@ int rt_set_fs_method(rt_ctx* c, int method)
         return fail(c, RT_EINVAL, "short characteristics take the linear source only");
     if (method != c->fs_method) {
         c->fs_method = method;
-        c->lstar_valid = c->coef_valid = false;   // Lambda* differs between methods
+        c->lstar_valid = c->coef_valid = c->rec_valid = false;   // Lambda* differs between methods
     }
     return RT_OK;
 }
@@ -1882,7 +1985,7 @@ int rt_set_source_order(rt_ctx* c, int order)
         return fail(c, RT_EINVAL, "the parabolic source needs RT_FP64 and long characteristics");
     if (order != c->src_order) {
         c->src_order = order;
-        c->lstar_valid = c->coef_valid = false;
+        c->lstar_valid = c->coef_valid = c->rec_valid = false;
     }
     return RT_OK;
 }

@@ -123,13 +123,24 @@ __device__ __forceinline__ void add_steps(unsigned long long* steps, unsigned lo
 // written to partial[slot]; block y walks slots zb, zb + gridDim.y, ...
 // The slot sums are then added in slot order, so J depends neither on
 // gridDim.y nor on the plane dispatch order.
+//
+// REC: also record the march as a linear map of S (the recorded operator,
+// FsRec): per (voxel, direction) the coefficient c_m of S(p_m), m >= 1,
+//   c_m = T_{m-1} w_up,{m-1} + T_m w_cur,m   (the last point: T_{L-1} w_up),
+// and per voxel and slot the coefficient of S at the voxel itself,
+// sum_d w_d w_cur,0, and the boundary term sum_d w_d T_L I_bc (rays that
+// reach the boundary plane); partial is not written (J comes from the
+// replay).  The march runs to the stricter cutoff cut * kRecCutMargin, so
+// that later sources, whose intensities may be smaller, still meet the
+// cutoff with the recorded lengths.
+template <bool REC>
 __global__ void __launch_bounds__(kThreads)
 k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
        const double* __restrict__ B, const double* __restrict__ G,
        const DirInfo* __restrict__ info,
        const StepGeo* __restrict__ off, const Bw4d* __restrict__ bw,
        const Bw4d* __restrict__ bwh, const double* __restrict__ smax_p, double cut,
-       double* __restrict__ partial, unsigned long long* __restrict__ steps)
+       double* __restrict__ partial, unsigned long long* __restrict__ steps, FsRec rec)
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int t = blockIdx.x * kThreads + threadIdx.x;
@@ -138,14 +149,16 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
     __shared__ double tab[kExpTable];
     fill_exp_table(tab);
     __syncthreads();
+    // lanes of this warp holding a voxel (the recorded lengths are per warp)
+    const unsigned amask = __ballot_sync(0xffffffffu, active);
     unsigned long long nsteps = 0;
     if (active) {
         const int j0 = t / nx, i0 = t - j0 * nx;
         const long long v = (long long)k0 * nxy + t;
-        const int need = cut_need(*smax_p, cut);
+        const int need = REC ? cut_need(*smax_p, cut * kRecCutMargin) : cut_need(*smax_p, cut);
         const double chi0 = chi[v], S0 = S[v];
         for (int slot = zb; slot < kSlots; slot += ZB) {
-            double Jp = 0.0;
+            double Jp = 0.0, C0 = 0.0, Bc = 0.0;
             for (int d = slot; d < g.ndir; d += kSlots) {
                 const DirInfo di = info[d];
                 const int s = di.sgn;
@@ -153,9 +166,10 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                 const StepGeo* od = off + (long long)d * nz;
                 const Bw4d* bd = bw + (long long)d * nz;
                 const Bw4d* bh = bwh + (long long)d * nz;
+                double* rc = REC ? rec.coef + rec_base(g, d, k0, s) + t : nullptr;
                 // ca, cb: chi times the half path length hs, so that a
                 // segment's optical depth is their sum
-                double I = 0.0, T = 1.0, ca = di.hs * chi0, sa = S0;
+                double I = 0.0, T = 1.0, ca = di.hs * chi0, sa = S0, cprev = 0.0;
                 bool early = false;
                 int m = 0;
                 for (; m < M; ++m) {
@@ -167,6 +181,11 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                     const double sb = bilin(S + pb, n, bd[m + 1]);
                     double wc, wu, e;
                     seg_weights64(ca + cb, tab, wc, wu, e);
+                    if (REC) {
+                        if (m == 0) C0 = fma(di.w, wc, C0);
+                        else rc[(long long)(m - 1) * nxy] = fma(T, wc, cprev);
+                        cprev = T * wu;
+                    }
                     I = fma(T, fma(wc, sa, wu * sb), I);
                     T *= e;
                     ca = cb;
@@ -191,8 +210,68 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
                     double ibc = bilin(B + pb, n, bd[M]);
                     if (bc == 2) ibc = fma(di.amu, bilin(G, n, bd[M]), ibc);  // B + |mu| dB/dtau
                     I = fma(T, ibc, I);
+                    if (REC) Bc = fma(di.w, T * ibc, Bc);
+                }
+                if (REC) {
+                    // the last point's coefficient, then zeros up to the
+                    // warp's longest ray (the replay runs that many steps)
+                    if (m > 0) rc[(long long)(m - 1) * nxy] = cprev;
+                    const int Lw = __reduce_max_sync(amask, m);
+                    for (int q = m; q < Lw; ++q) rc[(long long)q * nxy] = 0.0;
+                    if ((threadIdx.x & 31) == __ffs(amask) - 1)
+                        rec.lmax[((long long)d * nz + k0) * rec.nwp + (t >> 5)] = Lw;
                 }
                 nsteps += (unsigned long long)m;
+                Jp = fma(di.w, I, Jp);
+            }
+            if (REC) {
+                rec.c0[(long long)slot * g.N + v] = C0;
+                rec.bc[(long long)slot * g.N + v] = Bc;
+            } else {
+                partial[(long long)slot * g.N + v] = Jp;
+            }
+        }
+    }
+    if (steps) add_steps(steps, nsteps);
+}
+
+// Replay of the recorded march (FsRec) for a new source S: per (voxel,
+// direction) I = sum_m c_m S(p_m) over the warp's recorded length, plus
+// per slot the voxel's own term and the boundary term.  Five FP64
+// operations per step (the bilinear interpolation of S and one FMA)
+// against ~32 for the march, and 8 coefficient bytes streamed from memory.
+__global__ void __launch_bounds__(kThreads)
+k_fs64rep(Geometry g, const double* __restrict__ S, const DirInfo* __restrict__ info,
+          const StepGeo* __restrict__ off, const Bw4d* __restrict__ bw, FsRec rec,
+          double* __restrict__ partial, unsigned long long* __restrict__ steps)
+{
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const int t = blockIdx.x * kThreads + threadIdx.x;
+    const int k0 = plane_at(g, blockIdx.z), zb = blockIdx.y, ZB = gridDim.y;
+    unsigned long long nsteps = 0;
+    if (t < nxy) {
+        const int j0 = t / nx, i0 = t - j0 * nx;
+        const long long v = (long long)k0 * nxy + t;
+        const double S0 = S[v];
+        const double* __restrict__ coef = rec.coef;
+        for (int slot = zb; slot < kSlots; slot += ZB) {
+            double Jp = fma(rec.c0[(long long)slot * g.N + v], S0, rec.bc[(long long)slot * g.N + v]);
+            for (int d = slot; d < g.ndir; d += kSlots) {
+                const DirInfo di = info[d];
+                const int s = di.sgn;
+                const StepGeo* od = off + (long long)d * nz;
+                const Bw4d* bd = bw + (long long)d * nz;
+                const double* rc = coef + rec_base(g, d, k0, s) + t;
+                const int L = rec.lmax[((long long)d * nz + k0) * rec.nwp + (t >> 5)];
+                double I = 0.0;
+                for (int m = 0; m < L; ++m) {
+                    const long long pb = (long long)(k0 - (m + 1) * s) * nxy;
+                    const Nodes n = nodes_of(i0, j0, od[m + 1], nx, ny);
+                    RT_GUARD(g, pb + nodes_min(n), g.N, kSiteFs64) break;
+                    RT_GUARD(g, pb + nodes_max(n), g.N, kSiteFs64) break;
+                    I = fma(__ldg(rc + (long long)m * nxy), bilin(S + pb, n, bd[m + 1]), I);
+                }
+                nsteps += (unsigned long long)L;
                 Jp = fma(di.w, I, Jp);
             }
             partial[(long long)slot * g.N + v] = Jp;
@@ -383,13 +462,37 @@ cudaError_t launch_plane_order(const Geometry& g, double dz, const double* chi, 
 cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, const double* B,
                         const double* G, const DirInfo* info, const StepGeo* off,
                         const Bw4d* bw, const Bw4d* bwh, const double* smax, double cut,
-                        int groups, double* partial, unsigned long long* steps, cudaStream_t st)
+                        int groups, double* partial, unsigned long long* steps, cudaStream_t st,
+                        const FsRec* rec)
 {
     const int nxy = g.nx * g.ny;
     dim3 grid((nxy + kThreads - 1) / kThreads, groups, g.nz);
-    k_fs64<<<grid, kThreads, 0, st>>>(g, chi, S, B, G, info, off, bw, bwh, smax, cut, partial,
-                                      steps);
+    if (rec)
+        k_fs64<true><<<grid, kThreads, 0, st>>>(g, chi, S, B, G, info, off, bw, bwh, smax, cut,
+                                                partial, steps, *rec);
+    else
+        k_fs64<false><<<grid, kThreads, 0, st>>>(g, chi, S, B, G, info, off, bw, bwh, smax, cut,
+                                                 partial, steps, FsRec{});
     return cudaGetLastError();
+}
+
+cudaError_t launch_fs64rep(const Geometry& g, const double* S, const DirInfo* info,
+                           const StepGeo* off, const Bw4d* bw, const FsRec& rec, int groups,
+                           double* partial, unsigned long long* steps, cudaStream_t st)
+{
+    const int nxy = g.nx * g.ny;
+    dim3 grid((nxy + kThreads - 1) / kThreads, groups, g.nz);
+    k_fs64rep<<<grid, kThreads, 0, st>>>(g, S, info, off, bw, rec, partial, steps);
+    return cudaGetLastError();
+}
+
+long long rec_bytes(const Geometry& g)
+{
+    const long long nxy = (long long)g.nx * g.ny;
+    const long long nwp = (nxy + 31) / 32;
+    return (long long)g.ndir * nxy * ((long long)g.nz * (g.nz - 1) / 2) * (long long)sizeof(double) +
+           (long long)g.ndir * g.nz * nwp * (long long)sizeof(int) +
+           2LL * kSlots * g.N * (long long)sizeof(double);
 }
 
 namespace {

@@ -120,14 +120,50 @@ cudaError_t launch_dir_tables(const Geometry& g, double dx, double dy, double dz
 cudaError_t launch_plane_order(const Geometry& g, double dz, const double* chi, double* scratch,
                                int* order, cudaStream_t st);
 
+// The FP64 march recorded as a linear map of the source S (the opacities,
+// directions and boundary values fixed): J = sum_slots [c0 S_v + bc +
+// sum_{d in slot} w_d sum_{m=1..L} c_m S(p_m)].
+//   coef: c_m of voxel t of plane k0 and direction d at
+//     rec_base(g, d, k0, sgn_d) + (m-1) nx ny + t, m = 1..M (M the steps to
+//     the boundary plane), zero past the ray's own length;
+//   lmax[(d nz + k0) nwp + t/32]: the longest ray of the warp, the length
+//     the replay runs (nwp = warps per plane);
+//   c0, bc [kSlots][N]: the voxel's own coefficient and the boundary term.
+struct FsRec {
+    double* coef;
+    int* lmax;
+    double* c0;
+    double* bc;
+    int nwp;
+};
+// The recording march cuts the characteristics at cut * kRecCutMargin, so
+// that the recorded lengths still meet the cutoff for sources whose
+// intensities are up to 1/kRecCutMargin times smaller.
+constexpr double kRecCutMargin = 1e-2;
+__host__ __device__ __forceinline__ long long rec_base(const Geometry& g, int d, int k0, int sgn)
+{
+    const long long nxy = (long long)g.nx * g.ny;
+    const long long k = k0;
+    const long long before = sgn > 0 ? k * (k - 1) / 2 : k * (g.nz - 1) - k * (k - 1) / 2;
+    return ((long long)d * ((long long)g.nz * (g.nz - 1) / 2) + before) * nxy;
+}
+// Device bytes of an FsRec for grid g (coefficients, lengths, c0 and bc).
+long long rec_bytes(const Geometry& g);
+
 // FP64 formal solution: partial[kSlots][N]; `groups` (1..kSlots) is the
 // number of z-blocks walking the slots (a tuning knob, no effect on J).
 // G[ny][nx]: dB/dtau at the bottom nodes (LTE-diffusion inner boundary),
-// read only when bottom_bc == 2 (may be null otherwise).
+// read only when bottom_bc == 2 (may be null otherwise).  rec != null:
+// also record the march into *rec (FsRec), cut at cut * kRecCutMargin.
 cudaError_t launch_fs64(const Geometry& g, const double* chi, const double* S, const double* B,
                         const double* G, const DirInfo* info, const StepGeo* off,
                         const Bw4d* bw, const Bw4d* bwh, const double* smax, double cut,
-                        int groups, double* partial, unsigned long long* steps, cudaStream_t st);
+                        int groups, double* partial, unsigned long long* steps, cudaStream_t st,
+                        const FsRec* rec = nullptr);
+// The recorded march for source S: partial[kSlots][N] as launch_fs64.
+cudaError_t launch_fs64rep(const Geometry& g, const double* S, const DirInfo* info,
+                           const StepGeo* off, const Bw4d* bw, const FsRec& rec, int groups,
+                           double* partial, unsigned long long* steps, cudaStream_t st);
 // G[j][i] = (B[nz-1] - B[nz-2]) / (dz (chi[nz-1] + chi[nz-2]) / 2), and its
 // padded FP32 copy g2[2ny][2nx] if g2 != null.
 cudaError_t launch_diffusion_grad(const Geometry& g, double dz, const double* chi,

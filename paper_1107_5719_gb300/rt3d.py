@@ -90,6 +90,8 @@ _SIGS = {
     "rt_last_step_count": (C.c_int, [VP, C.POINTER(C.c_ulonglong)]),
     "rt_fs32_branch_counts": (C.c_int, [VP, VP, C.POINTER(C.c_ulonglong),
                                         C.POINTER(C.c_ulonglong)]),
+    "rt_set_fs_record": (C.c_int, [VP, C.c_longlong]),
+    "rt_fs_record_info": (C.c_int, [VP, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "rt_set_direction_groups": (C.c_int, [VP, C.c_int]),
     "rt_set_cutoff": (C.c_int, [VP, C.c_double]),
     "rt_set_profiling": (C.c_int, [VP, C.c_int]),
@@ -331,6 +333,17 @@ def rt_fs32_branch_counts(ctx, S=None):
     n, s = C.c_ulonglong(), C.c_ulonglong()
     _check(ctx, load().rt_fs32_branch_counts(ctx, p, C.byref(n), C.byref(s)))
     return n.value, s.value
+
+
+def rt_set_fs_record(ctx, max_bytes=-1):
+    return _check(ctx, load().rt_set_fs_record(ctx, int(max_bytes)))
+
+
+def rt_fs_record_info(ctx):
+    """(bytes held, recording valid) of the recorded FP64 march."""
+    n, v = C.c_longlong(), C.c_int()
+    _check(ctx, load().rt_fs_record_info(ctx, C.byref(n), C.byref(v)))
+    return n.value, bool(v.value)
 
 
 def rt_set_direction_groups(ctx, groups):
