@@ -67,6 +67,8 @@ struct rt_ctx {
     // replay it.  rec_mode: -1 automatic, 0 off, > 0 a byte limit.
     long long rec_mode = -1;
     FsRec rec{};
+    Rec32 rec32{};              // the FP32-sweep recording (same memory block)
+    float4* spair = nullptr;    // the replay's source records
     char* rec_mem = nullptr;
     long long rec_cap = 0;
     bool rec_valid = false;
@@ -193,6 +195,8 @@ void free_rec(rt_ctx* c)
     if (c->rec_mem) cudaFree(c->rec_mem);
     c->rec_mem = nullptr;
     c->rec = FsRec{};
+    c->rec32 = Rec32{};
+    c->spair = nullptr;
     c->rec_cap = 0;
     c->rec_valid = false;
 }
@@ -269,49 +273,76 @@ int auto_groups(const rt_ctx* c)
     return G;
 }
 
-// The recorded FP64 march: whether this context records and replays it
-// (FP64, long characteristics, linear source, a byte budget that admits
-// it), with its buffers sized for the grid and directions.  When it does
-// not fit, the march runs as it is every time.
+// Device memory for a recording of `need` bytes within the context's
+// budget (rec_mode): false when it does not fit or cannot be allocated.
+bool rec_reserve(rt_ctx* c, long long need)
+{
+    if (need <= c->rec_cap) return true;
+    long long limit = c->rec_mode;
+    if (limit < 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        // at most 60% of the device, leaving 2 GiB free
+        limit = (long long)(0.6 * (double)tot);
+        const long long avail = (long long)fr + c->rec_cap - (2LL << 30);
+        if (avail < limit) limit = avail;
+    }
+    if (need > limit) return false;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return false;
+    free_rec(c);
+    if (cudaMalloc((void**)&c->rec_mem, (size_t)need) != cudaSuccess) {
+        cudaGetLastError();
+        c->rec_mem = nullptr;
+        return false;
+    }
+    c->rec_cap = need;
+    return true;
+}
+
+long long up256(long long b) { return (b + 255) / 256 * 256; }
+
+// The recorded march: whether this context records and replays it (FP64
+// with long characteristics and the linear source, or the FP32 sweep; a
+// byte budget that admits it), with its buffers carved from one block.
+// When it does not fit, the march runs as it is every time.
 int ensure_rec(rt_ctx* c, bool& use)
 {
     use = false;
-    if (c->rec_mode == 0 || c->precision != RT_FP64 || c->fs_method != RT_FS_LONG ||
-        c->src_order != RT_SRC_LINEAR || c->g.nz < 2)
+    if (c->rec_mode == 0 || c->fs_method != RT_FS_LONG || c->src_order != RT_SRC_LINEAR ||
+        c->g.nz < 2 || (c->precision != RT_FP64 && c->precision != RT_FP32_SWEEP))
         return RT_OK;
-    const long long nxy = (long long)c->g.nx * c->g.ny;
-    const long long nwp = (nxy + 31) / 32;
-    auto up = [](long long b) { return (b + 255) / 256 * 256; };
-    const long long b_coef = up((long long)c->g.ndir * nxy * ((long long)c->g.nz * (c->g.nz - 1) / 2) *
-                                (long long)sizeof(double));
-    const long long b_lmax = up((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int));
-    const long long b_slot = up((long long)kSlots * c->g.N * (long long)sizeof(double));
-    const long long need = b_coef + b_lmax + 2 * b_slot;
-    if (need > c->rec_cap) {
-        long long limit = c->rec_mode;
-        if (limit < 0) {
-            size_t fr = 0, tot = 0;
-            CK(cudaMemGetInfo(&fr, &tot));
-            // at most 60% of the device, leaving 2 GiB free
-            limit = (long long)(0.6 * (double)tot);
-            const long long avail = (long long)fr + c->rec_cap - (2LL << 30);
-            if (avail < limit) limit = avail;
-        }
-        if (need > limit) return RT_OK;
-        CK(cudaStreamSynchronize(c->stream));
-        free_rec(c);
-        if (cudaMalloc((void**)&c->rec_mem, (size_t)need) != cudaSuccess) {
-            cudaGetLastError();
-            c->rec_mem = nullptr;
-            return RT_OK;
-        }
-        c->rec_cap = need;
+    const long long tri = (long long)c->g.nz * (c->g.nz - 1) / 2;
+    const long long b_slot = up256((long long)kSlots * c->g.N * (long long)sizeof(double));
+    if (c->precision == RT_FP64) {
+        const long long nxy = (long long)c->g.nx * c->g.ny;
+        const long long nwp = (nxy + 31) / 32;
+        const long long b_coef = up256((long long)c->g.ndir * nxy * tri * (long long)sizeof(double));
+        const long long b_lmax = up256((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int));
+        if (!rec_reserve(c, b_coef + b_lmax + 2 * b_slot)) return RT_OK;
+        c->rec.coef = reinterpret_cast<double*>(c->rec_mem);
+        c->rec.lmax = reinterpret_cast<int*>(c->rec_mem + b_coef);
+        c->rec.c0 = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax);
+        c->rec.bc = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax + b_slot);
+        c->rec.nwp = (int)nwp;
+    } else {
+        const long long npair = (long long)c->g.nx * ((c->g.ny + 1) / 2);
+        const long long nwp = (npair + 31) / 32;
+        const long long b_coef = up256((long long)c->g.ndir * rec32_steps4(c->g.nz) * nwp * 32 *
+                                       (long long)sizeof(float2));
+        const long long b_lmax = up256((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int));
+        const long long b_sp = up256(pair_records(c->g) * (long long)sizeof(float4));
+        if (!rec_reserve(c, b_coef + b_lmax + 2 * b_slot + b_sp)) return RT_OK;
+        char* q = c->rec_mem;
+        c->rec32.coef = reinterpret_cast<float2*>(q);
+        c->rec32.lmax = reinterpret_cast<int*>(q + b_coef);
+        c->rec32.tsum = reinterpret_cast<double*>(q + b_coef + b_lmax);
+        c->rec32.bc = reinterpret_cast<double*>(q + b_coef + b_lmax + b_slot);
+        c->rec32.nwp = (int)nwp;
+        c->spair = reinterpret_cast<float4*>(q + b_coef + b_lmax + 2 * b_slot);
     }
-    c->rec.coef = reinterpret_cast<double*>(c->rec_mem);
-    c->rec.lmax = reinterpret_cast<int*>(c->rec_mem + b_coef);
-    c->rec.c0 = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax);
-    c->rec.bc = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax + b_slot);
-    c->rec.nwp = (int)nwp;
     use = true;
     return RT_OK;
 }
@@ -626,8 +657,26 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
         if ((rc = fin_reference_march(c, G, count_steps ? c->d_steps : nullptr, c->stream)))
             return rc;
     } else {
-        CK(launch_fs32d(c->fin == 2 ? view32_fin(c) : view32(c), cut, G, c->threads32,
-                        count_steps ? c->d_steps : nullptr, c->stream));
+        // FP32 sweep (fin 0, or 2: the finishing stage's source change).  The
+        // recording is made from the source itself (fin 0) and serves both.
+        bool use = false;
+        if ((rc = ensure_rec(c, use))) return rc;
+        unsigned long long* sp = count_steps ? c->d_steps : nullptr;
+        if (use && !c->rec_valid && c->fin == 0) {
+            CK(launch_fs32rec(view32(c), cut * kRecCutMargin, G, c->rec32, sp, c->stream));
+            c->rec_valid = true;
+            c->stats.launches += 1;
+        }
+        if (use && c->rec_valid) {
+            CK(launch_pack_spairs(c->g, c->fin == 2 ? c->dS : c->S, c->spair, c->stream));
+            Rep32 rp{c->g, c->spair, c->info, c->poff32, c->bw32, c->rec32, c->partial,
+                     c->fin == 2 ? 1 : 0, plane_major32(c->g, c->order32)};
+            CK(launch_fs32rep(rp, G, c->threads32, sp, c->stream));
+            c->stats.launches += 1;
+        } else {
+            CK(launch_fs32d(c->fin == 2 ? view32_fin(c) : view32(c), cut, G, c->threads32, sp,
+                            c->stream));
+        }
     }
     if (c->profiling) {
         CK(cudaEventRecord(c->ev[1], c->stream));

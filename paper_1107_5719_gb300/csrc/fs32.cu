@@ -60,6 +60,14 @@ constexpr int kResident32 = kThreads32 * kMinBlocks32;
 // The fused batch launch keeps six blocks (80 registers): at seven it
 // spills in the loop, 171 against 157 ms per launch of 16 x 65^3 problems.
 constexpr int kResidentB32 = kThreads32 * RT_FS32B_MINB;
+#ifndef RT_FS32R_MINB
+#define RT_FS32R_MINB 8
+#endif
+// The replay of the recorded march: eight blocks (64 registers), since its
+// loads wait on memory more than its arithmetic; measured on the 65^3 slab,
+// 6.14 ms per replay against 6.49 at seven blocks (72 registers); at ten
+// blocks it spills 800 bytes per thread.
+constexpr int kResidentR32 = kThreads32 * RT_FS32R_MINB;
 
 
 // poff[d][m] = offset of the upstream node (x0, y0) of step m from the
@@ -102,6 +110,28 @@ __global__ void k_pack_pairs(Geometry g, const double* __restrict__ chi,
     }
 }
 
+// The replay's source records: spair[k][y][x] = {S_hi, S_lo} of the nodes
+// (x mod nx, y mod ny) and (x+1 mod nx, y mod ny), padded as k_pack_pairs.
+__global__ void k_pack_spairs(Geometry g, const double* __restrict__ S, float4* __restrict__ sp)
+{
+    const int nx = g.nx, ny = g.ny;
+    const long long W = 2LL * nx, R = 2LL * ny + 1, P = R * W;
+    const long long n = P * g.nz;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+         r += (long long)gridDim.x * blockDim.x) {
+        const long long k = r / P, rem = r - k * P;
+        const int y = (int)(rem / W), x = (int)(rem - (long long)y * W);
+        int j = y, i0 = x, i1 = x + 1;
+        while (j >= ny) j -= ny;
+        while (i0 >= nx) i0 -= nx;
+        while (i1 >= nx) i1 -= nx;
+        const long long row = (k * ny + j) * (long long)nx;
+        const double s0 = S[row + i0], s1 = S[row + i1];
+        const float h0 = (float)s0, h1 = (float)s1;
+        sp[r] = make_float4(h0, (float)(s0 - (double)h0), h1, (float)(s1 - (double)h1));
+    }
+}
+
 __global__ void k_pack_b2(Geometry g, const double* __restrict__ B, float2* __restrict__ b2)
 {
     const int nx = g.nx, ny = g.ny, nxy = nx * ny;
@@ -136,9 +166,11 @@ struct Ray32 {
 // One step of a voxel's characteristic, from p_m to p_m+1: the upstream
 // point's four nodes are u0 = {chi, S_hi} of (x0, y0) and (x1, y0), u1 the
 // same of (x0, y1), (x1, y1); l0, l1 their S_lo; b the bilinear weights.
-// Returns whether the segment took the series branch (x < 2).
+// Returns whether the segment took the series branch (x < 2); wc_T, wu_T:
+// the segment's weights times the transmission T_m (the recording stores
+// them as coefficients of S).
 __device__ __forceinline__ bool step32(Ray32& r, float hs, float4 b, float4 u0, float4 u1,
-                                       float2 l0, float2 l1)
+                                       float2 l0, float2 l1, float& wc_T, float& wu_T)
 {
     constexpr float kLog2e = 1.4426950408889634f;
     const float cb = b.x * u0.x + b.y * u0.z + b.z * u1.x + b.w * u1.z;
@@ -181,7 +213,36 @@ __device__ __forceinline__ bool step32(Ray32& r, float hs, float4 b, float4 u0, 
     r.T = Tn;
     r.ca = cb;
     r.da = db;
+    wc_T = wcT;
+    wu_T = wuT;
     return x < 2.0f;
+}
+
+// The boundary intensity at the ray's end point (B, or B + |mu| dB/dtau
+// for the LTE-diffusion boundary) in FP64 from the FP32 pairs, for the
+// recording; 0 for a zero boundary.
+__device__ __forceinline__ double boundary_value32(const View32& p, const DirInfo& di, int d,
+                                                   int M, int i0, int j0)
+{
+    const Geometry& g = p.g;
+    const int s = di.sgn;
+    const int bc = s > 0 ? g.top_bc : g.bottom_bc;
+    if (!bc) return 0.0;
+    const long long W = 2LL * g.nx, P = 4LL * g.nx * g.ny;
+    const StepGeo o = p.off[(long long)d * g.nz + M];
+    const float4 b = p.bw[(long long)d * g.nz + M];
+    long long ip = (j0 + o.oy) * W + (i0 + o.ox);
+    RT_GUARD(g, ip, P - W - 1, kSiteFs32) ip = 0;
+    const float2* pb = p.b2 + (s > 0 ? 0LL : P) + ip;
+    const float2 c00 = pb[0], c10 = pb[1], c01 = pb[W], c11 = pb[W + 1];
+    double v = (double)b.x * ((double)c00.x + c00.y) + (double)b.y * ((double)c10.x + c10.y) +
+               (double)b.z * ((double)c01.x + c01.y) + (double)b.w * ((double)c11.x + c11.y);
+    if (bc == 2) {
+        const float* pg = p.g2 + ip;
+        v += (double)di.amu32 *
+             ((double)b.x * pg[0] + (double)b.y * pg[1] + (double)b.z * pg[W] + (double)b.w * pg[W + 1]);
+    }
+    return v;
 }
 
 // s + lo += w (v + vlo): the product w v split exactly (TwoProduct by FMA)
@@ -253,17 +314,22 @@ __device__ __forceinline__ void boundary32(Ray32& r, const View32& p, const DirI
 // voxel whose own cutoff came first keeps adding its (negligible) terms.
 // The step count is that of each voxel's own cutoff.
 // COUNT (diagnostics only): also count the steps that took the series
-// branch of the segment weights into *series.
-template <int TB, bool COUNT>
+// branch of the segment weights into *series.  REC: also record the march
+// into rec (Rec32): per step the coefficients of S(p_m) - S_0 of both
+// voxels, T_{m-1} w_up + T_m w_cur while the voxel's ray is alive (zero
+// after it is cut), and per voxel and slot the boundary sums; partial is
+// then not written (J comes from the replay).
+template <int TB, bool COUNT, bool REC>
 __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int zb, int ZB,
                                         float cut, unsigned long long* __restrict__ steps,
-                                        unsigned long long* __restrict__ series)
+                                        unsigned long long* __restrict__ series, Rec32 rec)
 {
     const Geometry& g = p.g;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int nyp = (ny + 1) >> 1;
     const int t = tile * TB + threadIdx.x;
     const bool active = t < nx * nyp;
+    const unsigned amask = REC ? __ballot_sync(0xffffffffu, active) : 0u;
     unsigned long long nsteps = 0, nseries = 0;
     if (active) {
         const int jp = t / nx, i0 = t - jp * nx, j0 = 2 * jp;
@@ -296,6 +362,7 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
             // pipe of this GPU runs at 1/64 of the FP32 rate; measured on the
             // 65^3 slab: 8.7-9.0 ms against 9.13 with FP64 accumulation)
             float Ja = 0.f, Jalo = 0.f, Jb = 0.f, Jblo = 0.f;
+            double tsa = 0.0, bca = 0.0, tsb = 0.0, bcb = 0.0;   // REC: boundary sums
             for (int d = slot; d < g.ndir; d += kSlots) {
                 const DirInfo di = p.info[d];
                 const int s = di.sgn;
@@ -304,8 +371,11 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                 const float4* bd = p.bw + (long long)d * nz;
                 Ray32 a{ma.y, la.x, tca, 0.f, 0.f, 0.f, 1.f, ma.x, 0.f};
                 Ray32 b{mb.y, lb.x, tcb, 0.f, 0.f, 0.f, 1.f, mb.x, 0.f};
-                bool alive_a = true, alive_b = true, early = false;
+                bool alive_a = true, alive_b = two, early = false;
                 int na = 0, nb = 0, sa = 0, sb = 0;
+                // coefficient of p_m at rc[rec32_step(m)]
+                float2* rc = REC ? rec.coef + rec32_at(g, d, k0, s, t) : nullptr;
+                float cpa = 0.f, cpb = 0.f;   // REC: pending coefficient of the current point
                 int m = 0;
 #pragma unroll 2
                 for (; m < M; ++m) {
@@ -317,11 +387,21 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                     const float2* ql = pl + o;
                     const float4 u0 = __ldg(q), u1 = __ldg(q + W), u2 = __ldg(q + 2 * W);
                     const float2 l0 = __ldg(ql), l1 = __ldg(ql + W), l2 = __ldg(ql + 2 * W);
-                    const bool ba = step32(a, di.hs32, bw, u0, u1, l0, l1);
-                    const bool bb = step32(b, di.hs32, bw, u1, u2, l1, l2);
+                    float wca, wua, wcb, wub;
+                    const bool ba = step32(a, di.hs32, bw, u0, u1, l0, l1, wca, wua);
+                    const bool bb = step32(b, di.hs32, bw, u1, u2, l1, l2, wcb, wub);
                     if (COUNT) {
                         sa += alive_a && ba;
                         sb += alive_b && bb;
+                    }
+                    if (REC) {
+                        // point p_m gets this segment's w_cur (if alive) after
+                        // the previous segment's w_up
+                        const float2 c = make_float2(alive_a ? cpa + wca : cpa,
+                                                     alive_b ? cpb + wcb : cpb);
+                        cpa = alive_a ? wua : 0.f;
+                        cpb = alive_b ? wub : 0.f;
+                        if (m > 0) rc[rec32_step(m)] = c;
                     }
                     na += alive_a;
                     nb += alive_b;
@@ -333,7 +413,25 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                         break;
                     }
                 }
-                if (!early) {
+                if (REC) {
+                    if (m > 0) rc[rec32_step(m)] = make_float2(cpa, cpb);
+                    if (!early && alive_a) {
+                        tsa = fma(di.w, (double)a.T, tsa);
+                        bca = fma(di.w * (double)a.T, boundary_value32(p, di, d, M, i0, j0), bca);
+                    }
+                    if (!early && alive_b) {
+                        tsb = fma(di.w, (double)b.T, tsb);
+                        bcb = fma(di.w * (double)b.T, boundary_value32(p, di, d, M, i0, j0 + 1), bcb);
+                    }
+                    // zeros up to the warp's longest ray (the replay's length)
+                    const int Lw = __reduce_max_sync(amask, m);
+                    // (the replay reads whole blocks of four steps: zero them too,
+                    // up to the ray's room M rounded to four)
+                    const int Lz = min((Lw + 3) & ~3, (M + 3) & ~3);
+                    for (int q = m + 1; q <= Lz; ++q) rc[rec32_step(q)] = make_float2(0.f, 0.f);
+                    if ((threadIdx.x & 31) == __ffs(amask) - 1)
+                        rec.lmax[((long long)d * nz + k0) * rec.nwp + (t >> 5)] = Lw;
+                } else if (!early) {
                     boundary32(a, p, di, d, M, i0, j0);
                     if (two) boundary32(b, p, di, d, M, i0, j0 + 1);
                 }
@@ -342,8 +440,17 @@ __device__ __forceinline__ void march32(const View32& p, int tile, int k0, int z
                 pair_add(Ja, Jalo, di.w32, a.I, a.Ilo);
                 pair_add(Jb, Jblo, di.w32, b.I, b.Ilo);
             }
-            p.partial[(long long)slot * g.N + va] = (double)Ja + (double)Jalo;
-            if (two) p.partial[(long long)slot * g.N + va + nx] = (double)Jb + (double)Jblo;
+            if (REC) {
+                rec.tsum[(long long)slot * g.N + va] = tsa;
+                rec.bc[(long long)slot * g.N + va] = bca;
+                if (two) {
+                    rec.tsum[(long long)slot * g.N + va + nx] = tsb;
+                    rec.bc[(long long)slot * g.N + va + nx] = bcb;
+                }
+            } else {
+                p.partial[(long long)slot * g.N + va] = (double)Ja + (double)Jalo;
+                if (two) p.partial[(long long)slot * g.N + va + nx] = (double)Jb + (double)Jblo;
+            }
         }
     }
     if (steps) add_steps32(steps, nsteps);
@@ -357,7 +464,113 @@ k_fs32d(View32 p, float cut, unsigned long long* __restrict__ steps,
 {
     const int tile = p.pmajor ? blockIdx.y : blockIdx.x;
     const int k0 = p.pmajor ? blockIdx.x : blockIdx.y;
-    march32<TB, COUNT>(p, tile, k0, blockIdx.z, gridDim.z, cut, steps, series);
+    march32<TB, COUNT, false>(p, tile, k0, blockIdx.z, gridDim.z, cut, steps, series, Rec32{});
+}
+
+// The recording march (128 threads per block, once per opacity).
+__global__ void __launch_bounds__(kThreads32)
+k_fs32rec(View32 p, float cut, unsigned long long* __restrict__ steps, Rec32 rec)
+{
+    const int tile = p.pmajor ? blockIdx.y : blockIdx.x;
+    const int k0 = p.pmajor ? blockIdx.x : blockIdx.y;
+    march32<kThreads32, false, true>(p, tile, k0, blockIdx.z, gridDim.z, cut, steps, nullptr, rec);
+}
+
+// Replay of the recorded FP32 march (Rec32) for the source packed in
+// p.spair: per pair of voxels and direction, I - S_0 = sum_m c_m (S(p_m) -
+// S_0) over the warp's recorded length (difference form, Kahan sum), then
+// per voxel and slot the boundary sums: partial = sum_d w_d (I_d - S_0) +
+// bc - S_0 tsum (bc omitted for zero boundary intensities).  The interpolated
+// differences are formed as in the march (hi differences exact for nearby
+// values, the lo parts added once).
+template <int TB>
+__global__ void __launch_bounds__(TB, kResidentR32 / TB)
+k_fs32rep(Rep32 p, unsigned long long* __restrict__ steps)
+{
+    const Geometry& g = p.g;
+    const int tile = p.pmajor ? blockIdx.y : blockIdx.x;
+    const int k0 = p.pmajor ? blockIdx.x : blockIdx.y;
+    const int zb = blockIdx.z, ZB = gridDim.z;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const int nyp = (ny + 1) >> 1;
+    const int t = tile * TB + threadIdx.x;
+    unsigned long long nsteps = 0;
+    if (t < nx * nyp) {
+        const int jp = t / nx, i0 = t - jp * nx, j0 = 2 * jp;
+        const bool two = j0 + 1 < ny;
+        const long long va = (long long)k0 * nxy + (long long)j0 * nx + i0;
+        const long long W = 2LL * nx, P = (2LL * ny + 1) * W;
+        const long long base = k0 * P + j0 * W + i0;
+        const float4* pa = p.spair + base;
+        const float4 ma = pa[0], mb = pa[W];     // {S_hi, S_lo} of the voxels (and x+1)
+        const float sha = ma.x, sla = ma.y, shb = mb.x, slb = mb.y;
+        const double S0a = (double)sha + (double)sla, S0b = (double)shb + (double)slb;
+        for (int slot = zb; slot < kSlots; slot += ZB) {
+            float Ja = 0.f, Jalo = 0.f, Jb = 0.f, Jblo = 0.f;
+            for (int d = slot; d < g.ndir; d += kSlots) {
+                const DirInfo di = p.info[d];
+                const int s = di.sgn;
+                const int* od = p.poff + (long long)d * nz;
+                const float4* bd = p.bw + (long long)d * nz;
+                const float2* rc = p.rec.coef + rec32_at(g, d, k0, s, t);
+                const int L = p.rec.lmax[((long long)d * nz + k0) * p.rec.nwp + (t >> 5)];
+                float Ia = 0.f, Ial = 0.f, Ib = 0.f, Ibl = 0.f;
+                // one step: the upstream point of step m + 1, coefficients c
+                auto step = [&](int m, float2 c) {
+                    const int o = od[m + 1];
+                    const float4 b = bd[m + 1];
+                    const float4* q = pa + o;
+                    const float4 u0 = __ldg(q), u1 = __ldg(q + W), u2 = __ldg(q + 2 * W);
+                    const float dha = b.x * (u0.x - sha) + b.y * (u0.z - sha) + b.z * (u1.x - sha) +
+                                      b.w * (u1.z - sha);
+                    const float dla = b.x * u0.y + b.y * u0.w + b.z * u1.y + b.w * u1.w;
+                    const float dhb = b.x * (u1.x - shb) + b.y * (u1.z - shb) + b.z * (u2.x - shb) +
+                                      b.w * (u2.z - shb);
+                    const float dlb = b.x * u1.y + b.y * u1.w + b.z * u2.y + b.w * u2.w;
+                    const float ya = fmaf(c.x, dha + (dla - sla), Ial);
+                    const float ta = Ia + ya;
+                    Ial = ya - (ta - Ia);
+                    Ia = ta;
+                    const float yb = fmaf(c.y, dhb + (dlb - slb), Ibl);
+                    const float tb = Ib + yb;
+                    Ibl = yb - (tb - Ib);
+                    Ib = tb;
+                };
+                int m = 0;
+                // whole blocks of four steps without conditions, so that their
+                // loads can be issued together; then the remaining steps
+                for (; m + 4 <= L; m += 4) {
+                    RT_GUARD(g, base + od[m + 4], P * nz, kSiteFs32) break;
+                    RT_GUARD(g, base + od[m + 4] + 2 * W, P * nz, kSiteFs32) break;
+                    const float4* c4 = reinterpret_cast<const float4*>(rc + rec32_step(m + 1));
+                    const float4 cA = __ldg(c4), cB = __ldg(c4 + 1);
+                    step(m, make_float2(cA.x, cA.y));
+                    step(m + 1, make_float2(cA.z, cA.w));
+                    step(m + 2, make_float2(cB.x, cB.y));
+                    step(m + 3, make_float2(cB.z, cB.w));
+                }
+                for (; m < L; ++m) {
+                    RT_GUARD(g, base + od[m + 1], P * nz, kSiteFs32) break;
+                    RT_GUARD(g, base + od[m + 1] + 2 * W, P * nz, kSiteFs32) break;
+                    step(m, __ldg(rc + rec32_step(m + 1)));
+                }
+                nsteps += (unsigned long long)L * (two ? 2ull : 1ull);
+                pair_add(Ja, Jalo, di.w32, Ia, Ial);
+                pair_add(Jb, Jblo, di.w32, Ib, Ibl);
+            }
+            const long long ea = (long long)slot * g.N + va;
+            double ja = (double)Ja + (double)Jalo - S0a * p.rec.tsum[ea];
+            if (!p.zero_bc) ja += p.rec.bc[ea];
+            p.partial[ea] = ja;
+            if (two) {
+                const long long eb = ea + nx;
+                double jb = (double)Jb + (double)Jblo - S0b * p.rec.tsum[eb];
+                if (!p.zero_bc) jb += p.rec.bc[eb];
+                p.partial[eb] = jb;
+            }
+        }
+    }
+    if (steps) add_steps32(steps, nsteps);
 }
 
 int tiles32(const Geometry& g, int tb) { return (g.nx * ((g.ny + 1) / 2) + tb - 1) / tb; }
@@ -394,7 +607,7 @@ k_fs32_batch(const View32* __restrict__ views, const int* __restrict__ ids,
     const int zb = (int)(local / ((long long)tiles * p.g.nz));
     const int tile = p.pmajor ? (int)(tk / p.g.nz) : (int)(tk % tiles);
     const int k0 = p.pmajor ? (int)(tk % p.g.nz) : (int)(tk / tiles);
-    march32<TB, false>(p, tile, k0, zb, ZB, cut, steps, nullptr);
+    march32<TB, false, false>(p, tile, k0, zb, ZB, cut, steps, nullptr, Rec32{});
 }
 
 // dS = S - Sref (the source change the finishing stage marches)
@@ -483,6 +696,23 @@ cudaError_t launch_pack_pairs(const Geometry& g, const double* chi, const double
     return cudaGetLastError();
 }
 
+cudaError_t launch_pack_spairs(const Geometry& g, const double* S, float4* spair, cudaStream_t st)
+{
+    k_pack_spairs<<<grid1d(pair_records(g), 256), 256, 0, st>>>(g, S, spair);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fs32rec(const View32& p, double cut, int groups, const Rec32& rec,
+                           unsigned long long* steps, cudaStream_t st)
+{
+    const int tiles = tiles32(p.g, kThreads32);
+    if (p.pmajor && tiles32(p.g, 64) > 65535) return cudaErrorInvalidConfiguration;
+    const dim3 grid = p.pmajor ? dim3(p.g.nz, tiles, groups) : dim3(tiles, p.g.nz, groups);
+    k_fs32rec<<<grid, kThreads32, 0, st>>>(p, (float)cut, steps, rec);
+    return cudaGetLastError();
+}
+
+
 cudaError_t launch_pack_b2(const Geometry& g, const double* B, float2* b2, cudaStream_t st)
 {
     k_pack_b2<<<grid1d(2LL * g.nx * g.ny, 256), 256, 0, st>>>(g, B, b2);
@@ -566,6 +796,22 @@ cudaError_t launch_sum_groups_src(long long N, const double* partial, const doub
                                   double wsum, double* J, cudaStream_t st)
 {
     k_sum_groups_src<<<grid1d(N, 256), 256, 0, st>>>(N, partial, S, wsum, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fs32rep(const Rep32& p, int groups, int threads, unsigned long long* steps,
+                           cudaStream_t st)
+{
+    const int tb = block_threads32(threads);
+    if (p.pmajor && tiles32(p.g, 64) > 65535) return cudaErrorInvalidConfiguration;
+    const int tiles = tiles32(p.g, tb);
+    const dim3 grid = p.pmajor ? dim3(p.g.nz, tiles, groups) : dim3(tiles, p.g.nz, groups);
+    if (tb == 64)
+        k_fs32rep<64><<<grid, 64, 0, st>>>(p, steps);
+    else if (tb == 256)
+        k_fs32rep<256><<<grid, 256, 0, st>>>(p, steps);
+    else
+        k_fs32rep<kThreads32><<<grid, kThreads32, 0, st>>>(p, steps);
     return cudaGetLastError();
 }
 

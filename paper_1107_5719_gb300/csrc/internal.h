@@ -239,6 +239,70 @@ struct View32 {
 // exceed kPlaneMajorBytes, i.e. no longer stay in L2 together).
 constexpr long long kPlaneMajorBytes = 64ll << 20;
 int plane_major32(const Geometry& g, int order);
+// The FP32-sweep march recorded as a linear map of the source (difference
+// form): thread t of plane k0 marches voxels (i0, j0) and (i0, j0 + 1),
+// t = (j0/2) nx + i0 < npair = nx ceil(ny/2);
+//   coef: {c_m of the first voxel, of the second} at rec32_at(g, d, k0,
+//     sgn_d, t) + rec32_step(m), m = 1..M, c_m the coefficient of
+//     S(p_m) - S_0 (zero past the ray's cutoff);
+//   lmax[(d nz + k0) nwp + t/32]: the warp's longest ray (nwp = warps per
+//     plane of pairs);
+//   tsum, bc [kSlots][N]: sum_{d in slot} w_d T_L and w_d T_L I_bc over the
+//     rays that reach the boundary plane.
+struct Rec32 {
+    float2* coef;
+    int* lmax;
+    double* tsum;
+    double* bc;
+    int nwp;
+};
+// F(K) = sum_{k<K} 4 ceil(k/4): the steps of planes 0..K-1 rounded up to
+// blocks of four.
+__host__ __device__ __forceinline__ long long rec32_steps4(long long K)
+{
+    const int part[4] = {0, 0, 3, 5};
+    return K * (K - 1) / 2 + 6 * (K / 4) + part[K & 3];
+}
+// Offset of the coefficients of thread t (step 1) of plane k0, direction
+// d: per (direction, plane) one block per warp, [step/4][lane][step%4], so
+// that each lane reads four steps' pairs with two 16-byte loads and the
+// warp streams 1 KB per four steps; step m (1-based) is at
+// rec32_at(...) + rec32_step(m).
+__host__ __device__ __forceinline__ long long rec32_at(const Geometry& g, int d, int k0, int sgn,
+                                                        int t)
+{
+    const long long nw = ((long long)g.nx * ((g.ny + 1) / 2) + 31) / 32;   // warps per plane
+    const long long k = k0, nz = g.nz;
+    const long long before = sgn > 0 ? rec32_steps4(k) : rec32_steps4(nz) - rec32_steps4(nz - k);
+    const long long M = sgn > 0 ? k : nz - 1 - k;
+    const long long M4 = (M + 3) / 4 * 4;
+    return ((long long)d * rec32_steps4(nz) + before) * nw * 32 + (t >> 5) * M4 * 32 + (t & 31) * 4;
+}
+__host__ __device__ __forceinline__ long long rec32_step(int m)
+{
+    return (long long)((m - 1) >> 2) * 128 + ((m - 1) & 3);
+}
+// The replay: the source in spair (k_pack_spairs records), the march's
+// geometry tables and block order, the recording; zero_bc: the boundary
+// intensities are zero (the finishing stage's source change).
+struct Rep32 {
+    Geometry g;
+    const float4* spair;
+    const DirInfo* info;
+    const int* poff;
+    const float4* bw;
+    Rec32 rec;
+    double* partial;
+    int zero_bc;
+    int pmajor;
+};
+cudaError_t launch_pack_spairs(const Geometry& g, const double* S, float4* spair, cudaStream_t st);
+// Record the march of p (cut at `cut`, the caller's stricter cutoff) into rec.
+cudaError_t launch_fs32rec(const View32& p, double cut, int groups, const Rec32& rec,
+                           unsigned long long* steps, cudaStream_t st);
+cudaError_t launch_fs32rep(const Rep32& p, int groups, int threads, unsigned long long* steps,
+                           cudaStream_t st);
+
 // FP32 march of I - S_0: partial[kSlots][N] of sum_d w_d (I_d - S_0).
 // threads: threads per block, 64, 128 or 256 (anything else: 128); J does
 // not depend on it.  series != null (diagnostics): a kernel instantiation

@@ -572,7 +572,8 @@ class Solver:
 
     def __init__(self, problem, device: int = 0, precision: int = RT_FP64, groups: int = 0,
                  cutoff: Optional[float] = None, ng_period: int = 0, ng_min_delta: float = 0.0,
-                 os_method: int = RT_OS_JACOBI, fs_method: int = RT_FS_LONG):
+                 os_method: int = RT_OS_JACOBI, fs_method: int = RT_FS_LONG,
+                 record: Optional[int] = None):
         self.p = problem
         self.precision = precision
         self.ctx = rt_create(device, precision)
@@ -595,6 +596,8 @@ class Solver:
             rt_set_fs_method(self.ctx, fs_method)
         if getattr(problem, "src_order", 0):
             rt_set_source_order(self.ctx, problem.src_order)
+        if record is not None:
+            rt_set_fs_record(self.ctx, record)
 
     def formal_solution(self, S=None, want_lstar=True):
         return rt_formal_solution(self.ctx, S, self.shape, want_lstar)

@@ -52,7 +52,8 @@ def test_batch_equals_individual_solves(R, precision):
         assert r["converged"] and r["n_converged"] == len(probs)
         for i, p in enumerate(probs):
             J = R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx))
-            with R.Solver(p, precision=precision, ng_period=4, ng_min_delta=1e-6) as s:
+            with R.Solver(p, precision=precision, ng_period=4, ng_min_delta=1e-6,
+                          record=0) as s:   # the batch marches
                 ri = s.solve(tol=TOL[precision], max_iter=500)
             assert ri["iters"] == r["iters"][i]
             assert np.array_equal(J, ri["J"]), i
@@ -103,7 +104,8 @@ def test_batch_wavelengths_of_one_slab(R):
         r = R.rt_batch_solve(b, len(probs), tol=TOL[1], max_iter=2000)
         assert r["converged"]
         for i in (0, 5):
-            with R.Solver(probs[i], precision=1, ng_period=4, ng_min_delta=1e-6) as s:
+            with R.Solver(probs[i], precision=1, ng_period=4, ng_min_delta=1e-6,
+                          record=0) as s:   # the batch marches
                 ri = s.solve(tol=TOL[1], max_iter=2000)
             J = R.rt_batch_get_J(b, i, ri["J"].shape)
             assert np.array_equal(J, ri["J"])

@@ -101,7 +101,8 @@ def test_fs32_fixed_point_column_strong_scattering(R, eps):
     sits within 1e-6 of the FP64 fixed point (measured ~3e-8 on a 9x9x129
     slab at eps = 1e-6)."""
     p = W.slab_precision(n=3, nzz=129, eps=eps, n_theta=16, n_phi=4)
-    with R.Solver(p, precision=R.RT_FP64, ng_period=4) as s:
+    # the reference marches (its rounding floor at eps = 1e-6 is below 1e-11)
+    with R.Solver(p, precision=R.RT_FP64, ng_period=4, record=0) as s:
         r64 = s.solve(tol=1e-11, max_iter=4000)
     assert r64["converged"]
     with R.Solver(p, precision=R.RT_FP32_SWEEP, **NG32) as s:
@@ -156,7 +157,7 @@ def test_branch_counts_split_steps_by_segment_optical_depth(R):
     def counts(mu, phi):
         mu, phi = np.array(mu), np.array(phi)
         p = W.Problem(nx, ny, nz, chi, base.eps, base.B, mu, phi, np.full(len(mu), 1 / len(mu)))
-        with R.Solver(p, precision=R.RT_FP32_SWEEP, cutoff=0.0) as s:
+        with R.Solver(p, precision=R.RT_FP32_SWEEP, cutoff=0.0, record=0) as s:
             n, ser = R.rt_fs32_branch_counts(s.ctx, S)
             s.formal_solution(S, want_lstar=False)
             assert n == R.rt_last_step_count(s.ctx)

@@ -26,7 +26,8 @@ def R():
 
 def test_fp32_then_double_float_reaches_1e6(R):
     p = W.slab_precision(n=9, nzz=129, n_theta=32, n_phi=8)
-    with R.Solver(p, precision=R.RT_FP64, ng_period=4) as s:
+    # the reference marches (its rounding floor at eps = 1e-6 is below 1e-11)
+    with R.Solver(p, precision=R.RT_FP64, ng_period=4, record=0) as s:
         r64 = s.solve(tol=1e-11, max_iter=5000)
     assert r64["converged"]
     with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
@@ -86,7 +87,8 @@ def test_batch_fp32_then_double_float_equals_single(R):
     finally:
         R.rt_batch_destroy(b)
     for i, q in enumerate(probs):
-        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6,
+                      record=0) as s:   # the batch marches
             R.rt_set_df_finish(s.ctx, 0.0)
             a = s.solve(tol=5e-8, max_iter=3000)
             R.rt_set_precision(s.ctx, R.RT_DF64)
@@ -103,7 +105,8 @@ def test_automatic_double_float_finish(R):
     the FP32 sweep alone needs for 5e-8; afterwards the context is an
     FP32-sweep context again."""
     p = W.slab_precision(n=9, nzz=129, n_theta=32, n_phi=8)
-    with R.Solver(p, precision=R.RT_FP64, ng_period=4) as s:
+    # the reference marches (its rounding floor at eps = 1e-6 is below 1e-11)
+    with R.Solver(p, precision=R.RT_FP64, ng_period=4, record=0) as s:
         r64 = s.solve(tol=1e-11, max_iter=5000)
     with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
         R.rt_set_df_finish(s.ctx, 0.0)
@@ -134,7 +137,8 @@ def test_batch_automatic_finish_equals_single(R):
     finally:
         R.rt_batch_destroy(b)
     for i, q in enumerate(probs):
-        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6,
+                      record=0) as s:   # the batch marches
             R.rt_set_df_finish(s.ctx, 1e-6)
             r = s.solve(tol=1e-8, max_iter=3000)
         assert r["iters"] == rb["iters"][i]

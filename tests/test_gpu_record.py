@@ -1,4 +1,4 @@
-"""GPU FP64 recorded formal solution against the FP64 oracle.
+"""GPU recorded formal solution (FP64 and FP32 sweep) against the oracle.
 
 The first formal solution after the opacities, directions or boundary
 change records the march as a linear map of S; later ones replay it for
@@ -149,3 +149,58 @@ def test_converged_solve_replaying_matches_the_march(R):
     assert res[0]["converged"] and res[1]["converged"]
     assert np.allclose(res[1]["J"], res[0]["J"], rtol=1e-11, atol=0)
     assert abs(res[1]["iters"] - res[0]["iters"]) <= 1
+
+
+FS32_RTOL = 1e-6        # one FP32-sweep formal solution against the oracle
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "fp32-{nx}x{ny}x{nz}".format(**c))
+def test_fp32_record_then_replay_match_oracle(R, oracle_mod, case):
+    """The FP32 sweep records its march (difference form) and replays it for
+    other sources: both within the FP32 parity of the oracle, and the replay
+    of the recording source equal to the recording formal solution."""
+    p = _slab(case)
+    rng = np.random.default_rng(12)
+    S1 = 0.5 + 2.0 * rng.random(p.B.shape)
+    S2 = 0.1 + 5.0 * rng.random(p.B.shape)
+    with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+        J1, _ = s.formal_solution(S1, want_lstar=False)
+        nbytes, valid = R.rt_fs_record_info(s.ctx)
+        assert nbytes > 0 and valid
+        J2, _ = s.formal_solution(S2, want_lstar=False)
+        J1r, _ = s.formal_solution(S1, want_lstar=False)
+    assert np.array_equal(J1r, J1)
+    assert np.allclose(J1, oracle_mod.formal_solution(p, S1)[0], rtol=FS32_RTOL, atol=0)
+    assert np.allclose(J2, oracle_mod.formal_solution(p, S2)[0], rtol=FS32_RTOL, atol=0)
+
+
+def test_fp32_replay_agrees_with_the_march(R):
+    p = W.random_slab(21, 13, 9, n_theta=6, n_phi=5, seed=17, chi_decades=5.0)
+    S = 0.3 + np.random.default_rng(3).random(p.B.shape)
+    out = []
+    for mode in (0, -1):
+        with R.Solver(p, precision=R.RT_FP32_SWEEP) as s:
+            R.rt_set_fs_record(s.ctx, mode)
+            s.formal_solution(p.B, want_lstar=False)              # records (mode -1)
+            out.append(s.formal_solution(S, want_lstar=False)[0])
+    assert np.allclose(out[1], out[0], rtol=2e-7, atol=0)
+
+
+def test_fp32_solve_through_the_replay_meets_fp64(R):
+    """The FP32 form as created (finishing stage from delta < 1e-6; its
+    source-change marches replay the recording with zero boundary
+    intensities) converges to the FP64 fixed point within 1e-6, as the
+    marching solve does."""
+    p = W.slab_precision(n=5, nzz=33, eps=1e-4, n_theta=8, n_phi=4)
+    with R.Solver(p, precision=R.RT_FP64, ng_period=4, record=0) as s:
+        r64 = s.solve(tol=1e-11, max_iter=3000)
+    res = []
+    for mode in (0, -1):
+        with R.Solver(p, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
+            R.rt_set_fs_record(s.ctx, mode)
+            res.append(s.solve(tol=1e-9, max_iter=3000))
+            assert R.rt_fs_record_info(s.ctx)[1] == (mode == -1)
+    for r in res:
+        assert r["converged"]
+        assert np.max(np.abs(r["J"] - r64["J"]) / r64["J"]) < 1e-6
+    assert np.max(np.abs(res[1]["J"] - res[0]["J"]) / res[0]["J"]) < 1e-7
