@@ -60,6 +60,12 @@ FLOPS_COMMON_FP32 = 38
 FLOPS_CLOSED_FP32 = 45
 FLOPS_SERIES_FP32 = 61
 FLOPS_PER_STEP_FP32 = FLOPS_CLOSED_FP32     # lower bound: every step on the closed form
+# Replay of the recorded FP32 march, per voxel-step: 20 flops for the
+# interpolated source difference, 5 for the Kahan update; DRAM bytes per
+# replayed voxel-step from ncu on the 33^3 slab (4 coefficient bytes, the
+# blocks of four steps padded, and the source records)
+FLOPS_PER_STEP_FP32_REPLAY = 25
+REPLAY32_DRAM_BYTES_PER_STEP = 5.48
 # Thread instructions per step of k_fs32d (ncu, 65^3 slab, 32 x 32 directions)
 INSTR_PER_STEP_FP32 = 74.2
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
@@ -283,10 +289,11 @@ def timed_solves(R, p, precision, dev, stream, flush, warmup, steps, max_iter, c
         R.rt_destroy(ctx)
 
 
-def march_rate(R, p, precision, dev, stream, launches=5):
-    """Device time and executed steps per launch of the march alone: formal
-    solutions of the workload's source S = eps B + (1 - eps) B, timed with
-    the library's CUDA events."""
+def march_rate(R, p, precision, dev, stream, launches=5, record=0):
+    """Device time and executed steps per launch of the formal solution
+    alone: the march itself (record 0), or the replay of the recorded march
+    (record -1: the untimed first formal solution records); source
+    S = eps B + (1 - eps) B, timed with the library's CUDA events."""
     import torch
     S = torch.from_numpy(p.eps * p.B + (1 - p.eps) * p.B).to(dev)
     J = torch.empty_like(S)
@@ -299,10 +306,11 @@ def march_rate(R, p, precision, dev, stream, launches=5):
         R.rt_set_opacity(ctx, p.chi)
         R.rt_set_epsilon(ctx, p.eps)
         R.rt_set_planck(ctx, p.B)
+        R.rt_set_fs_record(ctx, record)
         R.rt_formal_solution_dev(ctx, S, J, None)
         stream.synchronize()
         branches = {}
-        if precision == R.RT_FP32_SWEEP:
+        if precision == R.RT_FP32_SWEEP and record == 0:
             # outside the timed launches: the branch-counting copy of the march
             n, ser = R.rt_fs32_branch_counts(ctx, S.cpu().numpy())
             branches = {"branch_count_steps": n, "series_steps": ser}
@@ -443,11 +451,34 @@ def run_only(args, dev, R):
     elif name == "config5":
         out = config5_iteration(R, dev, stream, args.ng)
     elif name == "march32":
-        m32 = march_rate(R, make_problem(args.workload), R.RT_FP32_SWEEP, dev, stream)
-        out = {"march": m32, "roofline": fp32_roofline(m32, R.rt_probe_peaks(dev.index))}
+        pw = make_problem(args.workload)
+        m32 = march_rate(R, pw, R.RT_FP32_SWEEP, dev, stream)
+        r32 = march_rate(R, pw, R.RT_FP32_SWEEP, dev, stream, record=-1)
+        probe = R.rt_probe_peaks(dev.index)
+        out = {"march": m32, "roofline": fp32_roofline(m32, probe),
+               "replay": r32, "replay_roofline": fp32_replay_roofline(r32)}
     else:
         raise SystemExit(f"unknown companion {name}")
     print(json.dumps({"only": name, name: out}), flush=True)
+
+
+def fp32_replay_roofline(r32):
+    """The replay of the recorded FP32 march: per voxel-step the
+    interpolated source difference (4 differences, 4 + 4 products and sums:
+    20 flops) and the Kahan update (5), 4 coefficient bytes streamed; it
+    waits on its loads (ncu: long-scoreboard stalls), so both the HBM
+    fraction of its coefficient stream and its FP32 rate are given."""
+    ms, n = r32["ms_per_launch"], r32["steps_per_launch"]
+    gbs = REPLAY32_DRAM_BYTES_PER_STEP * n / (ms / 1e3) / 1e9
+    tfl = FLOPS_PER_STEP_FP32_REPLAY * n / (ms / 1e3) / 1e12
+    return {"kernel": "k_fs32rep (replay of the recorded FP32 march)", "bound": "hbm",
+            "achieved": round(gbs, 1), "peak": round(MEASURED_HBM_GBS, 1), "unit": "GB/s",
+            "frac": round(gbs / MEASURED_HBM_GBS, 4),
+            "dram_bytes_per_step": REPLAY32_DRAM_BYTES_PER_STEP,
+            "flops_per_step": FLOPS_PER_STEP_FP32_REPLAY,
+            "achieved_tflops": round(tfl, 3), "frac_of_fp32_peak": round(tfl / PEAK_FP32_TFLOPS, 4),
+            "note": "latency-bound (ncu on the 33^3 slab: long-scoreboard stalls 10 per issue, "
+                    "issue 37%); DRAM bytes per step from that capture"}
 
 
 def fp32_roofline(m32, probe):
@@ -575,6 +606,7 @@ def run_ours(args):
         st32 = r32["stats"]
         ms32 = float(sum(r32["times"]))
         m32 = march_rate(R, p, R.RT_FP32_SWEEP, dev, stream)
+        rep32 = march_rate(R, p, R.RT_FP32_SWEEP, dev, stream, record=-1)
         fp32 = {"value": round(RP.weak_throughput(args.fp32_steps, ms32)[0], 6), "unit": "solves/s",
                 "form": "FP32 sweep + finishing stage from delta < 1e-6 (the default)",
                 "ms_per_step": round(ms32 / args.fp32_steps, 3),
@@ -585,6 +617,8 @@ def run_ours(args):
                 "speedup_vs_fp64": round(my_ms / args.steps / (ms32 / args.fp32_steps), 3),
                 "march": m32}
         fp32["roofline"] = fp32_roofline(m32, probe)
+        fp32["replay"] = rep32
+        fp32["replay_roofline"] = fp32_replay_roofline(rep32)
 
     # the double-float form (FP64-accurate march on the FP32 pipes)
     df64 = None
@@ -933,6 +967,10 @@ def config5_iteration(R, dev, stream, ng):
     t_create = time.time() - t0
     try:
         R.rt_batch_set_ng(bt, ng, NG_MIN_FP32)
+        # one iteration of all 64 problems: their recordings could not be held
+        # together (a 65^3 problem's at 64x64 directions alone takes 156 GB),
+        # so every problem marches
+        R.rt_batch_set_fs_record(bt, 0)
         R.rt_batch_set_stream(bt, stream)
         R.rt_batch_reset_stats(bt)
         R.rt_batch_set_profiling(bt, True)

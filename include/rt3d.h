@@ -487,6 +487,18 @@ int rt_batch_set_direction_groups(rt_batch *batch, int groups);
 int rt_batch_set_block_threads(rt_batch *batch, int threads);
 /* As rt_set_block_order, for every problem of the fused FP32 launch. */
 int rt_batch_set_block_order(rt_batch *batch, int order);
+/* Recorded formal solutions in a batch (see rt_set_fs_record): every
+ * problem records its march in its first formal solution and replays it
+ * afterwards (FP32 sweep: all replays in one fused launch), exactly as a
+ * single solve does, so the batch's iterates stay bit-identical to single
+ * solves.  A problem starts iterating once its recording fits in the
+ * budget beside the recordings held (max_bytes: -1 (default) 60% of the
+ * device, 0 no recordings, > 0 a byte limit), and returns the memory when
+ * it converges or reaches max_iter; problems run in waves when the budget
+ * holds fewer than all (65^3 x 1024 directions, FP32 sweep: 39 GB each).
+ * A problem whose recording could never fit marches from the start.
+ * Releases the recordings held.  RT_EINVAL for max_bytes < -1. */
+int rt_batch_set_fs_record(rt_batch *batch, long long max_bytes);
 /* on != 0 (the default): every outer iteration runs the operator-splitting
  * solves of all active problems (Sect. 2.3) as ONE CUDA graph, one
  * independent branch per problem (right-hand side, a device-side loop of

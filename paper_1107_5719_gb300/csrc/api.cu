@@ -308,12 +308,29 @@ long long up256(long long b) { return (b + 255) / 256 * 256; }
 // with long characteristics and the linear source, or the FP32 sweep; a
 // byte budget that admits it), with its buffers carved from one block.
 // When it does not fit, the march runs as it is every time.
+// Bytes a recording of this context's march takes (0: its form does not record).
+long long rec_need(const rt_ctx* c)
+{
+    if (c->fs_method != RT_FS_LONG || c->src_order != RT_SRC_LINEAR || c->g.nz < 2 ||
+        (c->precision != RT_FP64 && c->precision != RT_FP32_SWEEP))
+        return 0;
+    const long long tri = (long long)c->g.nz * (c->g.nz - 1) / 2;
+    const long long b_slot = up256((long long)kSlots * c->g.N * (long long)sizeof(double));
+    if (c->precision == RT_FP64) {
+        const long long nxy = (long long)c->g.nx * c->g.ny, nwp = (nxy + 31) / 32;
+        return up256((long long)c->g.ndir * nxy * tri * (long long)sizeof(double)) +
+               up256((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int)) + 2 * b_slot;
+    }
+    const long long npair = (long long)c->g.nx * ((c->g.ny + 1) / 2), nwp = (npair + 31) / 32;
+    return up256((long long)c->g.ndir * rec32_steps4(c->g.nz) * nwp * 32 * (long long)sizeof(float2)) +
+           up256((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int)) + 2 * b_slot +
+           up256(pair_records(c->g) * (long long)sizeof(float4));
+}
+
 int ensure_rec(rt_ctx* c, bool& use)
 {
     use = false;
-    if (c->rec_mode == 0 || c->fs_method != RT_FS_LONG || c->src_order != RT_SRC_LINEAR ||
-        c->g.nz < 2 || (c->precision != RT_FP64 && c->precision != RT_FP32_SWEEP))
-        return RT_OK;
+    if (c->rec_mode == 0 || rec_need(c) == 0) return RT_OK;
     const long long tri = (long long)c->g.nz * (c->g.nz - 1) / 2;
     const long long b_slot = up256((long long)kSlots * c->g.N * (long long)sizeof(double));
     if (c->precision == RT_FP64) {
@@ -1192,6 +1209,18 @@ struct rt_batch {
     bool use_graphs = true;
     int* d_sweeps = nullptr;        // sweeps of each problem's last OS step
     int* h_sweeps = nullptr;        // pinned
+    // Recorded marches: a problem starts iterating once its recording fits
+    // in the batch's budget (rec_mode: -1 automatic, 0 off, > 0 bytes), so
+    // that every problem records in its first formal solution as a single
+    // solve does; its memory returns when it converges.
+    long long rec_mode = -1;
+    std::vector<char> admitted;
+    Rep32* d_rviews = nullptr;      // replay views (device) and pinned host copies
+    Rep32* h_rviews = nullptr;
+    int* d_rids = nullptr;
+    long long* d_rprefix = nullptr;
+    int* h_rids = nullptr;          // pinned
+    long long* h_rprefix = nullptr; // pinned
     rt_stats stats{};
     std::string err;
 };
@@ -1234,6 +1263,64 @@ int batch_groups(const rt_batch* b, const std::vector<int>& act)
     int G = 1;
     while (G < kSlots && blocks * G < 64LL * (b->num_sms > 0 ? b->num_sms : 152)) G *= 2;
     return G;
+}
+
+// Admit waiting problems (in launch order) whose recorded march fits in the
+// batch's budget beside the recordings held; a problem whose form does not
+// record, or whose recording could never fit, starts at once and marches.
+// When nothing runs and a problem cannot get its memory, it starts marching
+// too, so that the solve always progresses.
+int batch_admit(rt_batch* b, int max_iter)
+{
+    long long limit = b->rec_mode;
+    if (limit < 0) {
+        size_t fr = 0, tot = 0;
+        BCK(cudaMemGetInfo(&fr, &tot));
+        limit = (long long)(0.6 * (double)tot);
+    }
+    long long used = 0;
+    bool running = false;
+    for (size_t p = 0; p < b->ctx.size(); ++p) {
+        used += b->ctx[p]->rec_cap;
+        if (b->admitted[p] && !b->converged[p] && b->iters[p] < max_iter) running = true;
+    }
+    for (int p : b->order) {
+        rt_ctx* c = b->ctx[p];
+        if (b->admitted[p] || b->converged[p] || b->iters[p] >= max_iter) continue;
+        const long long need = rec_need(c);
+        if (b->rec_mode == 0 || need == 0 || need > limit) {
+            c->rec_mode = 0;                      // marches
+        } else if (used + need <= limit) {
+            c->rec_mode = need;
+            bool use = false;
+            const int rc = ensure_rec(c, use);
+            if (rc) return bfail(b, rc, "problem %d: %s", p, rt_last_error(c));
+            if (use) {
+                used += c->rec_cap;
+            } else if (running) {
+                continue;                         // wait for memory
+            } else {
+                c->rec_mode = 0;
+            }
+        } else if (running) {
+            continue;                             // wait for memory
+        } else {
+            c->rec_mode = 0;
+        }
+        b->admitted[p] = 1;
+        running = true;
+    }
+    return RT_OK;
+}
+
+// A problem that stops iterating returns its recording's memory.
+void batch_release(rt_batch* b, int p)
+{
+    rt_ctx* c = b->ctx[p];
+    if (c->rec_cap) {
+        cudaStreamSynchronize(b->stream);
+        free_rec(c);
+    }
 }
 
 void bharvest(rt_batch* b)
@@ -1367,7 +1454,49 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
     BCK(cudaMemsetAsync(b->d_steps, 0, sizeof(unsigned long long), b->stream));
     if (b->profiling) BCK(cudaEventRecord(b->ev[0], b->stream));
     if (b->precision == RT_FP32_SWEEP) {
-        // one fused launch over the problems in the FP32 sweep, including
+        // problems holding a recording: record it in their first formal
+        // solution, then one fused replay over all of them (their source, or
+        // in the finishing stage its change, packed for the replay)
+        long long rtotal = 0;
+        int rq = 0;
+        std::vector<char> replays(b->ctx.size(), 0);
+        for (int p : act) {
+            rt_ctx* c = b->ctx[p];
+            if (c->precision != RT_FP32_SWEEP || c->fin == 1) continue;
+            bool use = false;
+            if ((rc = bpass(b, p, ensure_rec(c, use)))) return rc;
+            if (!use) continue;
+            if (!c->rec_valid) {
+                if (c->fin != 0) continue;
+                BCK(launch_fs32rec(view32(c), cut_of(c) * kRecCutMargin, G, c->rec32, b->d_steps,
+                                   b->stream));
+                c->rec_valid = true;
+                b->stats.launches += 1;
+            }
+            BCK(launch_pack_spairs(c->g, c->fin == 2 ? c->dS : c->S, c->spair, b->stream));
+            b->stats.launches += 1;
+            b->h_rviews[p] = Rep32{c->g, c->spair, c->info, c->poff32, c->bw32, c->rec32,
+                                   c->partial, c->fin == 2 ? 1 : 0, plane_major32(c->g, c->order32)};
+            b->h_rids[rq] = p;
+            b->h_rprefix[rq] = rtotal;
+            rtotal += fs32_blocks(c->g, G, b->threads32);
+            ++rq;
+            replays[p] = 1;
+        }
+        b->h_rprefix[rq] = rtotal;
+        if (rq > 0) {
+            BCK(cudaMemcpyAsync(b->d_rviews, b->h_rviews, sizeof(Rep32) * b->ctx.size(),
+                                cudaMemcpyHostToDevice, b->stream));
+            BCK(cudaMemcpyAsync(b->d_rids, b->h_rids, sizeof(int) * rq, cudaMemcpyHostToDevice,
+                                b->stream));
+            BCK(cudaMemcpyAsync(b->d_rprefix, b->h_rprefix, sizeof(long long) * (rq + 1),
+                                cudaMemcpyHostToDevice, b->stream));
+            BCK(launch_fs32rep_batch(b->d_rviews, b->d_rids, b->d_rprefix, rq, rtotal, G,
+                                     b->threads32, b->d_steps, b->stream));
+            b->stats.fs_launches += 1;
+            b->stats.launches += 1;
+        }
+        // one fused launch over the other problems in the FP32 sweep, including
         // those marching their source change in the finishing stage (act is
         // in launch order); a finishing-stage reference and problems switched
         // to the double-float march by hand run one launch each
@@ -1375,7 +1504,7 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
         int q = 0;
         for (int p : act) {
             rt_ctx* c = b->ctx[p];
-            if (c->precision != RT_FP32_SWEEP || c->fin == 1) continue;
+            if (c->precision != RT_FP32_SWEEP || c->fin == 1 || replays[p]) continue;
             const char want = c->fin == 2;
             if (b->view_fin[p] != want) {     // this problem's view changed form
                 b->h_views[p] = want ? view32_fin(c) : view32(c);
@@ -1414,12 +1543,25 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
     } else {
         for (int p : act) {
             rt_ctx* c = b->ctx[p];
-            if (b->precision == RT_DF64)
+            bool use = false;
+            if (b->precision == RT_FP64 && (rc = bpass(b, p, ensure_rec(c, use)))) return rc;
+            if (b->precision == RT_DF64) {
                 BCK(launch_fsdf(viewdf(c), cut_of(c), G, b->d_steps, b->stream));
-            else
+            } else if (use) {
+                if (!c->rec_valid) {
+                    BCK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw,
+                                    c->bwh, c->scal + 0, cut_of(c), G, c->partial, b->d_steps,
+                                    b->stream, &c->rec));
+                    c->rec_valid = true;
+                    b->stats.launches += 1;
+                }
+                BCK(launch_fs64rep(c->g, c->S, c->info, c->off, c->bw, c->rec, G, c->partial,
+                                   b->d_steps, b->stream));
+            } else {
                 BCK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw,
                                 c->bwh, c->scal + 0, cut_of(c), G, c->partial, b->d_steps,
                                 b->stream));
+            }
             b->stats.fs_launches += 1;
             b->stats.launches += 1;
         }
@@ -2133,6 +2275,7 @@ int rt_batch_create(rt_batch** out, int device, int precision, int nprob, const 
     b->iters.assign(nprob, 0);
     b->delta.assign(nprob, 0.0);
     b->converged.assign(nprob, 0);
+    b->admitted.assign(nprob, 0);
     BCK(cudaMallocHost((void**)&b->h_views, sizeof(View32) * nprob));
     for (int p = 0; p < nprob; ++p) b->h_views[p] = view32(b->ctx[p]);
     b->view_fin.assign(nprob, 0);
@@ -2143,6 +2286,13 @@ int rt_batch_create(rt_batch** out, int device, int precision, int nprob, const 
     BCK(cudaMalloc((void**)&b->d_delta, sizeof(double) * nprob));
     BCK(cudaMalloc((void**)&b->d_steps, sizeof(unsigned long long)));
     BCK(cudaMallocHost((void**)&b->h_ids, sizeof(int) * nprob));
+    BCK(cudaMalloc((void**)&b->d_rviews, sizeof(Rep32) * nprob));
+    BCK(cudaMallocHost((void**)&b->h_rviews, sizeof(Rep32) * nprob));
+    memset(b->h_rviews, 0, sizeof(Rep32) * nprob);
+    BCK(cudaMalloc((void**)&b->d_rids, sizeof(int) * nprob));
+    BCK(cudaMalloc((void**)&b->d_rprefix, sizeof(long long) * (nprob + 1)));
+    BCK(cudaMallocHost((void**)&b->h_rids, sizeof(int) * nprob));
+    BCK(cudaMallocHost((void**)&b->h_rprefix, sizeof(long long) * (nprob + 1)));
     BCK(cudaMallocHost((void**)&b->h_prefix, sizeof(long long) * (nprob + 1)));
     BCK(cudaMallocHost((void**)&b->h_delta, sizeof(double) * nprob));
     BCK(cudaMallocHost((void**)&b->h_steps, sizeof(unsigned long long)));
@@ -2164,6 +2314,12 @@ int rt_batch_destroy(rt_batch* b)
     if (b->h_sweeps) cudaFreeHost(b->h_sweeps);
     if (b->d_views) cudaFree(b->d_views);
     if (b->h_views) cudaFreeHost(b->h_views);
+    if (b->d_rviews) cudaFree(b->d_rviews);
+    if (b->h_rviews) cudaFreeHost(b->h_rviews);
+    if (b->d_rids) cudaFree(b->d_rids);
+    if (b->d_rprefix) cudaFree(b->d_rprefix);
+    if (b->h_rids) cudaFreeHost(b->h_rids);
+    if (b->h_rprefix) cudaFreeHost(b->h_rprefix);
     if (b->d_ids) cudaFree(b->d_ids);
     if (b->d_prefix) cudaFree(b->d_prefix);
     if (b->d_delta) cudaFree(b->d_delta);
@@ -2211,7 +2367,20 @@ int rt_batch_reset(rt_batch* b, int rebuild_lstar)
         b->iters[p] = 0;
         b->delta[p] = 0.0;
         b->converged[p] = 0;
+        b->admitted[p] = c->rec_cap > 0;   // a held recording keeps its place
     }
+    return RT_OK;
+}
+
+int rt_batch_set_fs_record(rt_batch* b, long long max_bytes)
+{
+    if (!b) return RT_EINVAL;
+    b->err.clear();
+    if (max_bytes < -1) return bfail(b, RT_EINVAL, "max_bytes must be -1 (automatic), 0 (off) or a byte limit");
+    BCK(cudaSetDevice(b->device));
+    for (size_t p = 0; p < b->ctx.size(); ++p) batch_release(b, (int)p);
+    std::fill(b->admitted.begin(), b->admitted.end(), 0);
+    b->rec_mode = max_bytes;
     return RT_OK;
 }
 
@@ -2230,6 +2399,8 @@ int rt_batch_set_precision(rt_batch* b, int precision)
         b->iters[p] = 0;        // a new stage: counts, deltas and convergence restart
         b->delta[p] = 0.0;
         b->converged[p] = 0;
+        batch_release(b, (int)p);
+        b->admitted[p] = 0;
     }
     b->precision = precision;
     return RT_OK;
@@ -2307,10 +2478,12 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
     } guard{b, std::vector<char>(P, 0), std::vector<double>(P, 0.0)};
     std::vector<char>& switched = guard.switched;
     std::vector<double>& ng_min0 = guard.ng_min0;
-    for (int it = 0; it < max_iter; ++it) {
+    // (problems admitted in waves: the loop runs until none is left)
+    for (long long it = 0; it < (long long)max_iter * P + 1; ++it) {
+        if ((rc = batch_admit(b, max_iter))) return rc;
         std::vector<int> act;
         for (int p : b->order)
-            if (!b->converged[p] && b->iters[p] < max_iter) act.push_back(p);
+            if (b->admitted[p] && !b->converged[p] && b->iters[p] < max_iter) act.push_back(p);
         if (act.empty()) break;
         if ((rc = batch_fs(b, act))) return rc;
         if (b->use_graphs)
@@ -2355,6 +2528,7 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
                 c->ng_min_delta = 0.0;
                 c->ng_count = 1;
             }
+            if (b->converged[p] || b->iters[p] >= max_iter) batch_release(b, p);
         }
     }
     int nconv = 0;

@@ -484,13 +484,10 @@ k_fs32rec(View32 p, float cut, unsigned long long* __restrict__ steps, Rec32 rec
 // differences are formed as in the march (hi differences exact for nearby
 // values, the lo parts added once).
 template <int TB>
-__global__ void __launch_bounds__(TB, kResidentR32 / TB)
-k_fs32rep(Rep32 p, unsigned long long* __restrict__ steps)
+__device__ __forceinline__ void replay32(const Rep32& p, int tile, int k0, int zb, int ZB,
+                                         unsigned long long* __restrict__ steps)
 {
     const Geometry& g = p.g;
-    const int tile = p.pmajor ? blockIdx.y : blockIdx.x;
-    const int k0 = p.pmajor ? blockIdx.x : blockIdx.y;
-    const int zb = blockIdx.z, ZB = gridDim.z;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int nyp = (ny + 1) >> 1;
     const int t = tile * TB + threadIdx.x;
@@ -571,6 +568,46 @@ k_fs32rep(Rep32 p, unsigned long long* __restrict__ steps)
         }
     }
     if (steps) add_steps32(steps, nsteps);
+}
+
+template <int TB>
+__global__ void __launch_bounds__(TB, kResidentR32 / TB)
+k_fs32rep(Rep32 p, unsigned long long* __restrict__ steps)
+{
+    const int tile = p.pmajor ? blockIdx.y : blockIdx.x;
+    const int k0 = p.pmajor ? blockIdx.x : blockIdx.y;
+    replay32<TB>(p, tile, k0, blockIdx.z, gridDim.z, steps);
+}
+
+// The replays of many problems in one launch, blocks assigned to problems
+// as in k_fs32_batch (the problem's view staged in shared memory).
+template <int TB>
+__global__ void __launch_bounds__(TB, kResidentR32 / TB)
+k_fs32rep_batch(const Rep32* __restrict__ views, const int* __restrict__ ids,
+                const long long* __restrict__ prefix, int nact, int ZB,
+                unsigned long long* __restrict__ steps)
+{
+    __shared__ Rep32 p;
+    __shared__ long long s_local;
+    if (threadIdx.x == 0) {
+        const long long b = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+        int lo = 0, hi = nact;  // prefix[lo] <= b < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= b) lo = mid; else hi = mid;
+        }
+        s_local = b < prefix[nact] ? b - prefix[lo] : -1;
+        if (s_local >= 0) p = views[ids[lo]];
+    }
+    __syncthreads();
+    const long long local = s_local;
+    if (local < 0) return;
+    const int tiles = (p.g.nx * ((p.g.ny + 1) >> 1) + TB - 1) / TB;
+    const long long tk = local % ((long long)tiles * p.g.nz);
+    const int zb = (int)(local / ((long long)tiles * p.g.nz));
+    const int tile = p.pmajor ? (int)(tk / p.g.nz) : (int)(tk % tiles);
+    const int k0 = p.pmajor ? (int)(tk % p.g.nz) : (int)(tk / tiles);
+    replay32<TB>(p, tile, k0, zb, ZB, steps);
 }
 
 int tiles32(const Geometry& g, int tb) { return (g.nx * ((g.ny + 1) / 2) + tb - 1) / tb; }
@@ -769,6 +806,27 @@ cudaError_t launch_fs32_batch(const View32* views, const int* ids, const long lo
     else
         k_fs32_batch<kThreads32><<<grid, kThreads32, 0, st>>>(views, ids, prefix, nact, groups, c,
                                                               steps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fs32rep_batch(const Rep32* views, const int* ids, const long long* prefix,
+                                 int nact, long long total_blocks, int groups, int threads,
+                                 unsigned long long* steps, cudaStream_t st)
+{
+    if (nact <= 0 || total_blocks <= 0) return cudaSuccess;
+    dim3 grid((unsigned)total_blocks, 1, 1);
+    if (total_blocks > 2147483647LL) {  // beyond grid.x: fold into y, surplus blocks return
+        grid.x = 1u << 30;
+        grid.y = (unsigned)((total_blocks + grid.x - 1) / grid.x);
+    }
+    const int tb = block_threads32(threads);
+    if (tb == 64)
+        k_fs32rep_batch<64><<<grid, 64, 0, st>>>(views, ids, prefix, nact, groups, steps);
+    else if (tb == 256)
+        k_fs32rep_batch<256><<<grid, 256, 0, st>>>(views, ids, prefix, nact, groups, steps);
+    else
+        k_fs32rep_batch<kThreads32><<<grid, kThreads32, 0, st>>>(views, ids, prefix, nact, groups,
+                                                                 steps);
     return cudaGetLastError();
 }
 

@@ -302,6 +302,11 @@ cudaError_t launch_fs32rec(const View32& p, double cut, int groups, const Rec32&
                            unsigned long long* steps, cudaStream_t st);
 cudaError_t launch_fs32rep(const Rep32& p, int groups, int threads, unsigned long long* steps,
                            cudaStream_t st);
+// The replays of the problems ids[0..nact) (views in device memory, blocks
+// as launch_fs32_batch: prefix of fs32_blocks per problem).
+cudaError_t launch_fs32rep_batch(const Rep32* views, const int* ids, const long long* prefix,
+                                 int nact, long long total_blocks, int groups, int threads,
+                                 unsigned long long* steps, cudaStream_t st);
 
 // FP32 march of I - S_0: partial[kSlots][N] of sum_d w_d (I_d - S_0).
 // threads: threads per block, 64, 128 or 256 (anything else: 128); J does

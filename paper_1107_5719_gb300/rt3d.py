@@ -91,6 +91,7 @@ _SIGS = {
     "rt_fs32_branch_counts": (C.c_int, [VP, VP, C.POINTER(C.c_ulonglong),
                                         C.POINTER(C.c_ulonglong)]),
     "rt_set_fs_record": (C.c_int, [VP, C.c_longlong]),
+    "rt_batch_set_fs_record": (C.c_int, [VP, C.c_longlong]),
     "rt_fs_record_info": (C.c_int, [VP, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "rt_set_direction_groups": (C.c_int, [VP, C.c_int]),
     "rt_set_cutoff": (C.c_int, [VP, C.c_double]),
@@ -337,6 +338,10 @@ def rt_fs32_branch_counts(ctx, S=None):
 
 def rt_set_fs_record(ctx, max_bytes=-1):
     return _check(ctx, load().rt_set_fs_record(ctx, int(max_bytes)))
+
+
+def rt_batch_set_fs_record(b, max_bytes=-1):
+    return _bcheck(b, load().rt_batch_set_fs_record(b, int(max_bytes)))
 
 
 def rt_fs_record_info(ctx):

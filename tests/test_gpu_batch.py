@@ -42,23 +42,60 @@ def _uneven(n_theta=6, n_phi=4):
 TOL = {1: 1e-6, 0: 1e-9}
 
 
+@pytest.mark.parametrize("record", [-1, 0], ids=["recorded", "marching"])
 @pytest.mark.parametrize("precision", [1, 0])
-def test_batch_equals_individual_solves(R, precision):
+def test_batch_equals_individual_solves(R, precision, record):
+    """Bit-identical to single solves, with the recorded march (record once,
+    replay in the fused launch) and without."""
     probs = _uneven()
     b = R.rt_batch_create(probs, precision=precision)
     try:
         R.rt_batch_set_ng(b, 4, 1e-6)
+        R.rt_batch_set_fs_record(b, record)
         r = R.rt_batch_solve(b, len(probs), tol=TOL[precision], max_iter=500)
         assert r["converged"] and r["n_converged"] == len(probs)
         for i, p in enumerate(probs):
             J = R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx))
             with R.Solver(p, precision=precision, ng_period=4, ng_min_delta=1e-6,
-                          record=0) as s:   # the batch marches
+                          record=record) as s:
                 ri = s.solve(tol=TOL[precision], max_iter=500)
             assert ri["iters"] == r["iters"][i]
             assert np.array_equal(J, ri["J"]), i
         st = R.rt_batch_get_stats(b)
         assert st["fs_launches"] == (max(r["iters"]) if precision == 1 else int(r["iters"].sum()))
+    finally:
+        R.rt_batch_destroy(b)
+
+
+def test_batch_recordings_in_waves(R):
+    """A budget that holds two recordings at a time: the problems run in
+    waves (each starts once memory frees), with the iterates of single
+    solves, bit for bit; the recordings' memory returns at the end."""
+    probs = _uneven()[:5]
+    sizes = []
+    for p in probs:
+        with R.Solver(p, precision=1) as s:
+            s.formal_solution(p.B, want_lstar=False)
+            sizes.append(R.rt_fs_record_info(s.ctx)[0])
+    b = R.rt_batch_create(probs, precision=1)
+    try:
+        R.rt_batch_set_ng(b, 4, 1e-6)
+        R.rt_batch_set_fs_record(b, sum(sorted(sizes)[-2:]))
+        r = R.rt_batch_solve(b, len(probs), tol=TOL[1], max_iter=500)
+        assert r["converged"]
+        st = R.rt_batch_get_stats(b)
+        assert st["iterations"] > max(r["iters"])        # more than one wave
+        for i, p in enumerate(probs):
+            with R.Solver(p, precision=1, ng_period=4, ng_min_delta=1e-6) as s:
+                ri = s.solve(tol=TOL[1], max_iter=500)
+            assert ri["iters"] == r["iters"][i]
+            assert np.array_equal(R.rt_batch_get_J(b, i, (p.nz, p.ny, p.nx)), ri["J"]), i
+    finally:
+        R.rt_batch_destroy(b)
+    b = R.rt_batch_create(probs[:1], precision=1)
+    try:
+        with pytest.raises(R.RtError):
+            R.rt_batch_set_fs_record(b, -5)
     finally:
         R.rt_batch_destroy(b)
 
@@ -104,8 +141,7 @@ def test_batch_wavelengths_of_one_slab(R):
         r = R.rt_batch_solve(b, len(probs), tol=TOL[1], max_iter=2000)
         assert r["converged"]
         for i in (0, 5):
-            with R.Solver(probs[i], precision=1, ng_period=4, ng_min_delta=1e-6,
-                          record=0) as s:   # the batch marches
+            with R.Solver(probs[i], precision=1, ng_period=4, ng_min_delta=1e-6) as s:
                 ri = s.solve(tol=TOL[1], max_iter=2000)
             J = R.rt_batch_get_J(b, i, ri["J"].shape)
             assert np.array_equal(J, ri["J"])

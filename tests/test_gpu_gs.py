@@ -104,8 +104,7 @@ def test_gs_batch_equals_single_solves(R):
     finally:
         R.rt_batch_destroy(b)
     for i, q in enumerate(probs):
-        with R.Solver(q, precision=R.RT_FP32_SWEEP, os_method=R.RT_OS_GAUSS_SEIDEL,
-                      record=0) as s:   # the batch marches
+        with R.Solver(q, precision=R.RT_FP32_SWEEP, os_method=R.RT_OS_GAUSS_SEIDEL) as s:
             r = s.solve(tol=1e-6, max_iter=300, tol_inner=1e-10, max_sweeps=300)
         assert r["iters"] == it[i]
         assert np.array_equal(r["J"], Jb[i])

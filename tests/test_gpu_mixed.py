@@ -87,8 +87,7 @@ def test_batch_fp32_then_double_float_equals_single(R):
     finally:
         R.rt_batch_destroy(b)
     for i, q in enumerate(probs):
-        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6,
-                      record=0) as s:   # the batch marches
+        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
             R.rt_set_df_finish(s.ctx, 0.0)
             a = s.solve(tol=5e-8, max_iter=3000)
             R.rt_set_precision(s.ctx, R.RT_DF64)
@@ -137,8 +136,7 @@ def test_batch_automatic_finish_equals_single(R):
     finally:
         R.rt_batch_destroy(b)
     for i, q in enumerate(probs):
-        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6,
-                      record=0) as s:   # the batch marches
+        with R.Solver(q, precision=R.RT_FP32_SWEEP, ng_period=4, ng_min_delta=1e-6) as s:
             R.rt_set_df_finish(s.ctx, 1e-6)
             r = s.solve(tol=1e-8, max_iter=3000)
         assert r["iters"] == rb["iters"][i]
