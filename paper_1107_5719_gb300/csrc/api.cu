@@ -729,10 +729,15 @@ int prepare_source(rt_ctx* c, const double* S_in, bool device)
         CK(launch_delta_source(c->g.N, c->S, c->S_ref, c->dS, c->stream));
         CK(cudaMemsetAsync(c->scal + 0, 0, sizeof(double), c->stream));
         CK(launch_absmax(c->g.N, c->dS, nullptr, c->scal + 0, nullptr, c->stream));
-        CK(launch_pack_pairs(c->g, c->chi, c->dS, c->pair, c->plo, c->stream));
-        c->stats.launches += 3;
+        if (!c->rec_valid) {   // the replay packs its own source records
+            CK(launch_pack_pairs(c->g, c->chi, c->dS, c->pair, c->plo, c->stream));
+            c->stats.launches += 1;
+        }
+        c->stats.launches += 2;
     } else if (c->precision == RT_FP32_SWEEP && c->fin == 1) {
         // the reference formal solution packs its own double-float nodes
+    } else if (c->precision == RT_FP32_SWEEP && c->rec_valid) {
+        // the replay packs its own source records
     } else if (c->precision == RT_FP32_SWEEP) {
         CK(launch_pack_pairs(c->g, c->chi, c->S, c->pair, c->plo, c->stream));
         c->stats.launches += 1;
@@ -1272,11 +1277,16 @@ int batch_groups(const rt_batch* b, const std::vector<int>& act)
 // too, so that the solve always progresses.
 int batch_admit(rt_batch* b, int max_iter)
 {
-    long long limit = b->rec_mode;
+    long long limit = b->rec_mode, reserve = 0, free_now = 0;
     if (limit < 0) {
+        // automatic: recordings up to 60% of the device, each admitted only
+        // while a quarter of the device stays free besides it (the problems'
+        // own buffers grow as they reach their finishing stage)
         size_t fr = 0, tot = 0;
         BCK(cudaMemGetInfo(&fr, &tot));
         limit = (long long)(0.6 * (double)tot);
+        reserve = (long long)(0.25 * (double)tot);
+        free_now = (long long)fr;
     }
     long long used = 0;
     bool running = false;
@@ -1290,13 +1300,14 @@ int batch_admit(rt_batch* b, int max_iter)
         const long long need = rec_need(c);
         if (b->rec_mode == 0 || need == 0 || need > limit) {
             c->rec_mode = 0;                      // marches
-        } else if (used + need <= limit) {
+        } else if (used + need <= limit && (reserve == 0 || need + reserve <= free_now)) {
             c->rec_mode = need;
             bool use = false;
             const int rc = ensure_rec(c, use);
             if (rc) return bfail(b, rc, "problem %d: %s", p, rt_last_error(c));
             if (use) {
                 used += c->rec_cap;
+                free_now -= c->rec_cap;
             } else if (running) {
                 continue;                         // wait for memory
             } else {
@@ -2010,6 +2021,7 @@ static int fs32_branch_counts(rt_ctx* c, const double* S, unsigned long long* st
         return fail(c, RT_EINVAL, "branch counts need the FP32-sweep long-characteristics march");
     if ((rc = prepare_source(c, S, false))) return rc;
     if ((rc = fs_prepare(c))) return rc;
+    CK(launch_pack_pairs(c->g, c->chi, c->S, c->pair, c->plo, c->stream));
     unsigned long long* d = nullptr;
     CK(cudaMalloc((void**)&d, 2 * sizeof(unsigned long long)));
     unsigned long long h[2] = {0, 0};
