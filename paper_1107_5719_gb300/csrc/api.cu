@@ -311,15 +311,20 @@ long long up256(long long b) { return (b + 255) / 256 * 256; }
 // Bytes a recording of this context's march takes (0: its form does not record).
 long long rec_need(const rt_ctx* c)
 {
-    if (c->fs_method != RT_FS_LONG || c->src_order != RT_SRC_LINEAR || c->g.nz < 2 ||
-        (c->precision != RT_FP64 && c->precision != RT_FP32_SWEEP))
+    if (c->fs_method != RT_FS_LONG || c->g.nz < 2 ||
+        (c->precision != RT_FP64 && c->precision != RT_FP32_SWEEP) ||
+        (c->src_order != RT_SRC_LINEAR && c->precision != RT_FP64))
         return 0;
     const long long tri = (long long)c->g.nz * (c->g.nz - 1) / 2;
     const long long b_slot = up256((long long)kSlots * c->g.N * (long long)sizeof(double));
     if (c->precision == RT_FP64) {
         const long long nxy = (long long)c->g.nx * c->g.ny, nwp = (nxy + 31) / 32;
+        const long long b_cdn = c->src_order == RT_SRC_PARABOLIC
+                                    ? up256((long long)c->g.ndir * c->g.N * (long long)sizeof(double))
+                                    : 0;
         return up256((long long)c->g.ndir * nxy * tri * (long long)sizeof(double)) +
-               up256((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int)) + 2 * b_slot;
+               up256((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int)) + 2 * b_slot +
+               b_cdn;
     }
     const long long npair = (long long)c->g.nx * ((c->g.ny + 1) / 2), nwp = (npair + 31) / 32;
     return up256((long long)c->g.ndir * rec32_steps4(c->g.nz) * nwp * 32 * (long long)sizeof(float2)) +
@@ -330,7 +335,8 @@ long long rec_need(const rt_ctx* c)
 int ensure_rec(rt_ctx* c, bool& use)
 {
     use = false;
-    if (c->rec_mode == 0 || rec_need(c) == 0) return RT_OK;
+    const long long need = rec_need(c);
+    if (c->rec_mode == 0 || need == 0) return RT_OK;
     const long long tri = (long long)c->g.nz * (c->g.nz - 1) / 2;
     const long long b_slot = up256((long long)kSlots * c->g.N * (long long)sizeof(double));
     if (c->precision == RT_FP64) {
@@ -338,12 +344,16 @@ int ensure_rec(rt_ctx* c, bool& use)
         const long long nwp = (nxy + 31) / 32;
         const long long b_coef = up256((long long)c->g.ndir * nxy * tri * (long long)sizeof(double));
         const long long b_lmax = up256((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int));
-        if (!rec_reserve(c, b_coef + b_lmax + 2 * b_slot)) return RT_OK;
+        if (!rec_reserve(c, need)) return RT_OK;
         c->rec.coef = reinterpret_cast<double*>(c->rec_mem);
         c->rec.lmax = reinterpret_cast<int*>(c->rec_mem + b_coef);
         c->rec.c0 = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax);
         c->rec.bc = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax + b_slot);
         c->rec.nwp = (int)nwp;
+        const bool para = c->src_order == RT_SRC_PARABOLIC;
+        c->rec.cdn = para ? reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax + 2 * b_slot)
+                          : nullptr;
+        c->rec.dn = para ? c->dn : nullptr;
     } else {
         const long long npair = (long long)c->g.nx * ((c->g.ny + 1) / 2);
         const long long nwp = (npair + 31) / 32;
@@ -645,9 +655,23 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
     const double cut = cut_of(c);
     if (c->profiling) CK(cudaEventRecord(c->ev[0], c->stream));
     if (c->precision == RT_FP64 && c->src_order == RT_SRC_PARABOLIC) {
-        CK(launch_fs64p(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->dn,
-                        c->scal + 0, cut, G, c->partial, count_steps ? c->d_steps : nullptr,
-                        c->stream));
+        // recorded like the linear source (with the downstream point's
+        // coefficients), else marched
+        bool use = false;
+        if ((rc = ensure_rec(c, use))) return rc;
+        unsigned long long* sp = count_steps ? c->d_steps : nullptr;
+        if (use && !c->rec_valid) {
+            CK(launch_fs64p(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->dn,
+                            c->scal + 0, cut, G, c->partial, sp, c->stream, &c->rec));
+            c->rec_valid = true;
+            c->stats.launches += 1;
+        }
+        if (use)
+            CK(launch_fs64rep(c->g, c->S, c->info, c->off, c->bw, c->rec, G, c->partial, sp,
+                              c->stream));
+        else
+            CK(launch_fs64p(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw, c->dn,
+                            c->scal + 0, cut, G, c->partial, sp, c->stream));
     } else if (c->precision == RT_FP64) {
         bool use = false;
         if ((rc = ensure_rec(c, use))) return rc;

@@ -236,7 +236,8 @@ k_fs64(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
 }
 
 // Replay of the recorded march (FsRec) for a new source S: per (voxel,
-// direction) I = sum_m c_m S(p_m) over the warp's recorded length, plus
+// direction) I = sum_m c_m S(p_m) over the warp's recorded length (and,
+// for the parabolic source, c_-1 S(p_-1) at the downstream point), plus
 // per slot the voxel's own term and the boundary term.  Five FP64
 // operations per step (the bilinear interpolation of S and one FMA)
 // against ~32 for the march, and 8 coefficient bytes streamed from memory.
@@ -264,6 +265,15 @@ k_fs64rep(Geometry g, const double* __restrict__ S, const DirInfo* __restrict__ 
                 const double* rc = coef + rec_base(g, d, k0, s) + t;
                 const int L = rec.lmax[((long long)d * nz + k0) * rec.nwp + (t >> 5)];
                 double I = 0.0;
+                if (rec.cdn) {   // parabolic source: the downstream point p_-1
+                    const int kd = k0 + s;
+                    if (kd >= 0 && kd < nz) {
+                        const DownGeo q = rec.dn[d];
+                        const Nodes n = nodes_of(i0, j0, StepGeo{q.ox, q.oy}, nx, ny);
+                        RT_GUARD(g, nodes_max(n), nxy, kSiteFs64) continue;
+                        I = rec.cdn[(long long)d * g.N + v] * bilin(S + (long long)kd * nxy, n, q.b);
+                    }
+                }
                 for (int m = 0; m < L; ++m) {
                     const long long pb = (long long)(k0 - (m + 1) * s) * nxy;
                     const Nodes n = nodes_of(i0, j0, od[m + 1], nx, ny);

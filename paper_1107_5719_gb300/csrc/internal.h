@@ -135,6 +135,11 @@ struct FsRec {
     double* c0;
     double* bc;
     int nwp;
+    // parabolic source: cdn[d N + v], the coefficient of S at the
+    // downstream point p_-1 (DownGeo) of voxel v in direction d; null for
+    // the linear source
+    double* cdn;
+    const DownGeo* dn;
 };
 // The recording march cuts the characteristics at cut * kRecCutMargin, so
 // that the recorded lengths still meet the cutoff for sources whose
@@ -172,11 +177,13 @@ cudaError_t launch_diffusion_grad(const Geometry& g, double dz, const double* ch
 // ---- parabolic source (para.cu) --------------------------------------------
 cudaError_t launch_down_tables(const Geometry& g, double dx, double dy, double dz,
                                const double* mu, const double* phi, DownGeo* dn, cudaStream_t st);
-// As launch_fs64 with the parabolic source.
+// As launch_fs64 with the parabolic source (rec != null: also record it,
+// with rec->cdn, cut at cut * kRecCutMargin).
 cudaError_t launch_fs64p(const Geometry& g, const double* chi, const double* S, const double* B,
                          const double* G, const DirInfo* info, const StepGeo* off,
                          const Bw4d* bw, const DownGeo* dn, const double* smax, double cut,
-                         int groups, double* partial, unsigned long long* steps, cudaStream_t st);
+                         int groups, double* partial, unsigned long long* steps, cudaStream_t st,
+                         const FsRec* rec = nullptr);
 cudaError_t launch_lstar64p(const Geometry& g, const double* chi, const DirInfo* info,
                             const StepGeo* off, const Bw4d* bw, const DownGeo* dn, double* lstar,
                             cudaStream_t st);

@@ -131,13 +131,20 @@ __device__ __forceinline__ void add_steps_p(unsigned long long* steps, unsigned 
 
 // Same decomposition as the linear march (one thread per voxel, 8 direction
 // slots summed in fixed order into partial[slot]).
+//
+// REC: also record the march as a linear map of S (FsRec).  Segment m adds
+// T_m P_up to the coefficient of S(p_{m+1}), T_m P_cur to p_m's and T_m
+// P_down to p_{m-1}'s (the first segment without a downstream point: the
+// linear weights), so p_{m-1}'s coefficient is complete after segment m:
+// p_{-1}'s goes to cdn, p_0's to the per-voxel c0, p_m's (m >= 1) to coef.
+template <bool REC>
 __global__ void __launch_bounds__(kThreadsP)
 k_fs64p(Geometry g, const double* __restrict__ chi, const double* __restrict__ S,
         const double* __restrict__ B, const double* __restrict__ G,
         const DirInfo* __restrict__ info, const StepGeo* __restrict__ off,
         const Bw4d* __restrict__ bw, const DownGeo* __restrict__ dn,
         const double* __restrict__ smax_p, double cut, double* __restrict__ partial,
-        unsigned long long* __restrict__ steps)
+        unsigned long long* __restrict__ steps, FsRec rec)
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     const int t = blockIdx.x * kThreadsP + threadIdx.x;
@@ -146,16 +153,17 @@ k_fs64p(Geometry g, const double* __restrict__ chi, const double* __restrict__ S
     __shared__ double tab[kExpTable];
     fill_exp_table(tab);
     __syncthreads();
+    const unsigned amask = __ballot_sync(0xffffffffu, active);
     unsigned long long nsteps = 0;
     if (active) {
         const int j0 = t / nx, i0 = t - j0 * nx;
         const long long v = (long long)k0 * nxy + t;
         // parabolic weights exceed the linear ones in magnitude by a small
         // factor: 4 more bits of margin in the transmission cutoff
-        const int need = cut_need(*smax_p, cut) + 4;
+        const int need = cut_need(*smax_p, REC ? cut * kRecCutMargin : cut) + 4;
         const double chi0 = chi[v], S0 = S[v];
         for (int slot = zb; slot < kSlots; slot += ZB) {
-            double Jp = 0.0;
+            double Jp = 0.0, C0 = 0.0, Bc = 0.0;
             for (int d = slot; d < g.ndir; d += kSlots) {
                 const DirInfo di = info[d];
                 const int s = di.sgn;
@@ -176,6 +184,9 @@ k_fs64p(Geometry g, const double* __restrict__ chi, const double* __restrict__ S
                     sprev = bilin_p(S + pd, n, q.b);
                 }
                 double I = 0.0, T = 1.0, ca = chi0, sa = S0;
+                // REC: pending coefficients of p_{m-1}, p_m and p_{m+1}
+                double* rc = REC ? rec.coef + rec_base(g, d, k0, s) + t : nullptr;
+                double pm1 = 0.0, p0 = 0.0, p1 = 0.0;
                 bool early = false;
                 int m = 0;
                 for (; m < M; ++m) {
@@ -193,10 +204,28 @@ k_fs64p(Geometry g, const double* __restrict__ chi, const double* __restrict__ S
                         double wc, wu;
                         seg_weights64(x, tab, wc, wu, e);
                         I = fma(T, fma(wc, sa, wu * sb), I);
+                        if (REC) {
+                            p0 += wc;
+                            p1 += wu;
+                        }
                     } else {
                         double pu, pc, pdn;
                         para_weights64(x, xprev, tab, pu, pc, pdn, e);
                         I = fma(T, fma(pu, sb, fma(pc, sa, pdn * sprev)), I);
+                        if (REC) {
+                            p1 = fma(T, pu, p1);
+                            p0 = fma(T, pc, p0);
+                            pm1 = fma(T, pdn, pm1);
+                        }
+                    }
+                    if (REC) {
+                        // p_{m-1} is complete
+                        if (m == 0) rec.cdn[(long long)d * g.N + v] = pm1;
+                        else if (m == 1) C0 = fma(di.w, pm1, C0);
+                        else rc[(long long)(m - 2) * nxy] = pm1;
+                        pm1 = p0;
+                        p0 = p1;
+                        p1 = 0.0;
                     }
                     T *= e;
                     xprev = x;
@@ -217,11 +246,32 @@ k_fs64p(Geometry g, const double* __restrict__ chi, const double* __restrict__ S
                     double ibc = bilin_p(B + pb, n, bd[M]);
                     if (bc == 2) ibc = fma(di.amu, bilin_p(G, n, bd[M]), ibc);
                     I = fma(T, ibc, I);
+                    if (REC) Bc = fma(di.w, T * ibc, Bc);
+                }
+                if (REC) {
+                    // the last two points (p_{m-1}, p_m); then zeros up to
+                    // the warp's longest ray
+                    if (m == 0) {
+                        rec.cdn[(long long)d * g.N + v] = 0.0;
+                    } else {
+                        if (m == 1) C0 = fma(di.w, pm1, C0);
+                        else rc[(long long)(m - 2) * nxy] = pm1;
+                        rc[(long long)(m - 1) * nxy] = p0;
+                    }
+                    const int Lw = __reduce_max_sync(amask, m);
+                    for (int q = m; q < Lw; ++q) rc[(long long)q * nxy] = 0.0;
+                    if ((threadIdx.x & 31) == __ffs(amask) - 1)
+                        rec.lmax[((long long)d * nz + k0) * rec.nwp + (t >> 5)] = Lw;
                 }
                 nsteps += (unsigned long long)m;
                 Jp = fma(di.w, I, Jp);
             }
-            partial[(long long)slot * g.N + v] = Jp;
+            if (REC) {
+                rec.c0[(long long)slot * g.N + v] = C0;
+                rec.bc[(long long)slot * g.N + v] = Bc;
+            } else {
+                partial[(long long)slot * g.N + v] = Jp;
+            }
         }
     }
     if (steps) add_steps_p(steps, nsteps);
@@ -338,12 +388,17 @@ cudaError_t launch_down_tables(const Geometry& g, double dx, double dy, double d
 cudaError_t launch_fs64p(const Geometry& g, const double* chi, const double* S, const double* B,
                          const double* G, const DirInfo* info, const StepGeo* off,
                          const Bw4d* bw, const DownGeo* dn, const double* smax, double cut,
-                         int groups, double* partial, unsigned long long* steps, cudaStream_t st)
+                         int groups, double* partial, unsigned long long* steps, cudaStream_t st,
+                         const FsRec* rec)
 {
     const int nxy = g.nx * g.ny;
     dim3 grid((nxy + kThreadsP - 1) / kThreadsP, groups, g.nz);
-    k_fs64p<<<grid, kThreadsP, 0, st>>>(g, chi, S, B, G, info, off, bw, dn, smax, cut, partial,
-                                        steps);
+    if (rec)
+        k_fs64p<true><<<grid, kThreadsP, 0, st>>>(g, chi, S, B, G, info, off, bw, dn, smax, cut,
+                                                  partial, steps, *rec);
+    else
+        k_fs64p<false><<<grid, kThreadsP, 0, st>>>(g, chi, S, B, G, info, off, bw, dn, smax, cut,
+                                                   partial, steps, FsRec{});
     return cudaGetLastError();
 }
 

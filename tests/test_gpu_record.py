@@ -204,3 +204,27 @@ def test_fp32_solve_through_the_replay_meets_fp64(R):
         assert r["converged"]
         assert np.max(np.abs(r["J"] - r64["J"]) / r64["J"]) < 1e-6
     assert np.max(np.abs(res[1]["J"] - res[0]["J"]) / res[0]["J"]) < 1e-7
+
+
+PARA_CASES = [c for c in CASES if c.get("chi_decades", 3.0) <= 3.0]
+
+
+@pytest.mark.parametrize("case", PARA_CASES, ids=lambda c: "para-{nx}x{ny}x{nz}".format(**c))
+def test_parabolic_record_then_replay_match_oracle(R, oracle_mod, case):
+    """The parabolic source records its march too (the coefficient of S at
+    the downstream point p_-1 beside those of the upstream points): the
+    recording and the replay of another source against the oracle."""
+    p = _slab(case)
+    p.src_order = 1
+    rng = np.random.default_rng(13)
+    S1 = 0.5 + 2.0 * rng.random(p.B.shape)
+    S2 = 0.1 + 5.0 * rng.random(p.B.shape)
+    with R.Solver(p) as s:
+        J1, _ = s.formal_solution(S1, want_lstar=False)
+        assert R.rt_fs_record_info(s.ctx)[1]
+        J2, _ = s.formal_solution(S2, want_lstar=False)
+    with R.Solver(p, record=0) as s:
+        J2m, _ = s.formal_solution(S2, want_lstar=False)
+    assert np.allclose(J1, oracle_mod.formal_solution(p, S1)[0], rtol=RTOL, atol=0)
+    assert np.allclose(J2, oracle_mod.formal_solution(p, S2)[0], rtol=RTOL, atol=0)
+    assert np.allclose(J2, J2m, rtol=1e-13, atol=0)
