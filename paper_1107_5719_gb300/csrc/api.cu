@@ -312,12 +312,11 @@ long long up256(long long b) { return (b + 255) / 256 * 256; }
 long long rec_need(const rt_ctx* c)
 {
     if (c->fs_method != RT_FS_LONG || c->g.nz < 2 ||
-        (c->precision != RT_FP64 && c->precision != RT_FP32_SWEEP) ||
         (c->src_order != RT_SRC_LINEAR && c->precision != RT_FP64))
         return 0;
     const long long tri = (long long)c->g.nz * (c->g.nz - 1) / 2;
     const long long b_slot = up256((long long)kSlots * c->g.N * (long long)sizeof(double));
-    if (c->precision == RT_FP64) {
+    if (c->precision == RT_FP64 || c->precision == RT_DF64) {   // same bytes per entry
         const long long nxy = (long long)c->g.nx * c->g.ny, nwp = (nxy + 31) / 32;
         const long long b_cdn = c->src_order == RT_SRC_PARABOLIC
                                     ? up256((long long)c->g.ndir * c->g.N * (long long)sizeof(double))
@@ -339,7 +338,18 @@ int ensure_rec(rt_ctx* c, bool& use)
     if (c->rec_mode == 0 || need == 0) return RT_OK;
     const long long tri = (long long)c->g.nz * (c->g.nz - 1) / 2;
     const long long b_slot = up256((long long)kSlots * c->g.N * (long long)sizeof(double));
-    if (c->precision == RT_FP64) {
+    if (c->precision == RT_DF64) {
+        const long long nxy = (long long)c->g.nx * c->g.ny;
+        const long long nwp = (nxy + 31) / 32;
+        const long long b_coef = up256((long long)c->g.ndir * nxy * tri * (long long)sizeof(float2));
+        const long long b_lmax = up256((long long)c->g.ndir * c->g.nz * nwp * (long long)sizeof(int));
+        if (!rec_reserve(c, need)) return RT_OK;
+        c->rec32.coef = reinterpret_cast<float2*>(c->rec_mem);
+        c->rec32.lmax = reinterpret_cast<int*>(c->rec_mem + b_coef);
+        c->rec32.tsum = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax);
+        c->rec32.bc = reinterpret_cast<double*>(c->rec_mem + b_coef + b_lmax + b_slot);
+        c->rec32.nwp = (int)nwp;
+    } else if (c->precision == RT_FP64) {
         const long long nxy = (long long)c->g.nx * c->g.ny;
         const long long nwp = (nxy + 31) / 32;
         const long long b_coef = up256((long long)c->g.ndir * nxy * tri * (long long)sizeof(double));
@@ -645,6 +655,27 @@ int run_fs_short(rt_ctx* c, double* Jout, bool count_steps)
     return RT_OK;
 }
 
+// The double-float formal solution of a context: recorded in the first one
+// after the opacities change and replayed, or marched when the recording
+// does not fit.
+int df_formal(rt_ctx* c, int G, unsigned long long* steps, cudaStream_t st)
+{
+    bool use = false;
+    int rc = ensure_rec(c, use);
+    if (rc) return rc;
+    const double cut = cut_of(c);
+    if (use && !c->rec_valid) {
+        CK(launch_fsdf(viewdf(c), cut * kRecCutMargin, G, steps, st, &c->rec32));
+        c->rec_valid = true;
+        c->stats.launches += 1;
+    }
+    if (use)
+        CK(launch_fsdfrep(viewdf(c), c->rec32, G, steps, st));
+    else
+        CK(launch_fsdf(viewdf(c), cut, G, steps, st));
+    return RT_OK;
+}
+
 int run_fs(rt_ctx* c, double* Jout, bool count_steps)
 {
     if (c->fs_method == RT_FS_SHORT) return run_fs_short(c, Jout, count_steps);
@@ -693,7 +724,7 @@ int run_fs(rt_ctx* c, double* Jout, bool count_steps)
                            c->stream));
         }
     } else if (c->precision == RT_DF64) {
-        CK(launch_fsdf(viewdf(c), cut, G, count_steps ? c->d_steps : nullptr, c->stream));
+        if ((rc = df_formal(c, G, count_steps ? c->d_steps : nullptr, c->stream))) return rc;
     } else if (c->fin == 1) {
         if ((rc = fin_reference_march(c, G, count_steps ? c->d_steps : nullptr, c->stream)))
             return rc;
@@ -1566,7 +1597,7 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
         for (int p : act) {
             rt_ctx* c = b->ctx[p];
             if (c->precision == RT_DF64) {
-                BCK(launch_fsdf(viewdf(c), cut_of(c), G, b->d_steps, b->stream));
+                if ((rc = bpass(b, p, df_formal(c, G, b->d_steps, b->stream)))) return rc;
             } else if (c->fin == 1) {
                 if ((rc = bpass(b, p, fin_reference_march(c, G, b->d_steps, b->stream)))) return rc;
             } else {
@@ -1581,7 +1612,7 @@ int batch_fs(rt_batch* b, const std::vector<int>& act)
             bool use = false;
             if (b->precision == RT_FP64 && (rc = bpass(b, p, ensure_rec(c, use)))) return rc;
             if (b->precision == RT_DF64) {
-                BCK(launch_fsdf(viewdf(c), cut_of(c), G, b->d_steps, b->stream));
+                if ((rc = bpass(b, p, df_formal(c, G, b->d_steps, b->stream)))) return rc;
             } else if (use) {
                 if (!c->rec_valid) {
                     BCK(launch_fs64(c->g, c->chi, c->S, c->B, c->gdiff, c->info, c->off, c->bw,

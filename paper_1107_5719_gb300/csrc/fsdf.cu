@@ -134,8 +134,15 @@ __device__ __forceinline__ void add_steps_df(unsigned long long* steps, unsigned
     if ((threadIdx.x & 31) == 0 && n) atomicAdd(steps, n);
 }
 
+// REC: also record the march as a linear map of the source (Rec32 with the
+// FP64 layout of rec_base: per (direction, plane) [step][voxel], one
+// double-float pair per entry): the coefficient of S(p_m) - S_0,
+// T_{m-1} w_up + T_m w_cur in double-float, and per voxel and slot the
+// boundary sums sum_d w_d T_L and w_d T_L I_bc; partial is then not
+// written (J comes from the replay).
+template <bool REC>
 __global__ void __launch_bounds__(kThreadsDF)
-k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
+k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps, Rec32 rec)
 {
     __shared__ dfl tab[2 * kExpTableDF];
     fill_exp_table_df(tab);
@@ -145,6 +152,7 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
     const int t = blockIdx.x * kThreadsDF + threadIdx.x;
     const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
     const bool active = t < nxy;
+    const unsigned amask = REC ? __ballot_sync(0xffffffffu, active) : 0u;
     unsigned long long nsteps = 0;
     if (active) {
         const int j0 = t / nx, i0 = t - j0 * nx;
@@ -159,7 +167,7 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
         const float tcut = smax > 0.f ? cut * S0.h / (2.0f * smax) : 0.f;
         const float4* nb = p.node + base;
         for (int slot = zb; slot < kSlots; slot += ZB) {
-            double Jp = 0.0;
+            double Jp = 0.0, tsum = 0.0, bcs = 0.0;
             for (int d = slot; d < g.ndir; d += kSlots) {
                 const DirInfo di = p.info[d];
                 const int s = di.sgn;
@@ -168,6 +176,8 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
                 const float4* bd = p.bw + (long long)d * nz * 2;
                 const dfl hs = df_make(di.hs32, di.hs32lo);
                 dfl I = df_make(0.f, 0.f), T = df_make(1.f, 0.f), ca = chi0, da = df_make(0.f, 0.f);
+                float2* rc = REC ? rec.coef + rec_base(g, d, k0, s) + t : nullptr;
+                dfl cprev = df_make(0.f, 0.f);
                 bool early = false;
                 int m = 0;
                 for (; m < M; ++m) {
@@ -185,6 +195,14 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
                     const dfl x = df_mul(hs, df_add_s(ca, cb));
                     dfl wc, wu, e;
                     seg_weights_df(x, tab, wc, wu, e);
+                    if (REC) {
+                        const dfl twu = df_mul(T, wu);
+                        if (m > 0) {
+                            const dfl c = df_add_s(cprev, df_mul(T, wc));
+                            rc[(long long)(m - 1) * nxy] = make_float2(c.h, c.l);
+                        }
+                        cprev = twu;
+                    }
                     I = df_add_s(I, df_mul(T, df_add_s(df_mul(wc, da), df_mul(wu, db))));
                     T = df_mul(T, e);
                     ca = cb;
@@ -214,16 +232,85 @@ k_fsdf(ViewDF p, float cut, unsigned long long* __restrict__ steps)
                                                     g01.y, g11.x, g11.y);
                             ibc = df_add_s(ibc, df_mul(df_make(di.amu32, di.amu32lo), gr));
                         }
+                        if (REC) bcs = fma(di.w * df_to_double(T), df_to_double(ibc), bcs);
                         ibc = df_sub_s(ibc, S0);
                     } else {
                         ibc = df_neg(S0);
                     }
                     I = df_add_s(I, df_mul(T, ibc));
+                    if (REC) tsum = fma(di.w, df_to_double(T), tsum);
+                }
+                if (REC) {
+                    if (m > 0) rc[(long long)(m - 1) * nxy] = make_float2(cprev.h, cprev.l);
+                    const int Lw = __reduce_max_sync(amask, m);
+                    for (int q = m; q < Lw; ++q) rc[(long long)q * nxy] = make_float2(0.f, 0.f);
+                    if ((threadIdx.x & 31) == __ffs(amask) - 1)
+                        rec.lmax[((long long)d * nz + k0) * rec.nwp + (t >> 5)] = Lw;
                 }
                 nsteps += (unsigned long long)m;
                 Jp = fma(di.w, df_to_double(I), Jp);
             }
-            p.partial[(long long)slot * g.N + v] = Jp;
+            if (REC) {
+                rec.tsum[(long long)slot * g.N + v] = tsum;
+                rec.bc[(long long)slot * g.N + v] = bcs;
+            } else {
+                p.partial[(long long)slot * g.N + v] = Jp;
+            }
+        }
+    }
+    if (steps) add_steps_df(steps, nsteps);
+}
+
+// Replay of the recorded double-float march for the source in p.node (its
+// S parts): per (voxel, direction) I - S_0 = sum_m c_m (S(p_m) - S_0) in
+// double-float over the warp's recorded length, then per slot the boundary
+// sums: partial = sum_d w_d (I_d - S_0) + bc - S_0 tsum.
+__global__ void __launch_bounds__(kThreadsDF)
+k_fsdfrep(ViewDF p, Rec32 rec, unsigned long long* __restrict__ steps)
+{
+    const Geometry& g = p.g;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    const int t = blockIdx.x * kThreadsDF + threadIdx.x;
+    const int k0 = blockIdx.y, zb = blockIdx.z, ZB = gridDim.z;
+    unsigned long long nsteps = 0;
+    if (t < nxy) {
+        const int j0 = t / nx, i0 = t - j0 * nx;
+        const long long v = (long long)k0 * nxy + t;
+        const long long W = 2LL * nx, P = 4LL * nxy;
+        const long long base = k0 * P + j0 * W + i0;
+        const float4 me = p.node[base];
+        const dfl S0 = df_make(me.z, me.w);
+        const double S0d = (double)me.z + (double)me.w;
+        // the S parts {S_hi, S_lo} of the node records
+        const float2* nb = reinterpret_cast<const float2*>(p.node + base) + 1;
+        for (int slot = zb; slot < kSlots; slot += ZB) {
+            double Jp = 0.0;
+            for (int d = slot; d < g.ndir; d += kSlots) {
+                const DirInfo di = p.info[d];
+                const int s = di.sgn;
+                const int* od = p.poff + (long long)d * nz;
+                const float4* bd = p.bw + (long long)d * nz * 2;
+                const float2* rc = rec.coef + rec_base(g, d, k0, s) + t;
+                const int L = rec.lmax[((long long)d * nz + k0) * rec.nwp + (t >> 5)];
+                dfl I = df_make(0.f, 0.f);
+                for (int m = 0; m < L; ++m) {
+                    const int o = od[m + 1];
+                    RT_GUARD(g, base + o, 4 * g.N, kSiteFsdf) break;
+                    RT_GUARD(g, base + o + W + 1, 4 * g.N, kSiteFsdf) break;
+                    const float4 wh = bd[2 * (m + 1)], wl = bd[2 * (m + 1) + 1];
+                    const float2* q = nb + 2LL * o;           // float2 stride: two per node
+                    const float2 q00 = __ldg(q), q10 = __ldg(q + 2);
+                    const float2 q01 = __ldg(q + 2 * W), q11 = __ldg(q + 2 * W + 2);
+                    const dfl sb = bilin_df(wh, wl, q00.x, q00.y, q10.x, q10.y, q01.x, q01.y,
+                                            q11.x, q11.y);
+                    const float2 c = __ldg(rc + (long long)m * nxy);
+                    I = df_add_s(I, df_mul(df_make(c.x, c.y), df_sub_s(sb, S0)));
+                }
+                nsteps += (unsigned long long)L;
+                Jp = fma(di.w, df_to_double(I), Jp);
+            }
+            const long long e = (long long)slot * g.N + v;
+            p.partial[e] = Jp + rec.bc[e] - S0d * rec.tsum[e];
         }
     }
     if (steps) add_steps_df(steps, nsteps);
@@ -534,13 +621,25 @@ cudaError_t launch_grad_df(const Geometry& g, const double* G, float2* out, cuda
 }
 
 cudaError_t launch_fsdf(const ViewDF& p, double cut, int groups, unsigned long long* steps,
-                        cudaStream_t st)
+                        cudaStream_t st, const Rec32* rec)
 {
     const int nxy = p.g.nx * p.g.ny;
     // planes in index order (g.zorder unused): 40.9 ms against 41.05 ms
     // with the order table on the 65^3 slab
     dim3 grid((nxy + kThreadsDF - 1) / kThreadsDF, p.g.nz, groups);
-    k_fsdf<<<grid, kThreadsDF, 0, st>>>(p, (float)cut, steps);
+    if (rec)
+        k_fsdf<true><<<grid, kThreadsDF, 0, st>>>(p, (float)cut, steps, *rec);
+    else
+        k_fsdf<false><<<grid, kThreadsDF, 0, st>>>(p, (float)cut, steps, Rec32{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fsdfrep(const ViewDF& p, const Rec32& rec, int groups,
+                           unsigned long long* steps, cudaStream_t st)
+{
+    const int nxy = p.g.nx * p.g.ny;
+    dim3 grid((nxy + kThreadsDF - 1) / kThreadsDF, p.g.nz, groups);
+    k_fsdfrep<<<grid, kThreadsDF, 0, st>>>(p, rec, steps);
     return cudaGetLastError();
 }
 

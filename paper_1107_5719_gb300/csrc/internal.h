@@ -356,8 +356,13 @@ cudaError_t launch_packdf(const Geometry& g, const double* chi, const double* S,
                           cudaStream_t st);
 cudaError_t launch_bw_df(long long n, const Bw4d* bw, float4* out, cudaStream_t st);
 cudaError_t launch_grad_df(const Geometry& g, const double* G, float2* out, cudaStream_t st);
+// rec != null: also record the march (Rec32 in the layout of rec_base, one
+// double-float pair per entry; lmax, tsum, bc as for the FP32 sweep).
 cudaError_t launch_fsdf(const ViewDF& p, double cut, int groups, unsigned long long* steps,
-                        cudaStream_t st);
+                        cudaStream_t st, const Rec32* rec = nullptr);
+// The recorded double-float march for the source in p.node.
+cudaError_t launch_fsdfrep(const ViewDF& p, const Rec32& rec, int groups,
+                           unsigned long long* steps, cudaStream_t st);
 
 // Finishing stage of the FP32 sweep (formal solution of a source change):
 // dS = S - Sref; *out = min |x|; J = Jref + wsum dS + sum_slot partial.

@@ -228,3 +228,22 @@ def test_parabolic_record_then_replay_match_oracle(R, oracle_mod, case):
     assert np.allclose(J1, oracle_mod.formal_solution(p, S1)[0], rtol=RTOL, atol=0)
     assert np.allclose(J2, oracle_mod.formal_solution(p, S2)[0], rtol=RTOL, atol=0)
     assert np.allclose(J2, J2m, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "df-{nx}x{ny}x{nz}".format(**c))
+def test_double_float_record_then_replay_match_oracle(R, oracle_mod, case):
+    """The double-float form records its march (double-float coefficients
+    of S(p_m) - S_0) and replays it: both within the FP64 bar of the oracle,
+    and the replay of the recording source equal to the recording solution."""
+    p = _slab(case)
+    rng = np.random.default_rng(14)
+    S1 = 0.5 + 2.0 * rng.random(p.B.shape)
+    S2 = 0.1 + 5.0 * rng.random(p.B.shape)
+    with R.Solver(p, precision=R.RT_DF64) as s:
+        J1, _ = s.formal_solution(S1, want_lstar=False)
+        assert R.rt_fs_record_info(s.ctx)[1]
+        J2, _ = s.formal_solution(S2, want_lstar=False)
+        J1r, _ = s.formal_solution(S1, want_lstar=False)
+    assert np.array_equal(J1r, J1)
+    assert np.allclose(J1, oracle_mod.formal_solution(p, S1)[0], rtol=RTOL, atol=0)
+    assert np.allclose(J2, oracle_mod.formal_solution(p, S2)[0], rtol=RTOL, atol=0)
