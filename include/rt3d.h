@@ -187,8 +187,8 @@ int rt_set_J(rt_ctx *ctx, const double *J);
  * the transmission cutoff are not counted). */
 int rt_last_step_count(rt_ctx *ctx, unsigned long long *steps);
 
-/* Recorded formal solution (RT_FP64 with long characteristics and the
- * linear source, and RT_FP32_SWEEP).
+/* Recorded formal solution (long characteristics: RT_FP64 with the linear
+ * or the parabolic source, RT_FP32_SWEEP, RT_DF64).
  * The march is linear in the source S once the opacities, directions and
  * boundary values are fixed (Sect. 2.2: I is a sum of weighted S values
  * along the characteristic plus the transmitted boundary intensity).  The
@@ -196,21 +196,25 @@ int rt_last_step_count(rt_ctx *ctx, unsigned long long *steps);
  * and also stores, per (voxel, direction, step), the coefficient of S at
  * that step's upstream point (the products of transmissions and segment
  * weights), cut at 1e-2 times the cutoff; every formal solution then
- * evaluates J from those coefficients and its S (five FP64 operations per
- * step instead of the weights' exponential and division), so J does not
- * depend on which formal solution recorded.  The FP32 sweep records FP32
- * coefficients of S(p_m) - S_0 for its difference form and replays them
- * with the interpolated source differences of its march (its finishing
- * stage replays the same recording for the source change).  Memory, FP64:
- * 8 ndir nx ny nz (nz-1)/2 bytes of coefficients plus 4 ndir nz
- * ceil(nx ny/32) + 128 N bytes (65^3 x 1024 directions: 72 GB); FP32
- * sweep: 8 ndir nx ceil(ny/2) nz (nz-1)/2 bytes of coefficients plus about
- * 4 ndir nz nx ny/64 + 128 N + the source records (65^3 x 1024: 36.5 GB).
- * max_bytes: -1 (default) records when that fits in 60% of the device and
- * leaves 2 GiB free, 0 never records, > 0 records when it fits in
- * max_bytes; otherwise every formal solution marches.  J agrees with the
- * march to rounding (the terms are summed in another order).  Other
- * precisions and methods ignore the setting.  RT_EINVAL for max_bytes < -1. */
+ * evaluates J from those coefficients and its S (FP64: five FP64
+ * operations per step instead of the weights' exponential and division),
+ * so J does not depend on which formal solution recorded.  The parabolic
+ * source also keeps the coefficient of S at the downstream point per
+ * (voxel, direction).  The FP32 sweep records FP32 coefficients of
+ * S(p_m) - S_0 for its difference form and replays them with the
+ * interpolated source differences of its march (its finishing stage
+ * replays the same recording for the source change); the double-float
+ * form records double-float coefficients of S(p_m) - S_0.  Memory, FP64
+ * and double-float: 8 ndir nx ny nz (nz-1)/2 bytes of coefficients plus
+ * 4 ndir nz ceil(nx ny/32) + 128 N bytes (65^3 x 1024 directions: 72 GB;
+ * parabolic: + 8 ndir N); FP32 sweep: about 8 ndir nx ceil(ny/2) nz (nz+6)/2
+ * bytes of coefficients (blocks of four steps) plus 4 ndir nz nx ny/64 +
+ * 128 N + the source records (65^3 x 1024: 38.9 GB).  max_bytes: -1
+ * (default) records when that fits in 60% of the device and leaves 2 GiB
+ * free, 0 never records, > 0 records when it fits in max_bytes; otherwise
+ * every formal solution marches.  J agrees with the march to rounding (the
+ * terms are summed in another order).  Short characteristics ignore the
+ * setting.  RT_EINVAL for max_bytes < -1. */
 int rt_set_fs_record(rt_ctx *ctx, long long max_bytes);
 /* Bytes held for the recorded march (0 if none) and whether a recording
  * valid for the current opacities, directions and boundary is held. */
