@@ -279,7 +279,7 @@ k_fs64rep(Geometry g, const double* __restrict__ S, const DirInfo* __restrict__ 
                     const Nodes n = nodes_of(i0, j0, od[m + 1], nx, ny);
                     RT_GUARD(g, pb + nodes_min(n), g.N, kSiteFs64) break;
                     RT_GUARD(g, pb + nodes_max(n), g.N, kSiteFs64) break;
-                    I = fma(__ldg(rc + (long long)m * nxy), bilin(S + pb, n, bd[m + 1]), I);
+                    I = fma(__ldcs(rc + (long long)m * nxy), bilin(S + pb, n, bd[m + 1]), I);
                 }
                 nsteps += (unsigned long long)L;
                 Jp = fma(di.w, I, Jp);

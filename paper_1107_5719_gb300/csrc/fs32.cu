@@ -539,8 +539,10 @@ __device__ __forceinline__ void replay32(const Rep32& p, int tile, int k0, int z
                 for (; m + 4 <= L; m += 4) {
                     RT_GUARD(g, base + od[m + 4], P * nz, kSiteFs32) break;
                     RT_GUARD(g, base + od[m + 4] + 2 * W, P * nz, kSiteFs32) break;
+                    // the coefficients are read once: streaming loads, so that
+                    // they do not displace the source records from the caches
                     const float4* c4 = reinterpret_cast<const float4*>(rc + rec32_step(m + 1));
-                    const float4 cA = __ldg(c4), cB = __ldg(c4 + 1);
+                    const float4 cA = __ldcs(c4), cB = __ldcs(c4 + 1);
                     step(m, make_float2(cA.x, cA.y));
                     step(m + 1, make_float2(cA.z, cA.w));
                     step(m + 2, make_float2(cB.x, cB.y));
@@ -549,7 +551,7 @@ __device__ __forceinline__ void replay32(const Rep32& p, int tile, int k0, int z
                 for (; m < L; ++m) {
                     RT_GUARD(g, base + od[m + 1], P * nz, kSiteFs32) break;
                     RT_GUARD(g, base + od[m + 1] + 2 * W, P * nz, kSiteFs32) break;
-                    step(m, __ldg(rc + rec32_step(m + 1)));
+                    step(m, __ldcs(rc + rec32_step(m + 1)));
                 }
                 nsteps += (unsigned long long)L * (two ? 2ull : 1ull);
                 pair_add(Ja, Jalo, di.w32, Ia, Ial);
@@ -574,9 +576,13 @@ template <int TB>
 __global__ void __launch_bounds__(TB, kResidentR32 / TB)
 k_fs32rep(Rep32 p, unsigned long long* __restrict__ steps)
 {
+    // the view read from shared memory holds fewer registers
+    __shared__ Rep32 sp;
+    if (threadIdx.x == 0) sp = p;
+    __syncthreads();
     const int tile = p.pmajor ? blockIdx.y : blockIdx.x;
     const int k0 = p.pmajor ? blockIdx.x : blockIdx.y;
-    replay32<TB>(p, tile, k0, blockIdx.z, gridDim.z, steps);
+    replay32<TB>(sp, tile, k0, blockIdx.z, gridDim.z, steps);
 }
 
 // The replays of many problems in one launch, blocks assigned to problems

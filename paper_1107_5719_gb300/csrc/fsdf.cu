@@ -303,7 +303,7 @@ k_fsdfrep(ViewDF p, Rec32 rec, unsigned long long* __restrict__ steps)
                     const float2 q01 = __ldg(q + 2 * W), q11 = __ldg(q + 2 * W + 2);
                     const dfl sb = bilin_df(wh, wl, q00.x, q00.y, q10.x, q10.y, q01.x, q01.y,
                                             q11.x, q11.y);
-                    const float2 c = __ldg(rc + (long long)m * nxy);
+                    const float2 c = __ldcs(rc + (long long)m * nxy);
                     I = df_add_s(I, df_mul(df_make(c.x, c.y), df_sub_s(sb, S0)));
                 }
                 nsteps += (unsigned long long)L;
