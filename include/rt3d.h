@@ -497,7 +497,8 @@ int rt_batch_set_block_order(rt_batch *batch, int order);
  * single solve does, so the batch's iterates stay bit-identical to single
  * solves.  A problem starts iterating once its recording fits in the
  * budget beside the recordings held (max_bytes: -1 (default) 60% of the
- * device while a quarter of it stays free, 0 no recordings, > 0 a byte
+ * device, while what the unconverged problems still allocate at their
+ * finishing stage and 4 GiB stay free; 0 no recordings; > 0 a byte
  * limit), and returns the memory when
  * it converges or reaches max_iter; problems run in waves when the budget
  * holds fewer than all (65^3 x 1024 directions, FP32 sweep: 39 GB each).

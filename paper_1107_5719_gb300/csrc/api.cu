@@ -1275,6 +1275,10 @@ struct rt_batch {
     // solve does; its memory returns when it converges.
     long long rec_mode = -1;
     std::vector<char> admitted;
+    // recording blocks returned by converged problems, handed to the next
+    // admitted ones (a large cudaMalloc/cudaFree per problem costs tens of
+    // milliseconds); freed when a solve ends
+    std::vector<std::pair<char*, long long>> rec_pool;
     Rep32* d_rviews = nullptr;      // replay views (device) and pinned host copies
     Rep32* h_rviews = nullptr;
     int* d_rids = nullptr;
@@ -1335,12 +1339,21 @@ int batch_admit(rt_batch* b, int max_iter)
     long long limit = b->rec_mode, reserve = 0, free_now = 0;
     if (limit < 0) {
         // automatic: recordings up to 60% of the device, each admitted only
-        // while a quarter of the device stays free besides it (the problems'
-        // own buffers grow as they reach their finishing stage)
+        // while what the unconverged problems still allocate (Ng's iterates;
+        // at their finishing stage the reference's double-float node planes
+        // and tables, S_ref, J_ref and the source change) stays free beside
+        // it, with 4 GiB to spare
         size_t fr = 0, tot = 0;
         BCK(cudaMemGetInfo(&fr, &tot));
         limit = (long long)(0.6 * (double)tot);
-        reserve = (long long)(0.25 * (double)tot);
+        reserve = 4LL << 30;
+        for (size_t p = 0; p < b->ctx.size(); ++p) {
+            const rt_ctx* c = b->ctx[p];
+            if (b->converged[p] || c->S_ref) continue;
+            reserve += 24 * c->g.N + (c->node4 ? 0 : 64 * c->g.N) +
+                       (c->ng_old[0] ? 0 : 24 * c->g.N) +     // Ng's older iterates
+                       36LL * c->g.ndir * c->g.nz + (1LL << 20);
+        }
         free_now = (long long)fr;
     }
     long long used = 0;
@@ -1349,11 +1362,26 @@ int batch_admit(rt_batch* b, int max_iter)
         used += b->ctx[p]->rec_cap;
         if (b->admitted[p] && !b->converged[p] && b->iters[p] < max_iter) running = true;
     }
+    for (auto& blk : b->rec_pool) used += blk.second;
     for (int p : b->order) {
         rt_ctx* c = b->ctx[p];
         if (b->admitted[p] || b->converged[p] || b->iters[p] >= max_iter) continue;
         const long long need = rec_need(c);
-        if (b->rec_mode == 0 || need == 0 || need > limit) {
+        // a pooled block that holds the recording
+        int pick = -1;
+        for (size_t i = 0; i < b->rec_pool.size(); ++i)
+            if (b->rec_pool[i].second >= need &&
+                (pick < 0 || b->rec_pool[i].second < b->rec_pool[pick].second))
+                pick = (int)i;
+        if (b->rec_mode != 0 && need > 0 && pick >= 0) {
+            c->rec_mem = b->rec_pool[pick].first;
+            c->rec_cap = b->rec_pool[pick].second;
+            b->rec_pool.erase(b->rec_pool.begin() + pick);
+            c->rec_mode = c->rec_cap;
+            bool use = false;
+            const int rc = ensure_rec(c, use);
+            if (rc) return bfail(b, rc, "problem %d: %s", p, rt_last_error(c));
+        } else if (b->rec_mode == 0 || need == 0 || need > limit) {
             c->rec_mode = 0;                      // marches
         } else if (used + need <= limit && (reserve == 0 || need + reserve <= free_now)) {
             c->rec_mode = need;
@@ -1379,14 +1407,29 @@ int batch_admit(rt_batch* b, int max_iter)
     return RT_OK;
 }
 
-// A problem that stops iterating returns its recording's memory.
+// A problem that stops iterating returns its recording's memory to the
+// batch's pool.
 void batch_release(rt_batch* b, int p)
 {
     rt_ctx* c = b->ctx[p];
     if (c->rec_cap) {
         cudaStreamSynchronize(b->stream);
-        free_rec(c);
+        b->rec_pool.emplace_back(c->rec_mem, c->rec_cap);
+        c->rec_mem = nullptr;
+        c->rec_cap = 0;
+        c->rec = FsRec{};
+        c->rec32 = Rec32{};
+        c->spair = nullptr;
+        c->rec_valid = false;
     }
+}
+
+void batch_free_pool(rt_batch* b)
+{
+    if (b->rec_pool.empty()) return;
+    cudaStreamSynchronize(b->stream);
+    for (auto& blk : b->rec_pool) cudaFree(blk.first);
+    b->rec_pool.clear();
 }
 
 void bharvest(rt_batch* b)
@@ -2376,6 +2419,7 @@ int rt_batch_destroy(rt_batch* b)
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     free_batch_graphs(b);
+    batch_free_pool(b);
     for (rt_ctx* c : b->ctx) rt_destroy(c);
     if (b->d_sweeps) cudaFree(b->d_sweeps);
     if (b->h_sweeps) cudaFreeHost(b->h_sweeps);
@@ -2446,6 +2490,7 @@ int rt_batch_set_fs_record(rt_batch* b, long long max_bytes)
     if (max_bytes < -1) return bfail(b, RT_EINVAL, "max_bytes must be -1 (automatic), 0 (off) or a byte limit");
     BCK(cudaSetDevice(b->device));
     for (size_t p = 0; p < b->ctx.size(); ++p) batch_release(b, (int)p);
+    batch_free_pool(b);
     std::fill(b->admitted.begin(), b->admitted.end(), 0);
     b->rec_mode = max_bytes;
     return RT_OK;
@@ -2469,6 +2514,7 @@ int rt_batch_set_precision(rt_batch* b, int precision)
         batch_release(b, (int)p);
         b->admitted[p] = 0;
     }
+    batch_free_pool(b);
     b->precision = precision;
     return RT_OK;
 }
@@ -2598,6 +2644,7 @@ static int batch_solve(rt_batch* b, double tol, int max_iter, double tol_inner, 
             if (b->converged[p] || b->iters[p] >= max_iter) batch_release(b, p);
         }
     }
+    batch_free_pool(b);
     int nconv = 0;
     for (int p = 0; p < P; ++p) {
         if (iters) iters[p] = b->iters[p];
