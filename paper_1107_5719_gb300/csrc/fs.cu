@@ -1,6 +1,7 @@
 // Formal solution kernels (Hauschildt & Baron 2011, Sect. 2.2): geometry
-// tables, the gather-form march along the characteristics, the J reduction
-// over directions and the nearest-neighbour Lambda*.
+// tables, the gather-form march along the characteristics, its recording as
+// a linear map of the source and the replay of that recording, the J
+// reduction over directions and the nearest-neighbour Lambda*.
 //
 // Design (GB300).  The paper tracks every characteristic from the boundary
 // planes in a 2D kernel and collects per-voxel results in a second pass

@@ -16,8 +16,15 @@
 // differences are formed from S stored as an unevaluated FP32 pair
 // (hi + lo, hi = fl32(S)), so they are accurate to FP32 relative to
 // themselves, and every FP32 rounding in the march scales with I - S_0
-// instead of S.  J = sum_d w_d S_0 + sum_d w_d (I_d - S_0) is accumulated in
-// FP64.  Lambda*, the operator splitting and the convergence test are FP64.
+// instead of S.  J = sum_d w_d S_0 + sum_d w_d (I_d - S_0), the sum over the
+// directions of a slot as an FP32 pair, the slots in FP64.  Lambda*, the
+// operator splitting and the convergence test are FP64.
+//
+// Recording.  For fixed opacities the march is linear in S: k_fs32rec
+// records, per voxel pair and step, the FP32 coefficients of S(p_m) - S_0
+// (and the boundary sums), and k_fs32rep / k_fs32rep_batch evaluate the
+// formal solution of any later source from them, forming the interpolated
+// source differences exactly as the march does.
 //
 // Layout.  chi and the S pair of two x-neighbouring nodes share one record:
 // pair[k][y][x] = {chi(x), S_hi(x), chi(x+1), S_hi(x+1)} (float4) and
